@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the amplitude estimator on one GB300 (or N, one rank each).
+
+Workload (the convergence sweep): the anharmonic oscillator
+V = q^2/2 + g q^4/24 with g = 10, T = 1, a = 0, b = 1, bisection depth
+s = 10 (the hierarchy gives N = 2^n, n = 0..10, from every path), 1e7
+samples in 100 blocks, Philox seed 1234, for every effective-action level
+p = 1..18, with W_p evaluated in double and in single precision (log-sum-exp
+reductions in double).  One step is one sweep point: level p (step k uses
+p = k mod 18 + 1) in both precisions.  The metric is slice-actions per second
+(one W_p evaluation on one slice, hierarchy slices included, with its share of
+the Philox, Box-Muller and bisection work), whole job over all ranks, and the
+time to a relative statistical error of 1e-4 in the top-level amplitude,
+double ("plain") against single precision ("chosen").
+
+--impl reference times the plain CPU oracle (the reference arm) on bounded
+samples of the same steps, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = ("slice-actions/s and time to 1e-4 rel. error in A_N(a,b;T): plain vs chosen, 1 GB300")
+UNIT = "slice-actions/s"
+P_LIST = workloads.CONFIG2_P
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no FP64 tensor path); see the design doc
+CPU_BUDGET_S = 15.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=18)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-API pass")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def step_p(k):
+    return P_LIST[k % len(P_LIST)]
+
+
+@__import__("functools").lru_cache(maxsize=None)
+def algorithmic_flops_per_slice(p):
+    """2 M_p + 8: the W_p Horner (M_p multiply-adds) plus forming x, xb and
+    accumulating (Sec. 2.1 / Eq. SNp), per slice-action."""
+    import paper_1105_0542_gb300 as su
+    m = len(su.speedup_generate_coeffs("aho", [1.0, 10.0], p, 0.5)[0])
+    return 2 * m + 8
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._p = None
+        self._t = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                        "-i", str(self.index), "-lms", "200"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self._p = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self._p.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self._p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._p.terminate()
+        try:
+            self._p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self._p.kill()
+        self._t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_sweep(steps, warmup, budget_s):
+    """The plain CPU oracle on bounded samples of the same steps: returns
+    (slice-actions, seconds, threads, description)."""
+    from oracle import mc
+    cores = os.cpu_count() or 1
+    inst = workloads.config2(1)
+    per_step = budget_s / max(steps, 1)
+    total_sa, total_t, used, counts = 0, 0.0, 1, []
+    for k in range(warmup + steps):
+        p = step_p(k)
+        o = mc.Oracle(inst.model, inst.params, p)
+        n = 16
+        t0 = time.perf_counter()
+        o.logweights(inst.a, inst.b, inst.T, inst.s, inst.seed, n, threads=cores)
+        dt = time.perf_counter() - t0
+        if k < warmup:
+            continue
+        n2 = max(16, int(n * per_step / max(dt, 1e-6)))
+        t0 = time.perf_counter()
+        _, used = o.logweights(inst.a, inst.b, inst.T, inst.s, inst.seed, n2, threads=cores)
+        total_t += time.perf_counter() - t0
+        total_sa += n2 * (2 * (1 << inst.s) - 2)
+        counts.append((p, n2))
+    desc = ("oracle (plain C, OpenMP over samples) on the first n samples of each timed step's "
+            "sweep point: " + ", ".join(f"p={p}:{n}" for p, n in counts))
+    return total_sa, total_t, used, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sa, t, used, desc = oracle_sweep(args.steps, args.warmup, CPU_BUDGET_S * 2)
+    v = sa / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "convergence sweep: AHO g=10 T=1 a=0 b=1 s=10 p=1..18 (bounded sample "
+                                   "per step on the host cores)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1105_0542_gb300 as su
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    su.load()
+
+    inst = workloads.config2(1)
+    n_mc = inst.n_mc
+    sample0 = rank * n_mc     # weak scaling: disjoint sample ranges of one run
+    kinds = ("fp64", "fp32")
+    ps = sorted({step_p(k) for k in range(args.warmup + args.steps)})
+    plans, bufs = {}, {}
+    for p in ps:
+        for prec in kinds:
+            pl = su.Plan(inst.model, inst.params, inst.a, inst.b, inst.T, p, inst.s, n_mc, inst.seed,
+                         precision=prec, n_blocks=inst.n_blocks, sample0=sample0)
+            plans[(p, prec)] = pl
+            bufs[(p, prec)] = (torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device=dev),
+                               torch.empty(pl.scratch_bytes, dtype=torch.uint8, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+    stream = torch.cuda.current_stream(dev)
+
+    def run_step(k, events=None):
+        p = step_p(k)
+        n = 0
+        for prec in kinds:
+            t, sc = bufs[(p, prec)]
+            if events is not None:
+                events[(k, prec)][0].record(stream)
+            n += plans[(p, prec)].su_plan_execute(t, sc, stream)
+            if events is not None:
+                events[(k, prec)][1].record(stream)
+        return n
+
+    for k in range(args.warmup):
+        flush.zero_()
+        run_step(k)
+    torch.cuda.synchronize()
+
+    ev = {(k, prec): (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for k in range(args.warmup, args.warmup + args.steps) for prec in kinds}
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches = 0
+    for i, k in enumerate(range(args.warmup, args.warmup + args.steps)):
+        flush.zero_()
+        step_ev[i][0].record(stream)
+        launches += run_step(k, ev)
+        step_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    # per precision: slice-actions, time, algorithmic flops
+    per = {prec: {"sa": 0, "ms": 0.0, "flops": 0.0} for prec in kinds}
+    for k in range(args.warmup, args.warmup + args.steps):
+        p = step_p(k)
+        for prec in kinds:
+            sa = plans[(p, prec)].slice_actions
+            per[prec]["sa"] += sa
+            per[prec]["ms"] += ev[(k, prec)][0].elapsed_time(ev[(k, prec)][1])
+            per[prec]["flops"] += sa * algorithmic_flops_per_slice(p)
+    total_sa = (per["fp64"]["sa"] + per["fp32"]["sa"]) * world
+    value = total_sa / (total_ms / 1e3)
+
+    # results of the last pass: relative errors for time-to-1e-4
+    ttr = {}
+    rel = {}
+    for prec in kinds:
+        for p in ps:
+            t, sc = bufs[(p, prec)]
+            res = plans[(p, prec)].su_plan_finalize(t.cpu().numpy(), sc)
+            rel[(p, prec)] = res[inst.s]["rel_err"]
+    p_ref = 10 if 10 in ps else ps[-1]
+    for prec in kinds:
+        ms = [ev[(k, prec)][0].elapsed_time(ev[(k, prec)][1]) for k in range(args.warmup, args.warmup + args.steps)
+              if step_p(k) == p_ref]
+        if ms:
+            ttr[prec] = (sum(ms) / len(ms) / 1e3) * (rel[(p_ref, prec)] / 1e-4) ** 2
+
+    # end to end through the host API (host buffers, copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.warmup, args.warmup + args.steps):
+            p = step_p(k)
+            for prec in kinds:
+                su.speedup_amplitude(inst.model, inst.params, inst.a, inst.b, inst.T, p, inst.s, n_mc, inst.seed,
+                                     precision=prec, n_blocks=inst.n_blocks, sample0=sample0)
+                m = len(su.speedup_generate_coeffs(inst.model, inst.params, p, 0.5)[0])
+                h2d += inst.s * m * (8 if prec == "fp64" else 4)
+                d2h += plans[(p, prec)].tuple_bytes + 4
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": total_sa / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // max(args.steps, 1),
+               "d2h_bytes_per_step": d2h // max(args.steps, 1)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    fp64_ms = per["fp64"]["ms"]
+    achieved = per["fp64"]["flops"] / (fp64_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "sampler_kernel<double, RING_EVEN> (+ its combine)",
+                "note": "algorithmic flops 2*M_p+8 per slice-action (W_p only); peak nominal FP64, "
+                        "not measured (MEASURED_PEAKS.json has none)"}
+    cpu = None
+    if not args.no_cpu:
+        sa, t, used, desc = oracle_sweep(args.steps, 0, CPU_BUDGET_S)
+        cpu = {"value": sa / t, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "convergence sweep: AHO g=10 T=1 a=0 b=1, s=10 (N=1..1024 via hierarchy), "
+                               "1e7 samples/100 blocks per rank, p=k mod 18+1 per step, W_p fp64 and fp32, "
+                               "log-sum-exp fp64",
+                   "l2": "flushed (256 MB write) before every step", "seed": inst.seed},
+        "per_precision": {prec: {"slice_actions_per_s": per[prec]["sa"] * world / (per[prec]["ms"] / 1e3),
+                                 "ms": per[prec]["ms"]} for prec in kinds},
+        "time_to_rel_1e-4_s": {"p": p_ref, "level": inst.s, "plain_fp64": ttr.get("fp64"),
+                               "chosen_fp32": ttr.get("fp32"),
+                               "speedup": (ttr["fp64"] / ttr["fp32"]) if "fp64" in ttr and "fp32" in ttr else None,
+                               "method": "per-sample cost x (rel_err/1e-4)^2 from the 1e7-sample run"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
+        "clocks": clock_info,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * speedup.h -- C ABI of the GB300 (sm_103a) path-integral Monte Carlo
+ * estimator of the discretized transition amplitude A_N^(p)(a,b;T) with
+ * level-p short-time effective actions (Balaz, Vidanovic, Stojiljkovic,
+ * Vudragovic, Belic, Bogojevic, "SPEEDUP Code for Calculation of Transition
+ * Amplitudes via the Effective Action Approach").
+ *
+ * Units: hbar = m = 1, imaginary time (Sec. 2).  A path has N = 2^s slices of
+ * width eps = T/N; q_0 = a, q_N = b.  The estimand (Sec. 4, Eq. SNp) is
+ *
+ *   A_N^(p)(a,b;T) = int dq_1..dq_{N-1} (2 pi eps)^(-N/2) exp(-S_N^(p)),
+ *   S_N^(p) = sum_k [ (q_{k+1}-q_k)^2/(2 eps) + eps W_p(x_k, xb_k; eps) ],
+ *
+ * x_k = (q_k+q_{k+1})/2, xb_k = (q_{k+1}-q_k)/2, and W_p the level-p
+ * effective potential (Sec. 2.1, Eq. ansatz truncated at m <= p-1, with the
+ * coefficients of Eq. 1Drec and Eq. diagonal).  Paths are drawn by bisection
+ * (Sec. 4.1) from a Philox4x32-10 stream, and the amplitudes of every level
+ * n = 0..s of the bisection hierarchy (N = 2^n, Sec. 4.1) come from the same
+ * paths.
+ *
+ * Conventions for every entry point:
+ *  - Returns SU_OK (0) or a negative SU_E* code; su_last_error() then gives a
+ *    one-line message (thread-local, valid until the next call on the thread).
+ *  - Host pointers are caller-owned and only read or written during the call.
+ *  - "Device" pointers are CUDA global-memory addresses on the current device,
+ *    caller-owned, written asynchronously on the given stream (NULL = the
+ *    legacy default stream); the caller synchronizes that stream before
+ *    reading them.
+ *  - Nothing here falls back to the CPU: without a usable CUDA device every
+ *    compute entry point returns SU_ECUDA.
+ */
+#ifndef SPEEDUP_H
+#define SPEEDUP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define SU_OK          0
+#define SU_EINVAL     -1   /* an argument is out of range or not finite      */
+#define SU_ENOMEM     -2   /* a host or device allocation failed              */
+#define SU_ECUDA      -3   /* a CUDA call failed or no device is usable       */
+#define SU_ETIMEOUT   -4   /* a bounded device-side wait ran out              */
+#define SU_ENONFINITE -5   /* a coefficient or a per-sample weight is NaN/Inf */
+#define SU_ENOTSUP    -6   /* valid, but larger than this build supports      */
+
+/* ---- potentials V(q) (Sec. 3.3) ------------------------------------------ */
+#define SU_HO    0   /* omega^2 q^2 / 2                        params: omega      */
+#define SU_AHO   1   /* A q^2/2 + g q^4/24                     params: A, g       */
+#define SU_DW    2   /* h (q^2 - 1)^2                          params: h          */
+#define SU_MPT   3   /* -lambda / cosh^2(alpha q)  (Eq. 1D-MPT) params: lambda, alpha */
+#define SU_POLY  4   /* sum_i v_i q^i, degree <= 8             params: v_0..v_d   */
+
+/* ---- arithmetic of the per-slice W_p evaluation --------------------------- */
+#define SU_FP64  0   /* everything in double                                   */
+#define SU_FP32  1   /* path and W_p in float, log-sum-exp reductions in double */
+
+#define SU_MAX_P 18  /* highest effective-action level                         */
+#define SU_MAX_S 10  /* deepest bisection level, N <= 1024                     */
+
+typedef struct {
+    int precision;        /* SU_FP64 (default) or SU_FP32                           */
+    int n_blocks;         /* contiguous sample blocks for the error estimate; 64    */
+    int hierarchy;        /* 1 (default): levels n = 0..s; 0: only n = 0 and n = s  */
+    uint32_t instance;    /* Philox counter word 1 (stream id of this instance); 0  */
+    double width_factor;  /* bisection width multiplier; 1 (default) = exact bridge,
+                             sqrt(2) = the literal sigma_n = sqrt(T/2^n) of Sec. 4.1;
+                             the Gaussian density ratio is added to every weight    */
+    void *stream;         /* cudaStream_t for all device work; NULL (default)      */
+    int64_t sample0;      /* first sample index: samples sample0 .. sample0+n_mc-1,
+                             so disjoint ranges on several devices form one run; 0  */
+} su_options;
+
+/* per bisection level n = 0..s (N = 2^n slices) */
+typedef struct {
+    double amp;        /* estimate of A_N^(p)(a,b;T)                              */
+    double log_amp;    /* its logarithm (finite where amp underflows)             */
+    double err;        /* std. dev. of the n_blocks block means / sqrt(n_blocks)  */
+    double rel_err;    /* err / amp                                               */
+    double err_naive;  /* sqrt((<f^2> - <f>^2) / (n - 1)), the Sec. 4.1 estimate  */
+    double ess;        /* effective sample size (sum f)^2 / sum f^2               */
+    double max_share;  /* largest single weight / sum of weights                  */
+    int64_t n;         /* samples used                                            */
+} su_level_result;
+
+/* Fill *opt with the defaults listed above. */
+void su_options_default(su_options *opt);
+
+/* One-line message for the last error on this thread ("" if none). */
+const char *su_last_error(void);
+
+/* Library and device description: writes at most cap bytes (NUL-terminated). */
+int su_version(char *buf, int cap);
+
+/*
+ * speedup_amplitude -- A_N^(p)(a,b;T) for every bisection level n = 0..s
+ * (N = 2^n), from n_mc bisection paths (Sec. 4 and 4.1).
+ *
+ *   model, params, n_params : potential (SU_* above) and its parameters.
+ *   a, b, T                 : endpoints and propagation time, T > 0.
+ *   p                       : effective-action level, 1..SU_MAX_P.
+ *   s                       : bisection depth, 0..SU_MAX_S.
+ *   n_mc                    : samples, >= 1.  Sample i (i = opt->sample0 ..
+ *                             opt->sample0 + n_mc - 1) uses the Philox counter
+ *                             (call t, opt->instance, i lo32, i hi32) under the
+ *                             key (seed lo32, seed hi32).
+ *   opt                     : NULL for defaults.
+ *   out                     : host, s+1 entries, out[n] for level n.  Level 0 is
+ *                             the analytic single-slice value with err = 0.
+ *                             Without the hierarchy only out[0] and out[s] are
+ *                             written.
+ *
+ * Host arguments in, host results out; the device work runs on opt->stream and
+ * the call returns after it.  Device scratch is allocated and freed inside.
+ */
+int speedup_amplitude(int model, const double *params, int n_params,
+                      double a, double b, double T, int p, int s,
+                      int64_t n_mc, uint64_t seed, const su_options *opt,
+                      su_level_result *out);
+
+/*
+ * speedup_generate_coeffs -- the level-p effective potential collapsed at a
+ * fixed eps (Eq. ansatz with the coefficients of Eq. 1Drec / Eq. diagonal,
+ * computed in double-double arithmetic and rounded):
+ *
+ *   W_p(x, xb; eps) = sum_{j=0}^{J} xb^(2j) sum_{i=0}^{D_j} P_{ij} z^i,
+ *   z = x^2 (SU_HO, SU_AHO, SU_DW and even SU_POLY), z = x (other SU_POLY),
+ *   z = 1/cosh^2(alpha x) (SU_MPT).
+ *
+ *   table    : host, capacity doubles; receives P, column j after column j-1,
+ *              i ascending within a column.
+ *   shape    : host, SU_MAX_P + 2 ints; shape[0] = J + 1 columns, shape[1] =
+ *              the ring (0: z = x^2, 1: z = x, 2: z = 1/cosh^2(alpha x)),
+ *              shape[2 + j] = D_j + 1 entries of column j.
+ *   n_terms  : host, receives the number of entries written.
+ * Returns SU_ENOTSUP if capacity is too small (n_terms still says how many).
+ */
+int speedup_generate_coeffs(int model, const double *params, int n_params, int p,
+                            double eps, double *table, int capacity, int *shape,
+                            int *n_terms);
+
+/* ---- device-resident interface (inputs and outputs stay in HBM) ----------- */
+
+typedef struct su_plan su_plan;
+
+/*
+ * su_plan_create -- validate, generate the coefficient tables of every level
+ * (host), and upload them to device memory owned by the plan.  Arguments as
+ * for speedup_amplitude.
+ */
+int su_plan_create(int model, const double *params, int n_params,
+                   double a, double b, double T, int p, int s,
+                   int64_t n_mc, uint64_t seed, const su_options *opt, su_plan **plan);
+
+/* Release a plan and its device memory (NULL is a no-op). */
+int su_plan_destroy(su_plan *plan);
+
+/*
+ * su_plan_sizes -- sizes of the caller-provided device buffers of
+ * su_plan_execute, in bytes: *tuple_bytes for d_tuples, *scratch_bytes for
+ * d_scratch; *levels = the number of levels sampled (s, or 1 without the
+ * hierarchy); *slice_actions = W_p evaluations per execute.
+ */
+int su_plan_sizes(const su_plan *plan, int64_t *tuple_bytes, int64_t *scratch_bytes,
+                  int *levels, int64_t *slice_actions);
+
+/*
+ * su_plan_execute -- sample the plan's n_mc paths on the device (Sec. 4.1) and
+ * reduce their weights per block and level (log-sum-exp in double).
+ *
+ *   d_tuples  : device, tuple_bytes; receives, for block b and sampled level
+ *               d (d = 0 is level s, d = 1 level s-1, ...), the four doubles
+ *               (M, S, Q, n): M = max w, S = sum exp(w - M),
+ *               Q = sum exp(2(w - M)), n = samples, at
+ *               d_tuples[4 * (b * levels + d)].
+ *   d_scratch : device, scratch_bytes, library-owned for the duration.
+ *   stream    : cudaStream_t or NULL.
+ * Asynchronous; the tuples are ready when the stream reaches this point.
+ * *launches (may be NULL) receives the number of kernel launches made.
+ */
+int su_plan_execute(su_plan *plan, void *d_tuples, void *d_scratch, void *stream,
+                    int *launches);
+
+/*
+ * su_plan_finalize -- turn host copies of the block tuples into per-level
+ * results exactly as speedup_amplitude does (out: s+1 entries).
+ * Also returns SU_ENONFINITE if the device flagged a non-finite weight
+ * (read from d_scratch, which must be the buffer execute used).
+ */
+int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_scratch,
+                     su_level_result *out);
+
+/*
+ * speedup_logweights -- per-sample log-weights (Sec. 4.1 normalisation written
+ * out): w_n = -eps_n sum_k W_p(x_k, xb_k; eps_n) on the level-n subpath, plus
+ * the width-factor correction, for samples sample0 .. sample0 + n_samples - 1
+ * and levels n = 1..s.
+ *
+ *   d_w : device, n_samples * s doubles, w[(i - sample0) * s + (n - 1)]
+ *         (written in double for both precisions).
+ * Asynchronous on opt->stream.  Requires s >= 1.
+ */
+int speedup_logweights(int model, const double *params, int n_params,
+                       double a, double b, double T, int p, int s,
+                       int64_t sample0, int64_t n_samples, uint64_t seed,
+                       const su_options *opt, double *d_w);
+
+/*
+ * speedup_philox_words -- the raw Philox4x32-10 output blocks of samples
+ * sample0 .. sample0 + n_samples - 1, calls 0 .. n_calls - 1:
+ *   d_out[((i - sample0) * n_calls + t) * 4 + r], r = 0..3   (device, uint32).
+ * Asynchronous on stream.
+ */
+int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
+                         int64_t n_samples, int n_calls, uint32_t *d_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPEEDUP_H */

@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) path-integral Monte Carlo estimator of transition
+amplitudes with level-p effective actions (SPEEDUP method).
+
+The compute path lives in libspeedup_gb300.so (C ABI: include/speedup.h);
+this package is its ctypes binding.  There is no CPU fallback: without the
+built library or a CUDA device the entry points raise.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTS, MODELS, PRECISIONS, Plan, SpeedupError, library_path, load, options,
+    speedup_amplitude, speedup_generate_coeffs, speedup_logweights, speedup_philox_words,
+    su_last_error, su_version,
+)

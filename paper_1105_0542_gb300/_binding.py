@@ -1,0 +1,232 @@
+"""Thin ctypes binding of the C ABI in include/speedup.h (same names).
+
+Argument marshalling only: every step of the estimator runs inside
+libspeedup_gb300.so.  Device buffers may be given as torch CUDA tensors or as
+raw integer addresses; streams as torch.cuda.Stream, a raw cudaStream_t
+integer, or None (the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SU_OK, SU_EINVAL, SU_ENOMEM, SU_ECUDA, SU_ETIMEOUT, SU_ENONFINITE, SU_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+MAX_P, MAX_S = 18, 10
+
+EXPORTS = [
+    "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
+    "speedup_generate_coeffs", "su_plan_create", "su_plan_destroy", "su_plan_sizes",
+    "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
+]
+
+
+class SpeedupError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"speedup error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("n_blocks", ctypes.c_int), ("hierarchy", ctypes.c_int),
+                ("instance", ctypes.c_uint32), ("width_factor", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64)]
+
+
+class LevelResult(ctypes.Structure):
+    _fields_ = [("amp", ctypes.c_double), ("log_amp", ctypes.c_double), ("err", ctypes.c_double),
+                ("rel_err", ctypes.c_double), ("err_naive", ctypes.c_double), ("ess", ctypes.c_double),
+                ("max_share", ctypes.c_double), ("n", ctypes.c_int64)]
+
+    def as_dict(self, level):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["level"] = level
+        return d
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libspeedup_gb300.so (building it first if asked); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libspeedup_gb300.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    i32, i64, u32, u64, d, vp = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+                                 ctypes.c_double, ctypes.c_void_p)
+    pd = ctypes.POINTER(ctypes.c_double)
+    pi = ctypes.POINTER(ctypes.c_int)
+    L.su_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.su_options_default.restype = None
+    L.su_last_error.restype = ctypes.c_char_p
+    L.su_version.argtypes = [ctypes.c_char_p, i32]
+    L.speedup_amplitude.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                    ctypes.POINTER(LevelResult)]
+    L.speedup_generate_coeffs.argtypes = [i32, pd, i32, i32, d, pd, i32, pi, pi]
+    L.su_plan_create.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                 ctypes.POINTER(vp)]
+    L.su_plan_destroy.argtypes = [vp]
+    L.su_plan_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), pi, ctypes.POINTER(i64)]
+    L.su_plan_execute.argtypes = [vp, vp, vp, vp, pi]
+    L.su_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
+    L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
+                                     ctypes.POINTER(Options), vp]
+    L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
+    for name in EXPORTS:
+        if name not in ("su_options_default", "su_last_error"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != SU_OK:
+        raise SpeedupError(rc, load().su_last_error().decode())
+
+
+def _model(m):
+    return MODELS[m] if isinstance(m, str) else int(m)
+
+
+def _params(params):
+    arr = (ctypes.c_double * max(len(params), 1))(*[float(v) for v in params])
+    return arr, len(params)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("device buffer must be a tensor or an integer address")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError("stream must be torch.cuda.Stream, int or None")
+
+
+def options(precision="fp64", n_blocks=64, hierarchy=True, instance=0, width_factor=1.0, stream=None,
+            sample0=0):
+    o = Options()
+    load().su_options_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.n_blocks = int(n_blocks)
+    o.hierarchy = 1 if hierarchy else 0
+    o.instance = int(instance)
+    o.width_factor = float(width_factor)
+    o.stream = _stream(stream)
+    o.sample0 = int(sample0)
+    return o
+
+
+def su_version():
+    buf = ctypes.create_string_buffer(512)
+    _check(load().su_version(buf, 512))
+    return buf.value.decode()
+
+
+def su_last_error():
+    return load().su_last_error().decode()
+
+
+def speedup_amplitude(model, params, a, b, T, p, s, n_mc, seed, **kw):
+    """Amplitude and errors for every level n = 0..s (list of dicts)."""
+    pr, npar = _params(params)
+    out = (LevelResult * (s + 1))()
+    o = options(**kw)
+    _check(load().speedup_amplitude(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
+                                    ctypes.byref(o), out))
+    return [out[n].as_dict(n) for n in range(s + 1)]
+
+
+def speedup_generate_coeffs(model, params, p, eps):
+    """(P, ncol, ring, lens): W_p = sum_j xb^(2j) sum_i P_ij z^i (see speedup.h)."""
+    pr, npar = _params(params)
+    cap = 4096
+    tab = (ctypes.c_double * cap)()
+    shape = (ctypes.c_int * (MAX_P + 2))()
+    nt = ctypes.c_int(0)
+    _check(load().speedup_generate_coeffs(_model(model), pr, npar, p, eps, tab, cap, shape,
+                                          ctypes.byref(nt)))
+    ncol = shape[0]
+    lens = [shape[2 + j] for j in range(ncol)]
+    return np.array(tab[:nt.value]), ncol, shape[1], lens
+
+
+def speedup_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, out, **kw):
+    """Per-sample log-weights into the device buffer out (n_samples x s doubles)."""
+    pr, npar = _params(params)
+    o = options(**kw)
+    _check(load().speedup_logweights(_model(model), pr, npar, a, b, T, p, s, int(sample0), int(n_samples),
+                                     int(seed), ctypes.byref(o), _ptr(out)))
+
+
+def speedup_philox_words(seed, instance, sample0, n_samples, n_calls, out, stream=None):
+    _check(load().speedup_philox_words(int(seed), int(instance), int(sample0), int(n_samples),
+                                       int(n_calls), _ptr(out), _stream(stream)))
+
+
+class Plan:
+    """su_plan_create / su_plan_execute / su_plan_finalize / su_plan_destroy."""
+
+    def __init__(self, model, params, a, b, T, p, s, n_mc, seed, **kw):
+        self.s = s
+        pr, npar = _params(params)
+        o = options(**kw)
+        h = ctypes.c_void_p()
+        _check(load().su_plan_create(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
+                                     ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        tb, sb, lv, sa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        _check(load().su_plan_sizes(h, ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(lv),
+                                    ctypes.byref(sa)))
+        self.tuple_bytes, self.scratch_bytes = tb.value, sb.value
+        self.levels, self.slice_actions = lv.value, sa.value
+
+    def su_plan_execute(self, d_tuples, d_scratch, stream=None):
+        """Launch; returns the number of kernel launches made."""
+        n = ctypes.c_int(0)
+        _check(load().su_plan_execute(self._h, _ptr(d_tuples), _ptr(d_scratch), _stream(stream),
+                                      ctypes.byref(n)))
+        return n.value
+
+    def su_plan_finalize(self, h_tuples, d_scratch=None):
+        out = (LevelResult * (self.s + 1))()
+        arr = np.ascontiguousarray(h_tuples, dtype=np.float64)
+        _check(load().su_plan_finalize(self._h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       _ptr(d_scratch), out))
+        return [out[n].as_dict(n) for n in range(self.s + 1)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().su_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,478 @@
+// Host side of the C ABI declared in include/speedup.h.
+//
+// A plan holds everything that does not depend on the samples: the validated
+// arguments, the level-p coefficient tables of every sampled level (generated
+// on the host, uploaded once), the launch configuration and the level-0 value.
+// Executing a plan launches the sampler (one bisection path per thread) and
+// the block combine; finalizing turns the per-block log-sum-exp tuples into
+// amplitudes and errors (Sec. 4.1: mean of the normalised e^{-S} and its
+// error, here from contiguous sample blocks).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/speedup.h"
+#include "generator.h"
+#include "sampler.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int64_t kMaxSamples = (int64_t)1 << 40;
+constexpr int64_t kMaxBlocks = (int64_t)1 << 20;
+
+double log_A_free(double a, double b, double T) {
+    return -0.5 * std::log(2.0 * M_PI * T) - (b - a) * (b - a) / (2.0 * T);
+}
+
+}  // namespace
+
+struct su_plan {
+    int model = 0;
+    std::vector<double> params;
+    double a = 0, b = 0, T = 1;
+    int p = 1, s = 0;
+    int64_t n_mc = 1;
+    uint64_t seed = 0;
+    su_options opt{};
+    su::Effective E;
+    double w0 = 0;            // level-0 log-weight -T W_p((a+b)/2, (b-a)/2; T)
+    double laf = 0;           // log of the free amplitude
+    int levels = 0;           // sampled levels
+    int64_t n_blocks = 1;
+    su::SamplerParams P{};
+    void *d_tables = nullptr;
+    int device = 0;
+    int grid = 0;
+    size_t smem = 0;
+    int64_t tuple_bytes = 0, scratch_bytes = 0, partial_bytes = 0;
+    int64_t slice_actions = 0;
+    double cancel_ratio = 1;  // largest sum|terms| / |sum| in the table collapse
+};
+
+extern "C" {
+
+void su_options_default(su_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = SU_FP64;
+    o->n_blocks = 64;
+    o->hierarchy = 1;
+    o->instance = 0;
+    o->width_factor = 1.0;
+    o->stream = nullptr;
+    o->sample0 = 0;
+}
+
+const char *su_last_error(void) { return g_err.c_str(); }
+
+int su_version(char *buf, int cap) {
+    if (!buf || cap <= 0) return fail(SU_EINVAL, "buffer missing");
+    int rt = 0, drv = 0, dev = -1, n = 0;
+    cudaRuntimeGetVersion(&rt);
+    cudaDriverGetVersion(&drv);
+    std::string s = "speedup-gb300 1 (sm_103a); cudart " + std::to_string(rt) + ", driver " +
+                    std::to_string(drv);
+    if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0 && cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceProp pr;
+        if (cudaGetDeviceProperties(&pr, dev) == cudaSuccess)
+            s += std::string("; device ") + pr.name + ", " + std::to_string(pr.multiProcessorCount) +
+                 " SMs, cc " + std::to_string(pr.major) + "." + std::to_string(pr.minor);
+    } else {
+        cudaGetLastError();
+        s += "; no CUDA device";
+    }
+    std::snprintf(buf, (size_t)cap, "%s", s.c_str());
+    return SU_OK;
+}
+
+int speedup_generate_coeffs(int model, const double *params, int n_params, int p, double eps,
+                            double *table, int capacity, int *shape, int *n_terms) {
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");
+    if (!table || !shape || !n_terms || capacity < 0) return fail(SU_EINVAL, "output missing");
+    su::Effective E;
+    std::string err;
+    int rc = su::build_effective(model, params, n_params, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    std::vector<double> P;
+    su::collapse(E, eps, P);
+    *n_terms = (int)P.size();
+    shape[0] = E.shape.ncol;
+    shape[1] = E.shape.ring;
+    for (int j = 0; j < SU_MAX_P; ++j) shape[2 + j] = j < E.shape.ncol ? E.shape.len[j] : 0;
+    if ((int)P.size() > capacity) return fail(SU_ENOTSUP, "table needs %d entries", (int)P.size());
+    for (size_t i = 0; i < P.size(); ++i) {
+        if (!std::isfinite(P[i])) return fail(SU_ENONFINITE, "non-finite coefficient");
+        table[i] = P[i];
+    }
+    return SU_OK;
+}
+
+static int validate(int model, const double *params, int n_params, double a, double b, double T,
+                    int p, int s, int64_t n_mc, const su_options &o) {
+    (void)model;
+    (void)params;
+    (void)n_params;
+    if (!std::isfinite(a) || !std::isfinite(b)) return fail(SU_EINVAL, "a and b must be finite");
+    if (!(T > 0) || !std::isfinite(T)) return fail(SU_EINVAL, "T must be finite and > 0");
+    if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
+    if (s < 0 || s > SU_MAX_S) return fail(SU_EINVAL, "s must be in 0..%d", SU_MAX_S);
+    if (n_mc < 1 || n_mc > kMaxSamples) return fail(SU_EINVAL, "n_mc must be in 1..2^40");
+    if (o.precision != SU_FP64 && o.precision != SU_FP32) return fail(SU_EINVAL, "unknown precision");
+    if (o.n_blocks < 1 || o.n_blocks > kMaxBlocks) return fail(SU_EINVAL, "n_blocks must be in 1..2^20");
+    if (!(o.width_factor > 0) || !std::isfinite(o.width_factor))
+        return fail(SU_EINVAL, "width_factor must be finite and > 0");
+    if (o.sample0 < 0 || o.sample0 + n_mc > kMaxSamples) return fail(SU_EINVAL, "sample0 out of range");
+    return SU_OK;
+}
+
+static int configure(su_plan &pl) {
+    using namespace su;
+    SamplerParams &P = pl.P;
+    const int S = pl.s;
+    const int prec = pl.opt.precision;
+    // tables of levels n = S..1 (row d = S - n), each scaled for the kernel
+    const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
+    const int M = pl.E.shape.M;
+    std::vector<double> tabd((size_t)std::max(S, 1) * M, 0.0);
+    for (int d = 0; d < S; ++d) {
+        const int n = S - d;
+        const double eps = pl.T / std::ldexp(1.0, n);
+        std::vector<double> t;
+        pl.cancel_ratio = std::max(pl.cancel_ratio, su::kernel_table(pl.E, eps, t));
+        for (int i = 0; i < M; ++i) {
+            if (!std::isfinite(t[i]) || (prec == SU_FP32 && !std::isfinite((float)t[i])))
+                return fail(SU_ENONFINITE, "non-finite coefficient at level %d", n);
+            tabd[(size_t)d * M + i] = t[i];
+        }
+    }
+    std::vector<unsigned char> blob(tabd.size() * rs);
+    if (prec == SU_FP32)
+        for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
+    else
+        std::memcpy(blob.data(), tabd.data(), blob.size());
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    CU(cudaGetDevice(&pl.device), "cudaGetDevice");
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
+    int smem_max = 0;
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl.device),
+       "smem limit");
+    CU(cudaMalloc(&pl.d_tables, blob.size()), "cudaMalloc(tables)");
+    CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
+
+    std::memset(&P, 0, sizeof P);
+    P.a = pl.a;
+    P.b = pl.b;
+    for (int n = 1; n <= S; ++n) P.sigma[n] = pl.opt.width_factor * std::sqrt(pl.T / std::ldexp(1.0, n + 1));
+    P.S = S;
+    P.F = std::min(S, kMaxFine);
+    P.levels = pl.levels;
+    P.wf_on = pl.opt.width_factor != 1.0;
+    P.lwf = std::log(pl.opt.width_factor);
+    P.hcoef = 0.5 * (1.0 - pl.opt.width_factor * pl.opt.width_factor);
+    P.ring = pl.E.shape.ring;
+    P.ncol = pl.E.shape.ncol;
+    P.M = M;
+    for (int j = 0; j < pl.E.shape.ncol; ++j) P.len[j] = pl.E.shape.len[j];
+    P.alpha = pl.E.shape.alpha;
+    P.tables = pl.d_tables;
+    P.seed = pl.seed;
+    P.instance = pl.opt.instance;
+    P.n_mc = pl.n_mc;
+    P.sample0 = pl.opt.sample0;
+    P.n_blocks = pl.n_blocks;
+
+    // launch shape: one path per thread, persistent grid over items
+    int occ = 0;
+    P.rounds = 1;
+    for (int it = 0; it < 2; ++it) {
+        const int chunk = kThreads * P.rounds;
+        const int64_t bsz = (pl.n_mc + pl.n_blocks - 1) / pl.n_blocks;
+        P.items_per_block = (bsz + chunk - 1) / chunk;
+        P.n_items = P.items_per_block * pl.n_blocks;
+        pl.smem = sampler_smem_bytes(P, prec);
+        if (pl.smem > (size_t)smem_max)
+            return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);
+        occ = sampler_occupancy(P, prec, pl.smem);
+        if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
+        if (it == 0) {
+            // fewer, larger items when there are many per resident CTA
+            const int64_t per = P.n_items / ((int64_t)sms * occ);
+            P.rounds = (int)std::max<int64_t>(1, std::min<int64_t>(4, per / 16));
+            if (P.rounds == 1) break;
+        }
+    }
+    pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
+    pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
+    pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + 256;
+    pl.tuple_bytes = pl.n_blocks * pl.levels * 4 * (int64_t)sizeof(double);
+    const int64_t N = (int64_t)1 << S;
+    pl.slice_actions = pl.n_mc * (pl.levels > 1 ? 2 * N - 2 : N);
+    if (S == 0) pl.slice_actions = 0;
+    return SU_OK;
+}
+
+int su_plan_create(int model, const double *params, int n_params, double a, double b, double T,
+                   int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt, su_plan **out) {
+    if (!out) return fail(SU_EINVAL, "plan pointer missing");
+    *out = nullptr;
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
+    if (rc) return rc;
+    std::unique_ptr<su_plan> pl(new (std::nothrow) su_plan);
+    if (!pl) return fail(SU_ENOMEM, "host allocation failed");
+    std::string err;
+    rc = su::build_effective(model, params, n_params, p, pl->E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    pl->model = model;
+    pl->params.assign(params, params + n_params);
+    pl->a = a;
+    pl->b = b;
+    pl->T = T;
+    pl->p = p;
+    pl->s = s;
+    pl->n_mc = n_mc;
+    pl->seed = seed;
+    pl->opt = o;
+    pl->levels = s == 0 ? 0 : (o.hierarchy ? s : 1);
+    pl->n_blocks = std::min<int64_t>(o.n_blocks, n_mc);
+    pl->w0 = -T * su::wp_host(pl->E, 0.5 * (a + b), 0.5 * (b - a), T);
+    pl->laf = log_A_free(a, b, T);
+    if (!std::isfinite(pl->w0) && !(std::isinf(pl->w0) && pl->w0 < 0))
+        return fail(SU_ENONFINITE, "level-0 weight is not finite");
+    rc = configure(*pl);
+    if (rc) {
+        if (pl->d_tables) cudaFree(pl->d_tables);
+        return rc;
+    }
+    *out = pl.release();
+    return SU_OK;
+}
+
+int su_plan_destroy(su_plan *pl) {
+    if (!pl) return SU_OK;
+    if (pl->d_tables) cudaFree(pl->d_tables);
+    delete pl;
+    return SU_OK;
+}
+
+int su_plan_sizes(const su_plan *pl, int64_t *tuple_bytes, int64_t *scratch_bytes, int *levels,
+                  int64_t *slice_actions) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (tuple_bytes) *tuple_bytes = pl->tuple_bytes;
+    if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
+    if (levels) *levels = pl->levels;
+    if (slice_actions) *slice_actions = pl->slice_actions;
+    return SU_OK;
+}
+
+int su_plan_execute(su_plan *pl, void *d_tuples, void *d_scratch, void *stream, int *launches) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (launches) *launches = 0;
+    if (pl->s == 0) return SU_OK;  // level 0 is analytic: nothing to sample
+    if (!d_tuples || !d_scratch) return fail(SU_EINVAL, "device buffers missing");
+    cudaStream_t st = (cudaStream_t)stream;
+    su::SamplerParams P = pl->P;
+    P.partial = static_cast<double *>(d_scratch);
+    P.flags = reinterpret_cast<int *>(static_cast<char *>(d_scratch) + pl->scratch_bytes - 256);
+    P.w_out = nullptr;
+    CU(cudaMemsetAsync(P.flags, 0, sizeof(int), st), "clear flags");
+    CU(su::launch_sampler(P, pl->opt.precision, pl->grid, pl->smem, st), "sampler launch");
+    CU(su::launch_combine(P.partial, static_cast<double *>(d_tuples), pl->n_blocks, pl->levels,
+                          P.items_per_block, st),
+       "combine launch");
+    if (launches) *launches = 2;
+    return SU_OK;
+}
+
+static void level_result(double laf, const double *tup, int64_t nb, int levels, int d,
+                         su_level_result *r) {
+    double M = -INFINITY;
+    int64_t n = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const double *t = tup + 4 * (b * levels + d);
+        n += (int64_t)t[3];
+        if (t[3] > 0 && t[0] > M) M = t[0];
+    }
+    r->n = n;
+    if (!(M > -INFINITY)) {
+        r->amp = 0;
+        r->log_amp = -INFINITY;
+        r->err = r->err_naive = 0;
+        r->rel_err = NAN;
+        r->ess = 0;
+        r->max_share = NAN;
+        return;
+    }
+    double S = 0, Q = 0;
+    std::vector<double> mu;
+    for (int64_t b = 0; b < nb; ++b) {
+        const double *t = tup + 4 * (b * levels + d);
+        if (!(t[3] > 0)) continue;
+        const double f = t[0] > -INFINITY ? std::exp(t[0] - M) : 0.0;
+        S += t[1] * f;
+        Q += t[2] * f * f;
+        mu.push_back(t[1] * f / t[3]);
+    }
+    const double mean = S / (double)n;
+    double err_b = NAN;
+    if (mu.size() > 1) {
+        double m = 0;
+        for (double v : mu) m += v;
+        m /= (double)mu.size();
+        double ss = 0;
+        for (double v : mu) ss += (v - m) * (v - m);
+        err_b = std::sqrt(ss / (double)(mu.size() - 1)) / std::sqrt((double)mu.size());
+    }
+    const double var = std::max(Q / (double)n - mean * mean, 0.0);
+    const double err_n = n > 1 ? std::sqrt(var / (double)(n - 1)) : NAN;
+    const double scale = std::exp(laf + M);
+    r->amp = scale * mean;
+    r->log_amp = laf + M + std::log(mean);
+    r->err = scale * err_b;
+    r->rel_err = err_b / mean;
+    r->err_naive = scale * err_n;
+    r->ess = S * S / Q;
+    r->max_share = 1.0 / S;
+}
+
+int su_plan_finalize(const su_plan *pl, const double *h_tuples, const void *d_scratch,
+                     su_level_result *out) {
+    if (!pl || !out) return fail(SU_EINVAL, "plan or output missing");
+    if (pl->s > 0 && d_scratch) {
+        int flags = 0;
+        CU(cudaMemcpy(&flags, static_cast<const char *>(d_scratch) + pl->scratch_bytes - 256, sizeof(int),
+                      cudaMemcpyDeviceToHost),
+           "read flags");
+        if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    }
+    su_level_result &r0 = out[0];
+    r0.amp = std::exp(pl->laf + pl->w0);
+    r0.log_amp = pl->laf + pl->w0;
+    r0.err = r0.err_naive = r0.rel_err = 0;
+    r0.ess = (double)pl->n_mc;
+    r0.max_share = 1.0 / (double)pl->n_mc;
+    r0.n = pl->n_mc;
+    if (pl->s == 0) return SU_OK;
+    if (!h_tuples) return fail(SU_EINVAL, "tuples missing");
+    for (int d = 0; d < pl->levels; ++d)
+        level_result(pl->laf, h_tuples, pl->n_blocks, pl->levels, d, &out[pl->s - d]);
+    return SU_OK;
+}
+
+int speedup_amplitude(int model, const double *params, int n_params, double a, double b, double T,
+                      int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt,
+                      su_level_result *out) {
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_plan *pl = nullptr;
+    int rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, opt, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    if (s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
+    cudaStream_t st = (cudaStream_t)pl->opt.stream;
+    void *dbuf = nullptr;
+    const int64_t tb = pl->tuple_bytes, sb = pl->scratch_bytes;
+    CU(cudaMallocAsync(&dbuf, (size_t)(tb + sb), st), "cudaMallocAsync");
+    std::vector<double> h((size_t)(tb / sizeof(double)) + 32);
+    void *d_tup = dbuf;
+    void *d_scr = static_cast<char *>(dbuf) + tb;
+    rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);
+    cudaError_t e = cudaSuccess;
+    if (rc == SU_OK) {
+        e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h.data() + tb / sizeof(double), static_cast<char *>(d_scr) + sb - 256,
+                                sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(dbuf, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "sampling");
+    int flags = 0;
+    std::memcpy(&flags, h.data() + tb / sizeof(double), sizeof(int));
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+int speedup_logweights(int model, const double *params, int n_params, double a, double b, double T,
+                       int p, int s, int64_t sample0, int64_t n_samples, uint64_t seed,
+                       const su_options *opt, double *d_w) {
+    if (s < 1) return fail(SU_EINVAL, "s must be >= 1 for per-sample weights");
+    if (!d_w) return fail(SU_EINVAL, "output missing");
+    if (sample0 < 0 || n_samples < 1 || sample0 + n_samples > kMaxSamples)
+        return fail(SU_EINVAL, "sample range out of bounds");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    o.hierarchy = 1;
+    o.n_blocks = 1;
+    su_plan *pl = nullptr;
+    int rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_samples, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    su::SamplerParams P = pl->P;
+    P.w_out = d_w;
+    P.sample0 = sample0;
+    P.partial = nullptr;
+    const size_t smem = su::sampler_smem_bytes(P, o.precision);
+    if (su::sampler_occupancy(P, o.precision, smem) < 1) return fail(SU_ECUDA, "sampler not resident");
+    int *d_flag = nullptr;
+    CU(cudaMallocAsync(&d_flag, sizeof(int), st), "cudaMallocAsync");
+    P.flags = d_flag;
+    cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = su::launch_sampler(P, o.precision, pl->grid, smem, st);
+    int flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_flag, st);
+    if (e != cudaSuccess) return cuda_fail(e, "per-sample weights");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return SU_OK;
+}
+
+int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                         int n_calls, uint32_t *d_out, void *stream) {
+    if (!d_out || sample0 < 0 || n_samples < 0 || n_calls < 0) return fail(SU_EINVAL, "bad arguments");
+    CU(su::launch_philox_words(seed, instance, sample0, n_samples, n_calls, d_out, (cudaStream_t)stream),
+       "philox launch");
+    return SU_OK;
+}
+
+}  // extern "C"

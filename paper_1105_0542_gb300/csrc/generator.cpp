@@ -1,0 +1,341 @@
+// Host generator of the level-p effective potential W_p (Sec. 2.1 and 3.3).
+//
+// The recursion Eq. 1Drec,
+//   8(m+k+1) c_{m,k} = (2k+2)(2k+1) c_{m,k+1} + c''_{m-1,k}
+//                      - sum_{l=0}^{m-2} sum_r c'_{l,r} c'_{m-l-2,k-r}
+//                      - sum_{l=1}^{m-2} sum_r 2r(2k-2r+2) c_{l,r} c_{m-l-1,k-r+1},
+//   r in [max(0, k-m+l+2), min(k, l)],
+// with c_{m,m} = V^(2m)/(2m+1)! (Eq. diagonal), evaluated for each m diagonal
+// first and then k = m-1..0 (Fig. 1), on polynomials in one ring variable:
+//
+//  * x itself for polynomial potentials (the model-specific mode of Sec. 3.3:
+//    derivatives taken explicitly while iterating);
+//  * u = 1/cosh^2(alpha x) for V = -lambda u (Eq. 1D-MPT).  With
+//    t = tanh(alpha x), du/dx = -2 alpha u t and t^2 = 1 - u, so
+//      f'(x) g'(x) = 4 alpha^2 u^2 (1-u) f_u g_u,
+//      f''(x)      = 4 alpha^2 u^2 (1-u) f_uu + (4 alpha^2 u - 6 alpha^2 u^2) f_u,
+//    and every c_{m,k} stays a polynomial in u (the content of
+//    Eq. 1D-MPTansatz: tanh^(2l) / cosh^(2m-2l+2) = (1-u)^l u^(m-l+1)).
+//
+// Coefficients are double-double numbers (a + b with |b| <= ulp(a)/2, using
+// Knuth's two-sum and the FMA-exact product), so that the collapse of many
+// terms of alternating sign at large eps still rounds to double correctly.
+// This file is host code; it is compiled with floating-point contraction off
+// so that the error-free transformations stay error-free on every host.
+#include "generator.h"
+
+#include <cmath>
+#include <cstdio>
+
+#include "../../include/speedup.h"
+
+namespace su {
+namespace {
+
+struct DD {
+    double hi, lo;
+};
+
+inline DD two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+inline DD fast_two_sum(double a, double b) {
+    double s = a + b;
+    return {s, b - (s - a)};
+}
+inline DD two_prod(double a, double b) {
+    double p = a * b;
+    return {p, std::fma(a, b, -p)};
+}
+inline DD add(DD a, DD b) {
+    DD s = two_sum(a.hi, b.hi);
+    DD t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+inline DD neg(DD a) { return {-a.hi, -a.lo}; }
+inline DD mul(DD a, DD b) {
+    DD p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return fast_two_sum(p.hi, p.lo);
+}
+inline DD mul_d(DD a, double b) {
+    DD p = two_prod(a.hi, b);
+    p.lo += a.lo * b;
+    return fast_two_sum(p.hi, p.lo);
+}
+inline DD div_d(DD a, double b) {
+    double q1 = a.hi / b;
+    DD r = add(a, neg(two_prod(q1, b)));
+    double q2 = r.hi / b;
+    DD q = fast_two_sum(q1, q2);
+    r = add(r, neg(two_prod(q2, b)));
+    return add(q, DD{r.hi / b, 0.0});
+}
+inline DD dd(double a) { return {a, 0.0}; }
+inline bool is_zero(DD a) { return a.hi == 0.0 && a.lo == 0.0; }
+
+using Poly = std::vector<DD>;
+
+void trim(Poly &a) {
+    while (!a.empty() && is_zero(a.back())) a.pop_back();
+}
+Poly padd(const Poly &a, const Poly &b) {
+    Poly r(std::max(a.size(), b.size()), dd(0));
+    for (size_t i = 0; i < a.size(); ++i) r[i] = add(r[i], a[i]);
+    for (size_t i = 0; i < b.size(); ++i) r[i] = add(r[i], b[i]);
+    trim(r);
+    return r;
+}
+Poly pscale(const Poly &a, DD s) {
+    Poly r(a.size());
+    for (size_t i = 0; i < a.size(); ++i) r[i] = mul(a[i], s);
+    trim(r);
+    return r;
+}
+Poly pmul(const Poly &a, const Poly &b) {
+    if (a.empty() || b.empty()) return {};
+    Poly r(a.size() + b.size() - 1, dd(0));
+    for (size_t i = 0; i < a.size(); ++i) {
+        if (is_zero(a[i])) continue;
+        for (size_t j = 0; j < b.size(); ++j)
+            if (!is_zero(b[j])) r[i + j] = add(r[i + j], mul(a[i], b[j]));
+    }
+    trim(r);
+    return r;
+}
+Poly pder(const Poly &a) {
+    Poly r;
+    for (size_t i = 1; i < a.size(); ++i) r.push_back(mul_d(a[i], (double)i));
+    trim(r);
+    return r;
+}
+// multiply by the monomial-sum sum_i m[i] u^i (small exact coefficients)
+Poly pmul_small(const Poly &a, const Poly &m) { return pmul(a, m); }
+
+// The ring: how x-derivatives act on the ring variable.
+struct RingOps {
+    bool sech2 = false;
+    Poly w;   // 4 alpha^2 u^2 (1 - u): the factor of products of first derivatives
+    Poly g;   // 4 alpha^2 u - 6 alpha^2 u^2: the factor of f_u in f''
+    // first derivative in the ring variable (x or u)
+    Poly d1(const Poly &f) const { return pder(f); }
+    // x-second derivative
+    Poly d2(const Poly &f) const {
+        if (!sech2) return pder(pder(f));
+        return padd(pmul_small(pder(pder(f)), w), pmul_small(pder(f), g));
+    }
+    // product of two x-first-derivatives given the ring derivatives fu, gu,
+    // summed beforehand: x-derivative products are w * (sum fu gu) in the u ring
+    Poly finish_products(const Poly &s) const { return sech2 ? pmul_small(s, w) : s; }
+};
+
+}  // namespace
+
+int build_effective(int model, const double *params, int n_params, int p, Effective &E,
+                    std::string &err) {
+    auto bad = [&](const char *m) {
+        err = m;
+        return SU_EINVAL;
+    };
+    if (p < 1 || p > SU_MAX_P) return bad("p must be in 1..18");
+    if (n_params < 0 || (n_params > 0 && !params)) return bad("params missing");
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return bad("non-finite potential parameter");
+    Poly V;
+    RingOps R;
+    double alpha = 0;
+    switch (model) {
+        case SU_HO:
+            if (n_params != 1) return bad("SU_HO takes 1 parameter (omega)");
+            V = {dd(0), dd(0), div_d(two_prod(params[0], params[0]), 2.0)};
+            break;
+        case SU_AHO:
+            if (n_params != 2) return bad("SU_AHO takes 2 parameters (A, g)");
+            V = {dd(0), dd(0), div_d(dd(params[0]), 2.0), dd(0), div_d(dd(params[1]), 24.0)};
+            break;
+        case SU_DW:
+            if (n_params != 1) return bad("SU_DW takes 1 parameter (h)");
+            V = {dd(params[0]), dd(0), mul_d(dd(params[0]), -2.0), dd(0), dd(params[0])};
+            break;
+        case SU_MPT: {
+            if (n_params != 2) return bad("SU_MPT takes 2 parameters (lambda, alpha)");
+            if (params[1] == 0.0) return bad("SU_MPT needs alpha != 0");
+            alpha = params[1];
+            V = {dd(0), dd(-params[0])};
+            DD a2 = two_prod(alpha, alpha);
+            DD a4 = mul_d(a2, 4.0), a6 = mul_d(a2, 6.0);
+            R.sech2 = true;
+            R.w = {dd(0), dd(0), a4, neg(a4)};
+            R.g = {dd(0), a4, neg(a6)};
+            break;
+        }
+        case SU_POLY:
+            if (n_params < 1 || n_params > 9) return bad("SU_POLY takes 1..9 coefficients");
+            for (int i = 0; i < n_params; ++i) V.push_back(dd(params[i]));
+            break;
+        default:
+            return bad("unknown model");
+    }
+    trim(V);
+
+    // x-derivatives of V of even order for the diagonal
+    std::vector<Poly> V2(p);
+    V2[0] = V;
+    for (int m = 1; m < p; ++m) V2[m] = R.d2(V2[m - 1]);
+
+    std::vector<std::vector<Poly>> c(p, std::vector<Poly>(p));
+    std::vector<std::vector<Poly>> cu(p, std::vector<Poly>(p));  // ring first derivatives
+    DD inv_fact = dd(1.0);  // 1/(2m+1)!, one exact-integer division at a time
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) inv_fact = div_d(div_d(inv_fact, 2.0 * m), 2.0 * m + 1.0);
+        c[m][m] = pscale(V2[m], inv_fact);
+        cu[m][m] = R.d1(c[m][m]);
+        for (int k = m - 1; k >= 0; --k) {
+            Poly acc = pscale(c[m][k + 1], dd((double)((2 * k + 2) * (2 * k + 1))));
+            acc = padd(acc, R.d2(c[m - 1][k]));
+            Poly prod;
+            for (int l = 0; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r)
+                    prod = padd(prod, pmul(cu[l][r], cu[m - l - 2][k - r]));
+            acc = padd(acc, pscale(R.finish_products(prod), dd(-1.0)));
+            for (int l = 1; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r) {
+                    int fac = 2 * r * (2 * k - 2 * r + 2);
+                    if (fac) acc = padd(acc, pscale(pmul(c[l][r], c[m - l - 1][k - r + 1]), dd(-(double)fac)));
+                }
+            c[m][k] = pscale(acc, div_d(dd(1.0), 8.0 * (m + k + 1)));
+            cu[m][k] = R.d1(c[m][k]);
+        }
+    }
+
+    // shape of the collapsed polynomial
+    bool even = !R.sech2;
+    for (int m = 0; m < p && even; ++m)
+        for (int k = 0; k <= m && even; ++k)
+            for (size_t i = 1; i < c[m][k].size(); i += 2)
+                if (!is_zero(c[m][k][i])) even = false;
+    Shape S;
+    S.ring = R.sech2 ? RING_SECH2 : (even ? RING_EVEN : RING_X);
+    S.alpha = alpha;
+    int ncol = 0;
+    std::vector<int> len(p, 0);
+    for (int k = 0; k < p; ++k) {
+        int deg = -1;
+        for (int m = k; m < p; ++m) deg = std::max(deg, (int)c[m][k].size() - 1);
+        if (deg >= 0) {
+            len[k] = (S.ring == RING_EVEN ? deg / 2 : deg) + 1;
+            ncol = k + 1;
+        }
+    }
+    if (ncol == 0) {  // V = 0: keep one (zero) entry so the table is never empty
+        ncol = 1;
+        len[0] = 1;
+    }
+    for (int k = 0; k < ncol; ++k)
+        if (len[k] == 0) len[k] = 1;  // interior empty column: one zero entry
+    S.ncol = ncol;
+    S.len.assign(len.begin(), len.begin() + ncol);
+    S.M = 0;
+    for (int k = 0; k < ncol; ++k) S.M += S.len[k];
+
+    E.p = p;
+    E.shape = S;
+    E.hi.assign(p, std::vector<std::vector<double>>(p));
+    E.lo.assign(p, std::vector<std::vector<double>>(p));
+    for (int m = 0; m < p; ++m)
+        for (int k = 0; k <= m; ++k)
+            for (const DD &v : c[m][k]) {
+                E.hi[m][k].push_back(v.hi);
+                E.lo[m][k].push_back(v.lo);
+            }
+    return SU_OK;
+}
+
+namespace {
+
+// P_ij(eps) in double-double; ratio = sum|terms| / |sum| (largest)
+void collapse_dd(const Effective &E, double eps, std::vector<DD> &P, double *ratio) {
+    const Shape &S = E.shape;
+    P.assign(S.M, dd(0));
+    std::vector<DD> absum(S.M, dd(0));
+    int off = 0;
+    for (int j = 0; j < S.ncol; ++j) {
+        DD ep = dd(1.0);  // eps^(m-j)
+        for (int m = j; m < E.p; ++m) {
+            const auto &h = E.hi[m][j];
+            const auto &l = E.lo[m][j];
+            for (size_t i = 0; i < h.size(); ++i) {
+                if (S.ring == RING_EVEN && (i & 1)) continue;
+                int ii = S.ring == RING_EVEN ? (int)i / 2 : (int)i;
+                DD t = mul(DD{h[i], l[i]}, ep);
+                P[off + ii] = add(P[off + ii], t);
+                absum[off + ii] = add(absum[off + ii], DD{std::fabs(t.hi), std::fabs(t.hi) == t.hi ? t.lo : -t.lo});
+            }
+            ep = mul_d(ep, eps);
+        }
+        off += S.len[j];
+    }
+    if (ratio) {
+        double r = 1.0;
+        for (int i = 0; i < S.M; ++i)
+            if (P[i].hi != 0.0) r = std::max(r, absum[i].hi / std::fabs(P[i].hi));
+        *ratio = r;
+    }
+}
+
+}  // namespace
+
+void collapse(const Effective &E, double eps, std::vector<double> &P) {
+    std::vector<DD> Pd;
+    collapse_dd(E, eps, Pd, nullptr);
+    P.resize(Pd.size());
+    for (size_t i = 0; i < Pd.size(); ++i) P[i] = Pd[i].hi;
+}
+
+double kernel_table(const Effective &E, double eps, std::vector<double> &T) {
+    std::vector<DD> Pd;
+    double ratio = 1.0;
+    collapse_dd(E, eps, Pd, &ratio);
+    const Shape &S = E.shape;
+    T.resize(S.M);
+    int off = 0;
+    for (int j = 0; j < S.ncol; ++j) {
+        double sj = std::ldexp(1.0, -2 * j);  // xb^(2j) = vs^(2j) / 4^j
+        for (int i = 0; i < S.len[j]; ++i) {
+            double si = S.ring == RING_EVEN ? std::ldexp(1.0, -2 * i)    // x^(2i) = us^(2i)/4^i
+                        : S.ring == RING_X  ? std::ldexp(1.0, -i)        // x^i = us^i / 2^i
+                                            : 1.0;
+            DD v = mul_d(mul_d(Pd[off + i], -eps), si * sj);  // powers of two: exact
+            T[off + i] = v.hi;
+        }
+        off += S.len[j];
+    }
+    return ratio;
+}
+
+double wp_host(const Effective &E, double x, double xb, double eps) {
+    std::vector<DD> Pd;
+    collapse_dd(E, eps, Pd, nullptr);
+    const Shape &S = E.shape;
+    double z = S.ring == RING_EVEN ? x * x
+               : S.ring == RING_X  ? x
+                                   : 1.0 / (std::cosh(S.alpha * x) * std::cosh(S.alpha * x));
+    DD y = two_prod(xb, xb);
+    DD acc = dd(0);
+    int off = S.M;
+    for (int j = S.ncol - 1; j >= 0; --j) {
+        off -= S.len[j];
+        DD h = dd(0);
+        for (int i = S.len[j] - 1; i >= 0; --i) h = add(mul_d(h, z), Pd[off + i]);
+        acc = add(mul(acc, y), h);
+    }
+    return acc.hi;
+}
+
+}  // namespace su

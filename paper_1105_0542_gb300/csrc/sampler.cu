@@ -1,0 +1,135 @@
+// Non-templated kernels of the amplitude estimator and the host launchers:
+// the block combine, the raw Philox words, and the dispatch to the sampler
+// instantiations (one translation unit per precision and ring, built from
+// sampler_inst.cu).
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "sampler_impl.cuh"
+
+namespace su {
+
+// defined in the sampler_inst.cu instantiations
+const void *sampler_entry_f64_0();
+const void *sampler_entry_f64_1();
+const void *sampler_entry_f64_2();
+const void *sampler_entry_f32_0();
+const void *sampler_entry_f32_1();
+const void *sampler_entry_f32_2();
+
+namespace {
+
+// ----------------------------------------------------------- combine
+__global__ void combine_kernel(const double *__restrict__ partial, double *__restrict__ tuples,
+                               int64_t n_blocks, int L, int64_t ipb) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_blocks * L) return;
+    const int64_t b = id / L;
+    const int d = (int)(id - b * L);
+    double M = -INFINITY, S = 0, Q = 0, n = 0;
+    for (int64_t r = 0; r < ipb; ++r) {
+        const double *p = partial + 4 * ((b * ipb + r) * L + d);
+        const double m2 = p[0];
+        n += p[3];
+        if (!(m2 > -INFINITY)) continue;
+        if (m2 > M) {
+            const double f = exp(M - m2);  // 0 when M = -inf
+            S = S * f + p[1];
+            Q = Q * f * f + p[2];
+            M = m2;
+        } else {
+            const double f = exp(m2 - M);
+            S += p[1] * f;
+            Q += p[2] * f * f;
+        }
+    }
+    double *o = tuples + 4 * id;
+    o[0] = M;
+    o[1] = S;
+    o[2] = Q;
+    o[3] = n;
+}
+
+// ------------------------------------------------------- raw Philox words
+__global__ void philox_words_kernel(uint64_t seed, uint32_t inst, int64_t sample0, int64_t ns,
+                                    int ncalls, uint32_t *out) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= ns * ncalls) return;
+    const int64_t i = id / ncalls;
+    const uint32_t t = (uint32_t)(id - i * ncalls);
+    const uint64_t s = (uint64_t)(sample0 + i);
+    const uint4 w = philox4x32_10(make_uint4(t, inst, (uint32_t)s, (uint32_t)(s >> 32)),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    reinterpret_cast<uint4 *>(out)[id] = w;
+}
+
+const void *pick(const SamplerParams &P, int precision) {
+    if (precision == SU_FP32)
+        return P.ring == RING_EVEN ? sampler_entry_f32_0() : P.ring == RING_X ? sampler_entry_f32_1() : sampler_entry_f32_2();
+    return P.ring == RING_EVEN ? sampler_entry_f64_0() : P.ring == RING_X ? sampler_entry_f64_1() : sampler_entry_f64_2();
+}
+
+}  // namespace
+
+size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
+    const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
+    const int C = 1 << (P.S - P.F);
+    size_t off = P.w_out ? 0 : sizeof(double) * (size_t)P.levels * kThreads * P.rounds;
+    off += rs * (size_t)P.S * P.M;
+    off = (off + 15) & ~(size_t)15;
+    off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    if (P.wf_on) off += sizeof(double) * (size_t)(P.S + 1) * kThreads;
+    return off;
+}
+
+// Opt the kernel in to the device's full dynamic shared memory once, so that
+// plans of different sizes can alternate without re-setting the attribute.
+static cudaError_t allow_full_smem(const void *fn) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return e;
+}
+
+int sampler_occupancy(const SamplerParams &P, int precision, size_t smem) {
+    const void *fn = pick(P, precision);
+    if (allow_full_smem(fn) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
+                           cudaStream_t st) {
+    void *args[] = {const_cast<SamplerParams *>(&P)};
+    const void *fn = pick(P, precision);
+    if (smem > 48 * 1024) {
+        cudaError_t e = allow_full_smem(fn);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, st);
+}
+
+cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
+                           int64_t items_per_block, cudaStream_t st) {
+    const int64_t n = n_blocks * levels;
+    const int th = 128;
+    combine_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(partial, tuples, n_blocks, levels,
+                                                               items_per_block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                                int n_calls, uint32_t *out, cudaStream_t st) {
+    const int64_t n = n_samples * n_calls;
+    if (n == 0) return cudaSuccess;
+    const int th = 256;
+    philox_words_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(seed, instance, sample0, n_samples,
+                                                                    n_calls, out);
+    return cudaGetLastError();
+}
+
+}  // namespace su

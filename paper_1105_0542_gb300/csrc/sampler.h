@@ -1,0 +1,58 @@
+// Internal interface between the host API and the device kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/speedup.h"
+
+namespace su {
+
+constexpr int kThreads = 128;   // threads per CTA of the sampler: one path per thread
+constexpr int kMaxFine = 5;     // depth of the register-resident bisection subtree
+
+// Everything the sampler needs, passed by value (it lives in the constant bank).
+struct SamplerParams {
+    // path: q_0 = a, q_N = b, N = 2^S, bisection widths sigma[n] (n = 1..S)
+    double a, b;
+    double sigma[SU_MAX_S + 1];
+    int S;
+    int F;                    // fine subtree depth, min(S, kMaxFine)
+    int levels;               // sampled levels: S with the hierarchy, else 1
+    // width-factor reweighting (Sec. 4.1 literal width): w_n += n_mid(n) lwf + hcoef * sum z^2
+    int wf_on;
+    double lwf, hcoef;
+    // effective potential tables: row d (level n = S - d), M entries each
+    int ring, ncol, M;
+    int len[SU_MAX_P];
+    double alpha;
+    const void *tables;       // device, levels * M elements of the kernel's precision
+    // Philox stream
+    uint64_t seed;
+    uint32_t instance;
+    // work decomposition: items = (block b, chunk r), chunk = kThreads * rounds samples
+    int64_t n_mc, sample0;
+    int64_t n_blocks;
+    int64_t items_per_block;
+    int64_t n_items;
+    int rounds;
+    // outputs
+    double *partial;          // device: per item and level, (M, S, Q, n)
+    double *w_out;            // device: per-sample mode when non-null, [sample][S]
+    int *flags;               // device: bit 0 = non-finite weight seen
+};
+
+// dynamic shared memory the sampler needs
+size_t sampler_smem_bytes(const SamplerParams &P, int precision);
+// max resident CTAs per SM for the sampler (after opting in to its smem)
+int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
+
+cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
+                           int64_t items_per_block, cudaStream_t st);
+cudaError_t launch_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
+                                int64_t n_samples, int n_calls, uint32_t *out, cudaStream_t st);
+
+}  // namespace su

@@ -1,0 +1,27 @@
+// One instantiation of the sampler kernel, selected at compile time:
+//   SU_PREC = 64 or 32 (double / float path and W_p), SU_RING = 0, 1, 2
+//   (z = x^2, x, sech^2(alpha x)).  The build compiles this file once per
+// pair so the six kernels compile in parallel.
+#include "sampler_impl.cuh"
+
+#ifndef SU_PREC
+#error "SU_PREC must be 64 or 32"
+#endif
+#ifndef SU_RING
+#error "SU_RING must be 0, 1 or 2"
+#endif
+
+#define SU_CAT2(a, b, c) a##b##_##c
+#define SU_CAT(a, b, c) SU_CAT2(a, b, c)
+
+namespace su {
+#if SU_PREC == 64
+using Real = double;
+#else
+using Real = float;
+#endif
+
+const void *SU_CAT(sampler_entry_f, SU_PREC, SU_RING)() {
+    return (const void *)sampler_kernel<Real, SU_RING>;
+}
+}  // namespace su

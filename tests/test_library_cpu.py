@@ -1,0 +1,148 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* the library builds, loads, and exports every entry point include/speedup.h
+  declares;
+* the host generator of W_p (double-double recursion + collapse) agrees with
+  the oracle's exact-rational c_{m,k} collapsed by hand (Eq. ansatz at fixed
+  eps), coefficient by coefficient, for every model family and p up to 18;
+* argument validation fails loudly with SU_EINVAL, and without a CUDA device
+  the compute entry points fail with SU_ECUDA instead of falling back.
+"""
+import math
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import paper_1105_0542_gb300 as su
+from oracle import effective_action as ea
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "speedup.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:su|speedup)_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = su.load()
+    declared = _declared_functions()
+    assert len(declared) >= 12
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(su.EXPORTS)
+
+
+def test_version_string():
+    v = su.su_version()
+    assert "sm_103a" in v
+
+
+def _exact_collapse(name, params, p, eps):
+    """P_ij from the oracle's exact c_{m,k}: W_p = sum_j xb^2j sum_i P_ij z^i."""
+    model = ea.make_model(name, [Fraction(v) for v in params])
+    c = ea.coefficients(model, p)
+    eps = Fraction(eps)
+    cols = {}
+    for (m, k), poly in c.items():
+        acc = cols.setdefault(k, [])
+        for i, v in enumerate(poly):
+            while len(acc) <= i:
+                acc.append(Fraction(0))
+            acc[i] += v * eps ** (m - k)
+    if model.kind == "t":
+        # t^(2i) = (1 - u)^i with u = 1/cosh^2(alpha x)
+        out = {}
+        for k, poly in cols.items():
+            u = [Fraction(0)] * (len(poly) // 2 + 2)
+            for i in range(0, len(poly), 2):
+                for r in range(i // 2 + 1):
+                    u[r] += poly[i] * math.comb(i // 2, r) * (-1) ** r
+            out[k] = u
+        return out, 2
+    even = all(v == 0 for poly in cols.values() for v in poly[1::2])
+    if even:
+        return {k: poly[0::2] for k, poly in cols.items()}, 0
+    return cols, 1
+
+
+@pytest.mark.parametrize("name,params,p,eps", [
+    ("aho", [1.0, 10.0], 18, 0.5),
+    ("aho", [1.0, 10.0], 18, 1.0 / 1024),
+    ("aho", [1.0, 1.0], 10, 0.25),
+    ("aho", [1.0, 10.0], 4, 1.0 / 16),
+    ("ho", [1.0], 12, 0.125),
+    ("dw", [5.0], 12, 5.0 / 64),
+    ("mpt", [3.0, 1.0], 12, 1.0 / 64),
+    ("mpt", [2.0, 0.7], 6, 0.3),
+    ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], 8, 0.1),
+    ("aho", [1.0, 10.0], 1, 1.0),
+])
+def test_generator_matches_oracle_exact_collapse(name, params, p, eps):
+    P, ncol, ring, lens = su.speedup_generate_coeffs(name, params, p, eps)
+    cols, ring_ref = _exact_collapse(name, params, p, eps)
+    assert ring == ring_ref
+    off = 0
+    for j in range(ncol):
+        ref = cols.get(j, [])
+        got = P[off:off + lens[j]]
+        off += lens[j]
+        # exact zeros come out as double-double residue far below the column's scale
+        floor = 1e-28 * max([abs(float(v)) for v in ref] + [1e-300])
+        for i in range(max(len(ref), len(got))):
+            r = float(ref[i]) if i < len(ref) else 0.0
+            g = float(got[i]) if i < len(got) else 0.0
+            assert abs(g - r) <= 2.3e-16 * abs(r) + floor, (j, i, g, r)
+    assert off == len(P)
+    # no coefficient of the exact collapse is missing from the shape
+    for j, ref in cols.items():
+        if any(ref):
+            assert j < ncol
+
+
+def test_generator_term_counts_of_the_anharmonic_oscillator():
+    counts = [len(su.speedup_generate_coeffs("aho", [1.0, 10.0], p, 0.1)[0]) for p in (4, 10, 12, 18)]
+    assert counts == [8, 21, 27, 48]
+
+
+@pytest.mark.parametrize("args,kw", [
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 0, 4, 100, 1), {}),        # p = 0
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 19, 4, 100, 1), {}),       # p = 19
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 11, 100, 1), {}),       # s = 11
+    (("aho", [1.0, 1.0], 0.0, 1.0, 0.0, 4, 4, 100, 1), {}),        # T = 0
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 0, 1), {}),          # n_mc = 0
+    (("aho", [1.0, 1.0], float("nan"), 1.0, 1.0, 4, 4, 10, 1), {}),
+    (("aho", [1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {}),              # wrong n_params
+    (("mpt", [3.0, 0.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {}),         # alpha = 0
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"n_blocks": 0}),
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"width_factor": -1.0}),
+    ((9, [1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {}),                  # unknown model
+])
+def test_invalid_arguments_are_rejected(args, kw):
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude(*args, **kw)
+    assert e.value.code == -1
+
+
+def test_no_device_means_an_error_not_a_fallback():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 1000, 1234)
+    assert e.value.code == -3
+
+
+def test_level_zero_needs_no_sampling_but_still_a_plan():
+    # s = 0 is analytic; the plan still checks for a device, so without one it fails
+    import torch
+    if torch.cuda.is_available():
+        r = su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 0, 10, 1)
+        assert r[0]["err"] == 0.0
+    else:
+        with pytest.raises(su.SpeedupError):
+            su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 0, 10, 1)
