@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API pass")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", choices=["fp64", "fp32"], default=None,
+                    help="profiling case: one warm-up and one timed execute of a small plan "
+                         "(level --profile-p of the sweep, s = 10, --profile-n samples); no JSON line")
+    ap.add_argument("--profile-p", type=int, default=10)
+    ap.add_argument("--profile-n", type=int, default=200_000)
     return ap.parse_args()
 
 
@@ -295,11 +300,15 @@ def run_ours(args):
 
     fp64_ms = per["fp64"]["ms"]
     achieved = per["fp64"]["flops"] / (fp64_ms / 1e3) / 1e12
+    fma64 = su.su_fma_peak("fp64")
+    fma32 = su.su_fma_peak("fp32")
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "kernel": "sampler_kernel<double, RING_EVEN> (+ its combine)",
-                "note": "algorithmic flops 2*M_p+8 per slice-action (W_p only); peak nominal FP64, "
-                        "not measured (MEASURED_PEAKS.json has none)"}
+                "measured_fma_peak_tflops": {"fp64": 2 * fma64 / 1e12, "fp32": 2 * fma32 / 1e12},
+                "frac_of_measured_fp64": achieved / (2 * fma64 / 1e12),
+                "note": "algorithmic flops 2*M_p+8 per slice-action (W_p only); peak = nominal FP64 "
+                        "(MEASURED_PEAKS.json has no FP64 figure); measured_fma_peak from su_fma_peak"}
     cpu = None
     if not args.no_cpu:
         sa, t, used, desc = oracle_sweep(args.steps, 0, CPU_BUDGET_S)
@@ -326,8 +335,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    import torch
+
+    import paper_1105_0542_gb300 as su
+    inst = workloads.config2(args.profile_p)
+    pl = su.Plan(inst.model, inst.params, inst.a, inst.b, inst.T, args.profile_p, inst.s, args.profile_n,
+                 inst.seed, precision=args.profile, n_blocks=inst.n_blocks)
+    t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device="cuda")
+    sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        pl.su_plan_execute(t, sc)
+    torch.cuda.synchronize()
+    res = pl.su_plan_finalize(t.cpu().numpy(), sc)
+    print(f"profile case {args.profile} p={args.profile_p} n={args.profile_n}: "
+          f"A_1024 = {res[inst.s]['amp']:.10g} +- {res[inst.s]['err']:.3g}")
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -217,6 +217,15 @@ int speedup_logweights(int model, const double *params, int n_params,
 int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
                          int64_t n_samples, int n_calls, uint32_t *d_out, void *stream);
 
+/*
+ * su_fma_peak -- measured multiply-add throughput of the current device in
+ * SU_FP64 or SU_FP32 (independent FMA chains on every SM, CUDA-event timed,
+ * best of three launches): *fma_per_s multiply-adds per second (x2 = flop/s).
+ * A measurement utility for the ALU roofline of the sampler; the paper has no
+ * counterpart.  Synchronous; allocates a small device buffer internally.
+ */
+int su_fma_peak(int precision, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

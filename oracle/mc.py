@@ -74,6 +74,9 @@ def lib():
             L.oracle_logweights.argtypes = [ctypes.POINTER(_WP), d, d, d, i32, u64, u32, i64, i64,
                                              i32, d, i32, pd]
             L.oracle_logweights.restype = i32
+            L.oracle_logweights_abs.argtypes = [ctypes.POINTER(_WP), d, d, d, i32, u64, u32, i64, i64,
+                                                i32, d, pd]
+            L.oracle_logweights_abs.restype = None
             _lib = L
     return _lib
 
@@ -150,6 +153,15 @@ class Oracle:
             used = lib().oracle_logweights(ctypes.byref(self._wp), a, b, T, s, seed, instance,
                                            sample0, nsamples, bits, wf, threads, _dptr(w))
         return w, used
+
+    def logweights_abs(self, a, b, T, s, seed, nsamples, sample0=0, instance=0, bits=53, wf=1.0):
+        """(nsamples, s) condition scales eps_n sum_k sum_terms |term| of the same
+        samples: the size of the numbers each w_n is summed from."""
+        out = np.empty((max(nsamples, 0), max(s, 0)), dtype=np.float64)
+        if s >= 1 and nsamples > 0:
+            lib().oracle_logweights_abs(ctypes.byref(self._wp), a, b, T, s, seed, instance, sample0,
+                                        nsamples, bits, wf, _dptr(out))
+        return out
 
     def amplitude(self, a, b, T, s, n_mc, seed, n_blocks=64, instance=0, bits=53, wf=1.0,
                   threads=1):

@@ -175,6 +175,26 @@ void oracle_path(uint64_t seed, uint32_t instance, uint64_t sample, int s,
     }
 }
 
+/* sum over the (m,k) terms of |c_{m,k}(z) eps^(m-k) xb^(2k)|: the size of the
+   numbers W_p is summed from, which bounds the rounding error of any order of
+   evaluating it (a condition measure, not part of the estimate) */
+double oracle_Wp_abs(const oracle_wp *W, double x, double xb, double eps)
+{
+    double z = (W->ring == 0) ? x : tanh(W->alpha * x);
+    double tot = 0.0;
+    for (int m = 0; m < W->p; ++m)
+        for (int k = 0; k <= m; ++k) {
+            int id = m * W->p + k;
+            const double *c = W->coef + W->off[id];
+            double zp = 1.0;
+            for (int i = 0; i < W->len[id]; ++i) {
+                tot += fabs(c[i] * zp) * pow(eps, (double)(m - k)) * pow(xb, (double)(2 * k));
+                zp *= z;
+            }
+        }
+    return tot;
+}
+
 /* log-weight of level n (1..s) for a given path */
 static double level_logweight(const oracle_wp *W, const double *q, int s, int n, double T)
 {
@@ -192,6 +212,35 @@ static double level_logweight(const oracle_wp *W, const double *q, int s, int n,
 double oracle_level0(const oracle_wp *W, double a, double b, double T)
 {
     return -T * oracle_Wp(W, 0.5 * (a + b), 0.5 * (b - a), T);
+}
+
+/* eps_n sum_k |W_p terms| on the level-n subpath: the condition scale of w_n */
+static double level_abs(const oracle_wp *W, const double *q, int s, int n, double T)
+{
+    double eps = T / (double)((int64_t)1 << n);
+    int64_t st = (int64_t)1 << (s - n);
+    double sum = 0.0;
+    for (int64_t k = 0; k < ((int64_t)1 << n); ++k) {
+        double ql = q[k * st], qr = q[(k + 1) * st];
+        sum += oracle_Wp_abs(W, 0.5 * (ql + qr), 0.5 * (qr - ql), eps);
+    }
+    return eps * sum;
+}
+
+/* condition scales a[(i - sample0) * s + (n - 1)] of the same samples as
+   oracle_logweights (plain loop, one thread) */
+void oracle_logweights_abs(const oracle_wp *W, double a, double b, double T, int s,
+                           uint64_t seed, uint32_t instance, int64_t sample0, int64_t nsamples,
+                           int bits, double wf, double *out)
+{
+    if (s < 1 || nsamples <= 0) return;
+    int64_t N = (int64_t)1 << s;
+    double *q = (double *)malloc(sizeof(double) * (size_t)(N + 1));
+    for (int64_t i = 0; i < nsamples; ++i) {
+        oracle_path(seed, instance, (uint64_t)(sample0 + i), s, a, b, T, bits, wf, q, NULL);
+        for (int n = 1; n <= s; ++n) out[i * s + (n - 1)] = level_abs(W, q, s, n, T);
+    }
+    free(q);
 }
 
 /*

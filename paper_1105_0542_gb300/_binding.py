@@ -23,6 +23,7 @@ EXPORTS = [
     "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
     "speedup_generate_coeffs", "su_plan_create", "su_plan_destroy", "su_plan_sizes",
     "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
+    "su_fma_peak",
 ]
 
 
@@ -87,6 +88,7 @@ def load(build_if_missing=True):
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
+    L.su_fma_peak.argtypes = [i32, pd]
     for name in EXPORTS:
         if name not in ("su_options_default", "su_last_error"):
             getattr(L, name).restype = i32
@@ -187,6 +189,14 @@ def speedup_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, o
 def speedup_philox_words(seed, instance, sample0, n_samples, n_calls, out, stream=None):
     _check(load().speedup_philox_words(int(seed), int(instance), int(sample0), int(n_samples),
                                        int(n_calls), _ptr(out), _stream(stream)))
+
+
+def su_fma_peak(precision="fp64"):
+    """Measured multiply-adds per second of the current device."""
+    v = ctypes.c_double(0)
+    _check(load().su_fma_peak(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                              ctypes.byref(v)))
+    return v.value
 
 
 class Plan:

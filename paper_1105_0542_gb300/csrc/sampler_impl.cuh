@@ -124,6 +124,77 @@ __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const 
     return acc;
 }
 
+// Sum of -eps W_p over NS slices of one level of a segment, the slices taken
+// between the points q[k STR] and q[(k+1) STR].  Slices are evaluated in
+// batches of B side by side: each table entry is loaded once per batch (a
+// broadcast shared-memory read) and feeds B independent multiply-add chains.
+template <typename R>
+struct Batch {
+    static constexpr int B = sizeof(R) == 8 ? 4 : 8;
+};
+
+template <typename R, int RING, int NS, int STR, int NQ>
+__device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab,
+                                       const SamplerParams &P, R alpha) {
+    constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
+    R total = 0;
+#pragma unroll
+    for (int k0 = 0; k0 < NS; k0 += B) {
+        R Z[B], Y[B], acc[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const R ql = q[(k0 + b) * STR], qr = q[(k0 + b + 1) * STR];
+            const R vs = qr - ql;
+            Y[b] = vs * vs;
+            Z[b] = ring_var<R, RING>(ql + qr, alpha);
+        }
+        int off = P.M;
+        {   // last column starts the outer Horner in x-bar^2
+            const int L = P.len[P.ncol - 1];
+            off -= L;
+            const R c = tab[off + L - 1];
+#pragma unroll
+            for (int b = 0; b < B; ++b) acc[b] = c;
+            for (int i = L - 2; i >= 0; --i) {
+                const R ci = tab[off + i];
+#pragma unroll
+                for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+            }
+        }
+        for (int j = P.ncol - 2; j >= 0; --j) {
+            const int L = P.len[j];
+            off -= L;
+            R h[B];
+            const R c = tab[off + L - 1];
+#pragma unroll
+            for (int b = 0; b < B; ++b) h[b] = c;
+            for (int i = L - 2; i >= 0; --i) {
+                const R ci = tab[off + i];
+#pragma unroll
+                for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) total += acc[b];
+    }
+    return total;
+}
+
+// levels d = D..F of a segment (level n = S - d uses every 2^d-th point)
+template <typename R, int RING, int F, int D>
+__device__ __forceinline__ void segment_levels(R (&acc)[F + 1], const R (&q)[(1 << F) + 1],
+                                               const R *__restrict__ tab, const SamplerParams &P,
+                                               R alpha, int S) {
+    if constexpr (D <= F) {
+        if (D < S) {
+            acc[D] += level_sum<R, RING, ((1 << F) >> D), (1 << D)>(q, tab + D * P.M, P, alpha);
+            segment_levels<R, RING, F, D + 1>(acc, q, tab, P, alpha, S);
+        }
+    }
+}
+
 // --------------------------------------------------------------- a path
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
@@ -218,19 +289,9 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__r
                 q[idx] = fma(sg, z, (R)0.5 * (q[idx - h] + q[idx + h]));
             }
         }
-        // top level: every slice of the segment
-#pragma unroll
-        for (int k = 0; k < NF; ++k) acc[0] += slice<R, RING>(q[k], q[k + 1], tab, P, alpha);
-        if (hier) {
-#pragma unroll
-            for (int d = 1; d <= F; ++d) {
-                if (d < S) {
-#pragma unroll
-                    for (int k = 0; k < (NF >> d); ++k)
-                        acc[d] += slice<R, RING>(q[k << d], q[(k + 1) << d], tab + d * M, P, alpha);
-                }
-            }
-        }
+        // top level: every slice of the segment; then the coarser levels
+        acc[0] += level_sum<R, RING, NF, 1>(q, tab, P, alpha);
+        if (hier) segment_levels<R, RING, F, 1>(acc, q, tab, P, alpha, S);
     }
 
     // ---- width-factor weight, cumulative over levels 1..n (stored in zz)
