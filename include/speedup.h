@@ -128,12 +128,12 @@ int speedup_amplitude(int model, const double *params, int n_params,
  *
  *   W_p(x, xb; eps) = sum_{j=0}^{J} xb^(2j) sum_{i=0}^{D_j} P_{ij} z^i,
  *   z = x^2 (SU_HO, SU_AHO, SU_DW and even SU_POLY), z = x (other SU_POLY),
- *   z = 1/cosh^2(alpha x) (SU_MPT).
+ *   z = tanh^2(alpha x) (SU_MPT).
  *
  *   table    : host, capacity doubles; receives P, column j after column j-1,
  *              i ascending within a column.
  *   shape    : host, SU_MAX_P + 2 ints; shape[0] = J + 1 columns, shape[1] =
- *              the ring (0: z = x^2, 1: z = x, 2: z = 1/cosh^2(alpha x)),
+ *              the ring (0: z = x^2, 1: z = x, 2: z = tanh^2(alpha x)),
  *              shape[2 + j] = D_j + 1 entries of column j.
  *   n_terms  : host, receives the number of entries written.
  * Returns SU_ENOTSUP if capacity is too small (n_terms still says how many).
@@ -216,6 +216,17 @@ int speedup_logweights(int model, const double *params, int n_params,
  */
 int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
                          int64_t n_samples, int n_calls, uint32_t *d_out, void *stream);
+
+/*
+ * speedup_normals -- the Gaussian normals the sampler draws (Sec. 4.1
+ * Box-Muller, both branches, from the Philox stream above): normal j of
+ * sample i is branch (j & 1) of call j >> 1, with 53-bit uniforms for SU_FP64
+ * and 24-bit uniforms (float arithmetic) for SU_FP32.
+ *   d_out[(i - sample0) * n_normals + j]   (device, double).
+ * Asynchronous on stream.
+ */
+int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                    int n_normals, int precision, double *d_out, void *stream);
 
 /*
  * su_fma_peak -- measured multiply-add throughput of the current device in

@@ -8,5 +8,6 @@ built library or a CUDA device the entry points raise.
 from ._binding import (  # noqa: F401
     EXPORTS, MODELS, PRECISIONS, Plan, SpeedupError, library_path, load, options,
     speedup_amplitude, speedup_generate_coeffs, speedup_logweights, speedup_philox_words, su_fma_peak,
+    speedup_normals,
     su_last_error, su_version,
 )

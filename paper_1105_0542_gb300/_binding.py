@@ -23,7 +23,7 @@ EXPORTS = [
     "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
     "speedup_generate_coeffs", "su_plan_create", "su_plan_destroy", "su_plan_sizes",
     "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
-    "su_fma_peak",
+    "su_fma_peak", "speedup_normals",
 ]
 
 
@@ -89,6 +89,7 @@ def load(build_if_missing=True):
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
     L.su_fma_peak.argtypes = [i32, pd]
+    L.speedup_normals.argtypes = [u64, u32, i64, i64, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("su_options_default", "su_last_error"):
             getattr(L, name).restype = i32
@@ -184,6 +185,13 @@ def speedup_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, o
     o = options(**kw)
     _check(load().speedup_logweights(_model(model), pr, npar, a, b, T, p, s, int(sample0), int(n_samples),
                                      int(seed), ctypes.byref(o), _ptr(out)))
+
+
+def speedup_normals(seed, instance, sample0, n_samples, n_normals, out, precision="fp64", stream=None):
+    """The sampler's normals into the device buffer out (n_samples x n_normals doubles)."""
+    _check(load().speedup_normals(int(seed), int(instance), int(sample0), int(n_samples), int(n_normals),
+                                  PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                                  _ptr(out), _stream(stream)))
 
 
 def speedup_philox_words(seed, instance, sample0, n_samples, n_calls, out, stream=None):

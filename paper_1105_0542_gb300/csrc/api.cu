@@ -467,6 +467,16 @@ int speedup_logweights(int model, const double *params, int n_params, double a, 
     return SU_OK;
 }
 
+int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                    int n_normals, int precision, double *d_out, void *stream) {
+    if (!d_out || sample0 < 0 || n_samples < 0 || n_normals < 0) return fail(SU_EINVAL, "bad arguments");
+    if (precision != SU_FP64 && precision != SU_FP32) return fail(SU_EINVAL, "unknown precision");
+    CU(su::launch_normals(seed, instance, sample0, n_samples, n_normals, precision, d_out,
+                          (cudaStream_t)stream),
+       "normals launch");
+    return SU_OK;
+}
+
 int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
                          int n_calls, uint32_t *d_out, void *stream) {
     if (!d_out || sample0 < 0 || n_samples < 0 || n_calls < 0) return fail(SU_EINVAL, "bad arguments");

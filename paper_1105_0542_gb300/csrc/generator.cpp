@@ -10,12 +10,17 @@
 //
 //  * x itself for polynomial potentials (the model-specific mode of Sec. 3.3:
 //    derivatives taken explicitly while iterating);
-//  * u = 1/cosh^2(alpha x) for V = -lambda u (Eq. 1D-MPT).  With
-//    t = tanh(alpha x), du/dx = -2 alpha u t and t^2 = 1 - u, so
-//      f'(x) g'(x) = 4 alpha^2 u^2 (1-u) f_u g_u,
-//      f''(x)      = 4 alpha^2 u^2 (1-u) f_uu + (4 alpha^2 u - 6 alpha^2 u^2) f_u,
-//    and every c_{m,k} stays a polynomial in u (the content of
-//    Eq. 1D-MPTansatz: tanh^(2l) / cosh^(2m-2l+2) = (1-u)^l u^(m-l+1)).
+//  * s = tanh^2(alpha x) for V = -lambda/cosh^2(alpha x) = -lambda (1 - s)
+//    (Eq. 1D-MPT).  With t = tanh(alpha x), dt/dx = alpha (1 - t^2), so
+//    ds/dx = 2 alpha t (1 - s), (ds/dx)^2 = 4 alpha^2 s (1-s)^2 and
+//    d2s/dx2 = 2 alpha^2 (1-s)(1-3s):
+//      f'(x) g'(x) = 4 alpha^2 s (1-s)^2 f_s g_s,
+//      f''(x)      = 4 alpha^2 s (1-s)^2 f_ss + 2 alpha^2 (1-s)(1-3s) f_s,
+//    and every c_{m,k} stays a polynomial in s (the content of
+//    Eq. 1D-MPTansatz: tanh^(2l) / cosh^(2m-2l+2) = s^l (1-s)^(m-l+1)).
+//    The basis s^i is chosen over powers of 1/cosh^2 = 1 - s because the
+//    latter alternate in sign with binomial growth and lose digits in
+//    single precision at large eps.
 //
 // Coefficients are double-double numbers (a + b with |b| <= ulp(a)/2, using
 // Knuth's two-sum and the FMA-exact product), so that the collapse of many
@@ -120,19 +125,19 @@ Poly pmul_small(const Poly &a, const Poly &m) { return pmul(a, m); }
 
 // The ring: how x-derivatives act on the ring variable.
 struct RingOps {
-    bool sech2 = false;
-    Poly w;   // 4 alpha^2 u^2 (1 - u): the factor of products of first derivatives
-    Poly g;   // 4 alpha^2 u - 6 alpha^2 u^2: the factor of f_u in f''
-    // first derivative in the ring variable (x or u)
+    bool tanh2 = false;
+    Poly w;   // 4 alpha^2 s (1-s)^2: the factor of products of first derivatives
+    Poly g;   // 2 alpha^2 (1-s)(1-3s): the factor of f_s in f''
+    // first derivative in the ring variable (x or s)
     Poly d1(const Poly &f) const { return pder(f); }
     // x-second derivative
     Poly d2(const Poly &f) const {
-        if (!sech2) return pder(pder(f));
+        if (!tanh2) return pder(pder(f));
         return padd(pmul_small(pder(pder(f)), w), pmul_small(pder(f), g));
     }
-    // product of two x-first-derivatives given the ring derivatives fu, gu,
-    // summed beforehand: x-derivative products are w * (sum fu gu) in the u ring
-    Poly finish_products(const Poly &s) const { return sech2 ? pmul_small(s, w) : s; }
+    // sum of products of two x-first-derivatives, given the sum of the
+    // products of their ring derivatives
+    Poly finish_products(const Poly &s) const { return tanh2 ? pmul_small(s, w) : s; }
 };
 
 }  // namespace
@@ -167,12 +172,13 @@ int build_effective(int model, const double *params, int n_params, int p, Effect
             if (n_params != 2) return bad("SU_MPT takes 2 parameters (lambda, alpha)");
             if (params[1] == 0.0) return bad("SU_MPT needs alpha != 0");
             alpha = params[1];
-            V = {dd(0), dd(-params[0])};
+            V = {dd(-params[0]), dd(params[0])};      // -lambda (1 - s)
             DD a2 = two_prod(alpha, alpha);
-            DD a4 = mul_d(a2, 4.0), a6 = mul_d(a2, 6.0);
-            R.sech2 = true;
-            R.w = {dd(0), dd(0), a4, neg(a4)};
-            R.g = {dd(0), a4, neg(a6)};
+            DD a4 = mul_d(a2, 4.0), a2x2 = mul_d(a2, 2.0);
+            R.tanh2 = true;
+            // 4 a^2 s (1 - 2s + s^2) and 2 a^2 (1 - 4s + 3s^2)
+            R.w = {dd(0), a4, mul_d(a4, -2.0), a4};
+            R.g = {a2x2, mul_d(a2x2, -4.0), mul_d(a2x2, 3.0)};
             break;
         }
         case SU_POLY:
@@ -215,13 +221,13 @@ int build_effective(int model, const double *params, int n_params, int p, Effect
     }
 
     // shape of the collapsed polynomial
-    bool even = !R.sech2;
+    bool even = !R.tanh2;
     for (int m = 0; m < p && even; ++m)
         for (int k = 0; k <= m && even; ++k)
             for (size_t i = 1; i < c[m][k].size(); i += 2)
                 if (!is_zero(c[m][k][i])) even = false;
     Shape S;
-    S.ring = R.sech2 ? RING_SECH2 : (even ? RING_EVEN : RING_X);
+    S.ring = R.tanh2 ? RING_TANH2 : (even ? RING_EVEN : RING_X);
     S.alpha = alpha;
     int ncol = 0;
     std::vector<int> len(p, 0);
@@ -325,7 +331,7 @@ double wp_host(const Effective &E, double x, double xb, double eps) {
     const Shape &S = E.shape;
     double z = S.ring == RING_EVEN ? x * x
                : S.ring == RING_X  ? x
-                                   : 1.0 / (std::cosh(S.alpha * x) * std::cosh(S.alpha * x));
+                                   : std::tanh(S.alpha * x) * std::tanh(S.alpha * x);
     DD y = two_prod(xb, xb);
     DD acc = dd(0);
     int off = S.M;

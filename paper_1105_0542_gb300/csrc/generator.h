@@ -16,7 +16,7 @@ namespace su {
 enum Ring : int {
     RING_EVEN = 0,   // z = x^2            (even polynomial potentials)
     RING_X = 1,      // z = x              (general polynomial potentials)
-    RING_SECH2 = 2,  // z = 1/cosh^2(alpha x)  (modified Poeschl-Teller)
+    RING_TANH2 = 2,  // z = tanh^2(alpha x)  (modified Poeschl-Teller)
 };
 
 struct Shape {
@@ -24,14 +24,14 @@ struct Shape {
     int ncol = 0;                 // J + 1 columns (powers xb^(2j))
     std::vector<int> len;         // entries of column j (D_j + 1)
     int M = 0;                    // total entries
-    double alpha = 0;             // for RING_SECH2
+    double alpha = 0;             // for RING_TANH2
 };
 
 struct Effective {
     int p = 0;
     Shape shape;
     // c[m][k] as polynomial in the ring variable (x for RING_EVEN/RING_X,
-    // u = sech^2 for RING_SECH2), stored as (hi, lo) pairs
+    // s = tanh^2(alpha x) for RING_TANH2), stored as (hi, lo) pairs
     std::vector<std::vector<std::vector<double>>> hi, lo;
 };
 
@@ -47,7 +47,7 @@ void collapse(const Effective &E, double eps, std::vector<double> &P);
 // The sampler's table for one level: entry (i, j) = -eps P_ij scaled to the
 // kernel's variables us = q_k + q_{k+1} and vs = q_{k+1} - q_k, so that the
 // per-slice contribution -eps W_p is sum_j (vs^2)^j sum_i T_ij Z^i with
-// Z = us^2 (RING_EVEN), us (RING_X) or sech^2(alpha us / 2) (RING_SECH2).
+// Z = us^2 (RING_EVEN), us (RING_X) or tanh^2(alpha us / 2) (RING_TANH2).
 // Also returns the largest ratio sum|terms| / |sum| met while collapsing (a
 // cancellation measure of the double-double sums).
 double kernel_table(const Effective &E, double eps, std::vector<double> &T);

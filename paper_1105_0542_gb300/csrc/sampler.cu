@@ -64,6 +64,32 @@ __global__ void philox_words_kernel(uint64_t seed, uint32_t inst, int64_t sample
     reinterpret_cast<uint4 *>(out)[id] = w;
 }
 
+// ------------------------------------------------ the sampler's normals
+// out[i * n + j] = normal j of sample sample0 + i, as the sampler forms it
+template <typename R>
+__global__ void __launch_bounds__(128) normals_kernel(uint64_t seed, uint32_t inst, int64_t sample0,
+                                                      int64_t ns, int n, double *out) {
+    __shared__ BMTables bm;
+    if constexpr (sizeof(R) == 8) bm_tables_init(&bm, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int calls = (n + 1) / 2;
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= ns * calls) return;
+    const int64_t i = id / calls;
+    const uint32_t t = (uint32_t)(id - i * calls);
+    Stream<R> st;
+    const uint64_t smp = (uint64_t)(sample0 + i);
+    st.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    st.inst = inst;
+    st.slo = (uint32_t)smp;
+    st.shi = (uint32_t)(smp >> 32);
+    st.bm = &bm;
+    R z0, z1;
+    st.pair(t, z0, z1);
+    out[i * n + 2 * t] = (double)z0;
+    if (2 * (int)t + 1 < n) out[i * n + 2 * t + 1] = (double)z1;
+}
+
 const void *pick(const SamplerParams &P, int precision) {
     if (precision == SU_FP32)
         return P.ring == RING_EVEN ? sampler_entry_f32_0() : P.ring == RING_X ? sampler_entry_f32_1() : sampler_entry_f32_2();
@@ -81,6 +107,7 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
     if (P.wf_on) off += sizeof(double) * (size_t)(P.S + 1) * kThreads;
+    if (precision == SU_FP64) off += sizeof(BMTables);
     return off;
 }
 
@@ -119,6 +146,19 @@ cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_bloc
     const int th = 128;
     combine_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(partial, tuples, n_blocks, levels,
                                                                items_per_block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                           int n_normals, int precision, double *out, cudaStream_t st) {
+    const int64_t n = n_samples * ((n_normals + 1) / 2);
+    if (n == 0) return cudaSuccess;
+    const int th = 128;
+    const unsigned grid = (unsigned)((n + th - 1) / th);
+    if (precision == SU_FP32)
+        normals_kernel<float><<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
+    else
+        normals_kernel<double><<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size
                            cudaStream_t st);
 cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
                            int64_t items_per_block, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
+                           int n_normals, int precision, double *out, cudaStream_t st);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
                                 int64_t n_samples, int n_calls, uint32_t *out, cudaStream_t st);
 

@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "boxmuller.cuh"
 #include "generator.h"
 #include "sampler.h"
 
@@ -51,24 +52,20 @@ struct Normal;
 
 template <>
 struct Normal<double> {
-    // 53-bit uniforms ((w0 2^21 + w1 >> 11) + 1/2) 2^-53 from (w0,w1) and (w2,w3)
-    static __device__ __forceinline__ void pair(uint4 w, double &z0, double &z1) {
+    // 53-bit uniforms ((w0 2^21 + w1 >> 11) + 1/2) 2^-53 from (w0,w1) and (w2,w3),
+    // through the table-driven routines of boxmuller.cuh
+    static __device__ __forceinline__ void pair(uint4 w, const BMTables *t, double &z0, double &z1) {
         const uint64_t a = ((uint64_t)w.x << 21) | (w.y >> 11);
         const uint64_t b = ((uint64_t)w.z << 21) | (w.w >> 11);
         const double u1 = ((double)a + 0.5) * 0x1p-53;
-        const double u2 = ((double)b + 0.5) * 0x1p-53;
-        const double r = sqrt(-2.0 * log(u1));
-        double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);
-        z0 = r * cs;
-        z1 = r * sn;
+        bm_rotate(bm_sqrt(bm_minus2log(u1, t)), b, t, z0, z1);
     }
 };
 
 template <>
 struct Normal<float> {
     // 24-bit uniforms ((w >> 8) + 1/2) 2^-24 from w0 and w2
-    static __device__ __forceinline__ void pair(uint4 w, float &z0, float &z1) {
+    static __device__ __forceinline__ void pair(uint4 w, const BMTables *, float &z0, float &z1) {
         const float u1 = ((float)(w.x >> 8) + 0.5f) * 0x1p-24f;
         const float u2 = ((float)(w.z >> 8) + 0.5f) * 0x1p-24f;
         const float r = sqrtf(-2.0f * logf(u1));
@@ -83,8 +80,9 @@ template <typename R>
 struct Stream {
     uint2 key;
     uint32_t inst, slo, shi;
+    const BMTables *bm;   // shared-memory node tables (double path)
     __device__ __forceinline__ void pair(uint32_t call, R &z0, R &z1) const {
-        Normal<R>::pair(philox4x32_10(make_uint4(call, inst, slo, shi), key), z0, z1);
+        Normal<R>::pair(philox4x32_10(make_uint4(call, inst, slo, shi), key), bm, z0, z1);
     }
 };
 
@@ -96,10 +94,11 @@ __device__ __forceinline__ R ring_var(R us, R alpha) {
     } else if constexpr (RING == RING_X) {
         return us;
     } else {
-        // 1/cosh^2(alpha us / 2) = 4 e / (1 + e)^2, e = exp(-|alpha us|)
-        const R e = exp(-fabs(alpha * us));
-        const R d = (R)1 + e;
-        return (R)4 * e / (d * d);
+        // tanh^2(alpha us / 2): tanh(y/2) = -em / (2 + em), em = expm1(-|y|),
+        // accurate also where tanh is small
+        const R em = expm1(-fabs(alpha * us));
+        const R t = -em / ((R)2 + em);
+        return t * t;
     }
 }
 
@@ -354,18 +353,23 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
     off += sizeof(R) * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
     double *zz = reinterpret_cast<double *>(smem_raw + off) + tid;
+    off += P.wf_on ? sizeof(double) * (size_t)(P.S + 1) * kThreads : 0;
+    BMTables *bm_smem = reinterpret_cast<BMTables *>(smem_raw + off);   // double path only
 
-    // stage the coefficient tables of every sampled level
+    // stage the coefficient tables of every sampled level (and the
+    // Box-Muller node tables of the double path)
     {
         const R *g = reinterpret_cast<const R *>(P.tables);
         const int n = P.S * P.M;
         for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
+        if constexpr (sizeof(R) == 8) bm_tables_init(bm_smem, tid, kThreads);
     }
     __syncthreads();
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.inst = P.instance;
+    st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
 
     const int warp = tid >> 5, lane = tid & 31;
     for (int64_t item = blockIdx.x; item < P.n_items; item += gridDim.x) {

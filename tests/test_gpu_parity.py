@@ -76,6 +76,21 @@ def test_philox_words_bit_exact(seed, inst, sample0):
             assert list(got[i, t]) == mc.philox_words(seed, inst, sample0 + i, t), (i, t)
 
 
+@pytest.mark.parametrize("prec,bits,tol", [("fp64", 53, 1e-15), ("fp32", 24, 1e-6)])
+def test_normals_match_oracle_box_muller(prec, bits, tol):
+    """The sampler's table-driven (double) and float Box-Muller against the
+    oracle's libm Box-Muller on the same Philox words: |dz| <= tol (1 + |z|)
+    (the oracle's own 2 pi u2 rounding is ~1e-16 |theta|)."""
+    ns, nn = 4000, 63
+    out = torch.zeros((ns, nn), dtype=torch.float64, device="cuda")
+    su.speedup_normals(77, 3, 123456789, ns, nn, out, precision=prec)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = np.stack([mc.normals(77, 3, 123456789 + i, nn, bits) for i in range(ns)])
+    assert float(np.max(np.abs(got - ref) / (1 + np.abs(ref)))) <= tol
+    assert np.isfinite(got).all()
+
+
 CASES = [
     # model, params, a, b, T, p, s, n, seed, sample0
     ("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 1000, 1234, 0),
@@ -249,8 +264,10 @@ def test_convergence_sweep_full_size_against_diagonalisation(prec):
 
 
 def test_fp32_and_fp64_means_agree():
+    # T = 5 with p = 12: levels n <= 3 (eps >= 5/8) lie outside the expansion's
+    # radius of convergence (their weights overflow); compare the sliced ones
     r64 = su.speedup_amplitude("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1_000_000, 7, precision="fp64")
     r32 = su.speedup_amplitude("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1_000_000, 8, precision="fp32")
-    for lev in range(1, 7):
+    for lev in range(4, 7):
         s = math.hypot(r64[lev]["err"], r32[lev]["err"])
         assert abs(r64[lev]["amp"] - r32[lev]["amp"]) <= 4 * s, lev

@@ -55,15 +55,8 @@ def _exact_collapse(name, params, p, eps):
                 acc.append(Fraction(0))
             acc[i] += v * eps ** (m - k)
     if model.kind == "t":
-        # t^(2i) = (1 - u)^i with u = 1/cosh^2(alpha x)
-        out = {}
-        for k, poly in cols.items():
-            u = [Fraction(0)] * (len(poly) // 2 + 2)
-            for i in range(0, len(poly), 2):
-                for r in range(i // 2 + 1):
-                    u[r] += poly[i] * math.comb(i // 2, r) * (-1) ** r
-            out[k] = u
-        return out, 2
+        # the library's ring variable is t^2 = tanh^2(alpha x): keep even powers
+        return {k: poly[0::2] for k, poly in cols.items()}, 2
     even = all(v == 0 for poly in cols.values() for v in poly[1::2])
     if even:
         return {k: poly[0::2] for k, poly in cols.items()}, 0
