@@ -175,11 +175,16 @@ def block_bounds(n_mc, n_blocks):
     return [(b * n_mc // n_blocks, (b + 1) * n_mc // n_blocks) for b in range(n_blocks)]
 
 
+def _exp(x):
+    """exp that returns inf instead of raising where the result overflows"""
+    return math.exp(x) if x < 709.78 else float("inf")
+
+
 def estimate(w, w0, a, b, T, n_blocks):
     """Per-level results from per-sample log-weights w (n_mc, s)."""
     n_mc, s = w.shape
     laf = log_A_free(a, b, T)
-    out = [dict(n=0, amp=math.exp(laf + w0), log_amp=laf + w0, err=0.0, rel_err=0.0,
+    out = [dict(n=0, amp=_exp(laf + w0), log_amp=laf + w0, err=0.0, rel_err=0.0,
                 err_naive=0.0, ess=float(n_mc), max_share=1.0 / max(n_mc, 1))]
     nb = min(n_blocks, n_mc)
     for lev in range(1, s + 1):
@@ -193,7 +198,7 @@ def estimate(w, w0, a, b, T, n_blocks):
         err_b = float(np.std(mu, ddof=1) / math.sqrt(nb)) if nb > 1 else float("nan")
         var = max(Q / n_mc - mean * mean, 0.0)
         err_n = math.sqrt(var / (n_mc - 1)) if n_mc > 1 else float("nan")
-        scale = math.exp(laf + M)
+        scale = _exp(laf + M)
         out.append(dict(n=lev, amp=scale * mean, log_amp=laf + M + math.log(mean),
                         err=scale * err_b, rel_err=err_b / mean, err_naive=scale * err_n,
                         ess=S * S / Q, max_share=1.0 / S))
