@@ -142,6 +142,55 @@ int speedup_generate_coeffs(int model, const double *params, int n_params, int p
                             double eps, double *table, int capacity, int *shape,
                             int *n_terms);
 
+/* ---- many instances in one persistent launch ------------------------------ */
+
+/* one amplitude A_N^(p)(a,b;T) with N = 2^s of a batch */
+typedef struct {
+    double a, b, T;
+    int s;               /* 0..SU_MAX_S */
+} su_instance;
+
+/*
+ * speedup_amplitude_batch -- the top-level amplitude A_N^(p)(a_i,b_i;T_i),
+ * N = 2^(s_i), of every instance of one model and level p (Sec. 4; e.g. a
+ * matrix of short-time amplitudes on an endpoint grid), from n_mc bisection
+ * paths each, in one persistent launch of the batched kernel (work items =
+ * (instance, block), deepest instances first, taken from an atomic queue),
+ * replayed from a CUDA graph.
+ *
+ *   inst, n_inst : host, 1..2^24 instances.  Instance i draws from Philox
+ *                  stream opt->instance + i (counter word 1), samples 0..n_mc-1.
+ *   opt          : precision, n_blocks, stream (width_factor must be 1,
+ *                  sample0 must be 0, hierarchy is ignored: top level only).
+ *   out          : host, n_inst entries, out[i] for level n = s_i (the
+ *                  analytic level-0 value with err 0 where s_i = 0).
+ */
+int speedup_amplitude_batch(int model, const double *params, int n_params, int p,
+                            const su_instance *inst, int64_t n_inst, int64_t n_mc,
+                            uint64_t seed, const su_options *opt, su_level_result *out);
+
+typedef struct su_batch_plan su_batch_plan;
+
+/* the same, split: create (host tables, per-instance data and the sorted work
+ * list uploaded to plan-owned device memory), sizes, execute, finalize */
+int su_batch_plan_create(int model, const double *params, int n_params, int p,
+                         const su_instance *inst, int64_t n_inst, int64_t n_mc,
+                         uint64_t seed, const su_options *opt, su_batch_plan **plan);
+int su_batch_plan_destroy(su_batch_plan *plan);
+/* *tuple_bytes: d_tuples size (n_inst * n_blocks * 4 doubles, [instance][block]
+ * (M, S, Q, n)); *scratch_bytes: d_scratch size; *slice_actions per execute */
+int su_batch_plan_sizes(const su_batch_plan *plan, int64_t *tuple_bytes, int64_t *scratch_bytes,
+                        int64_t *slice_actions);
+/* asynchronous on stream; the first call builds the plan's CUDA graph (a
+ * memset of the queue head and the persistent kernel), later calls replay it
+ * (and rebuild it if the buffers change); *launches = graph launches made */
+int su_batch_plan_execute(su_batch_plan *plan, void *d_tuples, void *d_scratch, void *stream,
+                          int *launches);
+/* host tuples in, out[n_inst] as speedup_amplitude_batch; d_scratch (may be
+ * NULL) is read for the non-finite flag */
+int su_batch_plan_finalize(const su_batch_plan *plan, const double *h_tuples,
+                           const void *d_scratch, su_level_result *out);
+
 /* ---- device-resident interface (inputs and outputs stay in HBM) ----------- */
 
 typedef struct su_plan su_plan;

@@ -23,7 +23,8 @@ EXPORTS = [
     "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
     "speedup_generate_coeffs", "su_plan_create", "su_plan_destroy", "su_plan_sizes",
     "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
-    "su_fma_peak", "speedup_normals",
+    "su_fma_peak", "speedup_normals", "speedup_amplitude_batch", "su_batch_plan_create",
+    "su_batch_plan_destroy", "su_batch_plan_sizes", "su_batch_plan_execute", "su_batch_plan_finalize",
 ]
 
 
@@ -37,6 +38,10 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_blocks", ctypes.c_int), ("hierarchy", ctypes.c_int),
                 ("instance", ctypes.c_uint32), ("width_factor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("T", ctypes.c_double), ("s", ctypes.c_int)]
 
 
 class LevelResult(ctypes.Structure):
@@ -90,6 +95,15 @@ def load(build_if_missing=True):
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
     L.su_fma_peak.argtypes = [i32, pd]
     L.speedup_normals.argtypes = [u64, u32, i64, i64, i32, i32, vp, vp]
+    pinst = ctypes.POINTER(Instance)
+    L.speedup_amplitude_batch.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options),
+                                          ctypes.POINTER(LevelResult)]
+    L.su_batch_plan_create.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options),
+                                       ctypes.POINTER(vp)]
+    L.su_batch_plan_destroy.argtypes = [vp]
+    L.su_batch_plan_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.su_batch_plan_execute.argtypes = [vp, vp, vp, vp, pi]
+    L.su_batch_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
     for name in EXPORTS:
         if name not in ("su_options_default", "su_last_error"):
             getattr(L, name).restype = i32
@@ -205,6 +219,67 @@ def su_fma_peak(precision="fp64"):
     _check(load().su_fma_peak(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                               ctypes.byref(v)))
     return v.value
+
+
+def _instances(instances):
+    n = len(instances)
+    arr = (Instance * max(n, 1))()
+    for i, (a, b, T, s) in enumerate(instances):
+        arr[i].a, arr[i].b, arr[i].T, arr[i].s = float(a), float(b), float(T), int(s)
+    return arr, n
+
+
+def speedup_amplitude_batch(model, params, p, instances, n_mc, seed, **kw):
+    """Top-level amplitude of every (a, b, T, s) instance (list of dicts)."""
+    pr, npar = _params(params)
+    arr, n = _instances(instances)
+    out = (LevelResult * max(n, 1))()
+    o = options(**kw)
+    _check(load().speedup_amplitude_batch(_model(model), pr, npar, p, arr, n, int(n_mc), int(seed),
+                                          ctypes.byref(o), out))
+    return [out[i].as_dict(instances[i][3]) for i in range(n)]
+
+
+class BatchPlan:
+    """su_batch_plan_create / _execute / _finalize / _destroy."""
+
+    def __init__(self, model, params, p, instances, n_mc, seed, **kw):
+        pr, npar = _params(params)
+        arr, n = _instances(instances)
+        self.n_inst = n
+        self.levels_of = [int(t[3]) for t in instances]
+        o = options(**kw)
+        h = ctypes.c_void_p()
+        _check(load().su_batch_plan_create(_model(model), pr, npar, p, arr, n, int(n_mc), int(seed),
+                                           ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        tb, sb, sa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().su_batch_plan_sizes(h, ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(sa)))
+        self.tuple_bytes, self.scratch_bytes, self.slice_actions = tb.value, sb.value, sa.value
+
+    def su_batch_plan_execute(self, d_tuples, d_scratch, stream=None):
+        n = ctypes.c_int(0)
+        _check(load().su_batch_plan_execute(self._h, _ptr(d_tuples), _ptr(d_scratch), _stream(stream),
+                                            ctypes.byref(n)))
+        return n.value
+
+    def su_batch_plan_finalize(self, h_tuples, d_scratch=None):
+        out = (LevelResult * max(self.n_inst, 1))()
+        arr = np.ascontiguousarray(h_tuples, dtype=np.float64)
+        _check(load().su_batch_plan_finalize(self._h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             _ptr(d_scratch), out))
+        return [out[i].as_dict(self.levels_of[i]) for i in range(self.n_inst)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().su_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

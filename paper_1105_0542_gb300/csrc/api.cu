@@ -12,7 +12,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -475,6 +477,303 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
                           (cudaStream_t)stream),
        "normals launch");
     return SU_OK;
+}
+
+// ----------------------------------------------------------------- batch
+
+}  // extern "C"
+
+struct su_batch_plan {
+    int p = 1;
+    int64_t n_inst = 0, n_mc = 1;
+    su_options opt{};
+    su::Effective E;
+    su::BatchParams B{};
+    void *d_inst = nullptr, *d_items = nullptr, *d_tables = nullptr;
+    std::vector<int> S;           // per instance
+    std::vector<double> laf, w0;  // log A_free and the level-0 weight per instance
+    int n_blocks = 1;
+    int grid = 0;
+    size_t smem = 0;
+    int64_t tuple_bytes = 0, scratch_bytes = 256, slice_actions = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    void *g_tuples = nullptr, *g_scratch = nullptr;
+};
+
+static void batch_free(su_batch_plan *pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->d_inst) cudaFree(pl->d_inst);
+    if (pl->d_items) cudaFree(pl->d_items);
+    if (pl->d_tables) cudaFree(pl->d_tables);
+    delete pl;
+}
+
+extern "C" {
+
+int su_batch_plan_create(int model, const double *params, int n_params, int p, const su_instance *inst,
+                         int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt,
+                         su_batch_plan **out) {
+    using namespace su;
+    if (!out) return fail(SU_EINVAL, "plan pointer missing");
+    *out = nullptr;
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    if (!inst || n_inst < 1 || n_inst > (1LL << 24)) return fail(SU_EINVAL, "n_inst must be in 1..2^24");
+    if ((uint64_t)o.instance + (uint64_t)n_inst > (1ULL << 32))
+        return fail(SU_EINVAL, "instance ids exceed 32 bits");
+    if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "the batched path samples the exact bridge only");
+    for (int64_t i = 0; i < n_inst; ++i) {
+        int rc = validate(model, params, n_params, inst[i].a, inst[i].b, inst[i].T, p, inst[i].s, n_mc, o);
+        if (rc) {
+            const std::string why = g_err;
+            return fail(rc, "instance %lld: %s", (long long)i, why.c_str());
+        }
+    }
+    if (o.sample0 != 0) return fail(SU_ENOTSUP, "sample0 must be 0 for a batch");
+    std::unique_ptr<su_batch_plan, void (*)(su_batch_plan *)> pl(new (std::nothrow) su_batch_plan, batch_free);
+    if (!pl) return fail(SU_ENOMEM, "host allocation failed");
+    std::string err;
+    int rc = build_effective(model, params, n_params, p, pl->E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    pl->p = p;
+    pl->n_inst = n_inst;
+    pl->n_mc = n_mc;
+    pl->opt = o;
+    pl->n_blocks = (int)std::min<int64_t>(o.n_blocks, n_mc);
+    if ((int64_t)pl->n_blocks * n_inst > (1LL << 31) - 1) return fail(SU_ENOTSUP, "too many work items");
+    const int prec = o.precision;
+    const int M = pl->E.shape.M;
+
+    // one table per distinct top-level eps; level-0 values from one collapse per distinct T
+    std::map<double, int> tab_of;
+    std::vector<double> tabd;
+    std::map<double, std::vector<double>> coll;
+    std::vector<BatchInstance> hin((size_t)n_inst);
+    pl->S.resize((size_t)n_inst);
+    pl->laf.resize((size_t)n_inst);
+    pl->w0.resize((size_t)n_inst);
+    int S_max = 0;
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const su_instance &q = inst[i];
+        BatchInstance &h = hin[(size_t)i];
+        std::memset(&h, 0, sizeof h);
+        h.a = q.a;
+        h.b = q.b;
+        h.S = q.s;
+        h.F = std::min(q.s, kMaxFine);
+        for (int n = 1; n <= q.s; ++n) h.sigma[n] = std::sqrt(q.T / std::ldexp(1.0, n + 1));
+        pl->S[(size_t)i] = q.s;
+        pl->laf[(size_t)i] = log_A_free(q.a, q.b, q.T);
+        auto c = coll.find(q.T);
+        if (c == coll.end()) {
+            std::vector<double> P;
+            collapse(pl->E, q.T, P);
+            c = coll.emplace(q.T, std::move(P)).first;
+        }
+        pl->w0[(size_t)i] = -q.T * wp_collapsed(pl->E.shape, c->second, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a));
+        if (q.s >= 1) {
+            const double eps = q.T / std::ldexp(1.0, q.s);
+            auto it = tab_of.find(eps);
+            if (it == tab_of.end()) {
+                std::vector<double> t;
+                kernel_table(pl->E, eps, t);
+                for (double v : t)
+                    if (!std::isfinite(v) || (prec == SU_FP32 && !std::isfinite((float)v)))
+                        return fail(SU_ENONFINITE, "non-finite coefficient at eps = %g", eps);
+                it = tab_of.emplace(eps, (int)tab_of.size()).first;
+                tabd.insert(tabd.end(), t.begin(), t.end());
+            }
+            h.table = it->second;
+            S_max = std::max(S_max, q.s);
+            pl->slice_actions += n_mc * ((int64_t)1 << q.s);
+        }
+    }
+    // work items (instance, block), costliest (deepest) first
+    std::vector<int2> items;
+    items.reserve((size_t)(n_inst * pl->n_blocks));
+    std::vector<int64_t> order((size_t)n_inst);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return pl->S[(size_t)x] > pl->S[(size_t)y]; });
+    for (int64_t i : order)
+        if (pl->S[(size_t)i] >= 1)
+            for (int bk = 0; bk < pl->n_blocks; ++bk) items.push_back(make_int2((int)i, bk));
+
+    const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> blob(std::max<size_t>(tabd.size(), 1) * rs, 0);
+    if (prec == SU_FP32)
+        for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
+    else if (!tabd.empty())
+        std::memcpy(blob.data(), tabd.data(), tabd.size() * sizeof(double));
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    int dev = 0, sms = 0, smem_max = 0;
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+    CU(cudaMalloc(&pl->d_tables, blob.size()), "cudaMalloc(tables)");
+    CU(cudaMemcpy(pl->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
+    CU(cudaMalloc(&pl->d_inst, sizeof(BatchInstance) * hin.size()), "cudaMalloc(instances)");
+    CU(cudaMemcpy(pl->d_inst, hin.data(), sizeof(BatchInstance) * hin.size(), cudaMemcpyHostToDevice),
+       "upload instances");
+    if (!items.empty()) {
+        CU(cudaMalloc(&pl->d_items, sizeof(int2) * items.size()), "cudaMalloc(items)");
+        CU(cudaMemcpy(pl->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice),
+           "upload items");
+    }
+
+    BatchParams &B = pl->B;
+    std::memset(&B, 0, sizeof B);
+    SamplerParams &P = B.base;
+    P.levels = 1;
+    P.ring = pl->E.shape.ring;
+    P.ncol = pl->E.shape.ncol;
+    P.M = M;
+    for (int j = 0; j < pl->E.shape.ncol; ++j) P.len[j] = pl->E.shape.len[j];
+    P.alpha = pl->E.shape.alpha;
+    P.tables = pl->d_tables;
+    P.seed = seed;
+    P.instance = o.instance;
+    B.inst = static_cast<const BatchInstance *>(pl->d_inst);
+    B.items = static_cast<const int2 *>(pl->d_items);
+    B.n_items = (int)items.size();
+    B.S_max = S_max;
+    B.n_mc = n_mc;
+    B.n_blocks = pl->n_blocks;
+    pl->smem = batch_smem_bytes(B, prec);
+    if (pl->smem > (size_t)smem_max) return fail(SU_ENOTSUP, "shared memory %zu exceeds %d", pl->smem, smem_max);
+    const int occ = batch_occupancy(B, prec, pl->smem);
+    if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
+    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, std::max(B.n_items, 1)));
+    pl->tuple_bytes = n_inst * pl->n_blocks * 4 * (int64_t)sizeof(double);
+    pl->scratch_bytes = 256;
+    *out = pl.release();
+    return SU_OK;
+}
+
+int su_batch_plan_destroy(su_batch_plan *pl) {
+    batch_free(pl);
+    return SU_OK;
+}
+
+int su_batch_plan_sizes(const su_batch_plan *pl, int64_t *tuple_bytes, int64_t *scratch_bytes,
+                        int64_t *slice_actions) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (tuple_bytes) *tuple_bytes = pl->tuple_bytes;
+    if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
+    if (slice_actions) *slice_actions = pl->slice_actions;
+    return SU_OK;
+}
+
+int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, void *stream, int *launches) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (!d_tuples || !d_scratch) return fail(SU_EINVAL, "device buffers missing");
+    if (launches) *launches = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    // instances with s = 0 have no samples: their tuples stay zero
+    CU(cudaMemsetAsync(d_tuples, 0, (size_t)pl->tuple_bytes, st), "clear tuples");
+    if (pl->B.n_items == 0) return SU_OK;
+    su::BatchParams B = pl->B;
+    B.tuples = static_cast<double *>(d_tuples);
+    B.counter = static_cast<int *>(d_scratch);
+    B.base.flags = static_cast<int *>(d_scratch) + 1;
+    const void *fn = su::batch_fn(B.base.ring, pl->opt.precision);
+    void *args[] = {&B};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = dim3(pl->grid);
+    kp.blockDim = dim3(su::kThreads);
+    kp.sharedMemBytes = (unsigned)pl->smem;
+    kp.kernelParams = args;
+    if (!pl->exec) {
+        // one graph per plan: clear the queue head and the flags, then the persistent kernel
+        CU(cudaGraphCreate(&pl->graph, 0), "graph create");
+        cudaMemsetParams mp{};
+        mp.dst = d_scratch;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 2;
+        mp.height = 1;
+        cudaGraphNode_t mnode;
+        CU(cudaGraphAddMemsetNode(&mnode, pl->graph, nullptr, 0, &mp), "graph memset node");
+        CU(cudaGraphAddKernelNode(&pl->knode, pl->graph, &mnode, 1, &kp), "graph kernel node");
+        CU(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiate");
+        pl->g_tuples = d_tuples;
+        pl->g_scratch = d_scratch;
+    } else if (pl->g_tuples != d_tuples || pl->g_scratch != d_scratch) {
+        // new buffers: rebuild (the memset node's destination changes too)
+        cudaGraphExecDestroy(pl->exec);
+        cudaGraphDestroy(pl->graph);
+        pl->exec = nullptr;
+        pl->graph = nullptr;
+        return su_batch_plan_execute(pl, d_tuples, d_scratch, stream, launches);
+    }
+    CU(cudaGraphLaunch(pl->exec, st), "graph launch");
+    if (launches) *launches = 1;
+    return SU_OK;
+}
+
+int su_batch_plan_finalize(const su_batch_plan *pl, const double *h_tuples, const void *d_scratch,
+                           su_level_result *out) {
+    if (!pl || !out || !h_tuples) return fail(SU_EINVAL, "plan, tuples or output missing");
+    if (d_scratch) {
+        int flags = 0;
+        CU(cudaMemcpy(&flags, static_cast<const int *>(d_scratch) + 1, sizeof(int), cudaMemcpyDeviceToHost),
+           "read flags");
+        if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    }
+    for (int64_t i = 0; i < pl->n_inst; ++i) {
+        su_level_result &r = out[i];
+        if (pl->S[(size_t)i] == 0) {
+            r.amp = std::exp(pl->laf[(size_t)i] + pl->w0[(size_t)i]);
+            r.log_amp = pl->laf[(size_t)i] + pl->w0[(size_t)i];
+            r.err = r.err_naive = r.rel_err = 0;
+            r.ess = (double)pl->n_mc;
+            r.max_share = 1.0 / (double)pl->n_mc;
+            r.n = pl->n_mc;
+        } else {
+            level_result(pl->laf[(size_t)i], h_tuples + 4 * i * pl->n_blocks, pl->n_blocks, 1, 0, &r);
+        }
+    }
+    return SU_OK;
+}
+
+int speedup_amplitude_batch(int model, const double *params, int n_params, int p, const su_instance *inst,
+                            int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt,
+                            su_level_result *out) {
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_batch_plan *pl = nullptr;
+    int rc = su_batch_plan_create(model, params, n_params, p, inst, n_inst, n_mc, seed, opt, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_batch_plan, int (*)(su_batch_plan *)> guard(pl, su_batch_plan_destroy);
+    cudaStream_t st = (cudaStream_t)pl->opt.stream;
+    void *dbuf = nullptr;
+    CU(cudaMallocAsync(&dbuf, (size_t)(pl->tuple_bytes + pl->scratch_bytes), st), "cudaMallocAsync");
+    std::vector<double> h((size_t)(pl->tuple_bytes / sizeof(double)) + 32);
+    void *d_scr = static_cast<char *>(dbuf) + pl->tuple_bytes;
+    rc = su_batch_plan_execute(pl, dbuf, d_scr, st, nullptr);
+    cudaError_t e = cudaSuccess;
+    int flags = 0;
+    if (rc == SU_OK) {
+        e = cudaMemcpyAsync(h.data(), dbuf, (size_t)pl->tuple_bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&flags, static_cast<int *>(d_scr) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(dbuf, st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "batched sampling");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return su_batch_plan_finalize(pl, h.data(), nullptr, out);
 }
 
 int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,

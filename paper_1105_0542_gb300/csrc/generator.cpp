@@ -344,4 +344,20 @@ double wp_host(const Effective &E, double x, double xb, double eps) {
     return acc.hi;
 }
 
+double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, double xb) {
+    const double z = S.ring == RING_EVEN ? x * x
+                     : S.ring == RING_X  ? x
+                                         : std::tanh(S.alpha * x) * std::tanh(S.alpha * x);
+    const double y = xb * xb;
+    double acc = 0;
+    int off = S.M;
+    for (int j = S.ncol - 1; j >= 0; --j) {
+        off -= S.len[j];
+        double h = 0;
+        for (int i = S.len[j] - 1; i >= 0; --i) h = h * z + P[off + i];
+        acc = acc * y + h;
+    }
+    return acc;
+}
+
 }  // namespace su

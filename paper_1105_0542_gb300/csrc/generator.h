@@ -55,4 +55,7 @@ double kernel_table(const Effective &E, double eps, std::vector<double> &T);
 // W_p(x, xb; eps) evaluated on the host from the double-double collapse.
 double wp_host(const Effective &E, double x, double xb, double eps);
 
+// W_p(x, xb; eps) from a collapse P already made for that eps (double).
+double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, double xb);
+
 }  // namespace su

@@ -17,6 +17,12 @@ const void *sampler_entry_f64_2();
 const void *sampler_entry_f32_0();
 const void *sampler_entry_f32_1();
 const void *sampler_entry_f32_2();
+const void *batch_entry_f64_0();
+const void *batch_entry_f64_1();
+const void *batch_entry_f64_2();
+const void *batch_entry_f32_0();
+const void *batch_entry_f32_1();
+const void *batch_entry_f32_2();
 
 namespace {
 
@@ -98,11 +104,30 @@ const void *pick(const SamplerParams &P, int precision) {
 
 }  // namespace
 
+const void *batch_fn(int ring, int precision) {
+    if (precision == SU_FP32)
+        return ring == RING_EVEN ? batch_entry_f32_0() : ring == RING_X ? batch_entry_f32_1() : batch_entry_f32_2();
+    return ring == RING_EVEN ? batch_entry_f64_0() : ring == RING_X ? batch_entry_f64_1() : batch_entry_f64_2();
+}
+
+size_t batch_smem_bytes(const BatchParams &B, int precision) {
+    const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
+    const int Cmax = 1 << (B.S_max > kMaxFine ? B.S_max - kMaxFine : 0);
+    size_t off = rs * (size_t)B.base.M + rs * (size_t)(SU_MAX_S + 1);
+    off = (off + 15) & ~(size_t)15;
+    off += rs * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    if (precision == SU_FP64) off += sizeof(BMTables);
+    return off;
+}
+
 size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
     const int C = 1 << (P.S - P.F);
-    size_t off = P.w_out ? 0 : sizeof(double) * (size_t)P.levels * kThreads * P.rounds;
+    size_t off = P.w_out ? 0 : rs * (size_t)P.levels * kThreads * P.rounds;
+    off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)P.S * P.M;
+    off += rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
@@ -119,6 +144,14 @@ static cudaError_t allow_full_smem(const void *fn) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     return e;
+}
+
+int batch_occupancy(const BatchParams &B, int precision, size_t smem) {
+    const void *fn = batch_fn(B.base.ring, precision);
+    if (allow_full_smem(fn) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 int sampler_occupancy(const SamplerParams &P, int precision, size_t smem) {

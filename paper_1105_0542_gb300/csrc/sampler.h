@@ -43,6 +43,30 @@ struct SamplerParams {
     int *flags;               // device: bit 0 = non-finite weight seen
 };
 
+// One instance of a batch (top level only).
+struct BatchInstance {
+    double a, b;
+    int S, F;
+    int table;                // index of its table in the batch's table list
+    int pad;
+    double sigma[SU_MAX_S + 1];
+};
+
+// The batched kernel's parameters: the shape and stream fields of base are
+// shared by all instances (same model and p); the per-instance fields of
+// base are unused.
+struct BatchParams {
+    SamplerParams base;
+    const BatchInstance *inst;
+    const int2 *items;        // (instance, block), costliest first
+    int n_items;
+    int S_max;
+    int64_t n_mc;             // samples per instance
+    int n_blocks;             // blocks per instance
+    double *tuples;           // [instance][block] (M, S, Q, n)
+    int *counter;             // work-queue head, zeroed before every launch
+};
+
 // dynamic shared memory the sampler needs
 size_t sampler_smem_bytes(const SamplerParams &P, int precision);
 // max resident CTAs per SM for the sampler (after opting in to its smem)
@@ -50,6 +74,9 @@ int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
 
 cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
                            cudaStream_t st);
+size_t batch_smem_bytes(const BatchParams &B, int precision);
+int batch_occupancy(const BatchParams &B, int precision, size_t smem);
+const void *batch_fn(int ring, int precision);
 cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
                            int64_t items_per_block, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,

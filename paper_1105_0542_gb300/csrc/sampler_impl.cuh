@@ -195,18 +195,28 @@ __device__ __forceinline__ void segment_levels(R (&acc)[F + 1], const R (&q)[(1 
 }
 
 // --------------------------------------------------------------- a path
+// Per-path configuration: endpoints, depth, sampled levels and the bisection
+// widths sigma[n], n = 1..S, in the kernel's precision (shared memory).
+template <typename R>
+struct PathCfg {
+    R a, b;
+    int S;
+    int levels;
+    const R *sigma;
+};
+
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
 template <typename R, int RING, int F>
-__device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__restrict__ tab,
-                                            R *__restrict__ qc, double *__restrict__ zz,
-                                            const Stream<R> &st, double *__restrict__ wout,
-                                            int wstride) {
+__device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCfg<R> &pc,
+                                            const R *__restrict__ tab, R *__restrict__ qc,
+                                            double *__restrict__ zz, const Stream<R> &st,
+                                            R *__restrict__ wout, int wstride) {
     constexpr int NF = 1 << F;
-    const int S = P.S;
+    const int S = pc.S;
     const int C = 1 << (S - F);
-    const bool hier = P.levels > 1;
+    const bool hier = pc.levels > 1;
     const int M = P.M;
     const R alpha = (R)P.alpha;
 
@@ -219,13 +229,13 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__r
 
     // ---- segment endpoints: bisection levels 1..S-F, heap order j = 0..C-2
     if (C > 1) {
-        qc[0] = (R)P.a;
-        qc[C * kThreads] = (R)P.b;
+        qc[0] = pc.a;
+        qc[C * kThreads] = pc.b;
         R carry = 0;
         uint32_t j = 0;
         for (int n = 1; n <= S - F; ++n) {
             const int hc = C >> n;
-            const R sg = (R)P.sigma[n];
+            const R sg = pc.sigma[n];
             for (int i = 0; i < (1 << (n - 1)); ++i, ++j) {
                 R z;
                 if ((j & 1u) == 0) {
@@ -252,15 +262,14 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__r
 
     for (int c = 0; c < C; ++c) {
         R q[NF + 1];
-        q[0] = C > 1 ? qc[c * kThreads] : (R)P.a;
-        q[NF] = C > 1 ? qc[(c + 1) * kThreads] : (R)P.b;
+        q[0] = C > 1 ? qc[c * kThreads] : pc.a;
+        q[NF] = C > 1 ? qc[(c + 1) * kThreads] : pc.b;
 #pragma unroll
         for (int l = 1; l <= F; ++l) {
             const int n = S - F + l;
             const uint32_t jbase = (1u << (n - 1)) - 1u + ((uint32_t)c << (l - 1));
-            const R sg = (R)P.sigma[n];
-            constexpr int h0 = 1;
-            const int h = h0 << (F - l);
+            const R sg = pc.sigma[n];
+            const int h = 1 << (F - l);
 #pragma unroll
             for (int il = 0; il < (1 << (l - 1)); ++il) {
                 const uint32_t j = jbase + (uint32_t)il;
@@ -301,12 +310,14 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__r
             zz[n * kThreads] = cum;
         }
     }
-    auto corr = [&](int n) -> double { return P.wf_on ? zz[n * kThreads] : 0.0; };
+    auto out = [&](int d, R v) {
+        wout[d * wstride] = P.wf_on ? (R)((double)v + zz[(S - d) * kThreads]) : v;
+    };
 
     // ---- outputs, level n = S - d
 #pragma unroll
     for (int d = 0; d <= F; ++d)
-        if (d == 0 || (hier && d < S)) wout[d * wstride] = (double)acc[d] + corr(S - d);
+        if (d == 0 || (hier && d < S)) out(d, acc[d]);
     if (hier) {
         for (int n = 1; n < S - F; ++n) {
             const int d = S - n;
@@ -315,13 +326,27 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const R *__r
             for (int k = 0; k < (1 << n); ++k)
                 sum += slice<R, RING>(qc[k * stp * kThreads], qc[(k + 1) * stp * kThreads], tab + d * M,
                                       P, alpha);
-            wout[d * wstride] = (double)sum + corr(n);
+            out(d, sum);
         }
     }
 }
 
+template <typename R, int RING>
+__device__ __forceinline__ void sample_path_any(int F, const SamplerParams &P, const PathCfg<R> &pc,
+                                                const R *tab, R *qc, double *zz, const Stream<R> &st,
+                                                R *wout, int wstride) {
+    switch (F) {
+        case 1: sample_path<R, RING, 1>(P, pc, tab, qc, zz, st, wout, wstride); break;
+        case 2: sample_path<R, RING, 2>(P, pc, tab, qc, zz, st, wout, wstride); break;
+        case 3: sample_path<R, RING, 3>(P, pc, tab, qc, zz, st, wout, wstride); break;
+        case 4: sample_path<R, RING, 4>(P, pc, tab, qc, zz, st, wout, wstride); break;
+        default: sample_path<R, RING, 5>(P, pc, tab, qc, zz, st, wout, wstride); break;
+    }
+}
+
 // -------------------------------------------------------- warp helpers
-__device__ __forceinline__ double warp_max(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -332,9 +357,51 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// e^x for x <= 0 in the reduction: double on the double path; on the single
+// path the exponential is taken in float (its weights carry single-precision
+// error already) and only the sums are kept in double
+__device__ __forceinline__ double lse_exp(double x) { return exp(x); }
+__device__ __forceinline__ double lse_exp(float x) { return (double)__expf(x); }
+
+// running log-sum-exp tuple (M, S = sum e^{w-M}, Q = sum e^{2(w-M)}) of one thread
+template <typename R>
+struct Lse {
+    R m = -INFINITY;
+    double s = 0, q = 0;
+    __device__ __forceinline__ void push(R w) {
+        if (!(w > (R)-INFINITY)) return;          // zero weight
+        if (w > m) {
+            const double f = lse_exp((R)(m - w)); // 0 for the first weight
+            s = fma(s, f, 1.0);
+            q = fma(q, f * f, 1.0);
+            m = w;
+        } else {
+            const double e = lse_exp((R)(w - m));
+            s += e;
+            q = fma(e, e, q);
+        }
+    }
+};
+
+// merge b into a (same convention), in double
+__device__ __forceinline__ void lse_merge(double &ma, double &sa, double &qa, double mb, double sb, double qb) {
+    if (!(mb > -INFINITY)) return;
+    if (mb > ma) {
+        const double f = exp(ma - mb);
+        sa = fma(sa, f, sb);
+        qa = fma(qa, f * f, qb);
+        ma = mb;
+    } else {
+        const double f = exp(mb - ma);
+        sa = fma(sb, f, sa);
+        qa = fma(qb, f * f, qa);
+    }
+}
+
 // ----------------------------------------------------------- the kernel
-// Shared memory: sw[levels][chunk] (double) | tables[levels][M] (R) |
-//                qc[(C+1)][kThreads] (R) | zz[S+1][kThreads] (double, if wf_on)
+// Shared memory: sw[levels][chunk] (R) | tables[levels][M] (R) | sigma[S+1] (R) |
+//                qc[(C+1)][kThreads] (R) | zz[S+1][kThreads] (double, if wf_on) |
+//                Box-Muller node tables (double path)
 template <typename R, int RING>
 __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -344,10 +411,13 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
     const bool per_sample = P.w_out != nullptr;
     const int C = 1 << (P.S - P.F);
 
-    double *sw = reinterpret_cast<double *>(smem_raw);
-    size_t off = per_sample ? 0 : sizeof(double) * (size_t)L * chunk;
+    R *sw = reinterpret_cast<R *>(smem_raw);
+    size_t off = per_sample ? 0 : sizeof(R) * (size_t)L * chunk;
+    off = (off + 15) & ~(size_t)15;
     R *tab = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)P.S * P.M;
+    R *sig = reinterpret_cast<R *>(smem_raw + off);
+    off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     R *qc = reinterpret_cast<R *>(smem_raw + off) + tid;
     off += sizeof(R) * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
@@ -356,15 +426,17 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
     off += P.wf_on ? sizeof(double) * (size_t)(P.S + 1) * kThreads : 0;
     BMTables *bm_smem = reinterpret_cast<BMTables *>(smem_raw + off);   // double path only
 
-    // stage the coefficient tables of every sampled level (and the
-    // Box-Muller node tables of the double path)
+    // stage the coefficient tables of every sampled level, the widths (and
+    // the Box-Muller node tables of the double path)
     {
         const R *g = reinterpret_cast<const R *>(P.tables);
         const int n = P.S * P.M;
         for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
+        for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)P.sigma[i];
         if constexpr (sizeof(R) == 8) bm_tables_init(bm_smem, tid, kThreads);
     }
     __syncthreads();
+    const PathCfg<R> pc{(R)P.a, (R)P.b, P.S, L, sig};
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
@@ -386,32 +458,19 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
             const uint64_t sample = (uint64_t)(P.sample0 + start + t);
             st.slo = (uint32_t)sample;
             st.shi = (uint32_t)(sample >> 32);
-            double wloc[SU_MAX_S];
-            double *wout;
-            int wstride;
-            if (per_sample) {
-                wout = wloc;
-                wstride = 1;
-            } else {
-                wout = sw + t;
-                wstride = chunk;
-            }
-            switch (P.F) {
-                case 1: sample_path<R, RING, 1>(P, tab, qc, zz, st, wout, wstride); break;
-                case 2: sample_path<R, RING, 2>(P, tab, qc, zz, st, wout, wstride); break;
-                case 3: sample_path<R, RING, 3>(P, tab, qc, zz, st, wout, wstride); break;
-                case 4: sample_path<R, RING, 4>(P, tab, qc, zz, st, wout, wstride); break;
-                default: sample_path<R, RING, 5>(P, tab, qc, zz, st, wout, wstride); break;
-            }
+            R wloc[SU_MAX_S];
+            R *wout = per_sample ? wloc : sw + t;
+            const int wstride = per_sample ? 1 : chunk;
+            sample_path_any<R, RING>(P.F, P, pc, tab, qc, zz, st, wout, wstride);
             bool bad = false;
             for (int d = 0; d < L; ++d) {
-                const double w = wout[d * wstride];
+                const R w = wout[d * wstride];
                 bad |= isnan(w) || (isinf(w) && w > 0);
             }
             if (bad) atomicOr(P.flags, 1);
             if (per_sample) {
                 double *dst = P.w_out + (start + t) * (int64_t)P.S;
-                for (int d = 0; d < L; ++d) dst[P.S - d - 1] = wloc[d];
+                for (int d = 0; d < L; ++d) dst[P.S - d - 1] = (double)wloc[d];
             }
         }
         if (per_sample) continue;
@@ -419,14 +478,14 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
         // log-sum-exp tuple of this item, per level, in a fixed order
         __syncthreads();
         for (int d = warp; d < L; d += kThreads / 32) {
-            const double *v = sw + (size_t)d * chunk;
-            double m = -INFINITY;
+            const R *v = sw + (size_t)d * chunk;
+            R m = (R)-INFINITY;
             for (int t = lane; t < cnt; t += 32) m = fmax(m, v[t]);
             m = warp_max(m);
             double s = 0, q = 0;
-            if (m > -INFINITY) {
+            if (m > (R)-INFINITY) {
                 for (int t = lane; t < cnt; t += 32) {
-                    const double e = exp(v[t] - m);
+                    const double e = lse_exp((R)(v[t] - m));
                     s += e;
                     q = fma(e, e, q);
                 }
@@ -435,13 +494,99 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
             q = warp_sum(q);
             if (lane == 0) {
                 double *o = P.partial + 4 * (item * L + d);
-                o[0] = m;
+                o[0] = (double)m;
                 o[1] = s;
                 o[2] = q;
                 o[3] = (double)cnt;
             }
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------- the batched kernel
+// Many instances (a_i, b_i, T_i, s_i) of one model and level p, top level
+// only, in one persistent launch: CTAs take work items (instance, block) from
+// an atomic queue ordered costliest first; each item's samples are reduced
+// per thread and then across the CTA in a fixed order.
+// Shared memory: table[M] (R) | sigma[S_max+1] (R) | qc[(C_max+1)][kThreads] (R) |
+//                Box-Muller node tables (double path)
+template <typename R, int RING>
+__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchParams B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    __shared__ double s_red[kThreads / 32][3];
+    const SamplerParams &P = B.base;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int Cmax = 1 << (B.S_max > kMaxFine ? B.S_max - kMaxFine : 0);
+
+    R *tab = reinterpret_cast<R *>(smem_raw);
+    size_t off = sizeof(R) * (size_t)P.M;
+    R *sig = reinterpret_cast<R *>(smem_raw + off);
+    off += sizeof(R) * (size_t)(SU_MAX_S + 1);
+    off = (off + 15) & ~(size_t)15;
+    R *qc = reinterpret_cast<R *>(smem_raw + off) + tid;
+    off += sizeof(R) * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    BMTables *bm_smem = reinterpret_cast<BMTables *>(smem_raw + off);
+    if constexpr (sizeof(R) == 8) bm_tables_init(bm_smem, tid, kThreads);
+
+    Stream<R> st;
+    st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
+
+    while (true) {
+        __syncthreads();   // previous item's shared memory is free
+        if (tid == 0) s_item = atomicAdd(B.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= B.n_items) break;
+        const int2 it = B.items[item];
+        const BatchInstance &in = B.inst[it.x];
+        const R *g = reinterpret_cast<const R *>(P.tables) + (size_t)in.table * P.M;
+        for (int i = tid; i < P.M; i += kThreads) tab[i] = g[i];
+        for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)in.sigma[i];
+        __syncthreads();
+        const PathCfg<R> pc{(R)in.a, (R)in.b, in.S, 1, sig};
+        st.inst = P.instance + (uint32_t)it.x;
+        const int64_t lo = (int64_t)it.y * B.n_mc / B.n_blocks;
+        const int64_t hi = ((int64_t)it.y + 1) * B.n_mc / B.n_blocks;
+        Lse<R> acc;
+        bool bad = false;
+        for (int64_t smp = lo + tid; smp < hi; smp += kThreads) {
+            st.slo = (uint32_t)smp;
+            st.shi = (uint32_t)((uint64_t)smp >> 32);
+            R w;
+            sample_path_any<R, RING>(in.F, P, pc, tab, qc, nullptr, st, &w, 1);
+            bad |= isnan(w) || (isinf(w) && w > 0);
+            acc.push(w);
+        }
+        if (bad) atomicOr(P.flags, 1);
+        // CTA merge in a fixed order: lanes by butterfly, then warps in order
+        double m = (double)acc.m, s = acc.s, q = acc.q;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const double mb = __shfl_xor_sync(0xffffffffu, m, o);
+            const double sb = __shfl_xor_sync(0xffffffffu, s, o);
+            const double qb = __shfl_xor_sync(0xffffffffu, q, o);
+            lse_merge(m, s, q, mb, sb, qb);
+        }
+        if (lane == 0) {
+            s_red[warp][0] = m;
+            s_red[warp][1] = s;
+            s_red[warp][2] = q;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double M0 = s_red[0][0], S0 = s_red[0][1], Q0 = s_red[0][2];
+            for (int w2 = 1; w2 < kThreads / 32; ++w2) lse_merge(M0, S0, Q0, s_red[w2][0], s_red[w2][1], s_red[w2][2]);
+            double *o = B.tuples + 4 * ((int64_t)it.x * B.n_blocks + it.y);
+            o[0] = M0;
+            o[1] = S0;
+            o[2] = Q0;
+            o[3] = (double)(hi - lo);
+        }
     }
 }
 

@@ -1,4 +1,4 @@
-// One instantiation of the sampler kernel, selected at compile time:
+// One instantiation of the sampler and batched kernels, selected at compile time:
 //   SU_PREC = 64 or 32 (double / float path and W_p), SU_RING = 0, 1, 2
 //   (z = x^2, x, sech^2(alpha x)).  The build compiles this file once per
 // pair so the six kernels compile in parallel.
@@ -23,5 +23,9 @@ using Real = float;
 
 const void *SU_CAT(sampler_entry_f, SU_PREC, SU_RING)() {
     return (const void *)sampler_kernel<Real, SU_RING>;
+}
+
+const void *SU_CAT(batch_entry_f, SU_PREC, SU_RING)() {
+    return (const void *)batch_kernel<Real, SU_RING>;
 }
 }  // namespace su
