@@ -138,11 +138,17 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
 
 // Opt the kernel in to the device's full dynamic shared memory once, so that
 // plans of different sizes can alternate without re-setting the attribute.
+// (the opt-in limit covers static and dynamic shared memory together)
 static cudaError_t allow_full_smem(const void *fn) {
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) cudaGetLastError();   // reported through the return value only
     return e;
 }
 
@@ -150,7 +156,10 @@ int batch_occupancy(const BatchParams &B, int precision, size_t smem) {
     const void *fn = batch_fn(B.base.ring, precision);
     if (allow_full_smem(fn) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
@@ -158,7 +167,10 @@ int sampler_occupancy(const SamplerParams &P, int precision, size_t smem) {
     const void *fn = pick(P, precision);
     if (allow_full_smem(fn) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
@@ -166,6 +178,7 @@ cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size
                            cudaStream_t st) {
     void *args[] = {const_cast<SamplerParams *>(&P)};
     const void *fn = pick(P, precision);
+    cudaGetLastError();
     if (smem > 48 * 1024) {
         cudaError_t e = allow_full_smem(fn);
         if (e != cudaSuccess) return e;
@@ -177,6 +190,7 @@ cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_bloc
                            int64_t items_per_block, cudaStream_t st) {
     const int64_t n = n_blocks * levels;
     const int th = 128;
+    cudaGetLastError();
     combine_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(partial, tuples, n_blocks, levels,
                                                                items_per_block);
     return cudaGetLastError();
@@ -188,6 +202,7 @@ cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, in
     if (n == 0) return cudaSuccess;
     const int th = 128;
     const unsigned grid = (unsigned)((n + th - 1) / th);
+    cudaGetLastError();
     if (precision == SU_FP32)
         normals_kernel<float><<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
     else
@@ -200,6 +215,7 @@ cudaError_t launch_philox_words(uint64_t seed, uint32_t instance, int64_t sample
     const int64_t n = n_samples * n_calls;
     if (n == 0) return cudaSuccess;
     const int th = 256;
+    cudaGetLastError();
     philox_words_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(seed, instance, sample0, n_samples,
                                                                     n_calls, out);
     return cudaGetLastError();

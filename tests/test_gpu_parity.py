@@ -269,7 +269,7 @@ def test_convergence_sweep_full_size_against_diagonalisation(prec):
 @pytest.mark.parametrize("name,params,T,levels", [
     ("dw", [5.0], 5.0, (6,)),            # eps >= 5/32 lies outside the convergence radius
     ("dw", [1.0], 1.0, (1, 2, 3, 4, 5, 6)),
-    ("mpt", [3.0, 1.0], 5.0, (3, 4, 5, 6)),
+    ("mpt", [3.0, 1.0], 5.0, (5, 6)),     # eps >= 5/8: rare weights near e^1000 in 2e5
 ])
 def test_fp32_and_fp64_means_agree(name, params, T, levels):
     """Single- and double-precision W_p give the same amplitude within the
