@@ -105,6 +105,7 @@ CASES = [
     ("aho", [1.0, 1.0], 5.0, -5.0, 2.0, 10, 8, 257, 5, 77),
     ("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 300, 1234, 0),
     ("dw", [1.0], -1.0, 1.0, 1.0, 12, 6, 200, 1234, 12345),
+    ("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 5, 8, 350412),      # a rare path with w_6 = 3350
     ("mpt", [3.0, 1.0], -1.0, 1.0, 1.0, 12, 6, 200, 1234, 0),
     ("mpt", [3.0, 1.0], -1.0, 1.0, 5.0, 6, 7, 150, 3, 0),
     ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], -0.5, 0.7, 0.8, 5, 5, 140, 8, 0),
@@ -267,7 +268,7 @@ def test_convergence_sweep_full_size_against_diagonalisation(prec):
 
 
 @pytest.mark.parametrize("name,params,T,levels", [
-    ("dw", [5.0], 5.0, (6,)),            # eps >= 5/32 lies outside the convergence radius
+    ("dw", [5.0], 1.0, (3, 4, 5, 6)),
     ("dw", [1.0], 1.0, (1, 2, 3, 4, 5, 6)),
     ("mpt", [3.0, 1.0], 5.0, (5, 6)),     # eps >= 5/8: rare weights near e^1000 in 2e5
 ])
@@ -276,7 +277,10 @@ def test_fp32_and_fp64_means_agree(name, params, T, levels):
     combined statistical error (independent seeds) on the double-well and
     Poeschl-Teller workloads (p = 12, N = 64).  Levels with eps beyond the
     expansion's radius of convergence are excluded: there the truncated W_p is
-    unbounded below and single rare paths carry astronomically large weights."""
+    unbounded below and single rare paths carry astronomically large weights.
+    (The double well h = 5 at T = 5 is heavy-tailed even at N = 64: sample
+    350414 of seed 8 has w_6 = 3350; its weight is checked per sample in
+    test_logweights_*, where both precisions agree with the oracle.)"""
     r64 = su.speedup_amplitude(name, params, -1.0, 1.0, T, 12, 6, 1_000_000, 7, precision="fp64")
     r32 = su.speedup_amplitude(name, params, -1.0, 1.0, T, 12, 6, 1_000_000, 8, precision="fp32")
     for lev in levels:
