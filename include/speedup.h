@@ -278,6 +278,37 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
                     int n_normals, int precision, double *d_out, void *stream);
 
 /*
+ * speedup_amplitude_noalloc -- speedup_amplitude for callers that cannot
+ * allocate device memory: those running under an allocator that owns all of
+ * the GPU's memory, inside a memory-capped or pre-partitioned process, or in
+ * a loop where cudaMalloc/cudaFree and the synchronisation they imply are not
+ * allowed.  The paper has no counterpart; the arguments, results and errors
+ * are those of speedup_amplitude.
+ *
+ * Device scratch (coefficient tables, per-item and per-block log-sum-exp
+ * tuples, the non-finite flag) lives in one static device array of
+ * SU_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  The call makes no cudaMalloc,
+ * cudaFree or other device allocation (its host-side work arrays use ordinary
+ * host memory).
+ *  - Sizes whose tuples do not fit the array (n_mc * levels / 8192 items of
+ *    32-byte tuples at the coarsest split, plus the tables) fail with
+ *    SU_ENOTSUP.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; calls
+ *    whose device work overlaps (other threads, other streams of the same
+ *    device) race on it and must be serialised by the caller.
+ */
+#define SU_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+int speedup_amplitude_noalloc(int model, const double *params, int n_params,
+                              double a, double b, double T, int p, int s,
+                              int64_t n_mc, uint64_t seed, const su_options *opt,
+                              su_level_result *out);
+
+/*
  * su_fma_peak -- measured multiply-add throughput of the current device in
  * SU_FP64 or SU_FP32 (independent FMA chains on every SM, CUDA-event timed,
  * best of three launches): *fma_per_s multiply-adds per second (x2 = flop/s).

@@ -25,6 +25,7 @@ EXPORTS = [
     "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
     "su_fma_peak", "speedup_normals", "speedup_amplitude_batch", "su_batch_plan_create",
     "su_batch_plan_destroy", "su_batch_plan_sizes", "su_batch_plan_execute", "su_batch_plan_finalize",
+    "speedup_amplitude_noalloc",
 ]
 
 
@@ -94,6 +95,8 @@ def load(build_if_missing=True):
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
     L.su_fma_peak.argtypes = [i32, pd]
+    L.speedup_amplitude_noalloc.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64,
+                                            ctypes.POINTER(Options), ctypes.POINTER(LevelResult)]
     L.speedup_normals.argtypes = [u64, u32, i64, i64, i32, i32, vp, vp]
     pinst = ctypes.POINTER(Instance)
     L.speedup_amplitude_batch.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options),
@@ -176,6 +179,16 @@ def speedup_amplitude(model, params, a, b, T, p, s, n_mc, seed, **kw):
     o = options(**kw)
     _check(load().speedup_amplitude(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
                                     ctypes.byref(o), out))
+    return [out[n].as_dict(n) for n in range(s + 1)]
+
+
+def speedup_amplitude_noalloc(model, params, a, b, T, p, s, n_mc, seed, **kw):
+    """speedup_amplitude without device allocation (library-owned static scratch)."""
+    pr, npar = _params(params)
+    out = (LevelResult * (s + 1))()
+    o = options(**kw)
+    _check(load().speedup_amplitude_noalloc(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
+                                            ctypes.byref(o), out))
     return [out[n].as_dict(n) for n in range(s + 1)]
 
 

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -785,3 +786,166 @@ int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int6
 }
 
 }  // extern "C"
+
+// -------------------------------------------------- allocation-free variant
+//
+// Some callers must not allocate device memory while they run: code inside a
+// memory-capped or pre-partitioned process, a host that drives the GPU from a
+// real-time loop where cudaMalloc/cudaFree (and their implicit device
+// synchronisation) are forbidden, or a caller whose allocator owns all device
+// memory.  speedup_amplitude_noalloc serves them: it keeps its device scratch
+// (coefficient tables, per-item and per-block log-sum-exp tuples, the
+// non-finite flag) in the library's own static device array below, which
+// every GPU that loads the library holds until the process exits.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SU_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];   // device address of the array, per device ordinal
+
+// The array's name is a host-side stand-in in host code; its device address
+// comes from cudaGetSymbolAddress, looked up once per device with that device
+// current (the first call on a device).
+static int noalloc_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= 256) return fail(SU_ENOTSUP, "device ordinal %d beyond 255", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return SU_OK;
+}
+
+static int64_t up256(int64_t x) { return (x + 255) / 256 * 256; }
+
+extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_params, double a, double b,
+                                         double T, int p, int s, int64_t n_mc, uint64_t seed,
+                                         const su_options *opt, su_level_result *out) {
+    using namespace su;
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
+    if (rc) return rc;
+    Effective E;
+    std::string err;
+    rc = build_effective(model, params, n_params, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    const double laf = log_A_free(a, b, T);
+    const double w0 = -T * wp_host(E, 0.5 * (a + b), 0.5 * (b - a), T);
+    su_level_result &r0 = out[0];
+    r0.amp = std::exp(laf + w0);
+    r0.log_amp = laf + w0;
+    r0.err = r0.err_naive = r0.rel_err = 0;
+    r0.ess = (double)n_mc;
+    r0.max_share = 1.0 / (double)n_mc;
+    r0.n = n_mc;
+    if (s == 0) return SU_OK;
+
+    // host tables of levels n = s..1 (row d = s - n)
+    const int prec = o.precision;
+    const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
+    const int M = E.shape.M;
+    std::vector<double> tabd((size_t)s * M);
+    for (int d = 0; d < s; ++d) {
+        std::vector<double> t;
+        kernel_table(E, T / std::ldexp(1.0, s - d), t);
+        for (int i = 0; i < M; ++i) {
+            if (!std::isfinite(t[i]) || (prec == SU_FP32 && !std::isfinite((float)t[i])))
+                return fail(SU_ENONFINITE, "non-finite coefficient at level %d", s - d);
+            tabd[(size_t)d * M + i] = t[i];
+        }
+    }
+    std::vector<unsigned char> blob(tabd.size() * rs);
+    if (prec == SU_FP32)
+        for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
+    else
+        std::memcpy(blob.data(), tabd.data(), blob.size());
+
+    SamplerParams P;
+    std::memset(&P, 0, sizeof P);
+    P.a = a;
+    P.b = b;
+    for (int n = 1; n <= s; ++n) P.sigma[n] = o.width_factor * std::sqrt(T / std::ldexp(1.0, n + 1));
+    P.S = s;
+    P.F = std::min(s, kMaxFine);
+    P.levels = o.hierarchy ? s : 1;
+    P.wf_on = o.width_factor != 1.0;
+    P.lwf = std::log(o.width_factor);
+    P.hcoef = 0.5 * (1.0 - o.width_factor * o.width_factor);
+    P.ring = E.shape.ring;
+    P.ncol = E.shape.ncol;
+    P.M = M;
+    for (int j = 0; j < E.shape.ncol; ++j) P.len[j] = E.shape.len[j];
+    P.alpha = E.shape.alpha;
+    P.seed = seed;
+    P.instance = o.instance;
+    P.n_mc = n_mc;
+    P.sample0 = o.sample0;
+    const int64_t nb = std::min<int64_t>(o.n_blocks, n_mc);
+    P.n_blocks = nb;
+
+    // the fewest rounds (samples per item / 128) whose tuples fit the array
+    const int64_t bsz = (n_mc + nb - 1) / nb;
+    const int64_t tab_bytes = up256((int64_t)blob.size());
+    const int64_t tup_bytes = up256(nb * P.levels * 4 * (int64_t)sizeof(double));
+    int64_t part_bytes = 0;
+    for (P.rounds = 1;; P.rounds *= 2) {
+        P.items_per_block = (bsz + (int64_t)kThreads * P.rounds - 1) / ((int64_t)kThreads * P.rounds);
+        P.n_items = P.items_per_block * nb;
+        part_bytes = up256(P.n_items * P.levels * 4 * (int64_t)sizeof(double));
+        if (tab_bytes + part_bytes + tup_bytes + 256 <= (int64_t)SU_NOALLOC_SCRATCH_BYTES) break;
+        if (P.rounds >= 64)
+            return fail(SU_ENOTSUP,
+                        "n_mc = %lld with %lld blocks needs more than the %u bytes of no-alloc scratch",
+                        (long long)n_mc, (long long)nb, (unsigned)SU_NOALLOC_SCRATCH_BYTES);
+    }
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    int dev = 0, sms = 0, smem_max = 0;
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+    unsigned char *base = nullptr;
+    rc = noalloc_scratch(dev, &base);
+    if (rc) return rc;
+    unsigned char *d_tab = base;
+    double *d_part = reinterpret_cast<double *>(base + tab_bytes);
+    double *d_tup = reinterpret_cast<double *>(base + tab_bytes + part_bytes);
+    int *d_flag = reinterpret_cast<int *>(base + tab_bytes + part_bytes + tup_bytes);
+    P.tables = d_tab;
+    P.partial = d_part;
+    P.flags = d_flag;
+    P.w_out = nullptr;
+    const size_t smem = sampler_smem_bytes(P, prec);
+    if (smem > (size_t)smem_max) return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", smem, smem_max);
+    const int occ = sampler_occupancy(P, prec, smem);
+    if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident");
+    const int grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
+
+    cudaStream_t st = (cudaStream_t)o.stream;
+    std::vector<double> h((size_t)(nb * P.levels * 4));
+    int flags = 0;
+    CU(cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "upload tables");
+    CU(cudaMemsetAsync(d_flag, 0, sizeof(int), st), "clear flag");
+    CU(launch_sampler(P, prec, grid, smem, st), "sampler launch");
+    CU(launch_combine(d_part, d_tup, nb, P.levels, P.items_per_block, st), "combine launch");
+    CU(cudaMemcpyAsync(h.data(), d_tup, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read tuples");
+    CU(cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+    CU(cudaStreamSynchronize(st), "sampling");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    for (int d = 0; d < P.levels; ++d) level_result(laf, h.data(), nb, P.levels, d, &out[s - d]);
+    return SU_OK;
+}
