@@ -191,6 +191,56 @@ int su_batch_plan_execute(su_batch_plan *plan, void *d_tuples, void *d_scratch, 
 int su_batch_plan_finalize(const su_batch_plan *plan, const double *h_tuples,
                            const void *d_scratch, su_level_result *out);
 
+/* ---- learned bisection proposal -------------------------------------------- */
+
+/*
+ * A small network proposes every bisection midpoint (Sec. 4.1) from the
+ * instance and the midpoint's parents: x = (a, b, T, n/s, q_L, q_R) ->
+ * Linear(6,128) -> GELU -> Linear(128,128) -> GELU -> Linear(128,128) -> GELU
+ * -> Linear(128,2) = (shift, ls), GELU(v) = v (1 + erf(v/sqrt 2))/2, and the
+ * midpoint is q = (q_L + q_R)/2 + sigma_n (shift + e^ls z) with the plain
+ * sampler's normal z.  Each midpoint adds the exact log density ratio
+ * z^2/2 - (shift + e^ls z)^2/2 + ls (bridge over proposal) to the weight of
+ * every level >= n, so the estimate of A_N^(p) stays unbiased for any
+ * network.  Bfloat16 weights and activations, float accumulation (tensor
+ * cores), single-precision path and W_p, double reductions.
+ *
+ * theta: SU_MLP_PARAMS floats, W1[128][6], b1[128], W2[128][128], b2[128],
+ * W3[128][128], b3[128], W4[2][128], b4[2] (matrices [out][in]).
+ */
+#define SU_MLP_PARAMS 34178
+
+typedef struct su_proposal su_proposal;
+
+/* upload a network (host theta, copied); SU_ENONFINITE on a NaN/Inf weight */
+int su_proposal_create(const float *theta, int n_params, su_proposal **prop);
+int su_proposal_destroy(su_proposal *prop);
+
+/* the network on n rows of features: d_X (device, n x 6 floats) ->
+ * d_Y (device, n x 2 floats: shift, ls).  Asynchronous on stream. */
+int su_mlp_forward(const su_proposal *prop, const float *d_X, int64_t n, float *d_Y, void *stream);
+
+/*
+ * speedup_amplitude_proposal -- speedup_amplitude with the midpoints drawn
+ * from the network (opt->precision must be SU_FP32, s <= 6, width_factor 1).
+ */
+int speedup_amplitude_proposal(int model, const double *params, int n_params,
+                               double a, double b, double T, int p, int s,
+                               int64_t n_mc, uint64_t seed, const su_options *opt,
+                               const su_proposal *prop, su_level_result *out);
+
+/*
+ * speedup_proposal_logweights -- per-sample log-weights of the proposal path
+ * (W_p sum plus the proposal's log density ratio), laid out as
+ * speedup_logweights; d_outs (device, may be NULL) receives the network's
+ * (shift, ls) per sample and heap index j: d_outs[((i - sample0) * (N-1) + j) * 2].
+ */
+int speedup_proposal_logweights(int model, const double *params, int n_params,
+                                double a, double b, double T, int p, int s,
+                                int64_t sample0, int64_t n_samples, uint64_t seed,
+                                const su_options *opt, const su_proposal *prop,
+                                double *d_w, float *d_outs);
+
 /* ---- device-resident interface (inputs and outputs stay in HBM) ----------- */
 
 typedef struct su_plan su_plan;

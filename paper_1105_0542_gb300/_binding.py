@@ -25,8 +25,10 @@ EXPORTS = [
     "su_plan_execute", "su_plan_finalize", "speedup_logweights", "speedup_philox_words",
     "su_fma_peak", "speedup_normals", "speedup_amplitude_batch", "su_batch_plan_create",
     "su_batch_plan_destroy", "su_batch_plan_sizes", "su_batch_plan_execute", "su_batch_plan_finalize",
-    "speedup_amplitude_noalloc",
+    "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
+    "speedup_amplitude_proposal", "speedup_proposal_logweights",
 ]
+MLP_PARAMS = 34178
 
 
 class SpeedupError(RuntimeError):
@@ -95,6 +97,14 @@ def load(build_if_missing=True):
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
     L.su_fma_peak.argtypes = [i32, pd]
+    pf = ctypes.POINTER(ctypes.c_float)
+    L.su_proposal_create.argtypes = [pf, i32, ctypes.POINTER(vp)]
+    L.su_proposal_destroy.argtypes = [vp]
+    L.su_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.speedup_amplitude_proposal.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                             vp, ctypes.POINTER(LevelResult)]
+    L.speedup_proposal_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
+                                              ctypes.POINTER(Options), vp, vp, vp]
     L.speedup_amplitude_noalloc.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64,
                                             ctypes.POINTER(Options), ctypes.POINTER(LevelResult)]
     L.speedup_normals.argtypes = [u64, u32, i64, i64, i32, i32, vp, vp]
@@ -293,6 +303,54 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class Proposal:
+    """A network uploaded for the learned proposal (su_proposal_create)."""
+
+    def __init__(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != MLP_PARAMS:
+            raise ValueError(f"the network has {MLP_PARAMS} parameters")
+        h = ctypes.c_void_p()
+        _check(load().su_proposal_create(th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), th.size,
+                                         ctypes.byref(h)))
+        self._h = h
+
+    def su_mlp_forward(self, X, Y, stream=None):
+        n = X.shape[0] if hasattr(X, "shape") else None
+        _check(load().su_mlp_forward(self._h, _ptr(X), int(n), _ptr(Y), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().su_proposal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def speedup_amplitude_proposal(model, params, a, b, T, p, s, n_mc, seed, proposal, **kw):
+    pr, npar = _params(params)
+    out = (LevelResult * (s + 1))()
+    kw.setdefault("precision", "fp32")
+    o = options(**kw)
+    _check(load().speedup_amplitude_proposal(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
+                                             ctypes.byref(o), proposal._h, out))
+    return [out[n].as_dict(n) for n in range(s + 1)]
+
+
+def speedup_proposal_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, proposal, out,
+                                outs=None, **kw):
+    pr, npar = _params(params)
+    kw.setdefault("precision", "fp32")
+    o = options(**kw)
+    _check(load().speedup_proposal_logweights(_model(model), pr, npar, a, b, T, p, s, int(sample0),
+                                              int(n_samples), int(seed), ctypes.byref(o), proposal._h,
+                                              _ptr(out), _ptr(outs)))
 
 
 class Plan:

@@ -23,6 +23,8 @@
 
 #include "../../include/speedup.h"
 #include "generator.h"
+#include "mlp.cuh"
+#include "proposal.h"
 #include "sampler.h"
 
 namespace {
@@ -787,6 +789,177 @@ int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int6
 
 }  // extern "C"
 
+// ------------------------------------------------------ learned proposal
+
+static int64_t up256(int64_t x) { return (x + 255) / 256 * 256; }
+
+struct su_proposal {
+    void *d_blob = nullptr;
+};
+
+extern "C" int su_proposal_create(const float *theta, int n_params, su_proposal **out) {
+    if (!out || !theta) return fail(SU_EINVAL, "arguments missing");
+    *out = nullptr;
+    if (n_params != su::mlp::kParams) return fail(SU_EINVAL, "the network has %d parameters", su::mlp::kParams);
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(theta[i])) return fail(SU_ENONFINITE, "non-finite network parameter %d", i);
+    std::vector<unsigned char> blob(su::mlp::kBlobBytes);
+    su::mlp::pack_blob(theta, blob.data());
+    std::unique_ptr<su_proposal> pr(new (std::nothrow) su_proposal);
+    if (!pr) return fail(SU_ENOMEM, "host allocation failed");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    CU(cudaMalloc(&pr->d_blob, blob.size()), "cudaMalloc(network)");
+    e = cudaMemcpy(pr->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(pr->d_blob);
+        return cuda_fail(e, "upload network");
+    }
+    *out = pr.release();
+    return SU_OK;
+}
+
+extern "C" int su_proposal_destroy(su_proposal *pr) {
+    if (!pr) return SU_OK;
+    if (pr->d_blob) cudaFree(pr->d_blob);
+    delete pr;
+    return SU_OK;
+}
+
+extern "C" int su_mlp_forward(const su_proposal *pr, const float *d_X, int64_t n, float *d_Y, void *stream) {
+    if (!pr || !d_X || !d_Y || n < 0) return fail(SU_EINVAL, "arguments missing");
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    if (n == 0) return SU_OK;
+    CU(su::launch_mlp_forward(static_cast<const unsigned char *>(pr->d_blob), d_X, n, d_Y, sms,
+                              (cudaStream_t)stream),
+       "network launch");
+    return SU_OK;
+}
+
+// plan + proposal parameters with 128-sample items (one path per thread of
+// the first 128 threads of a 256-thread CTA)
+static int proposal_setup(su_plan *pl, const su_proposal *pr, su::ProposalParams &Q, int &grid, size_t &smem) {
+    using namespace su;
+    std::memset(&Q, 0, sizeof Q);
+    Q.base = pl->P;
+    Q.blob = static_cast<const unsigned char *>(pr->d_blob);
+    Q.T = pl->T;
+    SamplerParams &P = Q.base;
+    P.rounds = 1;
+    const int64_t bsz = (pl->n_mc + pl->n_blocks - 1) / pl->n_blocks;
+    P.items_per_block = (bsz + mlp::kRows - 1) / mlp::kRows;
+    P.n_items = P.items_per_block * pl->n_blocks;
+    smem = proposal_smem_bytes(Q);
+    int dev = 0, sms = 0, smem_max = 0;
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+    if (smem > (size_t)smem_max) return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", smem, smem_max);
+    const int occ = proposal_occupancy(Q, smem);
+    if (occ < 1) return fail(SU_ECUDA, "proposal kernel cannot be resident");
+    grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
+    return SU_OK;
+}
+
+static int proposal_check(const su_options &o, int s, const su_proposal *pr) {
+    if (!pr) return fail(SU_EINVAL, "proposal missing");
+    if (o.precision != SU_FP32) return fail(SU_ENOTSUP, "the learned proposal runs the single-precision path");
+    if (s > 6) return fail(SU_ENOTSUP, "the learned proposal supports s <= 6 (N <= 64)");
+    if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "the learned proposal replaces the width factor");
+    return SU_OK;
+}
+
+extern "C" int speedup_amplitude_proposal(int model, const double *params, int n_params, double a, double b,
+                                          double T, int p, int s, int64_t n_mc, uint64_t seed,
+                                          const su_options *opt, const su_proposal *pr, su_level_result *out) {
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    int rc = proposal_check(o, s, pr);
+    if (rc) return rc;
+    su_plan *pl = nullptr;
+    rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    if (s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
+    su::ProposalParams Q;
+    int grid = 0;
+    size_t smem = 0;
+    rc = proposal_setup(pl, pr, Q, grid, smem);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const int64_t part_bytes = up256(Q.base.n_items * pl->levels * 4 * (int64_t)sizeof(double));
+    const int64_t tb = pl->tuple_bytes;
+    void *dbuf = nullptr;
+    CU(cudaMallocAsync(&dbuf, (size_t)(part_bytes + tb + 256), st), "cudaMallocAsync");
+    Q.base.partial = static_cast<double *>(dbuf);
+    double *d_tup = reinterpret_cast<double *>(static_cast<char *>(dbuf) + part_bytes);
+    Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(dbuf) + part_bytes + tb);
+    Q.base.w_out = nullptr;
+    Q.outs = nullptr;
+    std::vector<double> h((size_t)(tb / sizeof(double)));
+    int flags = 0;
+    cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = su::launch_proposal(Q, grid, smem, st);
+    if (e == cudaSuccess)
+        e = su::launch_combine(Q.base.partial, d_tup, pl->n_blocks, pl->levels, Q.base.items_per_block, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(dbuf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal sampling");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+extern "C" int speedup_proposal_logweights(int model, const double *params, int n_params, double a, double b,
+                                           double T, int p, int s, int64_t sample0, int64_t n_samples,
+                                           uint64_t seed, const su_options *opt, const su_proposal *pr,
+                                           double *d_w, float *d_outs) {
+    if (s < 1) return fail(SU_EINVAL, "s must be >= 1 for per-sample weights");
+    if (!d_w) return fail(SU_EINVAL, "output missing");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    o.hierarchy = 1;
+    o.n_blocks = 1;
+    o.sample0 = sample0;
+    int rc = proposal_check(o, s, pr);
+    if (rc) return rc;
+    su_plan *pl = nullptr;
+    rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_samples, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    su::ProposalParams Q;
+    int grid = 0;
+    size_t smem = 0;
+    rc = proposal_setup(pl, pr, Q, grid, smem);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    int *d_flag = nullptr;
+    CU(cudaMallocAsync(&d_flag, sizeof(int), st), "cudaMallocAsync");
+    Q.base.flags = d_flag;
+    Q.base.w_out = d_w;
+    Q.base.partial = nullptr;
+    Q.outs = d_outs;
+    int flags = 0;
+    cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = su::launch_proposal(Q, grid, smem, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_flag, st);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal per-sample weights");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return SU_OK;
+}
+
 // -------------------------------------------------- allocation-free variant
 //
 // Some callers must not allocate device memory while they run: code inside a
@@ -822,7 +995,6 @@ static int noalloc_scratch(int dev, unsigned char **out) {
     return SU_OK;
 }
 
-static int64_t up256(int64_t x) { return (x + 255) / 256 * 256; }
 
 extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_params, double a, double b,
                                          double T, int p, int s, int64_t n_mc, uint64_t seed,

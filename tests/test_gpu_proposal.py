@@ -1,0 +1,126 @@
+"""GPU parity of the learned bisection proposal (network on the tensor cores,
+proposal sampling and exact reweighting) against the oracle.
+
+* the network: tensor-core bfloat16 forward against the oracle's forward with
+  the same bfloat16 roundings of weights and layer inputs (float vs double
+  accumulation, so agreement to a few bfloat16 units of the outputs);
+* a network whose output layer is zero proposes the bridge itself: weights
+  equal the plain single-precision sampler's;
+* per-sample weights of a non-trivial proposal, replayed by the oracle from
+  the network outputs the device used (path and density ratio in double);
+* unbiasedness: the harmonic oscillator's exact discretized amplitude at every
+  level within 3 sigma with a non-trivial network.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1105_0542_gb300 as su  # noqa: E402
+from oracle import exact, mc  # noqa: E402
+from oracle import effective_action as ea  # noqa: E402
+from oracle import proposal as pr  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _theta(seed, scale_last=0.4):
+    th = pr.init(seed)
+    rng = np.random.default_rng(seed + 100)
+    k = pr.n_params() - (2 * 128 + 2)
+    th[k:] = rng.normal(0, scale_last / math.sqrt(128), 2 * 128 + 2)
+    return th
+
+
+def test_network_forward_matches_oracle():
+    th = _theta(1, 1.0)
+    rng = np.random.default_rng(2)
+    n = 1000
+    X = np.stack([np.full(n, -1.0), np.full(n, 1.0), np.full(n, 5.0), rng.integers(1, 7, n) / 6,
+                  rng.normal(0, 1.2, n), rng.normal(0, 1.2, n)], axis=1)
+    P = su.Proposal(th)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Yd = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    P.su_mlp_forward(Xd, Yd)
+    torch.cuda.synchronize()
+    Y = Yd.cpu().numpy().astype(np.float64)
+    # the oracle with the device's input rounding (float32 features, then bf16)
+    ref, _ = pr.forward(th.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
+                        bf16=True)
+    err = np.abs(Y - ref)
+    scale = np.abs(ref).max()
+    assert scale > 0.05
+    assert float(np.median(err)) <= 2e-3 * scale
+    assert float(err.max()) <= 2e-2 * scale
+
+
+def _allow(wo, wabs, rel, u):
+    scale = np.maximum(np.abs(wo), np.median(np.abs(wo), axis=0))
+    return np.maximum(rel * scale, 64 * u * wabs)
+
+
+def test_zero_output_layer_reproduces_the_plain_sampler():
+    th = pr.init(4)                       # output layer zero: shift = ls = 0
+    P = su.Proposal(th)
+    n, s = 300, 6
+    wq = torch.zeros((n, s), dtype=torch.float64, device="cuda")
+    su.speedup_proposal_logweights("dw", [5.0], -1.0, 1.0, 5.0, 12, s, 0, n, 9, P, wq)
+    wp = torch.zeros((n, s), dtype=torch.float64, device="cuda")
+    su.speedup_logweights("dw", [5.0], -1.0, 1.0, 5.0, 12, s, 0, n, 9, wp, precision="fp32")
+    torch.cuda.synchronize()
+    a, b = wq.cpu().numpy(), wp.cpu().numpy()
+    o = mc.Oracle("dw", [5.0], 12)
+    wo, _ = o.logweights(-1.0, 1.0, 5.0, s, 9, n, bits=24, threads=THREADS)
+    wabs = o.logweights_abs(-1.0, 1.0, 5.0, s, 9, n, bits=24)
+    allow = _allow(wo, wabs, 1e-5, 2.0 ** -24)
+    assert float(np.max(np.abs(a - wo) / allow)) <= 1.0
+    assert float(np.max(np.abs(a - b) / allow)) <= 2.0
+
+
+@pytest.mark.parametrize("model,params,a,b,T,p,s", [("dw", [5.0], -1.0, 1.0, 5.0, 12, 6),
+                                                    ("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4),
+                                                    ("mpt", [3.0, 1.0], -1.0, 1.0, 1.0, 6, 5)])
+def test_proposal_weights_replayed_by_the_oracle(model, params, a, b, T, p, s):
+    th = _theta(7, 0.6)
+    P = su.Proposal(th)
+    n, N = 64, 1 << s
+    w = torch.zeros((n, s), dtype=torch.float64, device="cuda")
+    outs = torch.zeros((n, N - 1, 2), dtype=torch.float32, device="cuda")
+    su.speedup_proposal_logweights(model, params, a, b, T, p, s, 5000, n, 3, P, w, outs)
+    torch.cuda.synchronize()
+    wg, og = w.cpu().numpy(), outs.cpu().numpy().astype(np.float64)
+    assert np.abs(og).max() > 1e-3        # the network moved the midpoints
+    m = ea.make_model(model, params)
+    for i in range(n):
+        q, corr = pr.proposal_path(th, a, b, T, s, 3, 5000 + i, bits=24, outs=og[i])
+        for lev in range(1, s + 1):
+            qq = q[:: 1 << (s - lev)]
+            eps = T / 2 ** lev
+            W = exact._wp_vec(m, p, 0.5 * (qq[1:] + qq[:-1]), 0.5 * (qq[1:] - qq[:-1]), eps)
+            wab = eps * float(np.sum(np.abs(W)))
+            ref = -eps * float(np.sum(W)) + corr[lev - 1]
+            allow = max(1e-5 * max(abs(ref), 1.0), 64 * 2.0 ** -24 * (wab + abs(corr[lev - 1])))
+            assert abs(wg[i, lev - 1] - ref) <= allow, (i, lev, wg[i, lev - 1], ref)
+
+
+def test_proposal_estimate_is_unbiased():
+    th = _theta(11, 0.5)
+    P = su.Proposal(th)
+    r = su.speedup_amplitude_proposal("ho", [1.0], 0.0, 1.0, 1.0, 4, 4, 400_000, 17, P, n_blocks=20)
+    for lev in range(1, 5):
+        ref = exact.ho_discretized(4, 2 ** lev, 0.0, 1.0, 1.0)
+        sig = max(r[lev]["err"], r[lev]["err_naive"])
+        assert abs(r[lev]["amp"] - ref) <= 3 * sig, (lev, r[lev]["amp"], ref, sig)
+    plain = su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 4, 400_000, 17, precision="fp32", n_blocks=20)
+    assert r[4]["ess"] < plain[4]["ess"]   # a random network is a worse proposal than the bridge
