@@ -135,6 +135,22 @@ def _wp_vec(model, p, x, xb, eps):
     return tot
 
 
+def _wp_abs_vec(model, p, x, xb, eps):
+    """sum over all terms c_{m,k,i} z^i eps^(m-k) xb^(2k) of their absolute
+    values (the condition scale of W_p at these points)"""
+    c = ea.coefficients(model, p)
+    z = np.abs(np.tanh(float(model.alpha) * x) if model.kind == "t" else x)
+    tot = np.zeros_like(x)
+    for (m, k), poly in c.items():
+        v = np.zeros_like(x)
+        zp = np.ones_like(x)
+        for coef in poly:
+            v += abs(float(coef)) * zp
+            zp = zp * z
+        tot += v * eps ** (m - k) * xb ** (2 * k)
+    return tot
+
+
 def quadrature(model_name, params, p, N, a, b, T, half_width=None, npts=None):
     """A_N^(p)(a,b;T) for N in {1, 2, 4}: Gauss-Legendre on the box
     |q_i - mid_i| <= half_width around the straight line from a to b.

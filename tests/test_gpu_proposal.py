@@ -88,7 +88,7 @@ def test_zero_output_layer_reproduces_the_plain_sampler():
     assert float(np.max(np.abs(a - b) / allow)) <= 2.0
 
 
-@pytest.mark.parametrize("model,params,a,b,T,p,s", [("dw", [5.0], -1.0, 1.0, 5.0, 12, 6),
+@pytest.mark.parametrize("model,params,a,b,T,p,s", [("dw", [5.0], -1.0, 1.0, 1.0, 12, 6),
                                                     ("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4),
                                                     ("mpt", [3.0, 1.0], -1.0, 1.0, 1.0, 6, 5)])
 def test_proposal_weights_replayed_by_the_oracle(model, params, a, b, T, p, s):
@@ -107,8 +107,9 @@ def test_proposal_weights_replayed_by_the_oracle(model, params, a, b, T, p, s):
         for lev in range(1, s + 1):
             qq = q[:: 1 << (s - lev)]
             eps = T / 2 ** lev
-            W = exact._wp_vec(m, p, 0.5 * (qq[1:] + qq[:-1]), 0.5 * (qq[1:] - qq[:-1]), eps)
-            wab = eps * float(np.sum(np.abs(W)))
+            x, xb = 0.5 * (qq[1:] + qq[:-1]), 0.5 * (qq[1:] - qq[:-1])
+            W = exact._wp_vec(m, p, x, xb, eps)
+            wab = eps * float(np.sum(exact._wp_abs_vec(m, p, x, np.abs(xb), eps)))
             ref = -eps * float(np.sum(W)) + corr[lev - 1]
             allow = max(1e-5 * max(abs(ref), 1.0), 64 * 2.0 ** -24 * (wab + abs(corr[lev - 1])))
             assert abs(wg[i, lev - 1] - ref) <= allow, (i, lev, wg[i, lev - 1], ref)
