@@ -241,6 +241,44 @@ int speedup_proposal_logweights(int model, const double *params, int n_params,
                                 const su_options *opt, const su_proposal *prop,
                                 double *d_w, float *d_outs);
 
+/*
+ * Training of the proposal (weighted maximum likelihood of midpoints of plain
+ * paths).  Loss over rows r (one row per midpoint: its features x_r, its
+ * standardized offset u_r = (q - (q_L + q_R)/2) / sigma_n, weight rw_r):
+ *   L = sum_r rw_r [ls_r + (u_r - shift_r)^2 e^(-2 ls_r) / 2] / sum_r rw_r.
+ * Bfloat16 tensor-core forward and backward, float accumulation and float
+ * master weights.
+ */
+typedef struct {
+    int64_t n_train;       /* plain paths to learn from; 1e6                        */
+    int steps;             /* Adam steps; 2000                                      */
+    int batch_paths;       /* paths per step (rows = batch_paths * (N-1)); 512      */
+    double lr;             /* Adam learning rate; 1e-3                              */
+    double clip_quantile;  /* top-level log-weights above this quantile are clipped
+                              for the training weights (rare huge weights would
+                              otherwise fit one path); 0.999                         */
+    uint64_t seed;         /* minibatch draws; 1                                    */
+} su_train_options;
+
+void su_train_options_default(su_train_options *t);
+
+/* loss and gradient (host, SU_MLP_PARAMS floats in theta's order) of n rows
+ * given on the device: d_X (n x 6), d_u (n), d_rw (n) floats.  Synchronous. */
+int su_mlp_loss_grad(const float *theta, const float *d_X, const float *d_u, const float *d_rw,
+                     int64_t n, double *loss, float *grad);
+
+/*
+ * speedup_train_proposal -- draw topt->n_train plain single-precision paths of
+ * the instance (seed), weigh them by their top-level weight (clipped at
+ * clip_quantile), and run topt->steps Adam steps on minibatches drawn in
+ * proportion to those weights.  theta: host, SU_MLP_PARAMS floats, initial
+ * network in, trained network out.  loss_out (host, steps doubles, may be
+ * NULL) receives the minibatch losses.  2 <= s <= 6.  Synchronous.
+ */
+int speedup_train_proposal(int model, const double *params, int n_params,
+                           double a, double b, double T, int p, int s, uint64_t seed,
+                           const su_train_options *topt, float *theta, double *loss_out);
+
 /* ---- device-resident interface (inputs and outputs stay in HBM) ----------- */
 
 typedef struct su_plan su_plan;

@@ -7,7 +7,7 @@ built library or a CUDA device the entry points raise.
 """
 from ._binding import (  # noqa: F401
     BatchPlan, EXPORTS, MLP_PARAMS, MODELS, PRECISIONS, Plan, Proposal,
-    speedup_amplitude_proposal, speedup_proposal_logweights, speedup_amplitude_batch, speedup_amplitude_noalloc, SpeedupError, library_path, load, options,
+    speedup_amplitude_proposal, speedup_proposal_logweights, speedup_train_proposal, su_mlp_loss_grad, speedup_amplitude_batch, speedup_amplitude_noalloc, SpeedupError, library_path, load, options,
     speedup_amplitude, speedup_generate_coeffs, speedup_logweights, speedup_philox_words, su_fma_peak,
     speedup_normals,
     su_last_error, su_version,

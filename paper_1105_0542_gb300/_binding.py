@@ -26,7 +26,8 @@ EXPORTS = [
     "su_fma_peak", "speedup_normals", "speedup_amplitude_batch", "su_batch_plan_create",
     "su_batch_plan_destroy", "su_batch_plan_sizes", "su_batch_plan_execute", "su_batch_plan_finalize",
     "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
-    "speedup_amplitude_proposal", "speedup_proposal_logweights",
+    "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
+    "su_mlp_loss_grad", "speedup_train_proposal",
 ]
 MLP_PARAMS = 34178
 
@@ -41,6 +42,11 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_blocks", ctypes.c_int), ("hierarchy", ctypes.c_int),
                 ("instance", ctypes.c_uint32), ("width_factor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64)]
+
+
+class TrainOptions(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_int64), ("steps", ctypes.c_int), ("batch_paths", ctypes.c_int),
+                ("lr", ctypes.c_double), ("clip_quantile", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class Instance(ctypes.Structure):
@@ -108,6 +114,11 @@ def load(build_if_missing=True):
     L.speedup_amplitude_noalloc.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64,
                                             ctypes.POINTER(Options), ctypes.POINTER(LevelResult)]
     L.speedup_normals.argtypes = [u64, u32, i64, i64, i32, i32, vp, vp]
+    L.su_train_options_default.argtypes = [ctypes.POINTER(TrainOptions)]
+    L.su_train_options_default.restype = None
+    L.su_mlp_loss_grad.argtypes = [pf, vp, vp, vp, i64, pd, pf]
+    L.speedup_train_proposal.argtypes = [i32, pd, i32, d, d, d, i32, i32, u64, ctypes.POINTER(TrainOptions), pf,
+                                         pd]
     pinst = ctypes.POINTER(Instance)
     L.speedup_amplitude_batch.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options),
                                           ctypes.POINTER(LevelResult)]
@@ -118,7 +129,7 @@ def load(build_if_missing=True):
     L.su_batch_plan_execute.argtypes = [vp, vp, vp, vp, pi]
     L.su_batch_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
     for name in EXPORTS:
-        if name not in ("su_options_default", "su_last_error"):
+        if name not in ("su_options_default", "su_last_error", "su_train_options_default"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -351,6 +362,35 @@ def speedup_proposal_logweights(model, params, a, b, T, p, s, sample0, n_samples
     _check(load().speedup_proposal_logweights(_model(model), pr, npar, a, b, T, p, s, int(sample0),
                                               int(n_samples), int(seed), ctypes.byref(o), proposal._h,
                                               _ptr(out), _ptr(outs)))
+
+
+def su_mlp_loss_grad(theta, X, u, rw):
+    """(loss, flat gradient) of the rows X (n x 6), u, rw given as CUDA tensors."""
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double(0)
+    pf = ctypes.POINTER(ctypes.c_float)
+    _check(load().su_mlp_loss_grad(th.ctypes.data_as(pf), _ptr(X), _ptr(u), _ptr(rw), int(X.shape[0]),
+                                   ctypes.byref(loss), g.ctypes.data_as(pf)))
+    return loss.value, g
+
+
+def speedup_train_proposal(model, params, a, b, T, p, s, seed, theta, n_train=None, steps=None, batch_paths=None,
+                           lr=None, clip_quantile=None, train_seed=None):
+    """Train the proposal network; returns (trained theta, per-step losses)."""
+    to = TrainOptions()
+    load().su_train_options_default(ctypes.byref(to))
+    for k, v in (("n_train", n_train), ("steps", steps), ("batch_paths", batch_paths), ("lr", lr),
+                 ("clip_quantile", clip_quantile), ("seed", train_seed)):
+        if v is not None:
+            setattr(to, k, v)
+    th = np.array(theta, dtype=np.float32, copy=True)
+    losses = np.zeros(to.steps, dtype=np.float64)
+    pr, npar = _params(params)
+    pf = ctypes.POINTER(ctypes.c_float)
+    _check(load().speedup_train_proposal(_model(model), pr, npar, a, b, T, p, s, int(seed), ctypes.byref(to),
+                                         th.ctypes.data_as(pf), losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return th, losses
 
 
 class Plan:

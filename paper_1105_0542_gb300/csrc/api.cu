@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,7 @@
 #include "mlp.cuh"
 #include "proposal.h"
 #include "sampler.h"
+#include "train.h"
 
 namespace {
 
@@ -957,6 +959,146 @@ extern "C" int speedup_proposal_logweights(int model, const double *params, int 
     cudaFreeAsync(d_flag, st);
     if (e != cudaSuccess) return cuda_fail(e, "proposal per-sample weights");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return SU_OK;
+}
+
+// ------------------------------------------------------- proposal training
+
+extern "C" void su_train_options_default(su_train_options *t) {
+    if (!t) return;
+    std::memset(t, 0, sizeof *t);
+    t->n_train = 1000000;
+    t->steps = 2000;
+    t->batch_paths = 512;
+    t->lr = 1e-3;
+    t->clip_quantile = 0.999;
+    t->seed = 1;
+}
+
+extern "C" int su_mlp_loss_grad(const float *theta, const float *d_X, const float *d_u, const float *d_rw,
+                                int64_t n, double *loss, float *grad) {
+    if (!theta || !d_X || !d_u || !d_rw || !loss || !grad || n < 1 || n > (1 << 22))
+        return fail(SU_EINVAL, "bad arguments");
+    const int R = (int)((n + 31) / 32 * 32);
+    su::train::Workspace ws;
+    CU(ws.reserve(R), "training workspace");
+    cudaStream_t st = nullptr;
+    double norm = 0;
+    {
+        std::vector<float> rw((size_t)n);
+        CU(cudaMemcpy(rw.data(), d_rw, (size_t)n * 4, cudaMemcpyDeviceToHost), "read weights");
+        for (float v : rw) norm += v;
+    }
+    if (!(norm > 0)) return fail(SU_EINVAL, "row weights must have a positive sum");
+    CU(cudaMemcpyAsync(ws.theta, theta, (size_t)su::mlp::kParams * 4, cudaMemcpyHostToDevice, st), "upload theta");
+    CU(su::train::rows_from_features(ws, d_X, d_u, d_rw, (int)n, R, st), "rows");
+    CU(su::train::loss_grad(ws, R, 1.0 / norm, true, st), "loss and gradient");
+    CU(cudaMemcpyAsync(grad, ws.grad, (size_t)su::mlp::kParams * 4, cudaMemcpyDeviceToHost, st), "read gradient");
+    CU(cudaMemcpyAsync(loss, ws.loss, 8, cudaMemcpyDeviceToHost, st), "read loss");
+    CU(cudaStreamSynchronize(st), "training step");
+    return SU_OK;
+}
+
+extern "C" int speedup_train_proposal(int model, const double *params, int n_params, double a, double b, double T,
+                                      int p, int s, uint64_t seed, const su_train_options *topt, float *theta,
+                                      double *loss_out) {
+    if (!theta) return fail(SU_EINVAL, "theta missing");
+    su_train_options to;
+    su_train_options_default(&to);
+    if (topt) to = *topt;
+    if (s < 2 || s > 6) return fail(SU_ENOTSUP, "training supports 2 <= s <= 6");
+    if (to.n_train < 64 || to.n_train > (1LL << 26)) return fail(SU_EINVAL, "n_train must be in 64..2^26");
+    if (to.steps < 1 || to.batch_paths < 32 || to.batch_paths % 32 != 0 || to.batch_paths > 16384)
+        return fail(SU_EINVAL, "steps >= 1, batch_paths a multiple of 32 in 32..16384");
+    if (!(to.lr > 0) || !(to.clip_quantile > 0 && to.clip_quantile <= 1)) return fail(SU_EINVAL, "bad lr or clip");
+    const int N = 1 << s, np1 = N + 1;
+    // 1. plain single-precision paths and their top-level weights
+    su_options o;
+    su_options_default(&o);
+    o.precision = SU_FP32;
+    o.hierarchy = 1;
+    o.n_blocks = 1;
+    su_plan *pl = nullptr;
+    int rc = su_plan_create(model, params, n_params, a, b, T, p, s, to.n_train, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    float *d_paths = nullptr;
+    double *d_w = nullptr;
+    int *d_flag = nullptr, *d_ids = nullptr;
+    float *d_sig = nullptr;
+    struct Free {
+        std::vector<void *> v;
+        ~Free() { for (void *q : v) cudaFree(q); }
+    } fr;
+    CU(cudaMalloc(&d_paths, (size_t)to.n_train * np1 * 4), "cudaMalloc(paths)");
+    fr.v.push_back(d_paths);
+    CU(cudaMalloc(&d_w, (size_t)to.n_train * s * 8), "cudaMalloc(weights)");
+    fr.v.push_back(d_w);
+    CU(cudaMalloc(&d_flag, 4), "cudaMalloc(flag)");
+    fr.v.push_back(d_flag);
+    CU(cudaMalloc(&d_ids, (size_t)to.batch_paths * 4), "cudaMalloc(ids)");
+    fr.v.push_back(d_ids);
+    CU(cudaMalloc(&d_sig, 16 * 4), "cudaMalloc(sigma)");
+    fr.v.push_back(d_sig);
+    su::SamplerParams P = pl->P;
+    P.w_out = d_w;
+    P.q_out = d_paths;
+    P.flags = d_flag;
+    P.partial = nullptr;
+    const size_t smem = su::sampler_smem_bytes(P, SU_FP32);
+    if (su::sampler_occupancy(P, SU_FP32, smem) < 1) return fail(SU_ECUDA, "sampler not resident");
+    CU(cudaMemset(d_flag, 0, 4), "clear flag");
+    CU(su::launch_sampler(P, SU_FP32, pl->grid, smem, nullptr), "path sampling");
+    std::vector<double> w((size_t)to.n_train * s);
+    CU(cudaMemcpy(w.data(), d_w, w.size() * 8, cudaMemcpyDeviceToHost), "read weights");
+    // 2. training weights: top-level log-weights clipped at a quantile (the
+    //    weighted likelihood of rare huge weights would fit one path), then
+    //    minibatches drawn in proportion to them
+    std::vector<double> wt((size_t)to.n_train);
+    for (int64_t i = 0; i < to.n_train; ++i) wt[(size_t)i] = w[(size_t)i * s + (s - 1)];
+    std::vector<double> srt = wt;
+    const size_t qi = std::min(srt.size() - 1, (size_t)(to.clip_quantile * (double)(srt.size() - 1)));
+    std::nth_element(srt.begin(), srt.begin() + qi, srt.end());
+    const double cap = srt[qi];
+    double mx = -INFINITY;
+    for (double &v : wt) {
+        if (!std::isfinite(v) && v > 0) return fail(SU_ENONFINITE, "a training weight is +Inf or NaN");
+        v = std::min(v, cap);
+        mx = std::max(mx, v);
+    }
+    std::vector<double> cdf(wt.size());
+    double acc = 0;
+    for (size_t i = 0; i < wt.size(); ++i) {
+        acc += std::isfinite(wt[i]) ? std::exp(wt[i] - mx) : 0.0;
+        cdf[i] = acc;
+    }
+    if (!(acc > 0)) return fail(SU_ENONFINITE, "all training weights vanish");
+    // 3. Adam on minibatches of batch_paths paths x (N-1) midpoints
+    const int R = to.batch_paths * (N - 1);
+    su::train::Workspace ws;
+    CU(ws.reserve(R), "training workspace");
+    float sig[16] = {0};
+    for (int n = 1; n <= s; ++n) sig[n] = (float)std::sqrt(T / std::ldexp(1.0, n + 1));
+    CU(cudaMemcpy(d_sig, sig, sizeof sig, cudaMemcpyHostToDevice), "upload sigma");
+    CU(cudaMemcpy(ws.theta, theta, (size_t)su::mlp::kParams * 4, cudaMemcpyHostToDevice), "upload theta");
+    CU(cudaMemset(ws.m, 0, (size_t)su::mlp::kParams * 8), "clear moments");   // m and v are adjacent
+    CU(su::train::fill(ws.rw, 1.0f, R, nullptr), "row weights");
+    std::mt19937_64 rng(to.seed);
+    std::uniform_real_distribution<double> uni(0.0, acc);
+    std::vector<int> ids((size_t)to.batch_paths);
+    for (int t = 1; t <= to.steps; ++t) {
+        for (int k = 0; k < to.batch_paths; ++k)
+            ids[(size_t)k] = (int)(std::upper_bound(cdf.begin(), cdf.end(), uni(rng)) - cdf.begin());
+        for (int &k : ids) k = std::min(k, (int)to.n_train - 1);
+        CU(cudaMemcpy(d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice), "upload ids");
+        CU(su::train::build_rows(ws, d_paths, np1, d_ids, to.batch_paths, (float)a, (float)b, (float)T, s, d_sig,
+                                 nullptr),
+           "rows");
+        CU(su::train::loss_grad(ws, R, 1.0 / R, true, nullptr), "loss and gradient");
+        CU(su::train::adam_step(ws, t, (float)to.lr, nullptr), "adam");
+        if (loss_out) CU(cudaMemcpy(&loss_out[t - 1], ws.loss, 8, cudaMemcpyDeviceToHost), "read loss");
+    }
+    CU(cudaMemcpy(theta, ws.theta, (size_t)su::mlp::kParams * 4, cudaMemcpyDeviceToHost), "read theta");
     return SU_OK;
 }
 

@@ -212,7 +212,7 @@ template <typename R, int RING, int F>
 __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCfg<R> &pc,
                                             const R *__restrict__ tab, R *__restrict__ qc,
                                             double *__restrict__ zz, const Stream<R> &st,
-                                            R *__restrict__ wout, int wstride) {
+                                            R *__restrict__ wout, int wstride, float *qout = nullptr) {
     constexpr int NF = 1 << F;
     const int S = pc.S;
     const int C = 1 << (S - F);
@@ -297,6 +297,11 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
                 q[idx] = fma(sg, z, (R)0.5 * (q[idx - h] + q[idx + h]));
             }
         }
+        if (qout) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) qout[c * NF + k] = (float)q[k];
+            if (c == C - 1) qout[C * NF] = (float)q[NF];
+        }
         // top level: every slice of the segment; then the coarser levels
         acc[0] += level_sum<R, RING, NF, 1>(q, tab, P, alpha);
         if (hier) segment_levels<R, RING, F, 1>(acc, q, tab, P, alpha, S);
@@ -334,13 +339,13 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
 template <typename R, int RING>
 __device__ __forceinline__ void sample_path_any(int F, const SamplerParams &P, const PathCfg<R> &pc,
                                                 const R *tab, R *qc, double *zz, const Stream<R> &st,
-                                                R *wout, int wstride) {
+                                                R *wout, int wstride, float *qout = nullptr) {
     switch (F) {
-        case 1: sample_path<R, RING, 1>(P, pc, tab, qc, zz, st, wout, wstride); break;
-        case 2: sample_path<R, RING, 2>(P, pc, tab, qc, zz, st, wout, wstride); break;
-        case 3: sample_path<R, RING, 3>(P, pc, tab, qc, zz, st, wout, wstride); break;
-        case 4: sample_path<R, RING, 4>(P, pc, tab, qc, zz, st, wout, wstride); break;
-        default: sample_path<R, RING, 5>(P, pc, tab, qc, zz, st, wout, wstride); break;
+        case 1: sample_path<R, RING, 1>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 2: sample_path<R, RING, 2>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 3: sample_path<R, RING, 3>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 4: sample_path<R, RING, 4>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        default: sample_path<R, RING, 5>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
     }
 }
 
@@ -461,7 +466,8 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
             R wloc[SU_MAX_S];
             R *wout = per_sample ? wloc : sw + t;
             const int wstride = per_sample ? 1 : chunk;
-            sample_path_any<R, RING>(P.F, P, pc, tab, qc, zz, st, wout, wstride);
+            float *qout = (per_sample && P.q_out) ? P.q_out + (start + t) * (int64_t)((1 << P.S) + 1) : nullptr;
+            sample_path_any<R, RING>(P.F, P, pc, tab, qc, zz, st, wout, wstride, qout);
             bool bad = false;
             for (int d = 0; d < L; ++d) {
                 const R w = wout[d * wstride];

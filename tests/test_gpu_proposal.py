@@ -125,3 +125,55 @@ def test_proposal_estimate_is_unbiased():
         assert abs(r[lev]["amp"] - ref) <= 3 * sig, (lev, r[lev]["amp"], ref, sig)
     plain = su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 4, 400_000, 17, precision="fp32", n_blocks=20)
     assert r[4]["ess"] < plain[4]["ess"]   # a random network is a worse proposal than the bridge
+
+
+def test_training_gradient_matches_oracle():
+    """The tensor-core forward/backward (bfloat16 operands, float accumulation)
+    against the oracle's double-precision loss and gradient."""
+    th = _theta(21, 1.0)
+    rng = np.random.default_rng(3)
+    n = 1000
+    X = np.stack([np.full(n, -1.0), np.full(n, 1.0), np.full(n, 5.0), rng.integers(1, 7, n) / 6,
+                  rng.normal(0, 1.2, n), rng.normal(0, 1.2, n)], axis=1)
+    u = rng.normal(0, 1.0, n)
+    rw = rng.uniform(0.2, 2.0, n)
+    dev = lambda v: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous()
+    L, g = su.su_mlp_loss_grad(th, dev(X), dev(u), dev(rw))
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)
+    Lr, gr = pr.loss_and_grad(f32(th), f32(X), f32(u), f32(rw))
+    assert L == pytest.approx(Lr, rel=2e-2, abs=2e-3)
+    g = g.astype(np.float64)
+    cos = float(g @ gr / (np.linalg.norm(g) * np.linalg.norm(gr)))
+    assert cos >= 0.998
+    # every layer's block, relative to its own size
+    k = 0
+    for o, i in pr.SIZES:
+        for size in (o * i, o):
+            blk, ref = g[k:k + size], gr[k:k + size]
+            k += size
+            assert np.linalg.norm(blk - ref) <= 0.06 * np.linalg.norm(ref) + 1e-7, (o, i, size)
+
+
+def test_training_lowers_the_loss():
+    th0 = pr.init(5).astype(np.float32)
+    th, losses = su.speedup_train_proposal("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 77, th0, n_train=200_000,
+                                           steps=400, batch_paths=256, lr=1e-3)
+    assert np.isfinite(losses).all()
+    assert losses[-50:].mean() < losses[:10].mean() - 0.05
+    assert np.abs(th - th0).max() > 1e-3
+
+
+def test_trained_proposal_is_unbiased_and_better():
+    """Trained on the harmonic oscillator, the proposal still reproduces the
+    exact discretized amplitude (exact reweighting) and has a larger effective
+    sample size than the bridge."""
+    th0 = pr.init(6).astype(np.float32)
+    th, losses = su.speedup_train_proposal("ho", [1.0], 0.0, 1.0, 2.0, 4, 6, 3, th0, n_train=200_000,
+                                           steps=600, batch_paths=256, lr=1e-3)
+    P = su.Proposal(th)
+    r = su.speedup_amplitude_proposal("ho", [1.0], 0.0, 1.0, 2.0, 4, 6, 400_000, 11, P, n_blocks=20)
+    plain = su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 2.0, 4, 6, 400_000, 12, precision="fp32", n_blocks=20)
+    ref = exact.ho_discretized(4, 64, 0.0, 1.0, 2.0)
+    sig = max(r[6]["err"], r[6]["err_naive"])
+    assert abs(r[6]["amp"] - ref) <= 3 * sig
+    assert r[6]["ess"] > plain[6]["ess"]
