@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-API pass")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched amplitude-matrix entry")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal entry")
     ap.add_argument("--profile", choices=["fp64", "fp32"], default=None,
                     help="profiling case: one warm-up and one timed execute of a small plan "
                          "(level --profile-p of the sweep, s = 10, --profile-n samples); no JSON line")
@@ -297,6 +298,9 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batched(su, torch, dev, stream, flush)
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(su, torch)
 
     if rank != 0:
         if dist is not None:
@@ -333,7 +337,7 @@ def run_ours(args):
                                "speedup": (ttr["fp64"] / ttr["fp32"]) if "fp64" in ttr and "fp32" in ttr else None,
                                "method": "per-sample cost x (rel_err/1e-4)^2 from the 1e7-sample run"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
-        "batched_amplitude_matrix": batched,
+        "batched_amplitude_matrix": batched, "learned_proposal": learned,
         "clocks": clock_info,
     }
     print(json.dumps(line))
@@ -369,6 +373,57 @@ def run_batched(su, torch, dev, stream, flush):
             "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "graph_launches": n,
             "plan_create_s": create_s, "median_rel_err": rel[len(rel) // 2] if rel else None,
             "dtype": "f32 W_p, f64 reductions"}
+
+
+def run_learned(su, torch):
+    """The learned proposal on the double well h = 5, T = 5, p = 12, N = 64:
+    train on plain single-precision paths, then estimate A_64 with the plain
+    sampler and with the proposal (same sample count, different seeds) and
+    compare the time to a relative statistical error of 1e-4."""
+    import numpy as np
+    x = workloads.CONFIG5
+    rng = np.random.default_rng(0)
+    sizes = [(128, 6), (128, 128), (128, 128), (2, 128)]
+    theta = []
+    for li, (o, i) in enumerate(sizes):
+        bnd = 1.0 / np.sqrt(i)
+        if li == len(sizes) - 1:
+            theta += [np.zeros(o * i), np.zeros(o)]
+        else:
+            theta += [rng.uniform(-bnd, bnd, o * i), rng.uniform(-bnd, bnd, o)]
+    theta = np.concatenate(theta).astype(np.float32)
+    n_train = 1_000_000
+    t0 = time.perf_counter()
+    th, losses = su.speedup_train_proposal(x.model, x.params, x.a, x.b, x.T, x.p, x.s, x.seed, theta,
+                                           n_train=n_train, steps=2000, batch_paths=512, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    P = su.Proposal(th)
+    n = 1_000_000
+    out = {}
+    for name, fn in (("plain", lambda: su.speedup_amplitude(x.model, x.params, x.a, x.b, x.T, x.p, x.s, n, 101,
+                                                            precision="fp32", n_blocks=100)),
+                     ("learned", lambda: su.speedup_amplitude_proposal(x.model, x.params, x.a, x.b, x.T, x.p, x.s,
+                                                                       n, 102, P, n_blocks=100))):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        top = r[x.s]
+        out[name] = {"s": dt, "amp": top["amp"], "rel_err": top["rel_err"], "ess": top["ess"],
+                     "max_share": top["max_share"],
+                     "time_to_rel_1e-4_s": dt * (top["rel_err"] / 1e-4) ** 2 if top["rel_err"] == top["rel_err"] else None}
+    macs = (2 ** x.s - 1) * (6 * 128 + 2 * 128 * 128 + 128 * 2)
+    return {"instance": "double well h=5, T=5, a=-1, b=1, p=12, N=64", "samples": n,
+            "train": {"paths": n_train, "steps": 2000, "batch_paths": 512, "seconds": train_s,
+                      "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())},
+            "plain": out["plain"], "learned": out["learned"],
+            "speedup_time_to_1e-4": (out["plain"]["time_to_rel_1e-4_s"] / out["learned"]["time_to_rel_1e-4_s"]
+                                     if out["plain"]["time_to_rel_1e-4_s"] and out["learned"]["time_to_rel_1e-4_s"]
+                                     else None),
+            "inference": {"macs_per_path": macs, "s_per_path": out["learned"]["s"] / n},
+            "note": "wall-clock through speedup_amplitude[_proposal] (host API, includes plan set-up)"}
 
 
 def run_profile(args):
