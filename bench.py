@@ -430,8 +430,8 @@ def run_learned(su, torch):
     is added because at T = 5 the truncated W_12 is unbounded below at large
     |x| and the plain estimate is dominated by single paths."""
     x = workloads.CONFIG5
-    cases = [_learned_case(su, torch, x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, x.seed, 1_000_000, 1_000_000),
-             _learned_case(su, torch, x.model, list(x.params), x.a, x.b, 1.0, x.p, x.s, x.seed, 1_000_000, 1_000_000)]
+    cases = [_learned_case(su, torch, x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, x.seed, x.n_mc, 1_000_000),
+             _learned_case(su, torch, x.model, list(x.params), x.a, x.b, 1.0, x.p, x.s, x.seed, x.n_mc, 1_000_000)]
     macs = (2 ** x.s - 1) * (6 * 128 + 2 * 128 * 128 + 128 * 2)
     return {"cases": cases,
             "inference": {"macs_per_path": macs, "s_per_path": cases[0]["learned"]["s"] / cases[0]["samples"]},

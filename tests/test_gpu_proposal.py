@@ -177,3 +177,22 @@ def test_trained_proposal_is_unbiased_and_better():
     sig = max(r[6]["err"], r[6]["err_naive"])
     assert abs(r[6]["amp"] - ref) <= 3 * sig
     assert r[6]["ess"] > plain[6]["ess"]
+
+
+def test_learned_proposal_recovers_the_continuum_double_well_amplitude():
+    """Double well h = 5 at T = 5 (p = 12, N = 64): the bridge's estimate is
+    ruled by rare paths on which the truncated W_p is hugely negative, while
+    the trained proposal never visits them and gives the continuum amplitude
+    of the sinc-DVR diagonalisation (the discretization error at p = 12 is far
+    below the statistical one)."""
+    th0 = pr.init(8).astype(np.float32)
+    th, losses = su.speedup_train_proposal("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1234, th0, n_train=1_000_000,
+                                           steps=2000, batch_paths=512, lr=1e-3)
+    assert np.isfinite(losses).all()
+    P = su.Proposal(th)
+    r = su.speedup_amplitude_proposal("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1_000_000, 99, P, n_blocks=50)
+    ref, _ = exact.dvr_amplitude(lambda x: 5.0 * (x * x - 1) ** 2, -1.0, 1.0, 5.0, L=8.0, dx=0.02)
+    top = r[6]
+    sig = max(top["err"], top["err_naive"])
+    assert top["ess"] > 1e4 and sig < 0.02 * ref
+    assert abs(top["amp"] - ref) <= 4 * sig, (top["amp"], ref, sig)

@@ -86,5 +86,6 @@ def config4(n_mc=100_000_000):
     return out
 
 
-# 5: the learned-proposal instance: double well h = 5, T = 5, p = 12, N = 64.
+# 5: the learned-proposal instance: double well h = 5, T = 5, p = 12, N = 64;
+# n_mc = 1e7 is the number of plain paths the proposal is trained on.
 CONFIG5 = Instance("dw", (5.0,), -1.0, 1.0, 5.0, 12, 6, 10_000_000, 1234, 64)
