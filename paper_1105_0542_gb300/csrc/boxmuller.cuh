@@ -14,8 +14,11 @@
 //    (c_32 = 1 exactly), r = (m - c_j)/c_j with |r| <= 1/192, and
 //    ln u1 = e ln 2 + ln c_j + ln(1 + r), ln(1 + r) by its Taylor series to
 //    r^8 (truncation below 2^-60 relative).
-//  * r = sqrt(v): two Newton steps for sqrt from a single-precision
-//    reciprocal-square-root seed.
+//  * r = sqrt(v): two Newton steps for sqrt from the approximate reciprocal
+//    square root (rsqrt.approx.f64).
+//  * the exponent and mantissa of u1 come from the 53-bit integer itself and
+//    the integer-to-double steps use bit patterns, so that the FP64 pipe only
+//    runs the arithmetic (about 34 operations per pair).
 //  * cos/sin(theta): the accurate-table method (Gal; Tang): theta =
 //    a_i + delta with a_i = 2 pi (i + 1/2)/256 from the top 8 bits of the
 //    53-bit integer behind u2, |delta| <= pi/256 from the remaining bits,
@@ -34,17 +37,29 @@ namespace {
 
 constexpr int kLogNodes = 97;    // c_j = 3/4 + j/128, j = 0..96
 constexpr int kTrigNodes = 256;  // a_i = 2 pi (i + 1/2) / 256
+constexpr int kExpNodes = 56;    // -2 e ln 2, e = 0..-55
+
+struct LogNode {
+    double l2;                   // -2 ln c_j
+    double inv;                  // 1 / c_j
+    double c;                    // c_j
+};
 
 struct BMTables {
-    double2 lg[kLogNodes];     // (-2 ln c_j, 1 / c_j)
-    double2 tr[kTrigNodes];    // (cos a_i, sin a_i)
+    LogNode lg[kLogNodes];
+    double e2[kExpNodes];        // -2 ln 2 * e for e = -k, k = 0..55
+    double2 tr[kTrigNodes];      // (cos a_i, sin a_i)
 };
 
 __device__ __forceinline__ void bm_tables_init(BMTables *t, int tid, int nthreads) {
     for (int j = tid; j < kLogNodes; j += nthreads) {
         const double c = 0.75 + j * (1.0 / 128.0);
-        t->lg[j] = make_double2(-2.0 * log(c), 1.0 / c);
+        t->lg[j].l2 = -2.0 * log(c);
+        t->lg[j].inv = 1.0 / c;
+        t->lg[j].c = c;
     }
+    for (int k = tid; k < kExpNodes; k += nthreads)
+        t->e2[k] = 2.0 * k * 0.69314718055994530942;   // -2 ln 2 * (-k)
     for (int i = tid; i < kTrigNodes; i += nthreads) {
         double s, c;
         sincospi((i + 0.5) / 128.0, &s, &c);
@@ -52,11 +67,28 @@ __device__ __forceinline__ void bm_tables_init(BMTables *t, int tid, int nthread
     }
 }
 
-// -2 ln(u1) for u1 in (0, 1] (u1 normal)
-__device__ __forceinline__ double bm_minus2log(double u1, const BMTables *__restrict__ t) {
-    const long long bits = __double_as_longlong(u1);
-    int e = (int)(bits >> 52) - 1023;
-    const long long mant = bits & 0x000FFFFFFFFFFFFFLL;
+// -2 ln(u1) for u1 = ((double)a + 1/2) 2^-53, a < 2^53, taking the binary
+// exponent and mantissa of u1 from the integer a (the same rounding to
+// nearest even as forming the double).
+__device__ __forceinline__ double bm_minus2log(uint64_t a, const BMTables *__restrict__ t) {
+    const uint64_t v = 2 * a + 1;               // u1 = v 2^-54, v odd
+    int e;                                      // u1 = 2^e (1 + mant 2^-52)
+    long long mant;
+    if (v < (1ULL << 53)) {                     // exact
+        const int pos = 63 - __clzll((long long)v);
+        e = pos - 54;
+        mant = (long long)((v << (52 - pos)) & ((1ULL << 52) - 1));
+    } else {                                    // 54 bits: the last one is a tie
+        uint64_t k = v >> 1;
+        k += k & 1;                             // to even
+        if (k >> 53) {
+            e = 0;
+            mant = 0;
+        } else {
+            e = -1;
+            mant = (long long)(k - (1ULL << 52));
+        }
+    }
     long long mbits;
     int j;
     if (mant >= (1LL << 51)) {           // m in [1.5, 2): use m/2 in [0.75, 1)
@@ -68,9 +100,8 @@ __device__ __forceinline__ double bm_minus2log(double u1, const BMTables *__rest
         j = 32 + (int)((mant + (1LL << 44)) >> 45);
     }
     const double m = __longlong_as_double(mbits);
-    const double2 node = t->lg[j];
-    const double c = 0.75 + j * (1.0 / 128.0);
-    const double r = (m - c) * node.y;   // m - c is exact
+    const LogNode node = t->lg[j];
+    const double r = (m - node.c) * node.inv;   // m - c is exact
     // -2 ln(1 + r) = r * sum_{k>=0} (-2) (-r)^k / (k + 1), to r^8
     double p = 2.0 / 8.0;
     p = fma(p, r, -2.0 / 7.0);
@@ -80,16 +111,16 @@ __device__ __forceinline__ double bm_minus2log(double u1, const BMTables *__rest
     p = fma(p, r, -2.0 / 3.0);
     p = fma(p, r, 2.0 / 2.0);
     p = fma(p, r, -2.0);
-    const double M2LN2 = -1.3862943611198906188;   // -2 ln 2
-    return fma(r, p, fma((double)e, M2LN2, node.x));
+    return fma(r, p, t->e2[-e] + node.l2);     // e in -54..0
 }
 
-// sqrt(v), v >= 0: Newton steps s <- s + (v - s^2) h from a float seed
+// sqrt(v), v >= 0: Newton steps s <- s + (v - s^2) h from the hardware's
+// approximate reciprocal square root (about 23 correct bits)
 __device__ __forceinline__ double bm_sqrt(double v) {
-    const float y = rsqrtf(fmaxf((float)v, 1e-30f));
-    const double yd = (double)y;
-    const double h = 0.5 * yd;
-    double s = v * yd;
+    double y;
+    asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(fmax(v, 1e-300)));
+    const double h = 0.5 * y;
+    double s = v * y;
     s = fma(fma(-s, s, v), h, s);
     s = fma(fma(-s, s, v), h, s);
     return s;
@@ -99,9 +130,12 @@ __device__ __forceinline__ double bm_sqrt(double v) {
 __device__ __forceinline__ void bm_rotate(double r, uint64_t b, const BMTables *__restrict__ t,
                                           double &z0, double &z1) {
     const int i = (int)(b >> 45);
+    // k = (b mod 2^45) - 2^44 as a double without a conversion: the bits of
+    // 2^52 + 2^51 + k, minus that offset (exact for |k| < 2^51)
     const long long k = (long long)(b & ((1ULL << 45) - 1)) - (1LL << 44);
+    const double kd = __longlong_as_double(0x4338000000000000LL + k) - 6755399441055744.0;
     const double C = 6.283185307179586477 * 0x1p-53;    // 2 pi / 2^53
-    const double d = fma((double)k, C, 0.5 * C);        // theta - a_i, |d| <= pi/256
+    const double d = fma(kd, C, 0.5 * C);               // theta - a_i, |d| <= pi/256
     const double d2 = d * d;
     const double cm1 = d2 * fma(fma(d2, -1.0 / 720.0, 1.0 / 24.0), d2, -0.5);          // cos d - 1
     const double sd = fma(d * d2, fma(fma(d2, -1.0 / 5040.0, 1.0 / 120.0), d2, -1.0 / 6.0), d);  // sin d

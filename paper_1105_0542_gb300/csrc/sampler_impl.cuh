@@ -57,8 +57,7 @@ struct Normal<double> {
     static __device__ __forceinline__ void pair(uint4 w, const BMTables *t, double &z0, double &z1) {
         const uint64_t a = ((uint64_t)w.x << 21) | (w.y >> 11);
         const uint64_t b = ((uint64_t)w.z << 21) | (w.w >> 11);
-        const double u1 = ((double)a + 0.5) * 0x1p-53;
-        bm_rotate(bm_sqrt(bm_minus2log(u1, t)), b, t, z0, z1);
+        bm_rotate(bm_sqrt(bm_minus2log(a, t)), b, t, z0, z1);
     }
 };
 
