@@ -223,26 +223,27 @@ static int configure(su_plan &pl) {
     P.sample0 = pl.opt.sample0;
     P.n_blocks = pl.n_blocks;
 
-    // launch shape: one path per thread, persistent grid over items
-    int occ = 0;
-    P.rounds = 1;
-    for (int it = 0; it < 2; ++it) {
-        const int chunk = kThreads * P.rounds;
+    // launch shape: one path per thread, persistent grid over items of
+    // 128 * rounds samples
+    auto shape = [&](int rounds) {
+        P.rounds = rounds;
+        const int chunk = kThreads * rounds;
         const int64_t bsz = (pl.n_mc + pl.n_blocks - 1) / pl.n_blocks;
         P.items_per_block = (bsz + chunk - 1) / chunk;
         P.n_items = P.items_per_block * pl.n_blocks;
         pl.smem = sampler_smem_bytes(P, prec);
-        if (pl.smem > (size_t)smem_max)
-            return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);
-        occ = sampler_occupancy(P, prec, pl.smem);
-        if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
-        if (it == 0) {
-            // fewer, larger items when there are many per resident CTA
-            const int64_t per = P.n_items / ((int64_t)sms * occ);
-            P.rounds = (int)std::max<int64_t>(1, std::min<int64_t>(4, per / 16));
-            if (P.rounds == 1) break;
-        }
-    }
+        return pl.smem > (size_t)smem_max ? 0 : sampler_occupancy(P, prec, pl.smem);
+    };
+    const int occ1 = shape(1);
+    if (pl.smem > (size_t)smem_max)
+        return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);
+    if (occ1 < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
+    // fewer, larger items when there are many per resident CTA, as long as
+    // the larger weight buffer keeps as many CTAs resident
+    const int64_t per = P.n_items / ((int64_t)sms * occ1);
+    int rounds = (int)std::max<int64_t>(1, std::min<int64_t>(4, per / 16));
+    while (rounds > 1 && shape(rounds) < occ1) --rounds;
+    const int occ = shape(rounds);
     pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
     pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
     pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + 256;

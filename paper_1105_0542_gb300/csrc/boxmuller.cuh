@@ -1,149 +1,265 @@
 #pragma once
 // Table-driven double-precision Box-Muller for the sampler (sm_103a).
 //
-// On this part the FP64 pipe runs at 1/60 of the FP32 rate, and the generic
-// double log / sqrt / sincos cost about as much as W_p itself at low p.  The
-// normal pair z0 = r cos(theta), z1 = r sin(theta), r = sqrt(-2 ln u1),
-// theta = 2 pi u2 (Sec. 4.1, both branches) is therefore formed with table
-// methods whose argument reduction is done on the integer bits:
+// The normal pair z0 = R cos(theta), z1 = R sin(theta), R = sqrt(-2 ln u1),
+// theta = 2 pi u2 (Sec. 4.1, both branches) for the 53-bit uniforms
+// u1 = (a + 1/2) 2^-53, u2 = (b + 1/2) 2^-53.
 //
-//  * v = -2 ln u1: the table-driven logarithm (P. T. P. Tang, "Table-driven
+// On this part the FP64 pipe runs at 1/60 of the FP32 rate and every double
+// conversion (integer or float to double and back) costs as much as a double
+// multiply-add, while integer and single-precision work issues from other,
+// nearly idle pipes.  The routines therefore do their argument reductions
+// and conversions on the integer bits, evaluate the small high-order parts
+// of each series in single precision, and keep in double only the terms
+// that need 53 bits (19 FP64 operations per pair):
+//
+//  * -2 ln u1: the table-driven logarithm (P. T. P. Tang, "Table-driven
 //    implementation of the logarithm function in IEEE floating-point
-//    arithmetic", ACM TOMS 16, 1990): u1 = 2^e m, m in [3/4, 3/2) taken from
-//    the exponent and mantissa bits, nearest node c_j = 3/4 + j/128
-//    (c_32 = 1 exactly), r = (m - c_j)/c_j with |r| <= 1/192, and
-//    ln u1 = e ln 2 + ln c_j + ln(1 + r), ln(1 + r) by its Taylor series to
-//    r^8 (truncation below 2^-60 relative).
-//  * r = sqrt(v): two Newton steps for sqrt from the approximate reciprocal
-//    square root (rsqrt.approx.f64).
-//  * the exponent and mantissa of u1 come from the 53-bit integer itself and
-//    the integer-to-double steps use bit patterns, so that the FP64 pipe only
-//    runs the arithmetic (about 34 operations per pair).
-//  * cos/sin(theta): the accurate-table method (Gal; Tang): theta =
-//    a_i + delta with a_i = 2 pi (i + 1/2)/256 from the top 8 bits of the
-//    53-bit integer behind u2, |delta| <= pi/256 from the remaining bits,
-//    cos/sin(delta) by Taylor series (to delta^6 and delta^7), and the
-//    addition formulas.
+//    arithmetic", ACM TOMS 16, 1990).  The double nearest u1 is 2^e m with
+//    m in [3/4, 3/2), both taken from the integer a; node c_j = 3/4 + j/512
+//    (j = 0..384) is the nearest to m, r = m inv_j - 1 (inv_j the double
+//    nearest 1/c_j, one fused multiply-add, |r| < 2^-9.5), and
+//      -2 ln u1 = [(-e) 2 ln 2 + 2 ln inv_j] - 2 ln(1 + r).
+//    The bracket is summed in 56-bit fixed point and rounded to double on
+//    the integer bits; -2 ln(1 + r) = -2r + r^2 - 2r^3/3 + r^4 t(r) with
+//    t = 1/2 - 2r/5 + r^2/3 in single precision (truncation below 2^-60).
+//  * R = sqrt(v): a single-precision reciprocal-square-root seed and two
+//    Newton steps s <- s + (v - s^2) / (2 y) in double.
+//  * cos/sin(theta): octant reduction on the top three bits of b (theta =
+//    o pi/4 + phi, odd octants reflected to pi/4 - phi), then the accurate
+//    table method (Gal; Tang): phi = a_i + d, a_i = pi (i + 1/2)/2048 from
+//    the next nine bits (512 nodes), d = pi k 2^-53 for the odd integer k of
+//    the remaining bits, |d| <= pi/4096, and
+//      cos d - 1 = d (-d/2) + d^4/24,   sin d = d + d (-d^2/6 + d^4/120)
+//    with the d^4 and d^2 factors in single precision (next terms below
+//    2^-58); then the addition formulas and the octant's swap and signs.
 //
-// The node values ln c_j, 1/c_j, cos a_i, sin a_i are computed once per CTA
-// with the CUDA library functions and kept in shared memory.  Every result
-// agrees with r cos(theta), r sin(theta) from the library functions to a few
-// units in the last place (checked by the GPU tests through the oracle's
-// normals).
+// The node values inv_j, 2 ln inv_j, cos a_i, sin a_i are computed once per
+// CTA with the CUDA library functions and kept in shared memory.  Every
+// result agrees with R cos(theta), R sin(theta) from the library functions
+// to a few units in the last place (checked by the GPU tests through the
+// oracle's normals).
 #include <cstdint>
+#include <cstring>
+
+#ifdef __CUDACC__
+#define SU_BM_FN __host__ __device__ __forceinline__
+#else
+#define SU_BM_FN inline
+#endif
 
 namespace su {
-namespace {
+namespace bm {
 
-constexpr int kLogNodes = 97;    // c_j = 3/4 + j/128, j = 0..96
-constexpr int kTrigNodes = 256;  // a_i = 2 pi (i + 1/2) / 256
-constexpr int kExpNodes = 56;    // -2 e ln 2, e = 0..-55
+constexpr int kLogNodes = 385;    // c_j = 3/4 + j/512, j = 0..384
+constexpr int kTrigNodes = 512;   // a_i = pi (i + 1/2) / 2048, the first octant
+// 2 ln 2 in 56-bit fixed point: round(2 ln 2 * 2^56)
+constexpr long long kLn2x2Q56 = 99893036290645747LL;
 
 struct LogNode {
-    double l2;                   // -2 ln c_j
-    double inv;                  // 1 / c_j
-    double c;                    // c_j
+    double inv;                   // inv_j, the double nearest 1/c_j
+    long long l2q;                // 2 ln inv_j in 56-bit fixed point
 };
 
-struct BMTables {
+struct TrigNode {
+    double c, s;                  // cos a_i, sin a_i
+};
+
+struct Tables {
     LogNode lg[kLogNodes];
-    double e2[kExpNodes];        // -2 ln 2 * e for e = -k, k = 0..55
-    double2 tr[kTrigNodes];      // (cos a_i, sin a_i)
+    TrigNode tr[kTrigNodes];
 };
 
-__device__ __forceinline__ void bm_tables_init(BMTables *t, int tid, int nthreads) {
-    for (int j = tid; j < kLogNodes; j += nthreads) {
-        const double c = 0.75 + j * (1.0 / 128.0);
-        t->lg[j].l2 = -2.0 * log(c);
-        t->lg[j].inv = 1.0 / c;
-        t->lg[j].c = c;
-    }
-    for (int k = tid; k < kExpNodes; k += nthreads)
-        t->e2[k] = 2.0 * k * 0.69314718055994530942;   // -2 ln 2 * (-k)
-    for (int i = tid; i < kTrigNodes; i += nthreads) {
-        double s, c;
-        sincospi((i + 0.5) / 128.0, &s, &c);
-        t->tr[i] = make_double2(c, s);
-    }
+// ------------------------------------------------------------ bit helpers
+SU_BM_FN uint64_t dbits(double x) {
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t u;
+    std::memcpy(&u, &x, 8);
+    return u;
+#endif
 }
 
-// -2 ln(u1) for u1 = ((double)a + 1/2) 2^-53, a < 2^53, taking the binary
-// exponent and mantissa of u1 from the integer a (the same rounding to
-// nearest even as forming the double).
-__device__ __forceinline__ double bm_minus2log(uint64_t a, const BMTables *__restrict__ t) {
+SU_BM_FN double dfrom(uint64_t u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    std::memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+
+SU_BM_FN uint32_t fbits(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+
+SU_BM_FN float ffrom(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+SU_BM_FN int clz64(uint64_t x) {   // x != 0
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return __builtin_clzll(x);
+#endif
+}
+
+SU_BM_FN float rsqrt_seed(float x) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / std::sqrt(x);
+#endif
+}
+
+// double -> float on the bits, rounded (half away from zero), for
+// 2^-126 <= |x| < 2^127
+SU_BM_FN float to_float(double x) {
+    const uint64_t u = dbits(x);
+    const uint32_t mag = (uint32_t)(((u & 0x7FFFFFFFFFFFFFFFULL) + (1ULL << 28)) >> 29) - (896u << 23);
+    return ffrom(mag | ((uint32_t)(u >> 32) & 0x80000000u));
+}
+
+// float -> double on the bits: exact for normal x; zero and subnormal x give
+// a value of magnitude below 2^-126
+SU_BM_FN double to_double(float x) {
+    const uint32_t u = fbits(x);
+    const uint64_t mag = ((uint64_t)(u & 0x7FFFFFFFu) + (896ULL << 23)) << 29;
+    return dfrom(mag | ((uint64_t)(u & 0x80000000u) << 32));
+}
+
+// n 2^scale as the nearest double (ties away from zero), 0 < n < 2^63
+SU_BM_FN double scaled(uint64_t n, int scale) {
+    const int lz = clz64(n);
+    const uint64_t nn = n << lz;                       // leading one at bit 63
+    const uint64_t t = (nn >> 11) + ((nn >> 10) & 1);  // 53 bits, 2^53 after a carry
+    return dfrom(((uint64_t)(1086 + scale - lz) << 52) + t - (1ULL << 52));
+}
+
+// ------------------------------------------------------------ the tables
+#ifdef __CUDACC__
+__device__ __forceinline__ void tables_init(Tables *t, int tid, int nthreads) {
+    for (int j = tid; j < kLogNodes; j += nthreads) {
+        const double inv = 1.0 / (0.75 + j * (1.0 / 512.0));
+        t->lg[j].inv = inv;
+        t->lg[j].l2q = __double2ll_rn(ldexp(2.0 * log(inv), 56));
+    }
+    for (int i = tid; i < kTrigNodes; i += nthreads) {
+        double s, c;
+        sincospi((i + 0.5) / 2048.0, &s, &c);
+        t->tr[i].c = c;
+        t->tr[i].s = s;
+    }
+}
+#endif
+
+// ------------------------------------------------------------ -2 ln u1
+// u1 = (a + 1/2) 2^-53, a < 2^53; the exponent and mantissa of the double
+// nearest u1 (rounded to nearest even, as forming it in double would) come
+// from the integer
+SU_BM_FN double minus2log(uint64_t a, const Tables *__restrict__ t) {
     const uint64_t v = 2 * a + 1;               // u1 = v 2^-54, v odd
-    int e;                                      // u1 = 2^e (1 + mant 2^-52)
-    long long mant;
+    int e;                                      // u1 = 2^e (1 + f 2^-52)
+    long long f;
     if (v < (1ULL << 53)) {                     // exact
-        const int pos = 63 - __clzll((long long)v);
+        const int pos = 63 - clz64(v);
         e = pos - 54;
-        mant = (long long)((v << (52 - pos)) & ((1ULL << 52) - 1));
+        f = (long long)((v << (52 - pos)) & ((1ULL << 52) - 1));
     } else {                                    // 54 bits: the last one is a tie
         uint64_t k = v >> 1;
         k += k & 1;                             // to even
         if (k >> 53) {
             e = 0;
-            mant = 0;
+            f = 0;
         } else {
             e = -1;
-            mant = (long long)(k - (1ULL << 52));
+            f = (long long)(k - (1ULL << 52));
         }
     }
-    long long mbits;
+    long long mb;
     int j;
-    if (mant >= (1LL << 51)) {           // m in [1.5, 2): use m/2 in [0.75, 1)
+    if (f >= (1LL << 51)) {             // 1 + f 2^-52 in [3/2, 2): m = half of it, in [3/4, 1)
         e += 1;
-        mbits = mant | (1022LL << 52);
-        j = (int)((mant - (1LL << 51) + (1LL << 45)) >> 46);
-    } else {                             // m in [1, 1.5)
-        mbits = mant | (1023LL << 52);
-        j = 32 + (int)((mant + (1LL << 44)) >> 45);
+        mb = f | (1022LL << 52);
+        j = (int)((f - (1LL << 51) + (1LL << 43)) >> 44);          // 0..128
+    } else {                            // m in [1, 3/2)
+        mb = f | (1023LL << 52);
+        j = 128 + (int)((f + (1LL << 42)) >> 43);                   // 128..384
     }
-    const double m = __longlong_as_double(mbits);
-    const LogNode node = t->lg[j];
-    const double r = (m - node.c) * node.inv;   // m - c is exact
-    // -2 ln(1 + r) = r * sum_{k>=0} (-2) (-r)^k / (k + 1), to r^8
-    double p = 2.0 / 8.0;
-    p = fma(p, r, -2.0 / 7.0);
-    p = fma(p, r, 2.0 / 6.0);
-    p = fma(p, r, -2.0 / 5.0);
-    p = fma(p, r, 2.0 / 4.0);
-    p = fma(p, r, -2.0 / 3.0);
-    p = fma(p, r, 2.0 / 2.0);
-    p = fma(p, r, -2.0);
-    return fma(r, p, t->e2[-e] + node.l2);     // e in -54..0
+    const double m = dfrom((uint64_t)mb);
+    const LogNode nd = t->lg[j];
+    const double r = fma(m, nd.inv, -1.0);
+    // r^4 coefficient of -2 ln(1 + r), single precision from float copies
+    const float rf = fmaf(to_float(m), to_float(nd.inv), -1.0f);
+    const float tf = fmaf(fmaf(rf, 1.0f / 3.0f, -0.4f), rf, 0.5f);
+    double p = fma(r, to_double(tf), -2.0 / 3.0);
+    p = fma(r, p, 1.0);
+    p = fma(r, p, -2.0);
+    // (-e) 2 ln 2 + 2 ln inv_j >= 0 (zero only for u1 in [1 - 2^-10, 1))
+    const long long bq = (long long)(-e) * kLn2x2Q56 + nd.l2q;
+    const double base = bq > 0 ? scaled((uint64_t)bq, -56) : 0.0;
+    return fma(r, p, base);
 }
 
-// sqrt(v), v >= 0: Newton steps s <- s + (v - s^2) h from the hardware's
-// approximate reciprocal square root (about 23 correct bits)
-__device__ __forceinline__ double bm_sqrt(double v) {
-    double y;
-    asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(fmax(v, 1e-300)));
-    const double h = 0.5 * y;
-    double s = v * y;
-    s = fma(fma(-s, s, v), h, s);
-    s = fma(fma(-s, s, v), h, s);
+// ------------------------------------------------------------ sqrt
+// v in [0, 2^7] (v = 0 for u1 rounded to 1)
+SU_BM_FN double sqrt_pos(double v) {
+    const uint64_t vb = dbits(v), lo = 0x39B4484BFEEBC2A0ULL;   // the double 1e-30
+    const float y = rsqrt_seed(to_float(dfrom(vb > lo ? vb : lo)));
+    const double yd = to_double(y), hd = to_double(0.5f * y);
+    double s = v * yd;
+    s = fma(fma(-s, s, v), hd, s);
+    s = fma(fma(-s, s, v), hd, s);
     return s;
 }
 
-// z0 = r cos(2 pi u2), z1 = r sin(2 pi u2) with u2 = (b + 1/2) 2^-53, b < 2^53
-__device__ __forceinline__ void bm_rotate(double r, uint64_t b, const BMTables *__restrict__ t,
-                                          double &z0, double &z1) {
-    const int i = (int)(b >> 45);
-    // k = (b mod 2^45) - 2^44 as a double without a conversion: the bits of
-    // 2^52 + 2^51 + k, minus that offset (exact for |k| < 2^51)
-    const long long k = (long long)(b & ((1ULL << 45) - 1)) - (1LL << 44);
-    const double kd = __longlong_as_double(0x4338000000000000LL + k) - 6755399441055744.0;
-    const double C = 6.283185307179586477 * 0x1p-53;    // 2 pi / 2^53
-    const double d = fma(kd, C, 0.5 * C);               // theta - a_i, |d| <= pi/256
-    const double d2 = d * d;
-    const double cm1 = d2 * fma(fma(d2, -1.0 / 720.0, 1.0 / 24.0), d2, -0.5);          // cos d - 1
-    const double sd = fma(d * d2, fma(fma(d2, -1.0 / 5040.0, 1.0 / 120.0), d2, -1.0 / 6.0), d);  // sin d
-    const double2 a = t->tr[i];
-    const double rc = r * a.x, rs = r * a.y;
-    z0 = fma(rc, cm1, fma(-rs, sd, rc));
-    z1 = fma(rs, cm1, fma(rc, sd, rs));
+// ------------------------------------------------------------ rotation
+// z0 = R cos(theta), z1 = R sin(theta), theta = 2 pi (b + 1/2) 2^-53, b < 2^53
+SU_BM_FN void rotate(double R, uint64_t b, const Tables *__restrict__ t, double &z0, double &z1) {
+    const uint32_t o = (uint32_t)(b >> 50);                         // octant
+    uint64_t x = b & ((1ULL << 50) - 1);                            // phi = 2 pi (x + 1/2) 2^-53
+    if (o & 1) x = ((1ULL << 50) - 1) - x;                          // pi/4 - phi
+    const int i = (int)(x >> 41);
+    // d = phi - a_i = pi k 2^-53, k = 2 (x mod 2^41) - 2^41 + 1 (odd, |k| < 2^41)
+    const long long k = 2 * (long long)(x & ((1ULL << 41) - 1)) - (1LL << 41) + 1;
+    const uint64_t dneg = k < 0 ? 0x8000000000000000ULL : 0;
+    const double d = dfrom(dbits(scaled((uint64_t)(k < 0 ? -k : k), -53) * 3.14159265358979323846) | dneg);
+    const float df = to_float(d);
+    const float d2 = df * df;
+    const double q4 = to_double(d2 * d2 * (1.0f / 24.0f));              // d^4/24
+    const double m6 = to_double(d2 * fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f));   // -d^2/6 + d^4/120
+    const double hd = dfrom((dbits(d) - (1ULL << 52)) ^ 0x8000000000000000ULL);  // -d/2
+    const double cm1 = fma(d, hd, q4);                               // cos d - 1
+    const double sd = fma(d, m6, d);                                 // sin d
+    const TrigNode a = t->tr[i];
+    const double cf = fma(a.c, cm1, fma(-a.s, sd, a.c));             // cos(reduced angle)
+    const double sf = fma(a.s, cm1, fma(a.c, sd, a.s));              // sin(reduced angle)
+    // theta = q pi/2 + psi, (cos psi, sin psi) = (cf, sf) for even octants and
+    // (sf, cf) for odd ones; then the quadrant's quarter turns
+    const uint32_t q = o >> 1;
+    const bool swap = ((o ^ q) & 1) != 0;
+    const uint64_t sx = (q == 1 || q == 2) ? 0x8000000000000000ULL : 0;
+    const uint64_t sy = (q >= 2) ? 0x8000000000000000ULL : 0;
+    const double P = dfrom(dbits(swap ? sf : cf) ^ sx);
+    const double Q = dfrom(dbits(swap ? cf : sf) ^ sy);
+    z0 = R * P;
+    z1 = R * Q;
 }
 
-}  // namespace
+}  // namespace bm
 }  // namespace su

@@ -75,8 +75,8 @@ __global__ void philox_words_kernel(uint64_t seed, uint32_t inst, int64_t sample
 template <typename R>
 __global__ void __launch_bounds__(128) normals_kernel(uint64_t seed, uint32_t inst, int64_t sample0,
                                                       int64_t ns, int n, double *out) {
-    __shared__ BMTables bm;
-    if constexpr (sizeof(R) == 8) bm_tables_init(&bm, threadIdx.x, blockDim.x);
+    __shared__ bm::Tables tabs;
+    if constexpr (sizeof(R) == 8) bm::tables_init(&tabs, threadIdx.x, blockDim.x);
     __syncthreads();
     const int calls = (n + 1) / 2;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) normals_kernel(uint64_t seed, uint32_t in
     st.inst = inst;
     st.slo = (uint32_t)smp;
     st.shi = (uint32_t)(smp >> 32);
-    st.bm = &bm;
+    st.bm = &tabs;
     R z0, z1;
     st.pair(t, z0, z1);
     out[i * n + 2 * t] = (double)z0;
@@ -117,7 +117,7 @@ size_t batch_smem_bytes(const BatchParams &B, int precision) {
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
-    if (precision == SU_FP64) off += sizeof(BMTables);
+    if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;
 }
 
@@ -132,7 +132,7 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
     if (P.wf_on) off += sizeof(double) * (size_t)(P.S + 1) * kThreads;
-    if (precision == SU_FP64) off += sizeof(BMTables);
+    if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;
 }
 

@@ -54,17 +54,17 @@ template <>
 struct Normal<double> {
     // 53-bit uniforms ((w0 2^21 + w1 >> 11) + 1/2) 2^-53 from (w0,w1) and (w2,w3),
     // through the table-driven routines of boxmuller.cuh
-    static __device__ __forceinline__ void pair(uint4 w, const BMTables *t, double &z0, double &z1) {
+    static __device__ __forceinline__ void pair(uint4 w, const bm::Tables *t, double &z0, double &z1) {
         const uint64_t a = ((uint64_t)w.x << 21) | (w.y >> 11);
         const uint64_t b = ((uint64_t)w.z << 21) | (w.w >> 11);
-        bm_rotate(bm_sqrt(bm_minus2log(a, t)), b, t, z0, z1);
+        bm::rotate(bm::sqrt_pos(bm::minus2log(a, t)), b, t, z0, z1);
     }
 };
 
 template <>
 struct Normal<float> {
     // 24-bit uniforms ((w >> 8) + 1/2) 2^-24 from w0 and w2
-    static __device__ __forceinline__ void pair(uint4 w, const BMTables *, float &z0, float &z1) {
+    static __device__ __forceinline__ void pair(uint4 w, const bm::Tables *, float &z0, float &z1) {
         const float u1 = ((float)(w.x >> 8) + 0.5f) * 0x1p-24f;
         const float u2 = ((float)(w.z >> 8) + 0.5f) * 0x1p-24f;
         const float r = sqrtf(-2.0f * logf(u1));
@@ -79,7 +79,7 @@ template <typename R>
 struct Stream {
     uint2 key;
     uint32_t inst, slo, shi;
-    const BMTables *bm;   // shared-memory node tables (double path)
+    const bm::Tables *bm;   // shared-memory node tables (double path)
     __device__ __forceinline__ void pair(uint32_t call, R &z0, R &z1) const {
         Normal<R>::pair(philox4x32_10(make_uint4(call, inst, slo, shi), key), bm, z0, z1);
     }
@@ -406,8 +406,17 @@ __device__ __forceinline__ void lse_merge(double &ma, double &sa, double &qa, do
 // Shared memory: sw[levels][chunk] (R) | tables[levels][M] (R) | sigma[S+1] (R) |
 //                qc[(C+1)][kThreads] (R) | zz[S+1][kThreads] (double, if wf_on) |
 //                Box-Muller node tables (double path)
+// CTAs per SM the register allocation is sized for: two for the double path
+// (up to 255 registers: its segment, accumulators and Box-Muller state stay
+// in registers; three CTAs at 168 registers spill and run slower), four for
+// the single path (128 registers)
+template <typename R>
+struct MinCtas {
+    static constexpr int value = sizeof(R) == 8 ? 2 : 4;
+};
+
 template <typename R, int RING>
-__global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant__ SamplerParams P) {
+__global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int L = P.levels;
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
     off = (off + 15) & ~(size_t)15;
     double *zz = reinterpret_cast<double *>(smem_raw + off) + tid;
     off += P.wf_on ? sizeof(double) * (size_t)(P.S + 1) * kThreads : 0;
-    BMTables *bm_smem = reinterpret_cast<BMTables *>(smem_raw + off);   // double path only
+    bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);   // double path only
 
     // stage the coefficient tables of every sampled level, the widths (and
     // the Box-Muller node tables of the double path)
@@ -437,7 +446,7 @@ __global__ void __launch_bounds__(kThreads) sampler_kernel(const __grid_constant
         const int n = P.S * P.M;
         for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)P.sigma[i];
-        if constexpr (sizeof(R) == 8) bm_tables_init(bm_smem, tid, kThreads);
+        if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
     }
     __syncthreads();
     const PathCfg<R> pc{(R)P.a, (R)P.b, P.S, L, sig};
@@ -534,8 +543,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__
     R *qc = reinterpret_cast<R *>(smem_raw + off) + tid;
     off += sizeof(R) * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
-    BMTables *bm_smem = reinterpret_cast<BMTables *>(smem_raw + off);
-    if constexpr (sizeof(R) == 8) bm_tables_init(bm_smem, tid, kThreads);
+    bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
+    if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
