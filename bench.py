@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched amplitude-matrix entry")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal entry")
-    ap.add_argument("--profile", choices=["fp64", "fp32"], default=None,
-                    help="profiling case: one warm-up and one timed execute of a small plan "
-                         "(level --profile-p of the sweep, s = 10, --profile-n samples); no JSON line")
+    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
+                    help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
+                         "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
+                         "every 16th instance of the amplitude matrix; proposal = the learned-proposal "
+                         "instance with a fixed random network (--profile-n samples)")
     ap.add_argument("--profile-p", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=200_000)
     return ap.parse_args()
@@ -442,6 +444,32 @@ def run_profile(args):
     import torch
 
     import paper_1105_0542_gb300 as su
+    if args.profile == "batch":
+        inst = workloads.config3()[::16]
+        tup = [(x.a, x.b, x.T, x.s) for x in inst]
+        pl = su.BatchPlan("aho", [1.0, 1.0], 10, tup, inst[0].n_mc, inst[0].seed, precision="fp32",
+                          n_blocks=inst[0].n_blocks)
+        t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device="cuda")
+        sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            pl.su_batch_plan_execute(t, sc)
+        torch.cuda.synchronize()
+        res = pl.su_batch_plan_finalize(t.cpu().numpy(), sc)
+        print(f"profile case batch: {len(tup)} instances, {pl.slice_actions} slice-actions, "
+              f"A_0 = {res[0]['amp']:.6g}")
+        return
+    if args.profile == "proposal":
+        import numpy as np
+        x = workloads.CONFIG5
+        theta = _init_theta(0)
+        k = theta.size - (2 * 128 + 2)
+        theta[k:] = np.random.default_rng(1).normal(0, 0.3 / np.sqrt(128), 2 * 128 + 2)
+        P = su.Proposal(theta)
+        for _ in range(2):
+            r = su.speedup_amplitude_proposal(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, args.profile_n,
+                                              x.seed, P, n_blocks=100)
+        print(f"profile case proposal n={args.profile_n}: A_64 = {r[x.s]['amp']:.6g}, ess {r[x.s]['ess']:.4g}")
+        return
     inst = workloads.config2(args.profile_p)
     pl = su.Plan(inst.model, inst.params, inst.a, inst.b, inst.T, args.profile_p, inst.s, args.profile_n,
                  inst.seed, precision=args.profile, n_blocks=inst.n_blocks)

@@ -126,16 +126,25 @@ __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const 
 // between the points q[k STR] and q[(k+1) STR].  Slices are evaluated in
 // batches of B side by side: each table entry is loaded once per batch (a
 // broadcast shared-memory read) and feeds B independent multiply-add chains.
+//
+// Double path (FP64-pipe bound): per slice T_00 + Z H(Z) + Y A(Y, Z), where H
+// is column 0 without its constant and A the outer Horner over columns 1..;
+// the two products go straight into two running sums and the NS constants
+// are added once, one FP64 operation per slice fewer than summing whole
+// slice values.  Single path (issue bound): whole slice values, the shorter
+// instruction stream.
 template <typename R>
 struct Batch {
-    static constexpr int B = sizeof(R) == 8 ? 4 : 8;
+    static constexpr int B = 8;
 };
 
 template <typename R, int RING, int NS, int STR, int NQ>
 __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab,
                                        const SamplerParams &P, R alpha) {
     constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
-    R total = 0;
+    constexpr bool kFold = sizeof(R) == 8;
+    const int L0 = P.len[0];
+    R ty = 0, tz = 0;
 #pragma unroll
     for (int k0 = 0; k0 < NS; k0 += B) {
         R Z[B], Y[B], acc[B];
@@ -146,38 +155,62 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
             Y[b] = vs * vs;
             Z[b] = ring_var<R, RING>(ql + qr, alpha);
         }
-        int off = P.M;
-        {   // last column starts the outer Horner in x-bar^2
-            const int L = P.len[P.ncol - 1];
-            off -= L;
-            const R c = tab[off + L - 1];
+        const int jlast = kFold ? 1 : 0;          // last column of the outer Horner
+        if (P.ncol - 1 >= jlast) {
+            int off = P.M;
+            {   // last column starts the outer Horner in x-bar^2
+                const int L = P.len[P.ncol - 1];
+                off -= L;
+                const R c = tab[off + L - 1];
 #pragma unroll
-            for (int b = 0; b < B; ++b) acc[b] = c;
-            for (int i = L - 2; i >= 0; --i) {
-                const R ci = tab[off + i];
+                for (int b = 0; b < B; ++b) acc[b] = c;
+                for (int i = L - 2; i >= 0; --i) {
+                    const R ci = tab[off + i];
 #pragma unroll
-                for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+                    for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+                }
+            }
+            for (int j = P.ncol - 2; j >= jlast; --j) {
+                const int L = P.len[j];
+                off -= L;
+                R h[B];
+                const R c = tab[off + L - 1];
+#pragma unroll
+                for (int b = 0; b < B; ++b) h[b] = c;
+                for (int i = L - 2; i >= 0; --i) {
+                    const R ci = tab[off + i];
+#pragma unroll
+                    for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                }
+#pragma unroll
+                for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
+            }
+            if constexpr (kFold) {
+#pragma unroll
+                for (int b = 0; b < B; ++b) ty = fma(acc[b], Y[b], ty);
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) ty += acc[b];
             }
         }
-        for (int j = P.ncol - 2; j >= 0; --j) {
-            const int L = P.len[j];
-            off -= L;
-            R h[B];
-            const R c = tab[off + L - 1];
+        if constexpr (kFold) {
+            if (L0 > 1) {
+                R h[B];
+                const R c = tab[L0 - 1];
 #pragma unroll
-            for (int b = 0; b < B; ++b) h[b] = c;
-            for (int i = L - 2; i >= 0; --i) {
-                const R ci = tab[off + i];
+                for (int b = 0; b < B; ++b) h[b] = c;
+                for (int i = L0 - 2; i >= 1; --i) {
+                    const R ci = tab[i];
 #pragma unroll
-                for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                    for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                }
+#pragma unroll
+                for (int b = 0; b < B; ++b) tz = fma(h[b], Z[b], tz);
             }
-#pragma unroll
-            for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
         }
-#pragma unroll
-        for (int b = 0; b < B; ++b) total += acc[b];
     }
-    return total;
+    if constexpr (kFold) return fma((R)NS, tab[0], ty + tz);
+    return ty;
 }
 
 // levels d = D..F of a segment (level n = S - d uses every 2^d-th point)
@@ -192,6 +225,18 @@ __device__ __forceinline__ void segment_levels(R (&acc)[F + 1], const R (&q)[(1 
         }
     }
 }
+
+// (l + r)/2 for the bisection midpoint.  Double path: the halving on the
+// exponent bits (an FP64 multiply costs as much as a multiply-add on this
+// part); sums below 2^-1021 in magnitude become zero, infinities and NaNs
+// pass through.
+__device__ __forceinline__ double mid(double l, double r) {
+    const long long u = __double_as_longlong(l + r);
+    const int E = (int)((u >> 52) & 0x7FF);
+    const long long h = E >= 2 ? (E == 0x7FF ? u : u - (1LL << 52)) : (u & (long long)0x8000000000000000ULL);
+    return __longlong_as_double(h);
+}
+__device__ __forceinline__ float mid(float l, float r) { return 0.5f * (l + r); }
 
 // --------------------------------------------------------------- a path
 // Per-path configuration: endpoints, depth, sampled levels and the bisection
@@ -247,8 +292,7 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
                 }
                 if (P.wf_on) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * i + 1) * hc;
-                qc[idx * kThreads] =
-                    fma(sg, z, (R)0.5 * (qc[(idx - hc) * kThreads] + qc[(idx + hc) * kThreads]));
+                qc[idx * kThreads] = fma(sg, z, mid(qc[(idx - hc) * kThreads], qc[(idx + hc) * kThreads]));
             }
         }
         cz[0] = carry;
@@ -293,7 +337,7 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
                 }
                 if (P.wf_on) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * il + 1) * h;
-                q[idx] = fma(sg, z, (R)0.5 * (q[idx - h] + q[idx + h]));
+                q[idx] = fma(sg, z, mid(q[idx - h], q[idx + h]));
             }
         }
         if (qout) {
@@ -526,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
 // Shared memory: table[M] (R) | sigma[S_max+1] (R) | qc[(C_max+1)][kThreads] (R) |
 //                Box-Muller node tables (double path)
 template <typename R, int RING>
-__global__ void __launch_bounds__(kThreads) batch_kernel(const __grid_constant__ BatchParams B) {
+__global__ void __launch_bounds__(kThreads, MinCtas<R>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ double s_red[kThreads / 32][3];
