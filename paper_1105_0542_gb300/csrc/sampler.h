@@ -40,7 +40,7 @@ struct SamplerParams {
     // outputs
     double *partial;          // device: per item and level, (M, S, Q, n)
     double *w_out;            // device: per-sample mode when non-null, [sample][S]
-    float *q_out;             // device: per-sample mode, path points [sample][N+1] (or null)
+    float *q_out;             // device: per-sample mode, single precision only: path points [sample][N+1] (or null)
     int *flags;               // device: bit 0 = non-finite weight seen
 };
 

@@ -252,7 +252,7 @@ struct PathCfg {
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
-template <typename R, int RING, int F>
+template <typename R, int RING, int F, bool WF>
 __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCfg<R> &pc,
                                             const R *__restrict__ tab, R *__restrict__ qc,
                                             double *__restrict__ zz, const Stream<R> &st,
@@ -264,7 +264,7 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
     const int M = P.M;
     const R alpha = (R)P.alpha;
 
-    if (P.wf_on)
+    if constexpr (WF)
         for (int n = 0; n <= S; ++n) zz[n * kThreads] = 0.0;
 
     R cz[F + 1];
@@ -290,7 +290,7 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
                 } else {
                     z = carry;
                 }
-                if (P.wf_on) zz[n * kThreads] += (double)z * (double)z;
+                if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * i + 1) * hc;
                 qc[idx * kThreads] = fma(sg, z, mid(qc[(idx - hc) * kThreads], qc[(idx + hc) * kThreads]));
             }
@@ -335,15 +335,17 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
                 } else {
                     z = cz[l];
                 }
-                if (P.wf_on) zz[n * kThreads] += (double)z * (double)z;
+                if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * il + 1) * h;
                 q[idx] = fma(sg, z, mid(q[idx - h], q[idx + h]));
             }
         }
-        if (qout) {
+        if constexpr (sizeof(R) == 4) {   // path output: single-precision paths only
+            if (qout) {
 #pragma unroll
-            for (int k = 0; k < NF; ++k) qout[c * NF + k] = (float)q[k];
-            if (c == C - 1) qout[C * NF] = (float)q[NF];
+                for (int k = 0; k < NF; ++k) qout[c * NF + k] = (float)q[k];
+                if (c == C - 1) qout[C * NF] = (float)q[NF];
+            }
         }
         // top level: every slice of the segment; then the coarser levels
         acc[0] += level_sum<R, RING, NF, 1>(q, tab, P, alpha);
@@ -351,7 +353,7 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
     }
 
     // ---- width-factor weight, cumulative over levels 1..n (stored in zz)
-    if (P.wf_on) {
+    if constexpr (WF) {
         double cum = 0;
         for (int n = 1; n <= S; ++n) {
             cum += (double)(1 << (n - 1)) * P.lwf + P.hcoef * zz[n * kThreads];
@@ -359,7 +361,10 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
         }
     }
     auto out = [&](int d, R v) {
-        wout[d * wstride] = P.wf_on ? (R)((double)v + zz[(S - d) * kThreads]) : v;
+        if constexpr (WF)
+            wout[d * wstride] = (R)((double)v + zz[(S - d) * kThreads]);
+        else
+            wout[d * wstride] = v;
     };
 
     // ---- outputs, level n = S - d
@@ -379,17 +384,37 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
     }
 }
 
+// The width-factor weight is a template switch: as a run-time test inside
+// the midpoint loop the compiler predicates it, and its double conversions
+// and multiply-add then occupy the FP64 pipe on every midpoint.
+template <typename R, int RING, bool WF>
+__device__ __forceinline__ void sample_path_f(int F, const SamplerParams &P, const PathCfg<R> &pc,
+                                              const R *tab, R *qc, double *zz, const Stream<R> &st,
+                                              R *wout, int wstride, float *qout) {
+    switch (F) {
+        case 1: sample_path<R, RING, 1, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 2: sample_path<R, RING, 2, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 3: sample_path<R, RING, 3, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 4: sample_path<R, RING, 4, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        default: sample_path<R, RING, 5, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+    }
+}
+
 template <typename R, int RING>
 __device__ __forceinline__ void sample_path_any(int F, const SamplerParams &P, const PathCfg<R> &pc,
                                                 const R *tab, R *qc, double *zz, const Stream<R> &st,
                                                 R *wout, int wstride, float *qout = nullptr) {
-    switch (F) {
-        case 1: sample_path<R, RING, 1>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 2: sample_path<R, RING, 2>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 3: sample_path<R, RING, 3>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 4: sample_path<R, RING, 4>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        default: sample_path<R, RING, 5>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-    }
+    if (P.wf_on)
+        sample_path_f<R, RING, true>(F, P, pc, tab, qc, zz, st, wout, wstride, qout);
+    else
+        sample_path_f<R, RING, false>(F, P, pc, tab, qc, zz, st, wout, wstride, qout);
+}
+
+// batched kernel: no width factor
+template <typename R, int RING>
+__device__ __forceinline__ void sample_path_plain(int F, const SamplerParams &P, const PathCfg<R> &pc,
+                                                  const R *tab, R *qc, const Stream<R> &st, R *wout) {
+    sample_path_f<R, RING, false>(F, P, pc, tab, qc, nullptr, st, wout, 1, nullptr);
 }
 
 // -------------------------------------------------------- warp helpers
@@ -616,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) batch_kernel(cons
             st.slo = (uint32_t)smp;
             st.shi = (uint32_t)((uint64_t)smp >> 32);
             R w;
-            sample_path_any<R, RING>(in.F, P, pc, tab, qc, nullptr, st, &w, 1);
+            sample_path_plain<R, RING>(in.F, P, pc, tab, qc, st, &w);
             bad |= isnan(w) || (isinf(w) && w > 0);
             acc.push(w);
         }
