@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched amplitude-matrix entry")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal entry")
+    ap.add_argument("--no-configs", action="store_true", help="skip the configuration 1 and 4 entries")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -151,6 +152,40 @@ def oracle_sweep(steps, warmup, budget_s):
     desc = ("oracle (plain C, OpenMP over samples) on the first n samples of each timed step's "
             "sweep point: " + ", ".join(f"p={p}:{n}" for p, n in counts))
     return total_sa, total_t, used, desc
+
+
+def oracle_configs(budget_s):
+    """The oracle on every configuration the device path runs, bounded:
+    configuration 1 in full, configurations 4 and 5 (its plain sampler) on the
+    first samples of each instance, and one single-thread figure (sweep point
+    p = 10).  Slice-actions per second and, from the oracle's own estimate,
+    the time to a relative error of 1e-4 (extrapolated)."""
+    from oracle import mc
+    cores = os.cpu_count() or 1
+    out = {}
+
+    def timed(x, n, threads, T=None):
+        o = mc.Oracle(x.model, list(x.params), x.p)
+        TT = x.T if T is None else T
+        t0 = time.perf_counter()
+        w, used = o.logweights(x.a, x.b, TT, x.s, x.seed, n, threads=threads)
+        dt = time.perf_counter() - t0
+        res = mc.estimate(w, o.level0(x.a, x.b, TT), x.a, x.b, TT, min(x.n_blocks, n))[x.s]
+        sa = n * (2 * (1 << x.s) - 2)
+        rel = res["rel_err"]
+        return {"instance": f"{x.model} {list(x.params)} T={TT} p={x.p} N={1 << x.s}", "samples": n,
+                "threads": used, "s": dt, "slice_actions_per_s": sa / dt, "rel_err": rel,
+                "time_to_rel_1e-4_s_extrapolated": dt * (rel / 1e-4) ** 2 if math.isfinite(rel) and rel < 1
+                else None}
+
+    out["config1"] = [timed(x, x.n_mc, cores) for x in workloads.CONFIG1]
+    n4 = max(1000, int(20_000 * budget_s / 10))
+    out["config4"] = [timed(x, n4, cores) for x in workloads.config4()]
+    x5 = workloads.CONFIG5
+    out["config5_plain"] = timed(x5, n4, cores)
+    x2 = workloads.config2(10)
+    out["single_thread_config2_p10"] = timed(x2, 200, 1)
+    return out
 
 
 def run_reference(args):
@@ -303,6 +338,9 @@ def run_ours(args):
     learned = None
     if not args.no_learned:
         learned = run_learned(su, torch)
+    small = None
+    if not args.no_configs:
+        small = run_small_configs(su, torch, dev, stream, flush)
 
     if rank != 0:
         if dist is not None:
@@ -323,7 +361,8 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu:
         sa, t, used, desc = oracle_sweep(args.steps, 0, CPU_BUDGET_S)
-        cpu = {"value": sa / t, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
+        cpu = {"value": sa / t, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
+               "per_config": oracle_configs(10.0)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
@@ -339,12 +378,67 @@ def run_ours(args):
                                "speedup": (ttr["fp64"] / ttr["fp32"]) if "fp64" in ttr and "fp32" in ttr else None,
                                "method": "per-sample cost x (rel_err/1e-4)^2 from the 1e7-sample run"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
-        "batched_amplitude_matrix": batched, "learned_proposal": learned,
+        "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
         "clocks": clock_info,
     }
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _mehler(omega, a, b, T):
+    """Harmonic-oscillator continuum amplitude (the Mehler kernel, m = hbar = 1)."""
+    sh, ch = math.sinh(omega * T), math.cosh(omega * T)
+    return math.sqrt(omega / (2 * math.pi * sh)) * math.exp(-omega * ((a * a + b * b) * ch - 2 * a * b) / (2 * sh))
+
+
+def run_small_configs(su, torch, dev, stream, flush):
+    """Configuration 1 (AHO g = 1 and HO, p = 4, N = 16, 1e5 samples, double
+    precision; latency-bound: timed through the host API per call) and
+    configuration 4 (double well h = 1, 5 and Poeschl-Teller, T = 1, 5, p = 12,
+    N = 64, 1e8 samples, single-precision W_p: device plans, CUDA events)."""
+    c1 = []
+    for x in workloads.CONFIG1:
+        call = lambda: su.speedup_amplitude(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, x.n_mc, x.seed,
+                                            precision="fp64", n_blocks=x.n_blocks)
+        call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            r = call()
+        dt = (time.perf_counter() - t0) / reps
+        top = r[x.s]
+        sa = x.n_mc * (2 * (1 << x.s) - 2)
+        e = {"instance": f"{x.model} {list(x.params)} a={x.a} b={x.b} T={x.T} p={x.p} N={1 << x.s}",
+             "samples": x.n_mc, "ms_per_call": dt * 1e3, "slice_actions_per_s": sa / dt,
+             "amp": top["amp"], "err": top["err"], "rel_err": top["rel_err"]}
+        if x.model == "ho":
+            e["mehler_continuum"] = _mehler(x.params[0], x.a, x.b, x.T)
+        c1.append(e)
+    c4 = []
+    for x in workloads.config4():
+        pl = su.Plan(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, x.n_mc, x.seed, precision="fp32",
+                     n_blocks=x.n_blocks)
+        t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device=dev)
+        sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device=dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.su_plan_execute(t, sc, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        top = pl.su_plan_finalize(t.cpu().numpy(), sc)[x.s]
+        rel = top["rel_err"]
+        c4.append({"instance": f"{x.model} {list(x.params)} a={x.a} b={x.b} T={x.T} p={x.p} N={1 << x.s}",
+                   "samples": x.n_mc, "ms": ms, "slice_actions_per_s": pl.slice_actions / (ms / 1e3),
+                   "amp": top["amp"], "log_amp": top["log_amp"], "rel_err": rel, "ess": top["ess"],
+                   "max_share": top["max_share"],
+                   "time_to_rel_1e-4_s": (ms / 1e3) * (rel / 1e-4) ** 2 if math.isfinite(rel) and rel < 1 else None})
+    return {"config1": c1, "config4": c4,
+            "note": "config 1 wall clock per host-API call (plan, tables, launch, tuples back); config 4 "
+                    "device time of one plan execute, L2 flushed before each"}
 
 
 def run_batched(su, torch, dev, stream, flush):

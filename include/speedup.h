@@ -356,9 +356,12 @@ int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0,
 
 /*
  * speedup_normals -- the Gaussian normals the sampler draws (Sec. 4.1
- * Box-Muller, both branches, from the Philox stream above): normal j of
- * sample i is branch (j & 1) of call j >> 1, with 53-bit uniforms for SU_FP64
- * and 24-bit uniforms (float arithmetic) for SU_FP32.
+ * Box-Muller, both branches, from the Philox stream above), j in the heap
+ * order of the bisection midpoints.  SU_FP64: normal j of sample i is branch
+ * (j & 1) of call j >> 1, 53-bit uniforms u1 from words (w0, w1) and u2 from
+ * (w2, w3).  SU_FP32: with j' = j + 1, normal j is slot j' & 3 of call
+ * j' >> 2; slots 0, 1 are the two branches from the 24-bit uniforms (float
+ * arithmetic) of w0 and w1, slots 2, 3 those of w2 and w3.
  *   d_out[(i - sample0) * n_normals + j]   (device, double).
  * Asynchronous on stream.
  */

@@ -16,8 +16,11 @@
  *  - Box-Muller (Sec. 4.1): r = sqrt(-2 ln u1), theta = 2 pi u2,
  *    z_{2t} = r cos theta, z_{2t+1} = r sin theta, both branches used.
  *    53-bit uniforms u = ((w0 * 2^21 + (w1 >> 11)) + 0.5) * 2^-53 from
- *    (w0,w1) and (w2,w3); 24-bit uniforms u = ((w >> 8) + 0.5) * 2^-24 from
- *    w0 and w2, rounded in float exactly as a float kernel forms them.
+ *    (w0,w1) and (w2,w3): normal j is branch j & 1 of call j >> 1.
+ *    24-bit uniforms u = ((w >> 8) + 0.5) * 2^-24, rounded in float exactly
+ *    as a float kernel forms them, four normals per call: with j' = j + 1,
+ *    normal j is branch j' & 1 of the pair (u1, u2) = (w0, w1) for
+ *    (j' & 3) < 2 and (w2, w3) otherwise, of call j' >> 2.
  *  - Bisection (Sec. 4.1): for level n = 1..s and i = 0..2^(n-1)-1 the normal
  *    with heap index j = 2^(n-1) - 1 + i places
  *      q[(2i+1) 2^(s-n)] = (q[i 2^(s-n+1)] + q[(i+1) 2^(s-n+1)]) / 2
@@ -92,19 +95,10 @@ void oracle_philox_words(uint64_t seed, uint32_t instance, uint64_t sample,
 
 /* ----------------------------------------------------------- Box-Muller */
 
-static void uniforms(const uint32_t w[4], int bits, double *u1, double *u2)
+static double u24(uint32_t w)
 {
-    if (bits == 53) {
-        uint64_t a = ((uint64_t)w[0] << 21) | (w[1] >> 11);
-        uint64_t b = ((uint64_t)w[2] << 21) | (w[3] >> 11);
-        *u1 = ((double)a + 0.5) * 0x1p-53;
-        *u2 = ((double)b + 0.5) * 0x1p-53;
-    } else {
-        volatile float fa = (float)(w[0] >> 8) + 0.5f;  /* rounded in float */
-        volatile float fb = (float)(w[2] >> 8) + 0.5f;
-        *u1 = (double)fa * 0x1p-24;
-        *u2 = (double)fb * 0x1p-24;
-    }
+    volatile float f = (float)(w >> 8) + 0.5f;  /* rounded in float */
+    return (double)f * 0x1p-24;
 }
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -113,12 +107,26 @@ static const double TWO_PI = 6.283185307179586476925286766559;
 static double normal_j(uint64_t seed, uint32_t instance, uint64_t sample, int64_t j, int bits)
 {
     uint32_t w[4];
-    oracle_philox_words(seed, instance, sample, (uint32_t)(j >> 1), w);
     double u1, u2;
-    uniforms(w, bits, &u1, &u2);
+    int branch;
+    if (bits == 53) {
+        oracle_philox_words(seed, instance, sample, (uint32_t)(j >> 1), w);
+        uint64_t a = ((uint64_t)w[0] << 21) | (w[1] >> 11);
+        uint64_t b = ((uint64_t)w[2] << 21) | (w[3] >> 11);
+        u1 = ((double)a + 0.5) * 0x1p-53;
+        u2 = ((double)b + 0.5) * 0x1p-53;
+        branch = (int)(j & 1);
+    } else {
+        int64_t jp = j + 1;
+        oracle_philox_words(seed, instance, sample, (uint32_t)(jp >> 2), w);
+        int pr = (int)((jp >> 1) & 1);
+        u1 = u24(w[2 * pr]);
+        u2 = u24(w[2 * pr + 1]);
+        branch = (int)(jp & 1);
+    }
     double r = sqrt(-2.0 * log(u1));
     double th = TWO_PI * u2;
-    return (j & 1) ? r * sin(th) : r * cos(th);
+    return branch ? r * sin(th) : r * cos(th);
 }
 
 void oracle_normals(uint64_t seed, uint32_t instance, uint64_t sample, int64_t n,

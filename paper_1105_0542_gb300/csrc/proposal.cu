@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
         const int cnt = (int)max((int64_t)0, min((int64_t)kRows, hi - start));
         const int p = tid;
         const bool valid = owner && p < cnt;
-        float carry = 0.f, c = 0.f;
+        float quad[4] = {0.f, 0.f, 0.f, 0.f}, c = 0.f;
         if (owner) {
             const uint64_t smp = (uint64_t)(P.sample0 + start + p);
             st.slo = (uint32_t)smp;
@@ -167,15 +167,10 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
                 tile_forward(blob, X0, H, out);
                 if (owner) {
                     const uint32_t j = (1u << (n - 1)) - 1u + (uint32_t)i;
-                    float z;
-                    if ((j & 1u) == 0) {
-                        float z0, z1;
-                        st.pair(j >> 1, z0, z1);
-                        z = z0;
-                        carry = z1;
-                    } else {
-                        z = carry;
-                    }
+                    // the plain single-precision stream: slot j' & 3 of call j' >> 2, j' = j + 1
+                    const uint32_t jp = j + 1;
+                    if (j == 0 || (jp & 3u) == 0) st.quad(jp >> 2, quad);
+                    const float z = pick4(quad, jp);
                     const float sh = out[2 * p], ls = out[2 * p + 1];
                     const float t = fmaf(__expf(ls), z, sh);
                     const float mid = 0.5f * (qs[kL * kRows + p] + qs[kR * kRows + p]);

@@ -71,29 +71,53 @@ __global__ void philox_words_kernel(uint64_t seed, uint32_t inst, int64_t sample
 }
 
 // ------------------------------------------------ the sampler's normals
-// out[i * n + j] = normal j of sample sample0 + i, as the sampler forms it
-template <typename R>
-__global__ void __launch_bounds__(128) normals_kernel(uint64_t seed, uint32_t inst, int64_t sample0,
-                                                      int64_t ns, int n, double *out) {
+// out[i * n + j] = normal j of sample sample0 + i, as the sampler forms it:
+// one thread per (sample, call); a call gives two normals on the double path
+// (j = 2t, 2t + 1) and four on the single path (j + 1 = 4t .. 4t + 3)
+__global__ void __launch_bounds__(128) normals_kernel_f64(uint64_t seed, uint32_t inst, int64_t sample0,
+                                                          int64_t ns, int n, double *out) {
     __shared__ bm::Tables tabs;
-    if constexpr (sizeof(R) == 8) bm::tables_init(&tabs, threadIdx.x, blockDim.x);
+    bm::tables_init(&tabs, threadIdx.x, blockDim.x);
     __syncthreads();
     const int calls = (n + 1) / 2;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= ns * calls) return;
     const int64_t i = id / calls;
     const uint32_t t = (uint32_t)(id - i * calls);
-    Stream<R> st;
+    Stream<double> st;
     const uint64_t smp = (uint64_t)(sample0 + i);
     st.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     st.inst = inst;
     st.slo = (uint32_t)smp;
     st.shi = (uint32_t)(smp >> 32);
     st.bm = &tabs;
-    R z0, z1;
+    double z0, z1;
     st.pair(t, z0, z1);
-    out[i * n + 2 * t] = (double)z0;
-    if (2 * (int)t + 1 < n) out[i * n + 2 * t + 1] = (double)z1;
+    out[i * n + 2 * t] = z0;
+    if (2 * (int)t + 1 < n) out[i * n + 2 * t + 1] = z1;
+}
+
+__global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_t inst, int64_t sample0,
+                                                          int64_t ns, int n, double *out) {
+    const int calls = n / 4 + 1;                 // j' = j + 1 runs over 1..n
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= ns * calls) return;
+    const int64_t i = id / calls;
+    const uint32_t t = (uint32_t)(id - i * calls);
+    Stream<float> st;
+    const uint64_t smp = (uint64_t)(sample0 + i);
+    st.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    st.inst = inst;
+    st.slo = (uint32_t)smp;
+    st.shi = (uint32_t)(smp >> 32);
+    st.bm = nullptr;
+    float z[4];
+    st.quad(t, z);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = 4 * (int)t + k - 1;
+        if (j >= 0 && j < n) out[i * n + j] = (double)z[k];
+    }
 }
 
 const void *pick(const SamplerParams &P, int precision) {
@@ -198,15 +222,16 @@ cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_bloc
 
 cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
                            int n_normals, int precision, double *out, cudaStream_t st) {
-    const int64_t n = n_samples * ((n_normals + 1) / 2);
-    if (n == 0) return cudaSuccess;
+    if (n_samples <= 0 || n_normals <= 0) return cudaSuccess;
+    const int64_t calls = precision == SU_FP32 ? n_normals / 4 + 1 : (n_normals + 1) / 2;
+    const int64_t n = n_samples * calls;
     const int th = 128;
     const unsigned grid = (unsigned)((n + th - 1) / th);
     cudaGetLastError();
     if (precision == SU_FP32)
-        normals_kernel<float><<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
+        normals_kernel_f32<<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
     else
-        normals_kernel<double><<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
+        normals_kernel_f64<<<grid, th, 0, st>>>(seed, instance, sample0, n_samples, n_normals, out);
     return cudaGetLastError();
 }
 

@@ -63,27 +63,49 @@ struct Normal<double> {
 
 template <>
 struct Normal<float> {
-    // 24-bit uniforms ((w >> 8) + 1/2) 2^-24 from w0 and w2
-    static __device__ __forceinline__ void pair(uint4 w, const bm::Tables *, float &z0, float &z1) {
-        const float u1 = ((float)(w.x >> 8) + 0.5f) * 0x1p-24f;
-        const float u2 = ((float)(w.z >> 8) + 0.5f) * 0x1p-24f;
+    // four normals per call: (z0, z1) from the 24-bit uniforms
+    // ((w >> 8) + 1/2) 2^-24 of (w0, w1), (z2, z3) from (w2, w3)
+    static __device__ __forceinline__ void bm24(uint32_t a, uint32_t b, float &z0, float &z1) {
+        const float u1 = ((float)(a >> 8) + 0.5f) * 0x1p-24f;
+        const float u2 = ((float)(b >> 8) + 0.5f) * 0x1p-24f;
         const float r = sqrtf(-2.0f * logf(u1));
         float sn, cs;
         sincospif(2.0f * u2, &sn, &cs);
         z0 = r * cs;
         z1 = r * sn;
     }
+    static __device__ __forceinline__ void quad(uint4 w, float (&z)[4]) {
+        bm24(w.x, w.y, z[0], z[1]);
+        bm24(w.z, w.w, z[2], z[3]);
+    }
 };
 
+// Stream layout.  Double path: normal j (heap order of the bisection
+// midpoints) is branch j & 1 of call j >> 1.  Single path: with j' = j + 1,
+// normal j is slot j' & 3 of call j' >> 2, so that from level 3 on every
+// level's normals start on a call boundary.
 template <typename R>
 struct Stream {
     uint2 key;
     uint32_t inst, slo, shi;
     const bm::Tables *bm;   // shared-memory node tables (double path)
-    __device__ __forceinline__ void pair(uint32_t call, R &z0, R &z1) const {
-        Normal<R>::pair(philox4x32_10(make_uint4(call, inst, slo, shi), key), bm, z0, z1);
+    __device__ __forceinline__ uint4 words(uint32_t call) const {
+        return philox4x32_10(make_uint4(call, inst, slo, shi), key);
+    }
+    __device__ __forceinline__ void pair(uint32_t call, double &z0, double &z1) const {
+        Normal<double>::pair(words(call), bm, z0, z1);
+    }
+    __device__ __forceinline__ void quad(uint32_t call, float (&z)[4]) const {
+        Normal<float>::quad(words(call), z);
     }
 };
+
+// v[s & 3] for a run-time slot
+__device__ __forceinline__ float pick4(const float (&v)[4], uint32_t s) {
+    const float lo = (s & 1u) ? v[1] : v[0];
+    const float hi = (s & 1u) ? v[3] : v[2];
+    return (s & 2u) ? hi : lo;
+}
 
 // ------------------------------------------------------------------ W_p
 template <typename R, int RING>
@@ -271,6 +293,10 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
 #pragma unroll
     for (int l = 0; l <= F; ++l) cz[l] = 0;
 
+    // single path: the quads of levels 1 and 2, which span several segments
+    // (or, with one segment, both levels)
+    float Q1[4] = {0.f, 0.f, 0.f, 0.f}, Q2[4] = {0.f, 0.f, 0.f, 0.f};
+
     // ---- segment endpoints: bisection levels 1..S-F, heap order j = 0..C-2
     if (C > 1) {
         qc[0] = pc.a;
@@ -282,13 +308,19 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
             const R sg = pc.sigma[n];
             for (int i = 0; i < (1 << (n - 1)); ++i, ++j) {
                 R z;
-                if ((j & 1u) == 0) {
-                    R z0, z1;
-                    st.pair(j >> 1, z0, z1);
-                    z = z0;
-                    carry = z1;
+                if constexpr (sizeof(R) == 8) {
+                    if ((j & 1u) == 0) {
+                        R z0, z1;
+                        st.pair(j >> 1, z0, z1);
+                        z = z0;
+                        carry = z1;
+                    } else {
+                        z = carry;
+                    }
                 } else {
-                    z = carry;
+                    const uint32_t jp = j + 1;
+                    if (j == 0 || (jp & 3u) == 0) st.quad(jp >> 2, Q1);
+                    z = pick4(Q1, jp);
                 }
                 if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * i + 1) * hc;
@@ -313,27 +345,54 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
             const uint32_t jbase = (1u << (n - 1)) - 1u + ((uint32_t)c << (l - 1));
             const R sg = pc.sigma[n];
             const int h = 1 << (F - l);
+            float qq[4];
 #pragma unroll
             for (int il = 0; il < (1 << (l - 1)); ++il) {
                 const uint32_t j = jbase + (uint32_t)il;
                 R z;
-                if ((j & 1u) == 0) {
-                    R z0, z1;
-                    st.pair(j >> 1, z0, z1);
-                    z = z0;
-                    cz[l] = z1;
-                } else if (il == 0 && c == 0) {
-                    if (C == 1) {
-                        z = cz[l - 1];  // second normal of the previous level's last call
-                    } else if (l == 1) {
-                        z = cz[0];      // carried from the segment-endpoint levels
-                    } else {
-                        R z0, z1;       // shared with the last segment: recompute
+                if constexpr (sizeof(R) == 8) {
+                    if ((j & 1u) == 0) {
+                        R z0, z1;
                         st.pair(j >> 1, z0, z1);
-                        z = z1;
+                        z = z0;
+                        cz[l] = z1;
+                    } else if (il == 0 && c == 0) {
+                        if (C == 1) {
+                            z = cz[l - 1];  // second normal of the previous level's last call
+                        } else if (l == 1) {
+                            z = cz[0];      // carried from the segment-endpoint levels
+                        } else {
+                            R z0, z1;       // shared with the last segment: recompute
+                            st.pair(j >> 1, z0, z1);
+                            z = z1;
+                        }
+                    } else {
+                        z = cz[l];
                     }
                 } else {
-                    z = cz[l];
+                    // j' = j + 1 = 2^(n-1) + c 2^(l-1) + il
+                    const uint32_t jp = j + 1;
+                    if (l >= 3) {               // aligned: whole quads inside the segment
+                        if ((il & 3) == 0) st.quad(jp >> 2, qq);
+                        z = qq[il & 3];
+                    } else if (l == 2) {
+                        if (C == 1) {           // j' = 2, 3: the quad of level 1
+                            z = Q1[2 + il];
+                        } else {                // a quad per two segments
+                            if (il == 0 && (c & 1) == 0) st.quad(jp >> 2, Q2);
+                            z = (c & 1) ? Q2[2 + il] : Q2[il];
+                        }
+                    } else {
+                        if (C == 1) {           // j' = 1
+                            st.quad(0, Q1);
+                            z = Q1[1];
+                        } else if (C == 2) {    // j' = 2 + c: the endpoint levels' quad
+                            z = c ? Q1[3] : Q1[2];
+                        } else {                // a quad per four segments
+                            if ((c & 3) == 0) st.quad(jp >> 2, Q1);
+                            z = pick4(Q1, (uint32_t)c);
+                        }
+                    }
                 }
                 if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
                 const int idx = (2 * il + 1) * h;

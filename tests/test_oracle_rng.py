@@ -63,28 +63,47 @@ def test_stream_layout_key_and_counter():
         [call, inst, sample & 0xFFFFFFFF, sample >> 32], [seed & 0xFFFFFFFF, seed >> 32])
 
 
-def _box_muller_ref(words, bits):
-    """Box-Muller from the raw words, written out in numpy."""
+def _box_muller_ref(words, bits, pair=0):
+    """Box-Muller from the raw words, written out in numpy: the 53-bit pair
+    from (w0, w1) and (w2, w3); the 24-bit pair `pair` from (w0, w1) or
+    (w2, w3)."""
     w = np.asarray(words, dtype=np.uint64)
     if bits == 53:
         u1 = ((w[0] << np.uint64(21)) | (w[1] >> np.uint64(11))).astype(np.float64)
         u2 = ((w[2] << np.uint64(21)) | (w[3] >> np.uint64(11))).astype(np.float64)
         u1, u2 = (u1 + 0.5) * 2.0 ** -53, (u2 + 0.5) * 2.0 ** -53
     else:
-        u1 = (np.float32(int(w[0]) >> 8) + np.float32(0.5)).astype(np.float64) * 2.0 ** -24
-        u2 = (np.float32(int(w[2]) >> 8) + np.float32(0.5)).astype(np.float64) * 2.0 ** -24
+        u1 = (np.float32(int(w[2 * pair]) >> 8) + np.float32(0.5)).astype(np.float64) * 2.0 ** -24
+        u2 = (np.float32(int(w[2 * pair + 1]) >> 8) + np.float32(0.5)).astype(np.float64) * 2.0 ** -24
     r = math.sqrt(-2.0 * math.log(u1))
     return r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2)
 
 
-@pytest.mark.parametrize("bits", [53, 24])
-def test_normals_follow_box_muller_of_the_stream(bits):
+def test_normals_follow_box_muller_of_the_stream_53():
+    """Double layout: normal j is branch j & 1 of call j >> 1."""
     seed, inst, sample = 99, 3, 12345
-    z = mc.normals(seed, inst, sample, 10, bits)
+    z = mc.normals(seed, inst, sample, 10, 53)
     for t in range(5):
-        z0, z1 = _box_muller_ref(mc.philox_words(seed, inst, sample, t), bits)
+        z0, z1 = _box_muller_ref(mc.philox_words(seed, inst, sample, t), 53)
         assert abs(z[2 * t] - z0) <= 1e-14 * max(1, abs(z0))
         assert abs(z[2 * t + 1] - z1) <= 1e-14 * max(1, abs(z1))
+
+
+def test_normals_follow_box_muller_of_the_stream_24():
+    """Single layout: with j' = j + 1, normal j is branch j' & 1 of pair
+    (j' >> 1) & 1 of call j' >> 2 (slot 0 of call 0 unused)."""
+    seed, inst, sample = 99, 3, 12345
+    n = 23
+    z = mc.normals(seed, inst, sample, n, 24)
+    for j in range(n):
+        jp = j + 1
+        pair = mc.philox_words(seed, inst, sample, jp >> 2)
+        ref = _box_muller_ref(pair, 24, (jp >> 1) & 1)[jp & 1]
+        assert abs(z[j] - ref) <= 1e-14 * max(1, abs(ref)), j
+    # from level 3 on (heap index 3, 7, 15, ...) a level starts a call
+    for n_lev in range(3, 8):
+        j0 = (1 << (n_lev - 1)) - 1
+        assert (j0 + 1) % 4 == 0
 
 
 @pytest.mark.parametrize("bits", [53, 24])
