@@ -72,6 +72,17 @@ typedef struct {
     void *stream;         /* cudaStream_t for all device work; NULL (default)      */
     int64_t sample0;      /* first sample index: samples sample0 .. sample0+n_mc-1,
                              so disjoint ranges on several devices form one run; 0  */
+    int seg_log2;         /* launch shape: bisection levels kept in registers, the
+                             path processed in segments of 2^seg_log2 slices, 1..5
+                             (capped at s); 0 (default) = automatic               */
+    int rounds;           /* launch shape: paths per thread per work item, 1..8;
+                             0 (default) = automatic.  Automatic = the shape
+                             su_autotune stored for this precision, model, p and s
+                             in this process, else the built-in rule (seg_log2 =
+                             4 for SU_FP64, 5 for SU_FP32, capped at s; rounds =
+                             1, doubled while the per-item tuples would exceed
+                             512 MB and as many CTAs stay resident).  The shape
+                             changes the order of the floating-point sums only. */
 } su_options;
 
 /* per bisection level n = 0..s (N = 2^n slices) */
@@ -329,6 +340,39 @@ int su_plan_execute(su_plan *plan, void *d_tuples, void *d_scratch, void *stream
  */
 int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_scratch,
                      su_level_result *out);
+
+/* ---- launch-shape autotuner ----------------------------------------------- */
+
+typedef struct {
+    int seg_log2;      /* su_options.seg_log2 of this shape                       */
+    int rounds;        /* su_options.rounds of this shape                         */
+    double ms;         /* device time of one execute of the probe plan (best of 2) */
+} su_tuning;
+
+/*
+ * su_autotune -- times every launch shape (seg_log2 = 1..min(s, 5), rounds =
+ * 1, 2, 4, 8 where the shared memory allows) of the sampler on n_probe
+ * samples of the given instance (opt: precision, n_blocks, hierarchy, stream;
+ * its seg_log2 and rounds are ignored), stores the fastest in a process-wide
+ * table under (precision, model, p, s), and returns it.  Later plans of that
+ * key with automatic shape use it.  No counterpart in the paper: a host-side
+ * search over this implementation's launch parameters.
+ *   best          : host, the fastest shape.
+ *   all, cap      : host, optional (NULL, 0): up to cap timed shapes.
+ *   n_all         : host, optional: shapes timed.
+ * Synchronous.  Errors: SU_EINVAL (arguments as for speedup_amplitude, s >= 1,
+ * n_probe >= 1), SU_ECUDA, SU_ENOMEM.
+ */
+int su_autotune(int model, const double *params, int n_params, double a, double b, double T,
+                int p, int s, int64_t n_probe, uint64_t seed, const su_options *opt,
+                su_tuning *best, su_tuning *all, int cap, int *n_all);
+
+/* Forget every shape su_autotune stored (automatic shapes revert to the rule). */
+int su_autotune_clear(void);
+
+/* The launch shape a plan uses. */
+int su_plan_shape(const su_plan *plan, int *seg_log2, int *rounds);
+
 
 /*
  * speedup_logweights -- per-sample log-weights (Sec. 4.1 normalisation written

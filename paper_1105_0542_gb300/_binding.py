@@ -27,7 +27,7 @@ EXPORTS = [
     "su_batch_plan_destroy", "su_batch_plan_sizes", "su_batch_plan_execute", "su_batch_plan_finalize",
     "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
     "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
-    "su_mlp_loss_grad", "speedup_train_proposal",
+    "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
 ]
 MLP_PARAMS = 34178
 
@@ -41,7 +41,15 @@ class SpeedupError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_blocks", ctypes.c_int), ("hierarchy", ctypes.c_int),
                 ("instance", ctypes.c_uint32), ("width_factor", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64)]
+                ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64), ("seg_log2", ctypes.c_int),
+                ("rounds", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("seg_log2", ctypes.c_int), ("rounds", ctypes.c_int), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class TrainOptions(ctypes.Structure):
@@ -99,6 +107,10 @@ def load(build_if_missing=True):
     L.su_plan_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), pi, ctypes.POINTER(i64)]
     L.su_plan_execute.argtypes = [vp, vp, vp, vp, pi]
     L.su_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
+    L.su_plan_shape.argtypes = [vp, pi, pi]
+    L.su_autotune.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                              ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
+    L.su_autotune_clear.argtypes = []
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
@@ -170,7 +182,7 @@ def _stream(s):
 
 
 def options(precision="fp64", n_blocks=64, hierarchy=True, instance=0, width_factor=1.0, stream=None,
-            sample0=0):
+            sample0=0, seg_log2=0, rounds=0):
     o = Options()
     load().su_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -180,7 +192,27 @@ def options(precision="fp64", n_blocks=64, hierarchy=True, instance=0, width_fac
     o.width_factor = float(width_factor)
     o.stream = _stream(stream)
     o.sample0 = int(sample0)
+    o.seg_log2 = int(seg_log2)
+    o.rounds = int(rounds)
     return o
+
+
+def su_autotune(model, params, a, b, T, p, s, n_probe, seed, **kw):
+    """Time every launch shape on n_probe samples, store the fastest for
+    (precision, model, p, s); returns (best, all) as dicts."""
+    pr, npar = _params(params)
+    o = options(**kw)
+    best = Tuning()
+    cap = 64
+    arr = (Tuning * cap)()
+    n = ctypes.c_int(0)
+    _check(load().su_autotune(_model(model), pr, npar, a, b, T, p, s, int(n_probe), int(seed), ctypes.byref(o),
+                              ctypes.byref(best), arr, cap, ctypes.byref(n)))
+    return best.as_dict(), [arr[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def su_autotune_clear():
+    _check(load().su_autotune_clear())
 
 
 def su_version():
@@ -409,6 +441,12 @@ class Plan:
                                     ctypes.byref(sa)))
         self.tuple_bytes, self.scratch_bytes = tb.value, sb.value
         self.levels, self.slice_actions = lv.value, sa.value
+
+    def su_plan_shape(self):
+        """(seg_log2, rounds) of this plan's launch."""
+        f, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().su_plan_shape(self._h, ctypes.byref(f), ctypes.byref(r)))
+        return f.value, r.value
 
     def su_plan_execute(self, d_tuples, d_scratch, stream=None):
         """Launch; returns the number of kernel launches made."""

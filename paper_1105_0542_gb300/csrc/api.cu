@@ -18,6 +18,7 @@
 #include <numeric>
 #include <random>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -32,6 +33,24 @@
 namespace {
 
 thread_local std::string g_err;
+
+// launch shapes stored by su_autotune, per (precision, model, p, s)
+struct TuneKey {
+    int precision, model, p, s;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(precision, model, p, s) < std::tie(o.precision, o.model, o.p, o.s);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, su_tuning> g_tune;
+
+bool tuned_shape(int precision, int model, int p, int s, su_tuning &out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({precision, model, p, s});
+    if (it == g_tune.end()) return false;
+    out = it->second;
+    return true;
+}
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -158,6 +177,8 @@ static int validate(int model, const double *params, int n_params, double a, dou
     if (!(o.width_factor > 0) || !std::isfinite(o.width_factor))
         return fail(SU_EINVAL, "width_factor must be finite and > 0");
     if (o.sample0 < 0 || o.sample0 + n_mc > kMaxSamples) return fail(SU_EINVAL, "sample0 out of range");
+    if (o.seg_log2 < 0 || o.seg_log2 > su::kMaxFine) return fail(SU_EINVAL, "seg_log2 must be in 0..5");
+    if (o.rounds < 0 || o.rounds > 8) return fail(SU_EINVAL, "rounds must be in 0..8");
     return SU_OK;
 }
 
@@ -205,8 +226,15 @@ static int configure(su_plan &pl) {
     P.a = pl.a;
     P.b = pl.b;
     for (int n = 1; n <= S; ++n) P.sigma[n] = pl.opt.width_factor * std::sqrt(pl.T / std::ldexp(1.0, n + 1));
+    // launch shape: explicit, else stored by su_autotune, else the rule
+    su_tuning tuned{};
+    const bool have_tuned = tuned_shape(prec, pl.model, pl.p, S, tuned);
+    // rule: 16-slice register segments in double (measured 1-5 % faster than
+    // 32 at 2 CTAs per SM), 32 in single precision
+    const int seg_rule = prec == SU_FP64 ? 4 : kMaxFine;
+    int seg = pl.opt.seg_log2 > 0 ? pl.opt.seg_log2 : (have_tuned ? tuned.seg_log2 : seg_rule);
     P.S = S;
-    P.F = std::min(S, kMaxFine);
+    P.F = std::min(S, std::max(1, seg));
     P.levels = pl.levels;
     P.wf_on = pl.opt.width_factor != 1.0;
     P.lwf = std::log(pl.opt.width_factor);
@@ -238,11 +266,17 @@ static int configure(su_plan &pl) {
     if (pl.smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);
     if (occ1 < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
-    // fewer, larger items when there are many per resident CTA, as long as
-    // the larger weight buffer keeps as many CTAs resident
-    const int64_t per = P.n_items / ((int64_t)sms * occ1);
-    int rounds = (int)std::max<int64_t>(1, std::min<int64_t>(4, per / 16));
-    while (rounds > 1 && shape(rounds) < occ1) --rounds;
+    // rule: one path per thread per item (the per-item reduction is cheap next
+    // to the sampling, and small items leave no tail), more only to keep the
+    // per-item tuples under 512 MB, and only while as many CTAs stay resident
+    int rounds = 1;
+    while (rounds < 8 && P.n_items * pl.levels * 32 > ((int64_t)512 << 20)) shape(rounds *= 2);
+    while (rounds > 1 && shape(rounds) < occ1) rounds /= 2;
+    if (pl.opt.rounds > 0 || (have_tuned && tuned.rounds > 0)) {
+        rounds = pl.opt.rounds > 0 ? pl.opt.rounds : tuned.rounds;
+        if (shape(rounds) < 1)
+            return fail(SU_ENOTSUP, "rounds = %d does not fit (shared memory %zu bytes)", rounds, pl.smem);
+    }
     const int occ = shape(rounds);
     pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
     pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
@@ -307,6 +341,13 @@ int su_plan_sizes(const su_plan *pl, int64_t *tuple_bytes, int64_t *scratch_byte
     if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
     if (levels) *levels = pl->levels;
     if (slice_actions) *slice_actions = pl->slice_actions;
+    return SU_OK;
+}
+
+int su_plan_shape(const su_plan *pl, int *seg_log2, int *rounds) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (seg_log2) *seg_log2 = pl->s > 0 ? pl->P.F : 0;
+    if (rounds) *rounds = pl->s > 0 ? pl->P.rounds : 0;
     return SU_OK;
 }
 
@@ -436,6 +477,90 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     std::memcpy(&flags, h.data() + tb / sizeof(double), sizeof(int));
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+// ------------------------------------------------------------ autotuner
+int su_autotune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return SU_OK;
+}
+
+int su_autotune(int model, const double *params, int n_params, double a, double b, double T, int p, int s,
+                int64_t n_probe, uint64_t seed, const su_options *opt, su_tuning *best, su_tuning *all,
+                int cap, int *n_all) {
+    if (!best) return fail(SU_EINVAL, "best missing");
+    if (n_all) *n_all = 0;
+    if (s < 1) return fail(SU_EINVAL, "s must be >= 1 to tune the sampler");
+    if (cap < 0 || (cap > 0 && !all)) return fail(SU_EINVAL, "all and cap inconsistent");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    o.seg_log2 = 0;
+    o.rounds = 0;
+    int rc = validate(model, params, n_params, a, b, T, p, s, n_probe, o);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    struct Res {
+        void *buf = nullptr;
+        size_t cap = 0;
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Res() {
+            if (buf) cudaFree(buf);
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } res;
+    CU(cudaEventCreate(&res.e[0]), "event");
+    CU(cudaEventCreate(&res.e[1]), "event");
+    std::vector<su_tuning> got;
+    for (int F = 1; F <= std::min(s, su::kMaxFine); ++F) {
+        for (int r : {1, 2, 4, 8}) {
+            su_options oc = o;
+            oc.seg_log2 = F;
+            oc.rounds = r;
+            su_plan *pl = nullptr;
+            rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_probe, seed, &oc, &pl);
+            if (rc == SU_ENOTSUP) continue;   // this shape's shared memory does not fit
+            if (rc) return rc;
+            std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+            const size_t need = (size_t)(pl->tuple_bytes + pl->scratch_bytes);
+            if (need > res.cap) {
+                if (res.buf) cudaFree(res.buf);
+                res.buf = nullptr;
+                res.cap = 0;
+                CU(cudaMalloc(&res.buf, need), "cudaMalloc(probe buffers)");
+                res.cap = need;
+            }
+            void *d_tup = res.buf, *d_scr = static_cast<char *>(res.buf) + pl->tuple_bytes;
+            rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);   // warm-up
+            if (rc) return rc;
+            float ms_best = INFINITY;
+            for (int k = 0; k < 2; ++k) {
+                CU(cudaEventRecord(res.e[0], st), "event record");
+                rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);
+                if (rc) return rc;
+                CU(cudaEventRecord(res.e[1], st), "event record");
+                CU(cudaEventSynchronize(res.e[1]), "probe");
+                float ms = 0;
+                CU(cudaEventElapsedTime(&ms, res.e[0], res.e[1]), "event time");
+                ms_best = std::min(ms_best, ms);
+            }
+            got.push_back({pl->P.F, pl->P.rounds, (double)ms_best});
+        }
+    }
+    if (got.empty()) return fail(SU_ENOTSUP, "no launch shape fits this device");
+    const su_tuning top = *std::min_element(got.begin(), got.end(),
+                                            [](const su_tuning &x, const su_tuning &y) { return x.ms < y.ms; });
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[{o.precision, model, p, s}] = top;
+    }
+    *best = top;
+    for (int i = 0; i < (int)got.size() && i < cap; ++i) all[i] = got[(size_t)i];
+    if (n_all) *n_all = (int)got.size();
+    g_err.clear();
+    return SU_OK;
 }
 
 int speedup_logweights(int model, const double *params, int n_params, double a, double b, double T,

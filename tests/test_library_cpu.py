@@ -114,6 +114,8 @@ def test_generator_term_counts_of_the_anharmonic_oscillator():
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"n_blocks": 0}),
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"width_factor": -1.0}),
     ((9, [1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {}),                  # unknown model
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"seg_log2": 6}),   # launch shape out of range
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"rounds": 9}),
 ])
 def test_invalid_arguments_are_rejected(args, kw):
     with pytest.raises(su.SpeedupError) as e:
