@@ -1043,6 +1043,7 @@ extern "C" int speedup_amplitude_proposal(int model, const double *params, int n
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(dbuf, st);
     if (e != cudaSuccess) return cuda_fail(e, "proposal sampling");
+    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return su_plan_finalize(pl, h.data(), nullptr, out);
 }
@@ -1084,6 +1085,7 @@ extern "C" int speedup_proposal_logweights(int model, const double *params, int 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(d_flag, st);
     if (e != cudaSuccess) return cuda_fail(e, "proposal per-sample weights");
+    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return SU_OK;
 }
@@ -1385,6 +1387,7 @@ extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_
     CU(cudaMemcpyAsync(h.data(), d_tup, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read tuples");
     CU(cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     CU(cudaStreamSynchronize(st), "sampling");
+    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     for (int d = 0; d < P.levels; ++d) level_result(laf, h.data(), nb, P.levels, d, &out[s - d]);
     return SU_OK;

@@ -1,6 +1,7 @@
 #pragma once
-// The proposal network on the tensor cores (sm_103a): bfloat16 operands,
-// float accumulation, 128 rows at a time.
+// The proposal network on the 5th-generation tensor cores (sm_103a):
+// tcgen05.mma with bfloat16 operands in shared memory and float accumulators
+// in tensor memory, 128 rows (paths) at a time.
 //
 // x = (a, b, T, n/s, q_L, q_R) -> Linear(6,128) -> GELU -> Linear(128,128)
 // -> GELU -> Linear(128,128) -> GELU -> Linear(128,2) = (shift, log-scale),
@@ -8,14 +9,19 @@
 // (W1[128][6], b1, W2[128][128], b2, W3[128][128], b3, W4[2][128], b4),
 // matrices stored [out][in].
 //
-// On the device the weights form one blob whose layout is the shared-memory
-// layout: bfloat16 matrices [out][in] with rows padded to 24 or 136 elements
-// (48 / 272 bytes, so the eight rows an ldmatrix reads fall into distinct
-// 16-byte bank groups), the 2-row output matrix padded to 8 zero rows, then
-// the float biases.  A CTA copies the blob once and keeps it resident.
+// Operand layout (A = activations [128 rows][K], B = weights [N rows][K],
+// both K-major): core matrices of 8 rows x 16 bytes (8 bf16), stored
+// contiguously; K-adjacent core matrices 128 bytes apart (the descriptor's
+// leading byte offset), 8-row groups K/8 * 128 bytes apart (stride byte
+// offset); no swizzle.  A CTA copies the weight blob (this layout, plus the
+// float biases) once and keeps it resident.
 //
-// Layer GEMMs use mma.sync m16n8k16 (bf16 x bf16 -> f32): warp w of 8 owns
-// rows 16w..16w+15 of the 128-row tile and all output columns.
+// One layer = K/16 MMAs of M = 128, N = 128 (N = 16 for the output layer,
+// rows 2..15 of W4 zero) issued by one thread into tensor-memory columns
+// [0, 128) (outputs: [128, 144)), a commit to an mbarrier, and an epilogue
+// in which warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows),
+// columns 64 (w / 4) .. +63, adds the bias, applies GELU and writes the
+// bfloat16 activations back into the A tile for the next layer.
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -24,38 +30,39 @@ namespace mlp {
 
 constexpr int kIn = 6, kHid = 128, kOut = 2;
 constexpr int kParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kHid + kOut;   // 34178
-constexpr int kS1 = 24;    // row stride (elements) of W1 and of the input tile
-constexpr int kSH = 136;   // row stride of W2, W3, W4 and of the hidden tile
-constexpr int kRows = 128; // rows per tile
+constexpr int kK1 = 16;        // layer-1 K: the 6 features, zero-padded
+constexpr int kNOut = 16;      // output-layer N: 2 outputs, zero-padded
+constexpr int kRows = 128;     // rows per tile = the MMA's M
 constexpr int kThreads = 256;
+constexpr int kTmemCols = 256; // [0, 128) hidden accumulator, [128, 144) outputs
 
-// blob layout, byte offsets
-constexpr int kOffW1 = 0;
-constexpr int kOffW2 = kOffW1 + kHid * kS1 * 2;
-constexpr int kOffW3 = kOffW2 + kHid * kSH * 2;
-constexpr int kOffW4 = kOffW3 + kHid * kSH * 2;
-constexpr int kOffB = kOffW4 + 8 * kSH * 2;
-constexpr int kBlobBytes = kOffB + (3 * kHid + 8) * 4;   // 79520
+// byte offset of element (r, k) of an operand with K columns
+__host__ __device__ constexpr int cm_off(int r, int k, int K) {
+    return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// blob layout (the shared-memory image), byte offsets
+constexpr int kOffW1 = 0;                                 // [128][16]
+constexpr int kOffW2 = kOffW1 + kHid * kK1 * 2;           // [128][128]
+constexpr int kOffW3 = kOffW2 + kHid * kHid * 2;          // [128][128]
+constexpr int kOffW4 = kOffW3 + kHid * kHid * 2;          // [16][128]
+constexpr int kOffB = kOffW4 + kNOut * kHid * 2;          // b1, b2, b3 [128], b4 [2] (+ pad), float
+constexpr int kBlobBytes = kOffB + (3 * kHid + 8) * 4;    // 75296
 static_assert(kBlobBytes % 16 == 0, "blob copies in 16-byte pieces");
 
 // tile buffers (shared memory, byte sizes)
-constexpr int kX0Bytes = kRows * kS1 * 2;
-constexpr int kHBytes = kRows * kSH * 2;
+constexpr int kX0Bytes = kRows * kK1 * 2;
+constexpr int kHBytes = kRows * kHid * 2;
 
 #ifdef __CUDACC__
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// ---- legacy warp-level helpers (mma.sync), used by the training GEMM
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n"
-                 : "=r"(r0), "=r"(r1)
                  : "r"(addr));
 }
 
@@ -70,92 +77,185 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 
 __device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
 
-// acc[16 n-tiles][4] of warp w (rows 16w..16w+15, columns 0..127) from the
-// input tile A (row stride sa elements, K = 16 * ksteps) and the matrix W
-// ([128][sw]), both in shared memory
-__device__ __forceinline__ void tile_gemm_128(float (&acc)[16][4], const __nv_bfloat16 *A, int sa,
-                                              const __nv_bfloat16 *W, int sw, int ksteps) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// ---- tcgen05 plumbing
+// shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: float accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
+
+struct Tc {
+    uint32_t tmem;     // tensor-memory base address (lane 0, first column)
+    uint32_t mbar;     // shared address of the MMA-completion mbarrier
+    uint32_t phase;    // parity of the next completion to wait for
+};
+
+// All threads: mbarrier init (thread 0), tensor-memory allocation (warp 0).
+// slot and bar are shared-memory words of the CTA.
+__device__ __forceinline__ Tc tc_begin(uint32_t *slot, uint64_t *bar) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    Tc t;
+    t.tmem = *slot;
+    t.mbar = smem_u32(bar);
+    t.phase = 0;
+    return t;
+}
+
+// All threads, after the last use: warp 0 frees the tensor memory.
+__device__ __forceinline__ void tc_end(const Tc &t) {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(kTmemCols));
+}
+
+// One layer's MMAs, D[:, col..col+N) = A[128][K] B[N][K]^T, issued by thread
+// 0 after the other threads' shared-memory writes (fenced for the async
+// proxy and synchronised by the caller), then committed to the mbarrier.
+__device__ __forceinline__ void tc_layer(const Tc &t, uint32_t a, uint32_t b, int K, int N, uint32_t col) {
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sbo = (uint32_t)(K / 8) * 128;
+        const uint32_t id = instr_desc(kRows, N);
+        for (int ks = 0; ks < K / 16; ++ks) {
+            const uint64_t ad = smem_desc(a + ks * 256, 128, sbo);
+            const uint64_t bd = smem_desc(b + ks * 256, 128, sbo);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(t.tmem + col),
+                "l"(ad), "l"(bd), "r"(id), "r"((uint32_t)(ks > 0)));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(t.mbar));
+    }
+}
+
+// All threads: wait (bounded) for the last commit; false if it never came.
+__device__ __forceinline__ bool tc_wait(Tc &t) {
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(t.mbar), "r"(t.phase));
+    t.phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-    for (int t = 0; t < 16; ++t)
-        acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-    const int arow = 16 * warp + (lane & 15);
-    const int acol = (lane >> 4) * 8;
-    const int brow = (lane & 7) + ((lane >> 4) << 3);
-    const int bcol = ((lane >> 3) & 1) * 8;
-    for (int ks = 0; ks < ksteps; ++ks) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(smem_u32(A + arow * sa + ks * 16 + acol), a0, a1, a2, a3);
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Epilogue of a hidden layer: bias + GELU of the accumulator, bfloat16, into
+// the A tile H ([128][128], operand layout); then fenced for the next MMA.
+__device__ __forceinline__ void tc_store_gelu(const Tc &t, const float *bias, unsigned char *H) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = 32 * (warp & 3) + lane;
+    const int c0 = 64 * (warp >> 2);
+    const uint32_t base = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
 #pragma unroll
-        for (int np = 0; np < 8; ++np) {   // two n8 tiles per ldmatrix.x4
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4(smem_u32(W + (np * 16 + brow) * sw + ks * 16 + bcol), b0, b1, b2, b3);
-            mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-            mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+    for (int cc = 0; cc < 64; cc += 16) {
+        float v[16];
+        tmem_ld16(base + (uint32_t)cc, v);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int c = c0 + cc + 8 * half;
+            uint4 w;
+            w.x = pack_bf16(gelu(v[8 * half + 0] + bias[c + 0]), gelu(v[8 * half + 1] + bias[c + 1]));
+            w.y = pack_bf16(gelu(v[8 * half + 2] + bias[c + 2]), gelu(v[8 * half + 3] + bias[c + 3]));
+            w.z = pack_bf16(gelu(v[8 * half + 4] + bias[c + 4]), gelu(v[8 * half + 5] + bias[c + 5]));
+            w.w = pack_bf16(gelu(v[8 * half + 6] + bias[c + 6]), gelu(v[8 * half + 7] + bias[c + 7]));
+            *reinterpret_cast<uint4 *>(H + cm_off(row, c, kHid)) = w;
         }
     }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
 }
 
-// bias + GELU, bfloat16, into the hidden tile H (row stride kSH)
-__device__ __forceinline__ void tile_store_gelu(const float (&acc)[16][4], const float *bias, __nv_bfloat16 *H) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r0 = 16 * warp + (lane >> 2);
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-        const int c = 8 * t + (lane & 3) * 2;
-        const float b0 = bias[c], b1 = bias[c + 1];
-        __nv_bfloat162 lo = __floats2bfloat162_rn(gelu(acc[t][0] + b0), gelu(acc[t][1] + b1));
-        __nv_bfloat162 hi = __floats2bfloat162_rn(gelu(acc[t][2] + b0), gelu(acc[t][3] + b1));
-        *reinterpret_cast<__nv_bfloat162 *>(H + r0 * kSH + c) = lo;
-        *reinterpret_cast<__nv_bfloat162 *>(H + (r0 + 8) * kSH + c) = hi;
-    }
-}
-
-// The whole network on one 128-row tile: inputs in X0 (bf16, [128][kS1],
-// columns 6..15 zero), hidden tile H ([128][kSH]), outputs (shift, ls) into
-// out[row * 2 + {0,1}].  All 256 threads of the CTA take part; contains
-// __syncthreads.
-__device__ __forceinline__ void tile_forward(const unsigned char *blob, const __nv_bfloat16 *X0,
-                                             __nv_bfloat16 *H, float *out) {
-    const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(blob + kOffW1);
-    const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(blob + kOffW2);
-    const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(blob + kOffW3);
-    const __nv_bfloat16 *W4 = reinterpret_cast<const __nv_bfloat16 *>(blob + kOffW4);
+// The whole network on one 128-row tile.  X0: the features in operand layout
+// ([128][16], columns 6..15 zero), written and synchronised by the caller
+// (fence.proxy.async by the writers, then __syncthreads); H: the hidden tile;
+// out[row * 2 + {0, 1}] = (shift, ls).  All 256 threads; returns false on
+// all threads if an MMA never completed (the tile's outputs are then invalid).
+__device__ __forceinline__ bool tile_forward(Tc &t, const unsigned char *blob, const unsigned char *X0,
+                                             unsigned char *H, float *out) {
     const float *B = reinterpret_cast<const float *>(blob + kOffB);
-    float acc[16][4];
-    tile_gemm_128(acc, X0, kS1, W1, kS1, 1);
-    tile_store_gelu(acc, B, H);
-    __syncthreads();
-    tile_gemm_128(acc, H, kSH, W2, kSH, 8);
-    __syncthreads();                    // every warp has read H
-    tile_store_gelu(acc, B + kHid, H);
-    __syncthreads();
-    tile_gemm_128(acc, H, kSH, W3, kSH, 8);
-    __syncthreads();
-    tile_store_gelu(acc, B + 2 * kHid, H);
-    __syncthreads();
-    // output layer: one n8 tile (rows 0, 1 of W4 are the network's, 2..7 zero)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-    const int arow = 16 * warp + (lane & 15);
-    const int acol = (lane >> 4) * 8;
-    const int brow = lane & 7;
-    const int bcol = ((lane >> 3) & 1) * 8;
-#pragma unroll
-    for (int ks = 0; ks < 8; ++ks) {
-        uint32_t a0, a1, a2, a3, b0, b1;
-        ldsm_x4(smem_u32(H + arow * kSH + ks * 16 + acol), a0, a1, a2, a3);
-        ldsm_x2(smem_u32(W4 + brow * kSH + ks * 16 + bcol), b0, b1);
-        mma_bf16(d, a0, a1, a2, a3, b0, b1);
+    const uint32_t sb = smem_u32(blob), sx = smem_u32(X0), sh = smem_u32(H);
+    bool ok = true;
+    tc_layer(t, sx, sb + kOffW1, kK1, kHid, 0);
+    ok &= tc_wait(t);
+    tc_store_gelu(t, B, H);
+    tc_layer(t, sh, sb + kOffW2, kHid, kHid, 0);
+    ok &= tc_wait(t);
+    tc_store_gelu(t, B + kHid, H);
+    tc_layer(t, sh, sb + kOffW3, kHid, kHid, 0);
+    ok &= tc_wait(t);
+    tc_store_gelu(t, B + 2 * kHid, H);
+    tc_layer(t, sh, sb + kOffW4, kHid, kNOut, kHid);
+    ok &= tc_wait(t);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {   // the output columns of the warp's 32 rows
+        uint32_t r0, r1;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                     : "=r"(r0), "=r"(r1)
+                     : "r"(t.tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)kHid));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int row = 32 * warp + lane;
+        out[2 * row] = __uint_as_float(r0) + B[3 * kHid];
+        out[2 * row + 1] = __uint_as_float(r1) + B[3 * kHid + 1];
     }
-    if ((lane & 3) == 0) {              // columns 0 and 1 live in lanes 0, 4, ..., 28
-        const int r0 = 16 * warp + (lane >> 2);
-        out[2 * r0] = d[0] + B[3 * kHid];
-        out[2 * r0 + 1] = d[1] + B[3 * kHid + 1];
-        out[2 * (r0 + 8)] = d[2] + B[3 * kHid];
-        out[2 * (r0 + 8) + 1] = d[3] + B[3 * kHid + 1];
-    }
-    __syncthreads();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// features of one row into the X0 tile (operand layout): columns 0..5, the
+// zero padding of columns 6..7 in the same 16-byte chunk
+__device__ __forceinline__ void store_features(unsigned char *X0, int row, __nv_bfloat16 f0, __nv_bfloat16 f1,
+                                               __nv_bfloat16 f2, __nv_bfloat16 f3, __nv_bfloat16 f4,
+                                               __nv_bfloat16 f5) {
+    __nv_bfloat162 p0 = __halves2bfloat162(f0, f1), p1 = __halves2bfloat162(f2, f3), p2 = __halves2bfloat162(f4, f5);
+    uint4 w;
+    w.x = *reinterpret_cast<uint32_t *>(&p0);
+    w.y = *reinterpret_cast<uint32_t *>(&p1);
+    w.z = *reinterpret_cast<uint32_t *>(&p2);
+    w.w = 0u;
+    *reinterpret_cast<uint4 *>(X0 + cm_off(row, 0, kK1)) = w;
 }
 #endif
 

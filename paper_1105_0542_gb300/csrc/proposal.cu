@@ -36,10 +36,14 @@ static uint16_t bf16_rn(float f) {
 
 void pack_blob(const float *theta, unsigned char *blob) {
     std::memset(blob, 0, kBlobBytes);
-    auto put = [&](int off, int stride, int rows, int cols, const float *src) {
-        uint16_t *dst = reinterpret_cast<uint16_t *>(blob + off);
+    // matrix [rows][cols] (row-major floats) into the operand layout with K
+    // columns (cols <= K, the rest zero)
+    auto put = [&](int off, int K, int rows, int cols, const float *src) {
         for (int r = 0; r < rows; ++r)
-            for (int c = 0; c < cols; ++c) dst[r * stride + c] = bf16_rn(src[r * cols + c]);
+            for (int c = 0; c < cols; ++c) {
+                const uint16_t v = bf16_rn(src[r * cols + c]);
+                std::memcpy(blob + off + cm_off(r, c, K), &v, 2);
+            }
     };
     const float *p = theta;
     const float *W1 = p;
@@ -57,10 +61,10 @@ void pack_blob(const float *theta, unsigned char *blob) {
     const float *W4 = p;
     p += kOut * kHid;
     const float *b4 = p;
-    put(kOffW1, kS1, kHid, kIn, W1);
-    put(kOffW2, kSH, kHid, kHid, W2);
-    put(kOffW3, kSH, kHid, kHid, W3);
-    put(kOffW4, kSH, kOut, kHid, W4);
+    put(kOffW1, kK1, kHid, kIn, W1);
+    put(kOffW2, kHid, kHid, kHid, W2);
+    put(kOffW3, kHid, kHid, kHid, W3);
+    put(kOffW4, kHid, kOut, kHid, W4);
     float *B = reinterpret_cast<float *>(blob + kOffB);
     std::memcpy(B, b1, kHid * 4);
     std::memcpy(B + kHid, b2, kHid * 4);
@@ -76,8 +80,8 @@ using mlp::kBlobBytes;
 using mlp::kX0Bytes;
 using mlp::kHBytes;
 using mlp::kRows;
-using mlp::kS1;
 using mlp::kIn;
+using mlp::Tc;
 using mlp::tile_forward;
 constexpr int kT = mlp::kThreads;
 
@@ -94,11 +98,13 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
     const SamplerParams &P = Q.base;
     const int tid = threadIdx.x;
     const int S = P.S, N = 1 << S, L = P.levels;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
     unsigned char *blob = smem_raw;
     size_t off = kBlobBytes;
-    __nv_bfloat16 *X0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + off);
+    unsigned char *X0 = smem_raw + off;
     off += kX0Bytes;
-    __nv_bfloat16 *H = reinterpret_cast<__nv_bfloat16 *>(smem_raw + off);
+    unsigned char *H = smem_raw + off;
     off += kHBytes;
     float *out = reinterpret_cast<float *>(smem_raw + off);
     off += kRows * 2 * 4;
@@ -117,9 +123,10 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
         const float *g = reinterpret_cast<const float *>(P.tables);
         for (int i = tid; i < S * P.M; i += kT) tab[i] = g[i];
         for (int i = tid; i <= SU_MAX_S; i += kT) sig[i] = (float)P.sigma[i];
-        for (int i = tid; i < kRows * kS1; i += kT) X0[i] = __float2bfloat16(0.f);
+        for (int i = tid; i < kX0Bytes / 16; i += kT) reinterpret_cast<uint4 *>(X0)[i] = make_uint4(0, 0, 0, 0);
     }
-    __syncthreads();
+    Tc tc = mlp::tc_begin(&tmem_slot, &mma_bar);   // contains __syncthreads
+    bool alive = true;
 
     const float fa = (float)P.a, fb = (float)P.b, fT = (float)Q.T;
     const __nv_bfloat16 ba = __float2bfloat16_rn(fa), bb = __float2bfloat16_rn(fb), bT = __float2bfloat16_rn(fT);
@@ -131,7 +138,7 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
     st.inst = P.instance;
     st.bm = nullptr;
 
-    for (int64_t item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+    for (int64_t item = blockIdx.x; alive && item < P.n_items; item += gridDim.x) {
         const int64_t bk = item / P.items_per_block;
         const int64_t r = item - bk * P.items_per_block;
         const int64_t lo = bk * P.n_mc / P.n_blocks;
@@ -149,22 +156,21 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
             qs[N * kRows + p] = fb;
             corr[p] = 0.f;
         }
-        for (int n = 1; n <= S; ++n) {
+        for (int n = 1; alive && n <= S; ++n) {
             const int h = N >> n;
             const __nv_bfloat16 bn = __float2bfloat16_rn((float)n / (float)S);
-            for (int i = 0; i < (1 << (n - 1)); ++i) {
+            for (int i = 0; alive && i < (1 << (n - 1)); ++i) {
                 const int kL = 2 * i * h, kM = kL + h, kR = kL + 2 * h;
-                if (owner) {
-                    __nv_bfloat16 *x = X0 + p * kS1;
-                    x[0] = ba;
-                    x[1] = bb;
-                    x[2] = bT;
-                    x[3] = bn;
-                    x[4] = __float2bfloat16_rn(qs[kL * kRows + p]);
-                    x[5] = __float2bfloat16_rn(qs[kR * kRows + p]);
-                }
+                if (owner)
+                    mlp::store_features(X0, p, ba, bb, bT, bn, __float2bfloat16_rn(qs[kL * kRows + p]),
+                                        __float2bfloat16_rn(qs[kR * kRows + p]));
+                asm volatile("fence.proxy.async.shared::cta;");
                 __syncthreads();
-                tile_forward(blob, X0, H, out);
+                if (!tile_forward(tc, blob, X0, H, out)) {
+                    if (tid == 0) atomicOr(P.flags, 4);   // an MMA never completed
+                    alive = false;
+                    break;
+                }
                 if (owner) {
                     const uint32_t j = (1u << (n - 1)) - 1u + (uint32_t)i;
                     // the plain single-precision stream: slot j' & 3 of call j' >> 2, j' = j + 1
@@ -185,6 +191,7 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
             }
             if (owner) corr[n * kRows + p] = c;
         }
+        if (!alive) break;
         // W_p on every level of the path, plus the proposal weight
         if (owner) {
             for (int d = 0; d < L; ++d) {
@@ -228,33 +235,45 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
         }
         __syncthreads();
     }
+    mlp::tc_end(tc);
 }
 
+// rows of features X (n x 6 floats) -> Y (n x 2); a tile whose MMAs never
+// complete gives NaN outputs and ends the CTA's work
 __global__ void __launch_bounds__(mlp::kThreads, 1) mlp_forward_kernel(const unsigned char *gblob,
                                                                        const float *X, int64_t n,
                                                                        float *Y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
     unsigned char *blob = smem_raw;
-    __nv_bfloat16 *X0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kBlobBytes);
-    __nv_bfloat16 *H = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kBlobBytes + kX0Bytes);
+    unsigned char *X0 = smem_raw + kBlobBytes;
+    unsigned char *H = smem_raw + kBlobBytes + kX0Bytes;
     float *out = reinterpret_cast<float *>(smem_raw + kBlobBytes + kX0Bytes + kHBytes);
     const int tid = threadIdx.x;
     copy16(blob, gblob, kBlobBytes, tid, kT);
-    for (int i = tid; i < kRows * kS1; i += kT) X0[i] = __float2bfloat16(0.f);
-    __syncthreads();
+    for (int i = tid; i < kX0Bytes / 16; i += kT) reinterpret_cast<uint4 *>(X0)[i] = make_uint4(0, 0, 0, 0);
+    Tc tc = mlp::tc_begin(&tmem_slot, &mma_bar);
     for (int64_t t0 = (int64_t)blockIdx.x * kRows; t0 < n; t0 += (int64_t)gridDim.x * kRows) {
         if (tid < kRows) {
             const int64_t r = t0 + tid;
-            for (int c = 0; c < kIn; ++c) X0[tid * kS1 + c] = __float2bfloat16_rn(r < n ? X[r * kIn + c] : 0.f);
+            float f[kIn];
+            for (int c = 0; c < kIn; ++c) f[c] = r < n ? X[r * kIn + c] : 0.f;
+            mlp::store_features(X0, tid, __float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]),
+                                __float2bfloat16_rn(f[2]), __float2bfloat16_rn(f[3]), __float2bfloat16_rn(f[4]),
+                                __float2bfloat16_rn(f[5]));
         }
+        asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
-        tile_forward(blob, X0, H, out);
+        const bool ok = tile_forward(tc, blob, X0, H, out);
         if (tid < kRows && t0 + tid < n) {
-            Y[(t0 + tid) * 2] = out[2 * tid];
-            Y[(t0 + tid) * 2 + 1] = out[2 * tid + 1];
+            Y[(t0 + tid) * 2] = ok ? out[2 * tid] : NAN;
+            Y[(t0 + tid) * 2 + 1] = ok ? out[2 * tid + 1] : NAN;
         }
         __syncthreads();
+        if (!ok) break;
     }
+    mlp::tc_end(tc);
 }
 
 const void *proposal_fn(int ring) {
