@@ -19,9 +19,10 @@
 // One layer = K/16 MMAs of M = 128, N = 128 (N = 16 for the output layer,
 // rows 2..15 of W4 zero) issued by one thread into tensor-memory columns
 // [0, 128) (outputs: [128, 144)), a commit to an mbarrier, and an epilogue
-// in which warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows),
-// columns 64 (w / 4) .. +63, adds the bias, applies GELU and writes the
-// bfloat16 activations back into the A tile for the next layer.
+// in which warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows) and
+// a quarter of the columns of its quadrant's rows (16 warps: 32 columns each),
+// adds the bias, applies GELU and writes the bfloat16 activations back into
+// the A tile for the next layer.
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -33,7 +34,8 @@ constexpr int kParams = kHid * kIn + kHid + 2 * (kHid * kHid + kHid) + kOut * kH
 constexpr int kK1 = 16;        // layer-1 K: the 6 features, zero-padded
 constexpr int kNOut = 16;      // output-layer N: 2 outputs, zero-padded
 constexpr int kRows = 128;     // rows per tile = the MMA's M
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;  // 16 warps: four per tensor-memory lane quadrant
+constexpr int kColsPerWarp = kHid * 4 / (kThreads / 32);   // epilogue columns of a warp
 constexpr int kTmemCols = 256; // [0, 128) hidden accumulator, [128, 144) outputs
 
 // byte offset of element (r, k) of an operand with K columns
@@ -186,10 +188,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __device__ __forceinline__ void tc_store_gelu(const Tc &t, const float *bias, unsigned char *H) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = 32 * (warp & 3) + lane;
-    const int c0 = 64 * (warp >> 2);
+    const int c0 = kColsPerWarp * (warp >> 2);
     const uint32_t base = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
 #pragma unroll
-    for (int cc = 0; cc < 64; cc += 16) {
+    for (int cc = 0; cc < kColsPerWarp; cc += 16) {
         float v[16];
         tmem_ld16(base + (uint32_t)cc, v);
 #pragma unroll
@@ -211,7 +213,7 @@ __device__ __forceinline__ void tc_store_gelu(const Tc &t, const float *bias, un
 // The whole network on one 128-row tile.  X0: the features in operand layout
 // ([128][16], columns 6..15 zero), written and synchronised by the caller
 // (fence.proxy.async by the writers, then __syncthreads); H: the hidden tile;
-// out[row * 2 + {0, 1}] = (shift, ls).  All 256 threads; returns false on
+// out[row * 2 + {0, 1}] = (shift, ls).  All kThreads threads; returns false on
 // all threads if an MMA never completed (the tile's outputs are then invalid).
 __device__ __forceinline__ bool tile_forward(Tc &t, const unsigned char *blob, const unsigned char *X0,
                                              unsigned char *H, float *out) {
