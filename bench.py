@@ -297,11 +297,21 @@ def run_ours(args):
     # results of the last pass: relative errors for time-to-1e-4
     ttr = {}
     rel = {}
+    top = {}
     for prec in kinds:
         for p in ps:
             t, sc = bufs[(p, prec)]
             res = plans[(p, prec)].su_plan_finalize(t.cpu().numpy(), sc)
             rel[(p, prec)] = res[inst.s]["rel_err"]
+            top[(p, prec)] = res[inst.s]
+    # single against double precision at every timed sweep point (independent
+    # streams: a statistical comparison, z = difference / combined error)
+    f32_vs_f64 = {}
+    for p in ps:
+        a, b = top[(p, "fp32")], top[(p, "fp64")]
+        sig = math.hypot(a["err"], b["err"])
+        f32_vs_f64[p] = {"fp64": b["amp"], "fp32": a["amp"], "rel_diff": (a["amp"] - b["amp"]) / b["amp"],
+                         "z": (a["amp"] - b["amp"]) / sig if sig > 0 else None}
     p_ref = 10 if 10 in ps else ps[-1]
     for prec in kinds:
         ms = [ev[(k, prec)][0].elapsed_time(ev[(k, prec)][1]) for k in range(args.warmup, args.warmup + args.steps)
@@ -377,6 +387,7 @@ def run_ours(args):
                                "chosen_fp32": ttr.get("fp32"),
                                "speedup": (ttr["fp64"] / ttr["fp32"]) if "fp64" in ttr and "fp32" in ttr else None,
                                "method": "per-sample cost x (rel_err/1e-4)^2 from the 1e7-sample run"},
+        "fp32_vs_fp64_top_level": f32_vs_f64,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
         "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
         "clocks": clock_info,
