@@ -268,7 +268,7 @@ typedef struct {
     double clip_quantile;  /* top-level log-weights above this quantile are clipped
                               for the training weights (rare huge weights would
                               otherwise fit one path); 0.999                         */
-    uint64_t seed;         /* minibatch draws; 1                                    */
+    uint64_t seed;         /* minibatch draws (Philox key, drawn on the device); 1  */
 } su_train_options;
 
 void su_train_options_default(su_train_options *t);
@@ -284,7 +284,9 @@ int su_mlp_loss_grad(const float *theta, const float *d_X, const float *d_u, con
  * clip_quantile), and run topt->steps Adam steps on minibatches drawn in
  * proportion to those weights.  theta: host, SU_MLP_PARAMS floats, initial
  * network in, trained network out.  loss_out (host, steps doubles, may be
- * NULL) receives the minibatch losses.  2 <= s <= 6.  Synchronous.
+ * NULL) receives the minibatch losses.  2 <= s <= 6.  Synchronous.  The
+ * minibatches are drawn on the device and one step is replayed as a CUDA
+ * graph on a stream of the call's own.
  */
 int speedup_train_proposal(int model, const double *params, int n_params,
                            double a, double b, double T, int p, int s, uint64_t seed,

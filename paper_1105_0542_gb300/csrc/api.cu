@@ -1201,31 +1201,58 @@ extern "C" int speedup_train_proposal(int model, const double *params, int n_par
         cdf[i] = acc;
     }
     if (!(acc > 0)) return fail(SU_ENONFINITE, "all training weights vanish");
-    // 3. Adam on minibatches of batch_paths paths x (N-1) midpoints
+    // 3. Adam on minibatches of batch_paths paths x (N-1) midpoints, drawn on
+    //    the device from the running sums of the weights; one step (draw, rows,
+    //    loss and gradient, Adam, loss record) is captured as a CUDA graph on a
+    //    stream of its own and replayed `steps` times
     const int R = to.batch_paths * (N - 1);
     su::train::Workspace ws;
     CU(ws.reserve(R), "training workspace");
+    double *d_cdf = nullptr, *d_losses = nullptr;
+    int *d_step = nullptr;
+    CU(cudaMalloc(&d_cdf, cdf.size() * sizeof(double)), "cudaMalloc(cdf)");
+    fr.v.push_back(d_cdf);
+    CU(cudaMalloc(&d_losses, (size_t)to.steps * sizeof(double)), "cudaMalloc(losses)");
+    fr.v.push_back(d_losses);
+    CU(cudaMalloc(&d_step, sizeof(int)), "cudaMalloc(step)");
+    fr.v.push_back(d_step);
+    struct GraphRes {
+        cudaStream_t st = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        ~GraphRes() {
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            if (st) cudaStreamDestroy(st);
+        }
+    } gr;
+    CU(cudaStreamCreateWithFlags(&gr.st, cudaStreamNonBlocking), "training stream");
     float sig[16] = {0};
     for (int n = 1; n <= s; ++n) sig[n] = (float)std::sqrt(T / std::ldexp(1.0, n + 1));
     CU(cudaMemcpy(d_sig, sig, sizeof sig, cudaMemcpyHostToDevice), "upload sigma");
+    CU(cudaMemcpy(d_cdf, cdf.data(), cdf.size() * sizeof(double), cudaMemcpyHostToDevice), "upload cdf");
     CU(cudaMemcpy(ws.theta, theta, (size_t)su::mlp::kParams * 4, cudaMemcpyHostToDevice), "upload theta");
     CU(cudaMemset(ws.m, 0, (size_t)su::mlp::kParams * 8), "clear moments");   // m and v are adjacent
+    CU(cudaMemset(d_step, 0, sizeof(int)), "clear step");
     CU(su::train::fill(ws.rw, 1.0f, R, nullptr), "row weights");
-    std::mt19937_64 rng(to.seed);
-    std::uniform_real_distribution<double> uni(0.0, acc);
-    std::vector<int> ids((size_t)to.batch_paths);
-    for (int t = 1; t <= to.steps; ++t) {
-        for (int k = 0; k < to.batch_paths; ++k)
-            ids[(size_t)k] = (int)(std::upper_bound(cdf.begin(), cdf.end(), uni(rng)) - cdf.begin());
-        for (int &k : ids) k = std::min(k, (int)to.n_train - 1);
-        CU(cudaMemcpy(d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice), "upload ids");
-        CU(su::train::build_rows(ws, d_paths, np1, d_ids, to.batch_paths, (float)a, (float)b, (float)T, s, d_sig,
-                                 nullptr),
-           "rows");
-        CU(su::train::loss_grad(ws, R, 1.0 / R, true, nullptr), "loss and gradient");
-        CU(su::train::adam_step(ws, t, (float)to.lr, nullptr), "adam");
-        if (loss_out) CU(cudaMemcpy(&loss_out[t - 1], ws.loss, 8, cudaMemcpyDeviceToHost), "read loss");
-    }
+    CU(cudaDeviceSynchronize(), "training set-up");
+    const int64_t n_train = to.n_train;
+    CU(cudaStreamBeginCapture(gr.st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t ce = su::train::sample_ids(d_cdf, n_train, acc, to.seed, d_step, to.batch_paths, d_ids, gr.st);
+    if (ce == cudaSuccess)
+        ce = su::train::build_rows(ws, d_paths, np1, d_ids, to.batch_paths, (float)a, (float)b, (float)T, s, d_sig,
+                                   gr.st);
+    if (ce == cudaSuccess) ce = su::train::loss_grad(ws, R, 1.0 / R, true, gr.st);
+    if (ce == cudaSuccess) ce = su::train::adam_step_dev(ws, d_step, (float)to.lr, gr.st);
+    if (ce == cudaSuccess) ce = su::train::step_tail(d_step, ws.loss, d_losses, gr.st);
+    const cudaError_t ee = cudaStreamEndCapture(gr.st, &gr.g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "capturing the training step");
+    CU(ee, "end capture");
+    CU(cudaGraphInstantiate(&gr.ge, gr.g, 0), "instantiate the training step");
+    for (int t = 0; t < to.steps; ++t) CU(cudaGraphLaunch(gr.ge, gr.st), "training step");
+    CU(cudaStreamSynchronize(gr.st), "training");
+    if (loss_out)
+        CU(cudaMemcpy(loss_out, d_losses, (size_t)to.steps * sizeof(double), cudaMemcpyDeviceToHost), "read losses");
     CU(cudaMemcpy(theta, ws.theta, (size_t)su::mlp::kParams * 4, cudaMemcpyDeviceToHost), "read theta");
     return SU_OK;
 }

@@ -10,41 +10,34 @@
 //
 // The hot path is ALU-bound (no HBM traffic per slice): paths live in
 // registers, the coefficient tables in shared memory.  A path of N = 2^S
-// slices is split into C = 2^(S-F) segments of 2^F slices (F = min(S, 5)):
+// slices is split into C = 2^(S-F) segments of 2^F slices (F <= min(S, 5),
+// the launch shape's segment size):
 // the C+1 segment endpoints (bisection levels 1..S-F) are generated first and
 // parked in shared memory; each segment's 2^F - 1 interior points (levels
 // S-F+1..S) are then generated in registers and all slices of the segment, at
 // every level, are evaluated before the next segment starts.
 //
-// Normal j of a sample (heap order: level n, midpoint i -> j = 2^(n-1)-1+i)
-// is Box-Muller branch (j & 1) of Philox call j >> 1.  Every call is computed
-// once and its second normal carried to the midpoint that uses it, except the
-// first midpoint of each in-register level in segment 0, whose call is shared
-// with the last midpoint of the previous level (in the last segment) and is
-// recomputed there (F-1 extra calls per path when C > 1).
+// Normal j of a sample (heap order: level n, midpoint i -> j = 2^(n-1)-1+i).
+// Double path: Box-Muller branch (j & 1) of Philox call j >> 1; every call is
+// computed once and its second normal carried to the midpoint that uses it,
+// except the first midpoint of each in-register level in segment 0, whose
+// call is shared with the last midpoint of the previous level (in the last
+// segment) and is recomputed there (F-1 extra calls per path when C > 1).
+// Single path: slot (j+1) & 3 of call (j+1) >> 2 (four normals per call), so
+// that from level 3 on a level's normals start on a call boundary; levels 1
+// and 2 of the register segment keep their call across segments.
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
 
 #include "boxmuller.cuh"
+#include "philox.cuh"
 #include "generator.h"
 #include "sampler.h"
 
 namespace su {
 namespace {
 
-// ---------------------------------------------------------------- Philox
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-    return c;
-}
 
 // ------------------------------------------------------------ Box-Muller
 template <typename R>

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "mlp.cuh"
+#include "philox.cuh"
 #include "train.h"
 
 namespace su {
@@ -320,6 +321,49 @@ __global__ void fill_kernel(float *p, float v, int n) {
     if (k < n) p[k] = v;
 }
 
+// Minibatch path ids of step *step: draw k is the 53-bit uniform u of Philox
+// call (*step, k, 0x7261696E, 0) under the key (seed lo, seed hi), and the id
+// is the first index whose cumulative weight exceeds u * total (a draw in
+// proportion to the weights).
+__global__ void sample_ids_kernel(const double *__restrict__ cdf, int64_t n, double total, uint2 key,
+                                  const int *__restrict__ step, int nb, int *ids) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)*step, (uint32_t)k, 0x7261696Eu, 0u), key);
+    const double u = ((double)(((uint64_t)w.x << 21) | (w.y >> 11)) + 0.5) * 0x1p-53;
+    const double x = u * total;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    ids[k] = (int)(lo < n ? lo : n - 1);
+}
+
+// Adam with the step number t = *step + 1 read on the device
+__global__ void adam_dev_kernel(float *th, const float *__restrict__ g, float *m, float *v, int n, float lr,
+                                float b1, float b2, float eps, const int *__restrict__ step) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float t = (float)(*step + 1);
+    const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    th[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+// record the step's loss and advance the step counter
+__global__ void step_tail_kernel(int *step, const double *__restrict__ loss, double *losses) {
+    losses[*step] = *loss;
+    *step += 1;
+}
+
 }  // namespace
 
 cudaError_t rows_from_features(Workspace &ws, const float *X, const float *u, const float *rw, int n, int R,
@@ -478,6 +522,25 @@ cudaError_t adam_step(Workspace &ws, int t, float lr, cudaStream_t st) {
     const float c1 = 1.f - std::pow(b1, (float)t), c2 = 1.f - std::pow(b2, (float)t);
     adam_kernel<<<(mlp::kParams + 255) / 256, 256, 0, st>>>(ws.theta, ws.grad, ws.m, ws.v, mlp::kParams, lr, b1, b2,
                                                            1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t sample_ids(const double *cdf, int64_t n, double total, uint64_t seed, const int *step, int nb,
+                       int *ids, cudaStream_t st) {
+    sample_ids_kernel<<<(nb + 127) / 128, 128, 0, st>>>(cdf, n, total,
+                                                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), step,
+                                                       nb, ids);
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step_dev(Workspace &ws, const int *step, float lr, cudaStream_t st) {
+    adam_dev_kernel<<<(mlp::kParams + 255) / 256, 256, 0, st>>>(ws.theta, ws.grad, ws.m, ws.v, mlp::kParams, lr,
+                                                               0.9f, 0.999f, 1e-8f, step);
+    return cudaGetLastError();
+}
+
+cudaError_t step_tail(int *step, const double *loss, double *losses, cudaStream_t st) {
+    step_tail_kernel<<<1, 1, 0, st>>>(step, loss, losses);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstddef>
+#include <cstdint>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -45,6 +46,15 @@ cudaError_t build_rows(Workspace &ws, const float *paths, int np1, const int *id
 cudaError_t rows_from_features(Workspace &ws, const float *X, const float *u, const float *rw, int n, int R,
                                cudaStream_t st);
 cudaError_t fill(float *p, float v, int n, cudaStream_t st);
+// minibatch path ids of step *step (device counter): nb draws in proportion to
+// the weights whose running sums are cdf[0..n) (total = cdf[n-1]), Philox under
+// the key seed
+cudaError_t sample_ids(const double *cdf, int64_t n, double total, uint64_t seed, const int *step, int nb,
+                       int *ids, cudaStream_t st);
+// Adam step with t = *step + 1 taken from the device
+cudaError_t adam_step_dev(Workspace &ws, const int *step, float lr, cudaStream_t st);
+// losses[*step] = *loss, then ++*step
+cudaError_t step_tail(int *step, const double *loss, double *losses, cudaStream_t st);
 
 }  // namespace train
 }  // namespace su
