@@ -37,6 +37,10 @@ METRIC = ("slice-actions/s and time to 1e-4 rel. error in A_N(a,b;T): plain vs c
 UNIT = "slice-actions/s"
 P_LIST = workloads.CONFIG2_P
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no FP64 tensor path); see the design doc
+# DRAM bytes (read + write) of one double-sampler launch of the p = 10 sweep
+# point on 2e5 samples, from the ncu capture summarised in
+# profiles/sampler_fp64_aho-g10_p10_s10_2e5.md; scaled by samples per launch
+FP64_TRAFFIC_BYTES, FP64_TRAFFIC_SAMPLES = 318_208, 200_000
 CPU_BUDGET_S = 15.0
 
 
@@ -362,7 +366,10 @@ def run_ours(args):
     fma64 = su.su_fma_peak("fp64")
     fma32 = su.su_fma_peak("fp32")
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": FP64_TRAFFIC_BYTES * n_mc / FP64_TRAFFIC_SAMPLES,
+                "traffic_note": "bytes per launch: DRAM read+write of the 2e5-sample ncu capture of the same "
+                                "kernel (p = 10) scaled by samples; the algorithmic bytes per slice-action are 0",
                 "kernel": "sampler_kernel<double, RING_EVEN> (+ its combine)",
                 "measured_fma_peak_tflops": {"fp64": 2 * fma64 / 1e12, "fp32": 2 * fma32 / 1e12},
                 "frac_of_measured_fp64": achieved / (2 * fma64 / 1e12),
