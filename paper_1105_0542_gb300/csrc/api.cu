@@ -1123,7 +1123,10 @@ extern "C" int su_mlp_loss_grad(const float *theta, const float *d_X, const floa
     CU(su::train::loss_grad(ws, R, 1.0 / norm, true, st), "loss and gradient");
     CU(cudaMemcpyAsync(grad, ws.grad, (size_t)su::mlp::kParams * 4, cudaMemcpyDeviceToHost, st), "read gradient");
     CU(cudaMemcpyAsync(loss, ws.loss, 8, cudaMemcpyDeviceToHost, st), "read loss");
+    int tstat = 0;
+    CU(cudaMemcpyAsync(&tstat, ws.status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
     CU(cudaStreamSynchronize(st), "training step");
+    if (tstat) return fail(SU_ETIMEOUT, "a tensor-core MMA of the training GEMMs did not complete");
     return SU_OK;
 }
 
@@ -1253,6 +1256,9 @@ extern "C" int speedup_train_proposal(int model, const double *params, int n_par
     CU(cudaStreamSynchronize(gr.st), "training");
     if (loss_out)
         CU(cudaMemcpy(loss_out, d_losses, (size_t)to.steps * sizeof(double), cudaMemcpyDeviceToHost), "read losses");
+    int tstat = 0;
+    CU(cudaMemcpy(&tstat, ws.status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (tstat) return fail(SU_ETIMEOUT, "a tensor-core MMA of the training GEMMs did not complete");
     CU(cudaMemcpy(theta, ws.theta, (size_t)su::mlp::kParams * 4, cudaMemcpyDeviceToHost), "read theta");
     return SU_OK;
 }

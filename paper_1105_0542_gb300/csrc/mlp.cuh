@@ -83,11 +83,13 @@ struct Tc {
     uint32_t tmem;     // tensor-memory base address (lane 0, first column)
     uint32_t mbar;     // shared address of the MMA-completion mbarrier
     uint32_t phase;    // parity of the next completion to wait for
+    uint32_t ncols;    // allocated columns
 };
 
-// All threads: mbarrier init (thread 0), tensor-memory allocation (warp 0).
-// slot and bar are shared-memory words of the CTA.
-__device__ __forceinline__ Tc tc_begin(uint32_t *slot, uint64_t *bar) {
+// All threads: mbarrier init (thread 0), allocation of ncols tensor-memory
+// columns (warp 0; a power of two >= 32).  slot and bar are shared-memory
+// words of the CTA.
+__device__ __forceinline__ Tc tc_begin(uint32_t *slot, uint64_t *bar, uint32_t ncols = kTmemCols) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
@@ -95,7 +97,7 @@ __device__ __forceinline__ Tc tc_begin(uint32_t *slot, uint64_t *bar) {
     }
     if ((tid >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                     "r"(kTmemCols));
+                     "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -105,6 +107,7 @@ __device__ __forceinline__ Tc tc_begin(uint32_t *slot, uint64_t *bar) {
     t.tmem = *slot;
     t.mbar = smem_u32(bar);
     t.phase = 0;
+    t.ncols = ncols;
     return t;
 }
 
@@ -114,7 +117,7 @@ __device__ __forceinline__ void tc_end(const Tc &t) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(t.ncols));
 }
 
 // One layer's MMAs, D[:, col..col+N) = A[128][K] B[N][K]^T, issued by thread

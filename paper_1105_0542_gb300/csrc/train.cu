@@ -12,10 +12,10 @@
 //   update    Adam on the float master weights.
 //
 // Every product is one "NT" GEMM, C[M][N] = sum_k A[m][k] B[n][k], bf16
-// operands with K contiguous, float accumulation (mma.sync m16n8k16), so the
-// activations and gradients are kept both row-major and transposed (bf16).
-// Products with K = R (the weight gradients) are split over K and summed with
-// atomic adds.
+// operands with K contiguous, float accumulation on the 5th-generation tensor
+// cores (tcgen05.mma, accumulator in tensor memory), so the activations and
+// gradients are kept both row-major and transposed (bf16).  Products with
+// K = R (the weight gradients) are split over K and summed with atomic adds.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -37,101 +37,112 @@ using mlp::kHid;
 using mlp::kIn;
 using mlp::kOut;
 constexpr int kK1 = 32;        // padded input width (K of the first layer)
-constexpr int kBM = 128, kBN = 128, kBK = 32, kLS = kBK + 8;   // smem row stride 40 elements
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                    uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-        "{%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
+constexpr int kBM = 128, kBN = 128, kBK = 32;   // output tile; K granularity
+constexpr int kTK = 128;                         // K staged per MMA round
+// A and B stages (64 KB), reused for the 128 x (128 + 4) float output tile:
+// 66 KB, so at most 3 CTAs (384 tensor-memory columns) per SM
+constexpr int kGemmSmem = 128 * (kBN + 4) * 4 > 2 * 128 * kTK * 2 ? 128 * (kBN + 4) * 4 : 2 * 128 * kTK * 2;
 
 // C[M][N] (+)= sum_k A[m][k] B[n][k] over the K-range of blockIdx.z.
-// A: [M][lda], B: [N][ldb] bf16 (lda, ldb multiples of 8); K multiple of 32.
-// 256 threads: warp (wm, wn) of 4 x 2 owns rows 32 wm.., columns 64 wn..
-__global__ void __launch_bounds__(256) gemm_nt(const __nv_bfloat16 *__restrict__ A, int lda,
-                                               const __nv_bfloat16 *__restrict__ B, int ldb,
-                                               float *__restrict__ C, int ldc, int M, int N, int K,
-                                               int kchunk, int atomic) {
-    __shared__ __align__(16) __nv_bfloat16 As[kBM * kLS];
-    __shared__ __align__(16) __nv_bfloat16 Bs[kBN * kLS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 3, wn = warp >> 2;
+// A: [M][lda], B: [N][ldb] bf16 (lda, ldb multiples of 8); K and the K-range
+// multiples of 32.  128 threads (one warp per tensor-memory lane quadrant).
+// Per round, 128 x 128 of A and min(N - n0, 128) x 128 of B are staged in the
+// operand layout of mlp.cuh (zeros outside M, N and the K-range), thread 0
+// issues K/16 MMAs (M = 128, N = the tile's width rounded up to 16) and
+// commits them; all threads wait (bounded) before the next round overwrites
+// the stage.  Epilogue: tcgen05.ld of each thread's row, stored or added.
+// A wait that gives up sets *status.
+__global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restrict__ A, int lda,
+                                                  const __nv_bfloat16 *__restrict__ B, int ldb,
+                                                  float *__restrict__ C, int ldc, int M, int N, int K,
+                                                  int kchunk, int atomic, int *status) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    unsigned char *sA = gsm, *sB = gsm + 128 * kTK * 2;
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mma_bar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     const int kb = blockIdx.z * kchunk;
     const int ke = min(K, kb + kchunk);
-    float acc[2][8][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-
-    for (int k0 = kb; k0 < ke; k0 += kBK) {
-        // 128 rows x 32 columns = 512 pieces of 8 elements per operand
-#pragma unroll
-        for (int it = 0; it < 2; ++it) {
-            const int idx = tid + it * 256;
-            const int r = idx >> 2, c = (idx & 3) * 8;
-            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-            if (m0 + r < M) va = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + k0 + c);
-            if (n0 + r < N) vb = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + k0 + c);
-            *reinterpret_cast<uint4 *>(As + r * kLS + c) = va;
-            *reinterpret_cast<uint4 *>(Bs + r * kLS + c) = vb;
+    const int nn = min(kBN, N - n0);
+    const int NT = (nn + 15) & ~15;
+    mlp::Tc tc = mlp::tc_begin(&tmem_slot, &mma_bar, 128);
+    bool ok = true;
+    for (int k0 = kb; k0 < ke; k0 += kTK) {
+        const int kn = min(kTK, ke - k0);
+        // 16-byte asynchronous copies, all in flight at once; a source size of
+        // 0 fills the destination with zeros (rows past M or N, K past the range)
+        for (int idx = tid; idx < 128 * (kTK / 8); idx += 128) {
+            const int r = idx / (kTK / 8), q = idx % (kTK / 8);
+            const bool kin = 8 * q < kn;
+            const bool ain = kin && m0 + r < M, bin = kin && r < nn;
+            const __nv_bfloat16 *ga = ain ? A + (size_t)(m0 + r) * lda + k0 + 8 * q : A;
+            const __nv_bfloat16 *gb = bin ? B + (size_t)(n0 + r) * ldb + k0 + 8 * q : B;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             mlp::smem_u32(sA + mlp::cm_off(r, 8 * q, kTK))),
+                         "l"(ga), "r"(ain ? 16 : 0));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             mlp::smem_u32(sB + mlp::cm_off(r, 8 * q, kTK))),
+                         "l"(gb), "r"(bin ? 16 : 0));
         }
+        asm volatile("cp.async.commit_group;");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < kBK; ks += 16) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int row = wm * 32 + mt * 16 + (lane & 15);
-                const int col = ks + (lane >> 4) * 8;
-                ldsm_x4(mlp::smem_u32(As + row * kLS + col), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = mlp::smem_u32(sA), b0 = mlp::smem_u32(sB);
+            const uint32_t id = mlp::instr_desc(kBM, NT);
+            for (int ks = 0; ks < kn / 16; ++ks) {
+                const uint64_t ad = mlp::smem_desc(a0 + ks * 256, 128, (kTK / 8) * 128);
+                const uint64_t bd = mlp::smem_desc(b0 + ks * 256, 128, (kTK / 8) * 128);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tc.tmem),
+                    "l"(ad), "l"(bd), "r"(id), "r"((uint32_t)(k0 > kb || ks > 0)));
             }
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                const int row = wn * 64 + np * 16 + (lane & 7) + ((lane >> 4) << 3);
-                const int col = ks + ((lane >> 3) & 1) * 8;
-                uint32_t b0, b1, b2, b3;
-                ldsm_x4(mlp::smem_u32(Bs + row * kLS + col), b0, b1, b2, b3);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                    mma(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
-                }
-            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc.mbar));
         }
+        ok &= mlp::tc_wait(tc);
         __syncthreads();
     }
+    if (ke > kb) {
+        // the accumulator tile through shared memory (the idle stage buffers,
+        // rows of NT + 4 floats), then row-contiguous stores or adds to C
+        float *Ts = reinterpret_cast<float *>(gsm);
+        const int ts = NT + 4;
+        const int trow = 32 * warp + lane;
+        for (int c = 0; c < NT; c += 16) {
+            float v[16];
+            mlp::tmem_ld16(tc.tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int r = m0 + wm * 32 + mt * 16 + (lane >> 2);
-            const int c = n0 + wn * 64 + nt * 8 + (lane & 3) * 2;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int rr = r + 8 * h;
-                if (rr >= M) continue;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    if (c + e >= N) continue;
-                    float *dst = C + (size_t)rr * ldc + c + e;
-                    if (atomic)
-                        atomicAdd(dst, acc[mt][nt][2 * h + e]);
-                    else
-                        *dst = acc[mt][nt][2 * h + e];
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(Ts + trow * ts + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        __syncthreads();
+        if (ok) {
+            const int nq = NT / 4;
+            for (int i = tid; i < 128 * nq; i += 128) {
+                const int r = i / nq, c = 4 * (i - r * nq);
+                const int row = m0 + r, col = n0 + c;
+                if (row >= M || col >= N) continue;
+                const float4 v = *reinterpret_cast<const float4 *>(Ts + r * ts + c);
+                float *dst = C + (size_t)row * ldc + col;
+                const float e[4] = {v.x, v.y, v.z, v.w};
+                const int cnt = min(4, N - col);
+                if (atomic) {
+                    for (int j = 0; j < cnt; ++j) atomicAdd(dst + j, e[j]);
+                } else if (cnt == 4 && ((ldc | col) & 3) == 0) {
+                    *reinterpret_cast<float4 *>(dst) = v;
+                } else {
+                    for (int j = 0; j < cnt; ++j) dst[j] = e[j];
                 }
             }
         }
+    }
+    if (!ok && tid == 0) atomicOr(status, 1);
+    mlp::tc_end(tc);
 }
 
 __device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
@@ -411,7 +422,10 @@ cudaError_t Workspace::reserve(int R) {
     const size_t og = take((size_t)(kHid * kK1 + 2 * kHid * kHid + kOut * kHid + 3 * kHid + kOut) * 4);
     const size_t oflat = take((size_t)mlp::kParams * 4 * 4);   // theta, grad, m, v
     const size_t oloss = take(8);
-    cudaError_t e = cudaMalloc(&base, off);
+    const size_t ostatus = take(4);
+    cudaError_t e = cudaFuncSetAttribute(gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {
         base = nullptr;
         return e;
@@ -451,11 +465,16 @@ cudaError_t Workspace::reserve(int R) {
     m = grad + mlp::kParams;
     v = m + mlp::kParams;
     loss = (double *)(p + oloss);
+    status = (int *)(p + ostatus);
+    e = cudaMemset(status, 0, sizeof(int));
+    if (e != cudaSuccess) return e;
     grad_bytes = og;
     cap_rows = R;
     gbytes = (size_t)(kHid * kK1 + 2 * kHid * kHid + kOut * kHid + 3 * kHid + kOut) * 4;
     return cudaSuccess;
 }
+
+static int *g_status = nullptr;   // the workspace's timeout word, set by loss_grad
 
 static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
                         int M, int N, int K, cudaStream_t st, bool split) {
@@ -467,12 +486,13 @@ static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
         splitk = (K + kchunk - 1) / kchunk;
     }
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splitk);
-    gemm_nt<<<grid, 256, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? 1 : 0);
+    gemm_nt<<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? 1 : 0, g_status);
     return cudaGetLastError();
 }
 
 cudaError_t loss_grad(Workspace &ws, int R, double inv_norm, bool use_rw, cudaStream_t st) {
     cudaGetLastError();
+    g_status = ws.status;
     if (R % 32 != 0 || R > ws.cap_rows) return cudaErrorInvalidValue;
     const int Rp = R;   // K of the weight-gradient GEMMs
     const float *th = ws.theta;

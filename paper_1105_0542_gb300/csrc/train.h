@@ -28,6 +28,7 @@ struct Workspace {
     float *dW1 = nullptr, *dW2 = nullptr, *dW3 = nullptr, *dW4 = nullptr, *db = nullptr;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // flat, kParams each
     double *loss = nullptr;
+    int *status = nullptr;                               // set when a tensor-core wait gave up
     size_t grad_bytes = 0, gbytes = 0;
 
     ~Workspace();
