@@ -1,0 +1,58 @@
+"""Space-discretized evolution operator and its spectrum (oracle side).
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__``.
+
+Sec. 5 (Fig. 3) obtains energy eigenvalues and eigenfunctions by
+diagonalising the matrix of short-time transition amplitudes on a grid: with
+x_i = -L + i Delta, i = 0..n-1, Delta = 2L/(n-1),
+
+    U_ij = Delta (2 pi t)^(-1/2) exp(-(x_j - x_i)^2/(2t) - t W_p(x, xb; t)),
+    x = (x_i + x_j)/2,  xb = (x_j - x_i)/2,
+
+the single-slice amplitude with the level-p effective potential (Eq.
+ansatz at eps = t), a quadrature of the integral kernel of e^(-tH).  Its
+eigenvalues approach e^(-t E_k), so E_k = -ln(lambda_k)/t.
+
+Written out plainly: W_p from the exact coefficients (``exact._wp_vec``) on
+every pair of grid points, numpy's symmetric eigensolver for the spectrum.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import effective_action as ea
+from . import exact
+
+
+def grid(L, n):
+    return np.linspace(-L, L, n)
+
+
+def evolution_matrix(model_name, params, p, t, L, n):
+    """U (n x n, float64) of the docstring."""
+    model = ea.make_model(model_name, params)
+    x = grid(L, n)
+    delta = 2.0 * L / (n - 1)
+    xi, xj = np.meshgrid(x, x, indexing="ij")
+    xm, xb = 0.5 * (xi + xj), 0.5 * (xj - xi)
+    W = exact._wp_vec(model, p, xm, xb, t)
+    expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - (xj - xi) ** 2 / (2.0 * t) - t * W
+    return np.exp(expo)
+
+
+def evolution_matrix_abs(model_name, params, p, t, L, n):
+    """t sum_terms |term| of W_p at every element: the size of the numbers
+    -t W_p is summed from (for rounding allowances)."""
+    model = ea.make_model(model_name, params)
+    x = grid(L, n)
+    xi, xj = np.meshgrid(x, x, indexing="ij")
+    return t * exact._wp_abs_vec(model, p, 0.5 * (xi + xj), np.abs(0.5 * (xj - xi)), t)
+
+
+def energies(U, t, k):
+    """The k lowest E = -ln(lambda)/t from the k largest eigenvalues of U."""
+    lam = np.linalg.eigvalsh(0.5 * (U + U.T))
+    lam = np.sort(lam)[::-1][:k]
+    return -np.log(lam) / t
