@@ -58,7 +58,7 @@ extern "C" {
 #define SU_FP64  0   /* everything in double                                   */
 #define SU_FP32  1   /* path and W_p in float, log-sum-exp reductions in double */
 
-#define SU_MAX_P 18  /* highest effective-action level                         */
+#define SU_MAX_P 32  /* highest effective-action level                         */
 #define SU_MAX_S 10  /* deepest bisection level, N <= 1024                     */
 
 typedef struct {
@@ -342,6 +342,33 @@ int su_plan_execute(su_plan *plan, void *d_tuples, void *d_scratch, void *stream
  */
 int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_scratch,
                      su_level_result *out);
+
+/* ---- evolution operator on a grid ----------------------------------------- */
+
+/*
+ * speedup_evolution_matrix -- the space-discretized short-time evolution
+ * operator whose diagonalisation gives energy eigenvalues and eigenfunctions
+ * (Sec. 5, Fig. 3): on the grid x_i = -L + i Delta, i = 0..n-1,
+ * Delta = 2L/(n-1) (each point rounded as (i Delta) + (-L), x_{n-1} = L),
+ *   U_ij = Delta (2 pi t)^(-1/2) exp(-(x_j - x_i)^2/(2t) - t W_p(x, xb; t)),
+ *   x = (x_i + x_j)/2, xb = (x_j - x_i)/2,
+ * the single-slice amplitude with the level-p effective potential, and
+ * U_ij = 0 where (x_j - x_i)^2/(2t) > 40 (the free factor is below e^-40 and
+ * the short-time expansion in xb^2 = O(t) does not apply).  U is symmetric;
+ * its eigenvalues approach e^(-t E_k) (E_k = -ln(lambda_k)/t) and its
+ * eigenvectors / sqrt(Delta) the eigenfunctions.
+ *   model, params, n_params, p : as for speedup_amplitude.
+ *   t     : propagation time of one slice, > 0.
+ *   L     : grid half-width, > 0.   n : grid points, 2..65536.
+ *   precision : SU_FP64 or SU_FP32 (W_p in float; the free factor and the
+ *           output in double).
+ *   d_U   : device, n*n doubles, row-major.
+ * Work on stream; returns after the matrix is written (the stream is
+ * synchronised).  Errors: SU_EINVAL, SU_ENONFINITE (a coefficient is not
+ * representable in the chosen precision), SU_ECUDA, SU_ENOMEM.
+ */
+int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
+                             int precision, double *d_U, void *stream);
 
 /* ---- launch-shape autotuner ----------------------------------------------- */
 

@@ -13,6 +13,12 @@ the single-slice amplitude with the level-p effective potential (Eq.
 ansatz at eps = t), a quadrature of the integral kernel of e^(-tH).  Its
 eigenvalues approach e^(-t E_k), so E_k = -ln(lambda_k)/t.
 
+Elements whose free-particle factor is below e^-40, (x_j - x_i)^2/(2t) > 40,
+are zero (reading E-1): they are below double resolution relative to the
+diagonal, and there xb^2 >> t, outside the short-time ordering of the
+expansion, where the truncated W_p can grow faster than the Gaussian decays
+(for the Poeschl-Teller potential the xb-series has a finite radius).
+
 Written out plainly: W_p from the exact coefficients (``exact._wp_vec``) on
 every pair of grid points, numpy's symmetric eigensolver for the spectrum.
 """
@@ -24,6 +30,9 @@ import numpy as np
 
 from . import effective_action as ea
 from . import exact
+
+
+BAND = 40.0   # largest (x_j - x_i)^2/(2t) of a nonzero element (reading E-1)
 
 
 def grid(L, n):
@@ -38,8 +47,10 @@ def evolution_matrix(model_name, params, p, t, L, n):
     xi, xj = np.meshgrid(x, x, indexing="ij")
     xm, xb = 0.5 * (xi + xj), 0.5 * (xj - xi)
     W = exact._wp_vec(model, p, xm, xb, t)
-    expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - (xj - xi) ** 2 / (2.0 * t) - t * W
-    return np.exp(expo)
+    free = (xj - xi) ** 2 / (2.0 * t)
+    band = free <= BAND
+    expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - free - t * np.where(band, W, 0.0)
+    return np.where(band, np.exp(expo), 0.0)
 
 
 def evolution_matrix_abs(model_name, params, p, t, L, n):

@@ -17,7 +17,7 @@ from . import build as _build
 SU_OK, SU_EINVAL, SU_ENOMEM, SU_ECUDA, SU_ETIMEOUT, SU_ENONFINITE, SU_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1}
-MAX_P, MAX_S = 18, 10
+MAX_P, MAX_S = 32, 10
 
 EXPORTS = [
     "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
@@ -28,6 +28,7 @@ EXPORTS = [
     "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
     "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
+    "speedup_evolution_matrix",
 ]
 MLP_PARAMS = 34178
 
@@ -111,6 +112,7 @@ def load(build_if_missing=True):
     L.su_autotune.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
                               ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
     L.su_autotune_clear.argtypes = []
+    L.speedup_evolution_matrix.argtypes = [i32, pd, i32, i32, d, d, i32, i32, vp, vp]
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
@@ -213,6 +215,15 @@ def su_autotune(model, params, a, b, T, p, s, n_probe, seed, **kw):
 
 def su_autotune_clear():
     _check(load().su_autotune_clear())
+
+
+def speedup_evolution_matrix(model, params, p, t, L, n, out, precision="fp64", stream=None):
+    """U_ij = Delta A_1^(p)(x_i, x_j; t) on x_i = -L + i Delta into the device
+    buffer out (n x n doubles)."""
+    pr, npar = _params(params)
+    _check(load().speedup_evolution_matrix(_model(model), pr, npar, int(p), float(t), float(L), int(n),
+                                           PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                                           _ptr(out), _stream(stream)))
 
 
 def su_version():

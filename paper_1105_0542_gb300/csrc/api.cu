@@ -479,6 +479,54 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     return su_plan_finalize(pl, h.data(), nullptr, out);
 }
 
+// ------------------------------------------------------- evolution operator
+int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
+                             int precision, double *d_U, void *stream) {
+    if (!d_U) return fail(SU_EINVAL, "output missing");
+    if (!(t > 0) || !std::isfinite(t)) return fail(SU_EINVAL, "t must be finite and > 0");
+    if (!(L > 0) || !std::isfinite(L)) return fail(SU_EINVAL, "L must be finite and > 0");
+    if (n < 2 || n > 65536) return fail(SU_EINVAL, "n must be in 2..65536");
+    if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
+    if (precision != SU_FP64 && precision != SU_FP32) return fail(SU_EINVAL, "unknown precision");
+    su::Effective E;
+    std::string err;
+    int rc = su::build_effective(model, params, n_params, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    std::vector<double> T;
+    su::kernel_table(E, t, T);
+    const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> blob(T.size() * rs);
+    for (size_t i = 0; i < T.size(); ++i) {
+        if (!std::isfinite(T[i]) || (precision == SU_FP32 && !std::isfinite((float)T[i])))
+            return fail(SU_ENONFINITE, "a coefficient of W_p is not representable at t = %g", t);
+        if (precision == SU_FP32) {
+            const float f = (float)T[i];
+            std::memcpy(blob.data() + i * rs, &f, rs);
+        } else {
+            std::memcpy(blob.data() + i * rs, &T[i], rs);
+        }
+    }
+    su::SamplerParams P;
+    std::memset(&P, 0, sizeof P);
+    P.ring = E.shape.ring;
+    P.ncol = E.shape.ncol;
+    P.M = E.shape.M;
+    for (int j = 0; j < E.shape.ncol; ++j) P.len[j] = E.shape.len[j];
+    P.alpha = E.shape.alpha;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *d_tab = nullptr;
+    CU(cudaMallocAsync(&d_tab, blob.size(), st), "cudaMallocAsync(table)");
+    cudaError_t e = cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+    const double delta = 2.0 * L / (double)(n - 1);
+    const double lognorm = std::log(delta) - 0.5 * std::log(2.0 * M_PI * t);
+    if (e == cudaSuccess) e = su::launch_evolution(P, precision, d_tab, L, delta, n, t, lognorm, d_U, st);
+    // the host copy of the table must outlive the asynchronous upload
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_tab, st);
+    if (e != cudaSuccess) return cuda_fail(e, "evolution matrix");
+    return SU_OK;
+}
+
 // ------------------------------------------------------------ autotuner
 int su_autotune_clear(void) {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -73,6 +73,11 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision);
 // max resident CTAs per SM for the sampler (after opting in to its smem)
 int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
 
+// U[i * n + j] = exp(lognorm - (x_j - x_i)^2 / (2t) - t W_p) on the grid
+// x_i = -L + i delta (evolution.cu); tab: the device table for eps = t
+cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
+                             double t, double lognorm, double *U, cudaStream_t st);
+
 cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
                            cudaStream_t st);
 size_t batch_smem_bytes(const BatchParams &B, int precision);

@@ -111,7 +111,11 @@ __device__ __forceinline__ R ring_var(R us, R alpha) {
         // tanh^2(alpha us / 2): tanh(y/2) = -em / (2 + em), em = expm1(-|y|),
         // accurate also where tanh is small
         const R em = expm1(-fabs(alpha * us));
-        const R t = -em / ((R)2 + em);
+        R t;
+        if constexpr (sizeof(R) == 4)
+            t = __fdividef(-em, 2.0f + em);   // 2 ulp; 2 + em in [1, 2]
+        else
+            t = -em / (2.0 + em);
         return t * t;
     }
 }

@@ -1,0 +1,102 @@
+"""GPU parity of the space-discretized evolution operator (Sec. 5, Fig. 3).
+
+* elements against the oracle's matrix (same grid, W_p from the exact
+  coefficients), compared in the exponent: |d log U| <= max(tol, 64 u A),
+  A = t sum_terms |term| of W_p (the rounding scale of -t W_p), tol = 1e-12
+  (double) or 1e-5 (single-precision W_p);
+* the matrix is exactly symmetric;
+* spectra: the eigenvalues of the device matrix (torch's symmetric
+  eigensolver) give the oracle's energies on the same grid (1e-10) and the
+  sinc-DVR energies of both Fig. 3 potentials at the figure's level p = 21
+  (1e-9);
+* the paper's grid of Fig. 3 (anharmonic, L = 8, Delta = 9.77e-4, n = 16385):
+  finite, positive, symmetric, and its diagonal matches the oracle at sampled
+  points.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1105_0542_gb300 as su  # noqa: E402
+from oracle import effective_action as ea  # noqa: E402
+from oracle import evolution as ev  # noqa: E402
+from oracle import exact  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _device_matrix(model, params, p, t, L, n, precision="fp64"):
+    U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    su.speedup_evolution_matrix(model, params, p, t, L, n, U, precision=precision)
+    torch.cuda.synchronize()
+    return U
+
+
+CASES = [("ho", [1.0], 12, 0.1, 8.0), ("aho", [1.0, 48.0], 21, 0.02, 8.0), ("aho", [-10.0, 12.0], 21, 0.1, 10.0),
+         ("dw", [5.0], 12, 0.05, 3.0), ("mpt", [3.0, 1.0], 12, 0.05, 6.0), ("aho", [1.0, 10.0], 32, 0.01, 4.0)]
+
+
+@pytest.mark.parametrize("prec,tol,u", [("fp64", 1e-12, 2.0 ** -53), ("fp32", 1e-5, 2.0 ** -24)])
+@pytest.mark.parametrize("model,params,p,t,L", CASES)
+def test_elements_match_oracle(model, params, p, t, L, prec, tol, u):
+    n = 203                              # ragged against the 32 x 8 thread blocks
+    got = _device_matrix(model, params, p, t, L, n, prec).cpu().numpy()
+    ref = ev.evolution_matrix(model, params, p, t, L, n)
+    A = ev.evolution_matrix_abs(model, params, p, t, L, n)
+    live = ref > 0
+    assert live.sum() > 3 * n            # a band around the diagonal
+    x = ev.grid(L, n)
+    free = (x[None, :] - x[:, None]) ** 2 / (2 * t)
+    # the same band (reading E-1); a difference only on its edge
+    assert np.all(np.abs(free[(got > 0) != live] - ev.BAND) < 1e-9)
+    live &= got > 0
+    d = np.abs(np.log(got[live]) - np.log(ref[live]))
+    allow = np.maximum(tol, 64 * u * A[live])
+    assert float(np.max(d / allow)) <= 1.0
+
+
+def test_matrix_is_exactly_symmetric():
+    U = _device_matrix("aho", [1.0, 48.0], 21, 0.02, 8.0, 1001)
+    assert torch.equal(U, U.T)
+
+
+@pytest.mark.parametrize("params,t,L,V", [([1.0, 48.0], 0.02, 8.0, lambda x: 0.5 * x * x + 2.0 * x ** 4),
+                                          ([-10.0, 12.0], 0.1, 10.0, lambda x: -5.0 * x * x + 0.5 * x ** 4)])
+def test_figure3_spectra(params, t, L, V):
+    n = 401
+    U = _device_matrix("aho", params, 21, t, L, n)
+    lam = torch.linalg.eigvalsh(U).cpu().numpy()[::-1][:8]
+    E = -np.log(lam) / t
+    Eo = ev.energies(ev.evolution_matrix("aho", params, 21, t, L, n), t, 8)
+    assert np.abs(E - Eo).max() <= 1e-10, E - Eo
+    _, Ed = exact.dvr_amplitude(V, 0.0, 0.0, 1.0, L=L, dx=0.01)
+    assert np.abs(E - Ed[:8]).max() <= 1e-9, E - Ed[:8]
+
+
+def test_paper_grid_of_figure3():
+    n, L, t, p = 16385, 8.0, 0.02, 21
+    U = _device_matrix("aho", [1.0, 48.0], p, t, L, n)
+    assert bool(torch.isfinite(U).all()) and bool((U >= 0).all())
+    idx = torch.arange(0, n, 997, device="cuda")
+    assert torch.equal(U[idx][:, idx], U[idx][:, idx].T)
+    # sampled elements near the diagonal against the oracle's formula
+    x = np.linspace(-L, L, n)
+    delta = 2 * L / (n - 1)
+    model = ea.make_model("aho", [1.0, 48.0])
+    Uh = U[idx].cpu().numpy()
+    for r, i in enumerate(idx.cpu().numpy()):
+        for j in (i, min(i + 3, n - 1), max(i - 50, 0)):
+            xm, xb = 0.5 * (x[i] + x[j]), 0.5 * (x[j] - x[i])
+            w = exact._wp_vec(model, p, np.array([xm]), np.array([xb]), t)[0]
+            ref = math.exp(math.log(delta) - 0.5 * math.log(2 * math.pi * t) - (x[j] - x[i]) ** 2 / (2 * t) - t * w)
+            assert Uh[r, j] == pytest.approx(ref, rel=1e-12)

@@ -108,6 +108,8 @@ CASES = [
     ("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 5, 8, 350412),      # a rare path with w_6 = 3350
     ("mpt", [3.0, 1.0], -1.0, 1.0, 1.0, 12, 6, 200, 1234, 0),
     ("mpt", [3.0, 1.0], -1.0, 1.0, 5.0, 6, 7, 150, 3, 0),
+    ("aho", [1.0, 10.0], 0.0, 1.0, 1.0, 21, 10, 96, 1234, 0),     # levels above the convergence sweep
+    ("aho", [1.0, 48.0], 0.0, 0.5, 0.5, 32, 8, 64, 7, 5000),
     ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], -0.5, 0.7, 0.8, 5, 5, 140, 8, 0),
     ("poly", [0.0, 1.0, 0.5], 0.3, -0.2, 1.5, 3, 9, 64, 8, 0),
     ("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 6, 1, 65, 2, 0),

@@ -74,6 +74,10 @@ def _exact_collapse(name, params, p, eps):
     ("mpt", [2.0, 0.7], 6, 0.3),
     ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], 8, 0.1),
     ("aho", [1.0, 10.0], 1, 1.0),
+    ("aho", [1.0, 48.0], 21, 0.02),          # the level of the evolution-operator spectra (Fig. 3)
+    ("aho", [-10.0, 12.0], 21, 0.1),
+    ("aho", [1.0, 10.0], 32, 1.0 / 64),
+    ("dw", [1.0], 24, 0.25),
 ])
 def test_generator_matches_oracle_exact_collapse(name, params, p, eps):
     P, ncol, ring, lens = su.speedup_generate_coeffs(name, params, p, eps)
@@ -104,7 +108,7 @@ def test_generator_term_counts_of_the_anharmonic_oscillator():
 
 @pytest.mark.parametrize("args,kw", [
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 0, 4, 100, 1), {}),        # p = 0
-    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 19, 4, 100, 1), {}),       # p = 19
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 33, 4, 100, 1), {}),       # p = 33
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 11, 100, 1), {}),       # s = 11
     (("aho", [1.0, 1.0], 0.0, 1.0, 0.0, 4, 4, 100, 1), {}),        # T = 0
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 0, 1), {}),          # n_mc = 0
@@ -141,3 +145,13 @@ def test_level_zero_needs_no_sampling_but_still_a_plan():
     else:
         with pytest.raises(su.SpeedupError):
             su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 0, 10, 1)
+
+
+@pytest.mark.parametrize("kw", [{"t": 0.0}, {"L": -1.0}, {"n": 1}, {"n": 70000}, {"p": 33}])
+def test_evolution_matrix_rejects_bad_arguments(kw):
+    args = {"model": "aho", "params": [1.0, 1.0], "p": 4, "t": 0.1, "L": 5.0, "n": 100}
+    args.update(kw)
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_evolution_matrix(args["model"], args["params"], args["p"], args["t"], args["L"], args["n"], 1 << 20)
+    assert e.value.code == -1
+
