@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched amplitude-matrix entry")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal entry")
     ap.add_argument("--no-configs", action="store_true", help="skip the configuration 1 and 4 entries")
+    ap.add_argument("--no-evolution", action="store_true", help="skip the evolution-operator (Fig. 3) entry")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -355,6 +356,9 @@ def run_ours(args):
     small = None
     if not args.no_configs:
         small = run_small_configs(su, torch, dev, stream, flush)
+    evolution = None
+    if not args.no_evolution:
+        evolution = run_evolution(su, torch, dev, stream, flush)
 
     if rank != 0:
         if dist is not None:
@@ -397,6 +401,7 @@ def run_ours(args):
         "fp32_vs_fp64_top_level": f32_vs_f64,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
         "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
+        "evolution_operator_fig3": evolution,
         "clocks": clock_info,
     }
     print(json.dumps(line))
@@ -457,6 +462,45 @@ def run_small_configs(su, torch, dev, stream, flush):
     return {"config1": c1, "config4": c4,
             "note": "config 1 wall clock per host-API call (plan, tables, launch, tuples back); config 4 "
                     "device time of one plan execute, L2 flushed before each"}
+
+
+def run_evolution(su, torch, dev, stream, flush):
+    """The evolution-operator spectra of Fig. 3 (Sec. 5): the matrix
+    U_ij = Delta A_1^(21)(x_i, x_j; t) on the figure's grid (anharmonic A = 1,
+    g = 48, t = 0.02, L = 8, Delta = 9.77e-4; double well A = -10, g = 12,
+    t = 0.1, L = 10, Delta = 1.22e-3) built on the device (CUDA events), and
+    the lowest ten energies -ln(lambda)/t from torch's symmetric eigensolver
+    on a 4097-point grid of the same L."""
+    out = []
+    for name, params, t, L, n in (("aho A=1 g=48", [1.0, 48.0], 0.02, 8.0, 16385),
+                                  ("double well A=-10 g=12", [-10.0, 12.0], 0.1, 10.0, 16385)):
+        U = torch.empty((n, n), dtype=torch.float64, device=dev)
+        su.speedup_evolution_matrix("aho", params, 21, t, L, n, U, stream=stream)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        su.speedup_evolution_matrix("aho", params, 21, t, L, n, U, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        band = int((U > 0).sum().item())
+        del U
+        m = 4097
+        Us = torch.empty((m, m), dtype=torch.float64, device=dev)
+        su.speedup_evolution_matrix("aho", params, 21, t, L, m, Us, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam = torch.linalg.eigvalsh(Us)
+        torch.cuda.synchronize()
+        eig_s = time.perf_counter() - t0
+        lam = lam.flip(0)[:10].cpu().numpy()
+        del Us
+        out.append({"potential": name, "p": 21, "t": t, "L": L, "n": n, "delta": 2 * L / (n - 1),
+                    "matrix_ms": ms, "elements_per_s": n * n / (ms / 1e3), "band_elements": band,
+                    "spectrum_grid": m, "eigvalsh_s": eig_s,
+                    "energies": [float(-math.log(v) / t) for v in lam]})
+    return {"cases": out, "note": "matrix: device time of one speedup_evolution_matrix; energies from torch's "
+                                  "eigensolver (cuSOLVER) on the 4097-point grid"}
 
 
 def run_batched(su, torch, dev, stream, flush):
