@@ -370,6 +370,20 @@ int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_
 int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
                              int precision, double *d_U, void *stream);
 
+/* ---- fault injection (test support) ---------------------------------------- */
+
+/* No counterpart in the paper: host-side hooks for the failure-detection tests.
+ * Every hook is off until set and fires once. */
+#define SU_FAULT_CLEAR        0  /* turn every hook off                                  */
+#define SU_FAULT_ALLOC        1  /* the arg-th device allocation from now fails (ENOMEM) */
+#define SU_FAULT_TABLE_NAN    2  /* the next coefficient table gets a NaN (ENONFINITE)   */
+#define SU_FAULT_QUEUE_STOP   3  /* the next batched execute stops after arg work items;
+                                    its finalize reports the missing samples (ECUDA)    */
+#define SU_FAULT_WITHHOLD_MMA 4  /* the next proposal launch withholds its first MMA
+                                    commit: the bounded wait (one second) runs out and
+                                    the call returns SU_ETIMEOUT                         */
+int su_fault_inject(int kind, int64_t arg);
+
 /* ---- launch-shape autotuner ----------------------------------------------- */
 
 typedef struct {
@@ -395,6 +409,11 @@ typedef struct {
 int su_autotune(int model, const double *params, int n_params, double a, double b, double T,
                 int p, int s, int64_t n_probe, uint64_t seed, const su_options *opt,
                 su_tuning *best, su_tuning *all, int cap, int *n_all);
+
+/* su_plan_execute with the device time of its launches: CUDA events around
+ * them on stream, *ms = elapsed milliseconds (synchronises the stop event). */
+int su_plan_execute_timed(su_plan *plan, void *d_tuples, void *d_scratch, void *stream, int *launches,
+                          float *ms);
 
 /* Forget every shape su_autotune stored (automatic shapes revert to the rule). */
 int su_autotune_clear(void);

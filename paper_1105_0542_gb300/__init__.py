@@ -9,6 +9,7 @@ from ._binding import (  # noqa: F401
     BatchPlan, EXPORTS, MLP_PARAMS, MODELS, PRECISIONS, Plan, Proposal, SpeedupError, library_path, load,
     options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_noalloc, speedup_amplitude_proposal,
     speedup_evolution_matrix, speedup_generate_coeffs, speedup_logweights, speedup_normals, speedup_philox_words,
-    speedup_proposal_logweights, speedup_train_proposal, su_autotune, su_autotune_clear, su_fma_peak,
+    speedup_proposal_logweights, speedup_train_proposal, su_autotune, su_autotune_clear, su_fault_inject,
+    su_fma_peak,
     su_last_error, su_mlp_loss_grad, su_version,
 )

@@ -28,7 +28,7 @@ EXPORTS = [
     "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
     "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
-    "speedup_evolution_matrix",
+    "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed",
 ]
 MLP_PARAMS = 34178
 
@@ -113,6 +113,8 @@ def load(build_if_missing=True):
                               ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
     L.su_autotune_clear.argtypes = []
     L.speedup_evolution_matrix.argtypes = [i32, pd, i32, i32, d, d, i32, i32, vp, vp]
+    L.su_fault_inject.argtypes = [i32, i64]
+    L.su_plan_execute_timed.argtypes = [vp, vp, vp, vp, pi, ctypes.POINTER(ctypes.c_float)]
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
@@ -224,6 +226,14 @@ def speedup_evolution_matrix(model, params, p, t, L, n, out, precision="fp64", s
     _check(load().speedup_evolution_matrix(_model(model), pr, npar, int(p), float(t), float(L), int(n),
                                            PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                                            _ptr(out), _stream(stream)))
+
+
+FAULTS = {"clear": 0, "alloc": 1, "table_nan": 2, "queue_stop": 3, "withhold_mma": 4}
+
+
+def su_fault_inject(kind, arg=0):
+    """Test support: arm one of the library's fault hooks (see speedup.h)."""
+    _check(load().su_fault_inject(FAULTS[kind] if isinstance(kind, str) else int(kind), int(arg)))
 
 
 def su_version():
@@ -458,6 +468,13 @@ class Plan:
         f, r = ctypes.c_int(0), ctypes.c_int(0)
         _check(load().su_plan_shape(self._h, ctypes.byref(f), ctypes.byref(r)))
         return f.value, r.value
+
+    def su_plan_execute_timed(self, d_tuples, d_scratch, stream=None):
+        """Launch and time on the device; returns (launches, milliseconds)."""
+        n, ms = ctypes.c_int(0), ctypes.c_float(0)
+        _check(load().su_plan_execute_timed(self._h, _ptr(d_tuples), _ptr(d_scratch), _stream(stream),
+                                            ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
 
     def su_plan_execute(self, d_tuples, d_scratch, stream=None):
         """Launch; returns the number of kernel launches made."""

@@ -8,6 +8,7 @@
 // amplitudes and errors (Sec. 4.1: mean of the normalised e^{-S} and its
 // error, here from contiguous sample blocks).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,7 +64,52 @@ int fail(int code, const char *fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();   // not sticky: clear it for the next call
+        return fail(SU_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
     return fail(SU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---- fault injection (test support; every hook off unless su_fault_inject
+// turned it on)
+std::atomic<int64_t> g_fault_alloc{0};     // > 0: that allocation from now fails
+std::atomic<int> g_fault_table_nan{0};     // the next coefficient table gets a NaN
+std::atomic<int64_t> g_fault_queue{0};     // > 0: batched launches stop after that many items
+std::atomic<int> g_fault_mma{0};           // the next proposal launch withholds its MMA commit
+
+bool take_alloc_fault() {
+    int64_t c = g_fault_alloc.load();
+    while (c > 0) {
+        if (g_fault_alloc.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
+// device allocations of this file go through these two (with the hook)
+cudaError_t dmalloc(void **p, size_t bytes) {
+    if (take_alloc_fault()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dmalloc_async(void **p, size_t bytes, cudaStream_t st) {
+    if (take_alloc_fault()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t bytes) {
+    return dmalloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+cudaError_t dmalloc_async(T **p, size_t bytes, cudaStream_t st) {
+    return dmalloc_async(reinterpret_cast<void **>(p), bytes, st);
 }
 
 #define CU(call, what)                                  \
@@ -196,6 +242,7 @@ static int configure(su_plan &pl) {
         const double eps = pl.T / std::ldexp(1.0, n);
         std::vector<double> t;
         pl.cancel_ratio = std::max(pl.cancel_ratio, su::kernel_table(pl.E, eps, t));
+        if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
         for (int i = 0; i < M; ++i) {
             if (!std::isfinite(t[i]) || (prec == SU_FP32 && !std::isfinite((float)t[i])))
                 return fail(SU_ENONFINITE, "non-finite coefficient at level %d", n);
@@ -219,7 +266,7 @@ static int configure(su_plan &pl) {
     int smem_max = 0;
     CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl.device),
        "smem limit");
-    CU(cudaMalloc(&pl.d_tables, blob.size()), "cudaMalloc(tables)");
+    CU(dmalloc(&pl.d_tables, blob.size()), "device allocation (tables)");
     CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
 
     std::memset(&P, 0, sizeof P);
@@ -370,6 +417,27 @@ int su_plan_execute(su_plan *pl, void *d_tuples, void *d_scratch, void *stream, 
     return SU_OK;
 }
 
+int su_plan_execute_timed(su_plan *pl, void *d_tuples, void *d_scratch, void *stream, int *launches, float *ms) {
+    if (!ms) return fail(SU_EINVAL, "ms missing");
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Ev {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Ev() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    CU(cudaEventCreate(&ev.e[0]), "event");
+    CU(cudaEventCreate(&ev.e[1]), "event");
+    CU(cudaEventRecord(ev.e[0], st), "event record");
+    const int rc = su_plan_execute(pl, d_tuples, d_scratch, stream, launches);
+    if (rc) return rc;
+    CU(cudaEventRecord(ev.e[1], st), "event record");
+    CU(cudaEventSynchronize(ev.e[1]), "event synchronize");
+    CU(cudaEventElapsedTime(ms, ev.e[0], ev.e[1]), "event time");
+    return SU_OK;
+}
+
 static void level_result(double laf, const double *tup, int64_t nb, int levels, int d,
                          su_level_result *r) {
     double M = -INFINITY;
@@ -442,6 +510,8 @@ int su_plan_finalize(const su_plan *pl, const double *h_tuples, const void *d_sc
     if (!h_tuples) return fail(SU_EINVAL, "tuples missing");
     for (int d = 0; d < pl->levels; ++d)
         level_result(pl->laf, h_tuples, pl->n_blocks, pl->levels, d, &out[pl->s - d]);
+    if (out[pl->s].n != pl->n_mc)
+        return fail(SU_ECUDA, "%lld of %lld samples reduced", (long long)out[pl->s].n, (long long)pl->n_mc);
     return SU_OK;
 }
 
@@ -457,7 +527,7 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     cudaStream_t st = (cudaStream_t)pl->opt.stream;
     void *dbuf = nullptr;
     const int64_t tb = pl->tuple_bytes, sb = pl->scratch_bytes;
-    CU(cudaMallocAsync(&dbuf, (size_t)(tb + sb), st), "cudaMallocAsync");
+    CU(dmalloc_async(&dbuf, (size_t)(tb + sb), st), "cudaMallocAsync");
     std::vector<double> h((size_t)(tb / sizeof(double)) + 32);
     void *d_tup = dbuf;
     void *d_scr = static_cast<char *>(dbuf) + tb;
@@ -477,6 +547,34 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     std::memcpy(&flags, h.data() + tb / sizeof(double), sizeof(int));
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+// ------------------------------------------------------ fault injection
+int su_fault_inject(int kind, int64_t arg) {
+    switch (kind) {
+        case SU_FAULT_CLEAR:
+            g_fault_alloc = 0;
+            g_fault_table_nan = 0;
+            g_fault_queue = 0;
+            g_fault_mma = 0;
+            return SU_OK;
+        case SU_FAULT_ALLOC:
+            if (arg < 1) return fail(SU_EINVAL, "the failing allocation is counted from 1");
+            g_fault_alloc = arg;
+            return SU_OK;
+        case SU_FAULT_TABLE_NAN:
+            g_fault_table_nan = 1;
+            return SU_OK;
+        case SU_FAULT_QUEUE_STOP:
+            if (arg < 1) return fail(SU_EINVAL, "the queue keeps at least one item");
+            g_fault_queue = arg;
+            return SU_OK;
+        case SU_FAULT_WITHHOLD_MMA:
+            g_fault_mma = 1;
+            return SU_OK;
+        default:
+            return fail(SU_EINVAL, "unknown fault kind %d", kind);
+    }
 }
 
 // ------------------------------------------------------- evolution operator
@@ -515,7 +613,7 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
     P.alpha = E.shape.alpha;
     cudaStream_t st = (cudaStream_t)stream;
     void *d_tab = nullptr;
-    CU(cudaMallocAsync(&d_tab, blob.size(), st), "cudaMallocAsync(table)");
+    CU(dmalloc_async(&d_tab, blob.size(), st), "device allocation (table)");
     cudaError_t e = cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
     const double delta = 2.0 * L / (double)(n - 1);
     const double lognorm = std::log(delta) - 0.5 * std::log(2.0 * M_PI * t);
@@ -577,7 +675,7 @@ int su_autotune(int model, const double *params, int n_params, double a, double 
                 if (res.buf) cudaFree(res.buf);
                 res.buf = nullptr;
                 res.cap = 0;
-                CU(cudaMalloc(&res.buf, need), "cudaMalloc(probe buffers)");
+                CU(dmalloc(&res.buf, need), "device allocation (probe buffers)");
                 res.cap = need;
             }
             void *d_tup = res.buf, *d_scr = static_cast<char *>(res.buf) + pl->tuple_bytes;
@@ -635,7 +733,7 @@ int speedup_logweights(int model, const double *params, int n_params, double a, 
     const size_t smem = su::sampler_smem_bytes(P, o.precision);
     if (su::sampler_occupancy(P, o.precision, smem) < 1) return fail(SU_ECUDA, "sampler not resident");
     int *d_flag = nullptr;
-    CU(cudaMallocAsync(&d_flag, sizeof(int), st), "cudaMallocAsync");
+    CU(dmalloc_async(&d_flag, sizeof(int), st), "cudaMallocAsync");
     P.flags = d_flag;
     cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
     if (e == cudaSuccess) e = su::launch_sampler(P, o.precision, pl->grid, smem, st);
@@ -761,6 +859,7 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
             if (it == tab_of.end()) {
                 std::vector<double> t;
                 kernel_table(pl->E, eps, t);
+                if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
                 for (double v : t)
                     if (!std::isfinite(v) || (prec == SU_FP32 && !std::isfinite((float)v)))
                         return fail(SU_ENONFINITE, "non-finite coefficient at eps = %g", eps);
@@ -799,13 +898,13 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
     CU(cudaGetDevice(&dev), "cudaGetDevice");
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
-    CU(cudaMalloc(&pl->d_tables, blob.size()), "cudaMalloc(tables)");
+    CU(dmalloc(&pl->d_tables, blob.size()), "device allocation (tables)");
     CU(cudaMemcpy(pl->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
-    CU(cudaMalloc(&pl->d_inst, sizeof(BatchInstance) * hin.size()), "cudaMalloc(instances)");
+    CU(dmalloc(&pl->d_inst, sizeof(BatchInstance) * hin.size()), "device allocation (instances)");
     CU(cudaMemcpy(pl->d_inst, hin.data(), sizeof(BatchInstance) * hin.size(), cudaMemcpyHostToDevice),
        "upload instances");
     if (!items.empty()) {
-        CU(cudaMalloc(&pl->d_items, sizeof(int2) * items.size()), "cudaMalloc(items)");
+        CU(dmalloc(&pl->d_items, sizeof(int2) * items.size()), "device allocation (items)");
         CU(cudaMemcpy(pl->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice),
            "upload items");
     }
@@ -867,6 +966,14 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
     B.base.flags = static_cast<int *>(d_scratch) + 1;
     const void *fn = su::batch_fn(B.base.ring, pl->opt.precision);
     void *args[] = {&B};
+    const int64_t stop = g_fault_queue.exchange(0);
+    if (stop > 0) {   // fault injection: the queue ends after `stop` items
+        B.n_items = (int)std::min<int64_t>(B.n_items, stop);
+        CU(cudaMemsetAsync(d_scratch, 0, 8, st), "clear queue");
+        CU(cudaLaunchKernel(fn, dim3(pl->grid), dim3(su::kThreads), args, pl->smem, st), "batch launch");
+        if (launches) *launches = 1;
+        return SU_OK;
+    }
     cudaKernelNodeParams kp{};
     kp.func = const_cast<void *>(fn);
     kp.gridDim = dim3(pl->grid);
@@ -921,6 +1028,9 @@ int su_batch_plan_finalize(const su_batch_plan *pl, const double *h_tuples, cons
             r.n = pl->n_mc;
         } else {
             level_result(pl->laf[(size_t)i], h_tuples + 4 * i * pl->n_blocks, pl->n_blocks, 1, 0, &r);
+            if (r.n != pl->n_mc)
+                return fail(SU_ECUDA, "instance %lld: %lld of %lld samples reduced (the work queue ended early)",
+                            (long long)i, (long long)r.n, (long long)pl->n_mc);
         }
     }
     return SU_OK;
@@ -936,7 +1046,7 @@ int speedup_amplitude_batch(int model, const double *params, int n_params, int p
     std::unique_ptr<su_batch_plan, int (*)(su_batch_plan *)> guard(pl, su_batch_plan_destroy);
     cudaStream_t st = (cudaStream_t)pl->opt.stream;
     void *dbuf = nullptr;
-    CU(cudaMallocAsync(&dbuf, (size_t)(pl->tuple_bytes + pl->scratch_bytes), st), "cudaMallocAsync");
+    CU(dmalloc_async(&dbuf, (size_t)(pl->tuple_bytes + pl->scratch_bytes), st), "cudaMallocAsync");
     std::vector<double> h((size_t)(pl->tuple_bytes / sizeof(double)) + 32);
     void *d_scr = static_cast<char *>(dbuf) + pl->tuple_bytes;
     rc = su_batch_plan_execute(pl, dbuf, d_scr, st, nullptr);
@@ -989,7 +1099,7 @@ extern "C" int su_proposal_create(const float *theta, int n_params, su_proposal 
         cudaGetLastError();
         return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
     }
-    CU(cudaMalloc(&pr->d_blob, blob.size()), "cudaMalloc(network)");
+    CU(dmalloc(&pr->d_blob, blob.size()), "device allocation (network)");
     e = cudaMemcpy(pr->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(pr->d_blob);
@@ -1066,6 +1176,7 @@ extern "C" int speedup_amplitude_proposal(int model, const double *params, int n
     std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
     if (s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
     su::ProposalParams Q;
+    std::memset(&Q, 0, sizeof Q);
     int grid = 0;
     size_t smem = 0;
     rc = proposal_setup(pl, pr, Q, grid, smem);
@@ -1074,10 +1185,11 @@ extern "C" int speedup_amplitude_proposal(int model, const double *params, int n
     const int64_t part_bytes = up256(Q.base.n_items * pl->levels * 4 * (int64_t)sizeof(double));
     const int64_t tb = pl->tuple_bytes;
     void *dbuf = nullptr;
-    CU(cudaMallocAsync(&dbuf, (size_t)(part_bytes + tb + 256), st), "cudaMallocAsync");
+    CU(dmalloc_async(&dbuf, (size_t)(part_bytes + tb + 256), st), "cudaMallocAsync");
     Q.base.partial = static_cast<double *>(dbuf);
     double *d_tup = reinterpret_cast<double *>(static_cast<char *>(dbuf) + part_bytes);
     Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(dbuf) + part_bytes + tb);
+    Q.withhold = g_fault_mma.exchange(0);
     Q.base.w_out = nullptr;
     Q.outs = nullptr;
     std::vector<double> h((size_t)(tb / sizeof(double)));
@@ -1115,14 +1227,16 @@ extern "C" int speedup_proposal_logweights(int model, const double *params, int 
     if (rc) return rc;
     std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
     su::ProposalParams Q;
+    std::memset(&Q, 0, sizeof Q);
     int grid = 0;
     size_t smem = 0;
     rc = proposal_setup(pl, pr, Q, grid, smem);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)o.stream;
     int *d_flag = nullptr;
-    CU(cudaMallocAsync(&d_flag, sizeof(int), st), "cudaMallocAsync");
+    CU(dmalloc_async(&d_flag, sizeof(int), st), "cudaMallocAsync");
     Q.base.flags = d_flag;
+    Q.withhold = g_fault_mma.exchange(0);
     Q.base.w_out = d_w;
     Q.base.partial = nullptr;
     Q.outs = d_outs;
@@ -1209,15 +1323,15 @@ extern "C" int speedup_train_proposal(int model, const double *params, int n_par
         std::vector<void *> v;
         ~Free() { for (void *q : v) cudaFree(q); }
     } fr;
-    CU(cudaMalloc(&d_paths, (size_t)to.n_train * np1 * 4), "cudaMalloc(paths)");
+    CU(dmalloc(&d_paths, (size_t)to.n_train * np1 * 4), "device allocation (paths)");
     fr.v.push_back(d_paths);
-    CU(cudaMalloc(&d_w, (size_t)to.n_train * s * 8), "cudaMalloc(weights)");
+    CU(dmalloc(&d_w, (size_t)to.n_train * s * 8), "device allocation (weights)");
     fr.v.push_back(d_w);
-    CU(cudaMalloc(&d_flag, 4), "cudaMalloc(flag)");
+    CU(dmalloc(&d_flag, 4), "device allocation (flag)");
     fr.v.push_back(d_flag);
-    CU(cudaMalloc(&d_ids, (size_t)to.batch_paths * 4), "cudaMalloc(ids)");
+    CU(dmalloc(&d_ids, (size_t)to.batch_paths * 4), "device allocation (ids)");
     fr.v.push_back(d_ids);
-    CU(cudaMalloc(&d_sig, 16 * 4), "cudaMalloc(sigma)");
+    CU(dmalloc(&d_sig, 16 * 4), "device allocation (sigma)");
     fr.v.push_back(d_sig);
     su::SamplerParams P = pl->P;
     P.w_out = d_w;
@@ -1261,11 +1375,11 @@ extern "C" int speedup_train_proposal(int model, const double *params, int n_par
     CU(ws.reserve(R), "training workspace");
     double *d_cdf = nullptr, *d_losses = nullptr;
     int *d_step = nullptr;
-    CU(cudaMalloc(&d_cdf, cdf.size() * sizeof(double)), "cudaMalloc(cdf)");
+    CU(dmalloc(&d_cdf, cdf.size() * sizeof(double)), "device allocation (cdf)");
     fr.v.push_back(d_cdf);
-    CU(cudaMalloc(&d_losses, (size_t)to.steps * sizeof(double)), "cudaMalloc(losses)");
+    CU(dmalloc(&d_losses, (size_t)to.steps * sizeof(double)), "device allocation (losses)");
     fr.v.push_back(d_losses);
-    CU(cudaMalloc(&d_step, sizeof(int)), "cudaMalloc(step)");
+    CU(dmalloc(&d_step, sizeof(int)), "device allocation (step)");
     fr.v.push_back(d_step);
     struct GraphRes {
         cudaStream_t st = nullptr;

@@ -77,7 +77,8 @@ __host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
+constexpr unsigned long long kWaitNs = 1000000000ull;   // a wait gives up after one second
+constexpr int kWaitPolls = 1 << 28;                      // and after this many polls in any case
 
 struct Tc {
     uint32_t tmem;     // tensor-memory base address (lane 0, first column)
@@ -123,8 +124,10 @@ __device__ __forceinline__ void tc_end(const Tc &t) {
 // One layer's MMAs, D[:, col..col+N) = A[128][K] B[N][K]^T, issued by thread
 // 0 after the other threads' shared-memory writes (fenced for the async
 // proxy and synchronised by the caller), then committed to the mbarrier.
-__device__ __forceinline__ void tc_layer(const Tc &t, uint32_t a, uint32_t b, int K, int N, uint32_t col) {
-    if (threadIdx.x == 0) {
+// withhold (fault injection): issue nothing, so the wait runs out.
+__device__ __forceinline__ void tc_layer(const Tc &t, uint32_t a, uint32_t b, int K, int N, uint32_t col,
+                                         bool withhold = false) {
+    if (threadIdx.x == 0 && !withhold) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t sbo = (uint32_t)(K / 8) * 128;
         const uint32_t id = instr_desc(kRows, N);
@@ -140,14 +143,24 @@ __device__ __forceinline__ void tc_layer(const Tc &t, uint32_t a, uint32_t b, in
     }
 }
 
-// All threads: wait (bounded) for the last commit; false if it never came.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+
+// All threads: wait (bounded: one second of the global timer) for the last
+// commit; false if it never came.
 __device__ __forceinline__ bool tc_wait(Tc &t) {
     uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; ++it)
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < kWaitPolls && !done; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
             : "r"(t.mbar), "r"(t.phase));
+        if (!done && (it & 255) == 255 && global_ns() - t0 > kWaitNs) break;
+    }
     t.phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     return done != 0;
@@ -201,23 +214,24 @@ __device__ __forceinline__ void tc_store_gelu(const Tc &t, const float *bias, un
 // ([128][16], columns 6..15 zero), written and synchronised by the caller
 // (fence.proxy.async by the writers, then __syncthreads); H: the hidden tile;
 // out[row * 2 + {0, 1}] = (shift, ls).  All kThreads threads; returns false on
-// all threads if an MMA never completed (the tile's outputs are then invalid).
+// all threads if an MMA never completed (the tile's outputs are then invalid
+// and the caller must stop).  withhold: fault injection (see tc_layer).
 __device__ __forceinline__ bool tile_forward(Tc &t, const unsigned char *blob, const unsigned char *X0,
-                                             unsigned char *H, float *out) {
+                                             unsigned char *H, float *out, bool withhold = false) {
     const float *B = reinterpret_cast<const float *>(blob + kOffB);
     const uint32_t sb = smem_u32(blob), sx = smem_u32(X0), sh = smem_u32(H);
-    bool ok = true;
-    tc_layer(t, sx, sb + kOffW1, kK1, kHid, 0);
-    ok &= tc_wait(t);
+    // each wait's outcome agreed by the whole CTA before the epilogue reads
+    tc_layer(t, sx, sb + kOffW1, kK1, kHid, 0, withhold);
+    if (!__syncthreads_and(tc_wait(t) ? 1 : 0)) return false;
     tc_store_gelu(t, B, H);
     tc_layer(t, sh, sb + kOffW2, kHid, kHid, 0);
-    ok &= tc_wait(t);
+    if (!__syncthreads_and(tc_wait(t) ? 1 : 0)) return false;
     tc_store_gelu(t, B + kHid, H);
     tc_layer(t, sh, sb + kOffW3, kHid, kHid, 0);
-    ok &= tc_wait(t);
+    if (!__syncthreads_and(tc_wait(t) ? 1 : 0)) return false;
     tc_store_gelu(t, B + 2 * kHid, H);
     tc_layer(t, sh, sb + kOffW4, kHid, kNOut, kHid);
-    ok &= tc_wait(t);
+    if (!__syncthreads_and(tc_wait(t) ? 1 : 0)) return false;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4) {   // the output columns of the warp's 32 rows
         uint32_t r0, r1;
@@ -230,7 +244,8 @@ __device__ __forceinline__ bool tile_forward(Tc &t, const unsigned char *blob, c
         out[2 * row + 1] = __uint_as_float(r1) + B[3 * kHid + 1];
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    return __syncthreads_and(ok ? 1 : 0) != 0;
+    __syncthreads();
+    return true;
 }
 
 // features of one row into the X0 tile (operand layout): columns 0..5, the

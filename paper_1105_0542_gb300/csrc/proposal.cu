@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
                                         __float2bfloat16_rn(qs[kR * kRows + p]));
                 asm volatile("fence.proxy.async.shared::cta;");
                 __syncthreads();
-                if (!tile_forward(tc, blob, X0, H, out)) {
+                if (!tile_forward(tc, blob, X0, H, out, Q.withhold != 0)) {
                     if (tid == 0) atomicOr(P.flags, 4);   // an MMA never completed
                     alive = false;
                     break;

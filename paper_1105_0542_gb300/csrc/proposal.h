@@ -14,6 +14,7 @@ struct ProposalParams {
     const unsigned char *blob;   // device: network blob (mlp::kBlobBytes)
     double T;                    // propagation time (a network input)
     float *outs;                 // per-sample mode: (shift, ls) per sample and heap index, or null
+    int withhold;                // fault injection: the first tile withholds its MMA commit
 };
 
 size_t proposal_smem_bytes(const ProposalParams &Q);

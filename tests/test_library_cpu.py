@@ -155,3 +155,20 @@ def test_evolution_matrix_rejects_bad_arguments(kw):
         su.speedup_evolution_matrix(args["model"], args["params"], args["p"], args["t"], args["L"], args["n"], 1 << 20)
     assert e.value.code == -1
 
+
+def test_fault_hooks_validate_and_the_nan_table_fails_before_any_device_work():
+    with pytest.raises(su.SpeedupError) as e:
+        su.su_fault_inject(9)
+    assert e.value.code == -1
+    with pytest.raises(su.SpeedupError) as e:
+        su.su_fault_inject("alloc", 0)
+    assert e.value.code == -1
+    # the tables are built and checked before the device is touched
+    su.su_fault_inject("table_nan")
+    try:
+        with pytest.raises(su.SpeedupError) as e:
+            su.speedup_amplitude("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 100, 1)
+        assert e.value.code == -5
+    finally:
+        su.su_fault_inject("clear")
+
