@@ -410,6 +410,20 @@ int su_autotune(int model, const double *params, int n_params, double a, double 
                 int p, int s, int64_t n_probe, uint64_t seed, const su_options *opt,
                 su_tuning *best, su_tuning *all, int cap, int *n_all);
 
+/*
+ * su_plan_execute_range -- checkpoint / resume: sample only the error blocks
+ * [b0, b1) of the plan (block b = samples [b n_mc / n_blocks, (b+1) n_mc /
+ * n_blocks) of the run) and write only their tuples in d_tuples; the other
+ * blocks' tuples are left as they are.  A run interrupted after blocks
+ * [0, k) is checkpointed by saving the tuple array (n_blocks * levels * 4
+ * doubles) and resumed, in any later process, by loading it into d_tuples
+ * and executing [k, n_blocks): the counter-based stream and the per-block
+ * reduction make the result identical to the uninterrupted run, bit for bit.
+ * No counterpart in the paper (its C code runs to completion).
+ */
+int su_plan_execute_range(su_plan *plan, int64_t b0, int64_t b1, void *d_tuples, void *d_scratch, void *stream,
+                          int *launches);
+
 /* su_plan_execute with the device time of its launches: CUDA events around
  * them on stream, *ms = elapsed milliseconds (synchronises the stop event). */
 int su_plan_execute_timed(su_plan *plan, void *d_tuples, void *d_scratch, void *stream, int *launches,

@@ -28,7 +28,7 @@ EXPORTS = [
     "speedup_amplitude_noalloc", "su_proposal_create", "su_proposal_destroy", "su_mlp_forward",
     "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
-    "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed",
+    "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
 ]
 MLP_PARAMS = 34178
 
@@ -115,6 +115,7 @@ def load(build_if_missing=True):
     L.speedup_evolution_matrix.argtypes = [i32, pd, i32, i32, d, d, i32, i32, vp, vp]
     L.su_fault_inject.argtypes = [i32, i64]
     L.su_plan_execute_timed.argtypes = [vp, vp, vp, vp, pi, ctypes.POINTER(ctypes.c_float)]
+    L.su_plan_execute_range.argtypes = [vp, i64, i64, vp, vp, vp, pi]
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
@@ -468,6 +469,13 @@ class Plan:
         f, r = ctypes.c_int(0), ctypes.c_int(0)
         _check(load().su_plan_shape(self._h, ctypes.byref(f), ctypes.byref(r)))
         return f.value, r.value
+
+    def su_plan_execute_range(self, b0, b1, d_tuples, d_scratch, stream=None):
+        """Sample error blocks [b0, b1) only (checkpoint / resume); returns launches."""
+        n = ctypes.c_int(0)
+        _check(load().su_plan_execute_range(self._h, int(b0), int(b1), _ptr(d_tuples), _ptr(d_scratch),
+                                            _stream(stream), ctypes.byref(n)))
+        return n.value
 
     def su_plan_execute_timed(self, d_tuples, d_scratch, stream=None):
         """Launch and time on the device; returns (launches, milliseconds)."""

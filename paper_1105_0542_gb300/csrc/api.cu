@@ -400,18 +400,28 @@ int su_plan_shape(const su_plan *pl, int *seg_log2, int *rounds) {
 
 int su_plan_execute(su_plan *pl, void *d_tuples, void *d_scratch, void *stream, int *launches) {
     if (!pl) return fail(SU_EINVAL, "plan missing");
+    return su_plan_execute_range(pl, 0, pl->n_blocks, d_tuples, d_scratch, stream, launches);
+}
+
+int su_plan_execute_range(su_plan *pl, int64_t b0, int64_t b1, void *d_tuples, void *d_scratch, void *stream,
+                          int *launches) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
     if (launches) *launches = 0;
-    if (pl->s == 0) return SU_OK;  // level 0 is analytic: nothing to sample
+    if (b0 < 0 || b1 > pl->n_blocks || b0 > b1) return fail(SU_EINVAL, "block range out of 0..%lld", (long long)pl->n_blocks);
+    if (pl->s == 0 || b0 == b1) return SU_OK;  // level 0 is analytic: nothing to sample
     if (!d_tuples || !d_scratch) return fail(SU_EINVAL, "device buffers missing");
     cudaStream_t st = (cudaStream_t)stream;
     su::SamplerParams P = pl->P;
+    P.item0 = b0 * P.items_per_block;
+    P.n_items = b1 * P.items_per_block;
+    const int grid = (int)std::min<int64_t>(pl->grid, P.n_items - P.item0);
     P.partial = static_cast<double *>(d_scratch);
     P.flags = reinterpret_cast<int *>(static_cast<char *>(d_scratch) + pl->scratch_bytes - 256);
     P.w_out = nullptr;
     CU(cudaMemsetAsync(P.flags, 0, sizeof(int), st), "clear flags");
-    CU(su::launch_sampler(P, pl->opt.precision, pl->grid, pl->smem, st), "sampler launch");
-    CU(su::launch_combine(P.partial, static_cast<double *>(d_tuples), pl->n_blocks, pl->levels,
-                          P.items_per_block, st),
+    CU(su::launch_sampler(P, pl->opt.precision, grid, pl->smem, st), "sampler launch");
+    CU(su::launch_combine(P.partial, static_cast<double *>(d_tuples), b0, b1 - b0, pl->levels, P.items_per_block,
+                          st),
        "combine launch");
     if (launches) *launches = 2;
     return SU_OK;
@@ -1197,7 +1207,7 @@ extern "C" int speedup_amplitude_proposal(int model, const double *params, int n
     cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
     if (e == cudaSuccess) e = su::launch_proposal(Q, grid, smem, st);
     if (e == cudaSuccess)
-        e = su::launch_combine(Q.base.partial, d_tup, pl->n_blocks, pl->levels, Q.base.items_per_block, st);
+        e = su::launch_combine(Q.base.partial, d_tup, 0, pl->n_blocks, pl->levels, Q.base.items_per_block, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1578,7 +1588,7 @@ extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_
     CU(cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "upload tables");
     CU(cudaMemsetAsync(d_flag, 0, sizeof(int), st), "clear flag");
     CU(launch_sampler(P, prec, grid, smem, st), "sampler launch");
-    CU(launch_combine(d_part, d_tup, nb, P.levels, P.items_per_block, st), "combine launch");
+    CU(launch_combine(d_part, d_tup, 0, nb, P.levels, P.items_per_block, st), "combine launch");
     CU(cudaMemcpyAsync(h.data(), d_tup, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read tuples");
     CU(cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     CU(cudaStreamSynchronize(st), "sampling");

@@ -27,12 +27,12 @@ const void *batch_entry_f32_2();
 namespace {
 
 // ----------------------------------------------------------- combine
-__global__ void combine_kernel(const double *__restrict__ partial, double *__restrict__ tuples,
+__global__ void combine_kernel(const double *__restrict__ partial, double *__restrict__ tuples, int64_t b0,
                                int64_t n_blocks, int L, int64_t ipb) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n_blocks * L) return;
-    const int64_t b = id / L;
-    const int d = (int)(id - b * L);
+    const int64_t b = b0 + id / L;
+    const int d = (int)(id - (id / L) * L);
     double M = -INFINITY, S = 0, Q = 0, n = 0;
     for (int64_t r = 0; r < ipb; ++r) {
         const double *p = partial + 4 * ((b * ipb + r) * L + d);
@@ -50,7 +50,7 @@ __global__ void combine_kernel(const double *__restrict__ partial, double *__res
             Q += p[2] * f * f;
         }
     }
-    double *o = tuples + 4 * id;
+    double *o = tuples + 4 * (b * L + d);
     o[0] = M;
     o[1] = S;
     o[2] = Q;
@@ -210,12 +210,13 @@ cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size
     return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, st);
 }
 
-cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
+cudaError_t launch_combine(const double *partial, double *tuples, int64_t b0, int64_t n_blocks, int levels,
                            int64_t items_per_block, cudaStream_t st) {
     const int64_t n = n_blocks * levels;
+    if (n == 0) return cudaSuccess;
     const int th = 128;
     cudaGetLastError();
-    combine_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(partial, tuples, n_blocks, levels,
+    combine_kernel<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(partial, tuples, b0, n_blocks, levels,
                                                                items_per_block);
     return cudaGetLastError();
 }

@@ -35,7 +35,8 @@ struct SamplerParams {
     int64_t n_mc, sample0;
     int64_t n_blocks;
     int64_t items_per_block;
-    int64_t n_items;
+    int64_t n_items;          // items [item0, n_items) are this launch's (block ranges)
+    int64_t item0;
     int rounds;
     // outputs
     double *partial;          // device: per item and level, (M, S, Q, n)
@@ -83,7 +84,8 @@ cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size
 size_t batch_smem_bytes(const BatchParams &B, int precision);
 int batch_occupancy(const BatchParams &B, int precision, size_t smem);
 const void *batch_fn(int ring, int precision);
-cudaError_t launch_combine(const double *partial, double *tuples, int64_t n_blocks, int levels,
+// tuples of blocks [b0, b0 + n_blocks) from their items' partial tuples
+cudaError_t launch_combine(const double *partial, double *tuples, int64_t b0, int64_t n_blocks, int levels,
                            int64_t items_per_block, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
                            int n_normals, int precision, double *out, cudaStream_t st);

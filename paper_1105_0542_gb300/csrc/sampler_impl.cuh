@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
 
     const int warp = tid >> 5, lane = tid & 31;
-    for (int64_t item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+    for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t b = item / P.items_per_block;
         const int64_t r = item - b * P.items_per_block;
         const int64_t lo = b * P.n_mc / P.n_blocks;
