@@ -136,5 +136,35 @@ def test_family_derivatives_against_numerical_differentiation():
             assert got[j] == pytest.approx(ref, rel=1e-9, abs=1e-9 * max(1.0, abs(ref))), (x0, j)
 
 
+def test_sech2_derivatives_to_the_highest_order_far_from_the_centre():
+    """All orders the general mode uses (up to 2p - 2 = 22) where tanh is
+    near +-1 and the derivatives are small against their polynomial
+    coefficients (|u| up to 4): the cancellation-prone region."""
+    mp.mp.dps = 60
+    J = 22
+    for B, alpha, d in ((-3.0, 1.0, 0.0), (0.4, 2.0, 0.5)):
+        params = _params(sech=[(B, alpha, d)])
+        for x0 in (-2.2, 0.3, 1.7, 3.0 / alpha + d, 4.0):
+            got = gv.derivatives(params, np.array([x0]), J)[:, 0]
+            f = lambda z: B * mp.sech(alpha * (z - d)) ** 2  # noqa: E731
+            for j in range(J + 1):
+                ref = float(mp.diff(f, mp.mpf(x0), j))
+                assert got[j] == pytest.approx(ref, rel=1e-12, abs=1e-300), (B, x0, j)
+
+
+def test_sech2_leibniz_rule_matches_the_tanh_polynomials():
+    """The Leibniz recursion on tanh' = 1 - tanh^2 and the polynomials
+    P_n(t) (P_0 = 1 - t^2, P_{n+1} = (1 - t^2) P_n') are the same
+    derivatives: equal at rational t in exact arithmetic."""
+    J = 12
+    P = gv._sech2_polys(J)
+    for t in (Fraction(0), Fraction(1, 3), Fraction(-5, 7), Fraction(9, 10)):
+        T = [t]
+        for n in range(J + 1):
+            T.append((1 if n == 0 else 0) - sum(math.comb(n, k) * T[k] * T[n - k] for k in range(n + 1)))
+        for n in range(J + 1):
+            assert sum(c * t ** i for i, c in enumerate(P[n])) == T[n + 1], (t, n)
+
+
 def test_term_counts():
     assert [gv.term_count(p) for p in (1, 2, 4, 6, 8, 10)] == [1, 3, 15, 58, 193, 585]
