@@ -6,8 +6,8 @@ this package is its ctypes binding.  There is no CPU fallback: without the
 built library or a CUDA device the entry points raise.
 """
 from ._binding import (  # noqa: F401
-    BatchPlan, EXPORTS, MLP_PARAMS, MODELS, PRECISIONS, Plan, Proposal, SpeedupError, library_path, load,
-    options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_noalloc, speedup_amplitude_proposal,
+    BatchPlan, EXPORTS, GENERAL_MAX_P, MLP_PARAMS, MODELS, PRECISIONS, Plan, Proposal, SpeedupError, library_path, load,
+    general_params, options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_noalloc, speedup_amplitude_proposal,
     speedup_evolution_matrix, speedup_generate_coeffs, speedup_logweights, speedup_normals, speedup_philox_words,
     speedup_proposal_logweights, speedup_train_proposal, su_autotune, su_autotune_clear, su_fault_inject,
     su_fma_peak,

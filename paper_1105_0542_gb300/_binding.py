@@ -15,7 +15,8 @@ import numpy as np
 from . import build as _build
 
 SU_OK, SU_EINVAL, SU_ENOMEM, SU_ECUDA, SU_ETIMEOUT, SU_ENONFINITE, SU_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4}
+MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4, "general": 5}
+GENERAL_MAX_P = 12
 PRECISIONS = {"fp64": 0, "fp32": 1}
 MAX_P, MAX_S = 32, 10
 
@@ -155,6 +156,23 @@ def load(build_if_missing=True):
 def _check(rc):
     if rc != SU_OK:
         raise SpeedupError(rc, load().su_last_error().decode())
+
+
+def general_params(poly=(), gauss=(), sech=()):
+    """The 33 parameters of the general potential (model "general"):
+    poly = (a_0, .., a_d), d <= 8; gauss = up to four (A, beta, c) for
+    A e^{-beta (q - c)^2}; sech = up to four (B, alpha, d) for
+    B sech^2(alpha (q - d))."""
+    if len(poly) > 9 or len(gauss) > 4 or len(sech) > 4:
+        raise ValueError("degree <= 8, at most four Gaussian and four sech^2 terms")
+    out = [float(v) for v in poly] + [0.0] * (9 - len(poly))
+    for terms in (gauss, sech):
+        for t in terms:
+            if len(t) != 3:
+                raise ValueError("each Gaussian or sech^2 term has three parameters")
+            out += [float(v) for v in t]
+        out += [0.0] * (3 * (4 - len(terms)))
+    return tuple(out)
 
 
 def _model(m):

@@ -148,7 +148,34 @@ struct su_plan {
     int64_t tuple_bytes = 0, scratch_bytes = 0, partial_bytes = 0;
     int64_t slice_actions = 0;
     double cancel_ratio = 1;  // largest sum|terms| / |sum| in the table collapse
+    // SU_GENERAL: the monomial program of W_p, the potential's families and
+    // their device image (GeneralDev | nodes | entry powers)
+    std::shared_ptr<const su::GeneralEffective> G;
+    su::GeneralPotential V{};
+    void *d_general = nullptr;
 };
+
+namespace {
+
+// The monomial program of W_p for a general potential depends on p only;
+// built once per p (milliseconds at p = 12) and shared.
+std::shared_ptr<const su::GeneralEffective> general_program(int p, int &rc, std::string &err) {
+    static std::mutex mu;
+    static std::map<int, std::shared_ptr<const su::GeneralEffective>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(p);
+    if (it != cache.end()) {
+        rc = SU_OK;
+        return it->second;
+    }
+    auto G = std::make_shared<su::GeneralEffective>();
+    rc = su::build_general(p, *G, err);
+    if (rc) return nullptr;
+    cache.emplace(p, G);
+    return G;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -190,6 +217,7 @@ int speedup_generate_coeffs(int model, const double *params, int n_params, int p
                             double *table, int capacity, int *shape, int *n_terms) {
     if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");
     if (!table || !shape || !n_terms || capacity < 0) return fail(SU_EINVAL, "output missing");
+    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the general potential has no collapsed table");
     su::Effective E;
     std::string err;
     int rc = su::build_effective(model, params, n_params, p, E, err);
@@ -210,7 +238,6 @@ int speedup_generate_coeffs(int model, const double *params, int n_params, int p
 
 static int validate(int model, const double *params, int n_params, double a, double b, double T,
                     int p, int s, int64_t n_mc, const su_options &o) {
-    (void)model;
     (void)params;
     (void)n_params;
     if (!std::isfinite(a) || !std::isfinite(b)) return fail(SU_EINVAL, "a and b must be finite");
@@ -225,6 +252,70 @@ static int validate(int model, const double *params, int n_params, double a, dou
     if (o.sample0 < 0 || o.sample0 + n_mc > kMaxSamples) return fail(SU_EINVAL, "sample0 out of range");
     if (o.seg_log2 < 0 || o.seg_log2 > su::kMaxFine) return fail(SU_EINVAL, "seg_log2 must be in 0..5");
     if (o.rounds < 0 || o.rounds > 8) return fail(SU_EINVAL, "rounds must be in 0..8");
+    if (model == SU_GENERAL) {
+        if (p > su::kGenMaxP) return fail(SU_ENOTSUP, "the general potential supports p <= %d", su::kGenMaxP);
+        if (o.precision != SU_FP64) return fail(SU_ENOTSUP, "the general potential is evaluated in double only");
+    }
+    return SU_OK;
+}
+
+// Device image of the general program and potential: one allocation holding
+// GeneralDev, the depth-first nodes and the entries' powers of vs^2.
+static int upload_general(su_plan &pl) {
+    using namespace su;
+    const GeneralEffective &G = *pl.G;
+    const GeneralPotential &V = pl.V;
+    GeneralDev D;
+    std::memset(&D, 0, sizeof D);
+    D.J = G.J;
+    D.K = G.K;
+    D.n_nodes = (int)G.depth.size();
+    D.n_entries = (int)G.entry_k.size();
+    D.ng = V.ng;
+    D.ns = V.ns;
+    if (G.J >= kGenMaxSym || G.K > kGenMaxP) return fail(SU_EINVAL, "internal: general program out of range");
+    std::vector<GeneralNode> nodes((size_t)D.n_nodes);
+    for (int t = 0; t < D.n_nodes; ++t) {
+        if (G.depth[(size_t)t] > kGenMaxDepth || G.count[(size_t)t] > 65535)
+            return fail(SU_EINVAL, "internal: general program node out of range");
+        nodes[(size_t)t].depth = (unsigned char)G.depth[(size_t)t];
+        nodes[(size_t)t].sym = (unsigned char)G.sym[(size_t)t];
+        nodes[(size_t)t].count = (unsigned short)G.count[(size_t)t];
+        nodes[(size_t)t].first = G.first[(size_t)t];
+    }
+    std::vector<unsigned char> ek(G.entry_k.begin(), G.entry_k.end());
+    for (int j = 0; j <= std::min(G.J, 8); ++j)   // V^(j) of the polynomial: a_i i!/(i-j)!
+        for (int i = j; i <= 8; ++i) {
+            double f = 1.0;
+            for (int r = 0; r < j; ++r) f *= (double)(i - r);
+            D.poly_der[j][i] = V.a[i] * f;
+        }
+    for (int g = 0; g < V.ng; ++g) {
+        for (int r = 0; r < 3; ++r) D.gauss[g][r] = V.gauss[g][r];
+        D.gauss[g][3] = std::sqrt(V.gauss[g][1]);
+    }
+    for (int q = 0; q < V.ns; ++q) {
+        for (int r = 0; r < 3; ++r) D.sech[q][r] = V.sech[q][r];
+        double sc = V.sech[q][0];                  // B alpha^n (n+1)!
+        for (int n = 0; n <= G.J; ++n) {
+            sc *= (double)(n + 1);
+            D.sech_scale[q][n] = sc;
+            sc *= V.sech[q][1];
+        }
+    }
+    for (int n = 1; n <= kGenMaxSym; ++n) D.inv[n] = 1.0 / (double)n;
+    const size_t o_nodes = (sizeof(GeneralDev) + 15) & ~(size_t)15;
+    const size_t o_k = (o_nodes + nodes.size() * sizeof(GeneralNode) + 15) & ~(size_t)15;
+    const size_t bytes = o_k + ek.size();
+    CU(dmalloc(&pl.d_general, bytes), "device allocation (general program)");
+    char *base = static_cast<char *>(pl.d_general);
+    D.nodes = reinterpret_cast<const GeneralNode *>(base + o_nodes);
+    D.entry_k = reinterpret_cast<const unsigned char *>(base + o_k);
+    std::vector<unsigned char> blob(bytes, 0);
+    std::memcpy(blob.data(), &D, sizeof D);
+    std::memcpy(blob.data() + o_nodes, nodes.data(), nodes.size() * sizeof(GeneralNode));
+    std::memcpy(blob.data() + o_k, ek.data(), ek.size());
+    CU(cudaMemcpy(pl.d_general, blob.data(), bytes, cudaMemcpyHostToDevice), "upload general program");
     return SU_OK;
 }
 
@@ -235,13 +326,17 @@ static int configure(su_plan &pl) {
     const int prec = pl.opt.precision;
     // tables of levels n = S..1 (row d = S - n), each scaled for the kernel
     const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
-    const int M = pl.E.shape.M;
+    const bool general = pl.model == SU_GENERAL;
+    const int M = general ? (int)pl.G->entry_k.size() : pl.E.shape.M;
     std::vector<double> tabd((size_t)std::max(S, 1) * M, 0.0);
     for (int d = 0; d < S; ++d) {
         const int n = S - d;
         const double eps = pl.T / std::ldexp(1.0, n);
         std::vector<double> t;
-        pl.cancel_ratio = std::max(pl.cancel_ratio, su::kernel_table(pl.E, eps, t));
+        if (general)
+            su::general_table(*pl.G, eps, t);
+        else
+            pl.cancel_ratio = std::max(pl.cancel_ratio, su::kernel_table(pl.E, eps, t));
         if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
         for (int i = 0; i < M; ++i) {
             if (!std::isfinite(t[i]) || (prec == SU_FP32 && !std::isfinite((float)t[i])))
@@ -268,6 +363,10 @@ static int configure(su_plan &pl) {
        "smem limit");
     CU(dmalloc(&pl.d_tables, blob.size()), "device allocation (tables)");
     CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
+    if (general) {
+        const int rc = upload_general(pl);
+        if (rc) return rc;
+    }
 
     std::memset(&P, 0, sizeof P);
     P.a = pl.a;
@@ -286,12 +385,13 @@ static int configure(su_plan &pl) {
     P.wf_on = pl.opt.width_factor != 1.0;
     P.lwf = std::log(pl.opt.width_factor);
     P.hcoef = 0.5 * (1.0 - pl.opt.width_factor * pl.opt.width_factor);
-    P.ring = pl.E.shape.ring;
-    P.ncol = pl.E.shape.ncol;
+    P.ring = general ? RING_GENERAL : pl.E.shape.ring;
+    P.ncol = general ? 0 : pl.E.shape.ncol;
     P.M = M;
-    for (int j = 0; j < pl.E.shape.ncol; ++j) P.len[j] = pl.E.shape.len[j];
-    P.alpha = pl.E.shape.alpha;
+    for (int j = 0; j < P.ncol; ++j) P.len[j] = pl.E.shape.len[j];
+    P.alpha = general ? 0.0 : pl.E.shape.alpha;
     P.tables = pl.d_tables;
+    P.general = static_cast<const GeneralDev *>(pl.d_general);
     P.seed = pl.seed;
     P.instance = pl.opt.instance;
     P.n_mc = pl.n_mc;
@@ -347,7 +447,12 @@ int su_plan_create(int model, const double *params, int n_params, double a, doub
     std::unique_ptr<su_plan> pl(new (std::nothrow) su_plan);
     if (!pl) return fail(SU_ENOMEM, "host allocation failed");
     std::string err;
-    rc = su::build_effective(model, params, n_params, p, pl->E, err);
+    if (model == SU_GENERAL) {
+        rc = su::general_potential(params, n_params, pl->V, err);
+        if (!rc) pl->G = general_program(p, rc, err);
+    } else {
+        rc = su::build_effective(model, params, n_params, p, pl->E, err);
+    }
     if (rc) return fail(rc, "%s", err.c_str());
     pl->model = model;
     pl->params.assign(params, params + n_params);
@@ -361,13 +466,15 @@ int su_plan_create(int model, const double *params, int n_params, double a, doub
     pl->opt = o;
     pl->levels = s == 0 ? 0 : (o.hierarchy ? s : 1);
     pl->n_blocks = std::min<int64_t>(o.n_blocks, n_mc);
-    pl->w0 = -T * su::wp_host(pl->E, 0.5 * (a + b), 0.5 * (b - a), T);
+    pl->w0 = model == SU_GENERAL ? -T * su::general_wp_host(*pl->G, pl->V, 0.5 * (a + b), 0.5 * (b - a), T)
+                                 : -T * su::wp_host(pl->E, 0.5 * (a + b), 0.5 * (b - a), T);
     pl->laf = log_A_free(a, b, T);
     if (!std::isfinite(pl->w0) && !(std::isinf(pl->w0) && pl->w0 < 0))
         return fail(SU_ENONFINITE, "level-0 weight is not finite");
     rc = configure(*pl);
     if (rc) {
         if (pl->d_tables) cudaFree(pl->d_tables);
+        if (pl->d_general) cudaFree(pl->d_general);
         return rc;
     }
     *out = pl.release();
@@ -377,6 +484,7 @@ int su_plan_create(int model, const double *params, int n_params, double a, doub
 int su_plan_destroy(su_plan *pl) {
     if (!pl) return SU_OK;
     if (pl->d_tables) cudaFree(pl->d_tables);
+    if (pl->d_general) cudaFree(pl->d_general);
     delete pl;
     return SU_OK;
 }
@@ -596,6 +704,7 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
     if (n < 2 || n > 65536) return fail(SU_EINVAL, "n must be in 2..65536");
     if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
     if (precision != SU_FP64 && precision != SU_FP32) return fail(SU_EINVAL, "unknown precision");
+    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the evolution operator takes the collapsed-table models only");
     su::Effective E;
     std::string err;
     int rc = su::build_effective(model, params, n_params, p, E, err);
@@ -814,6 +923,7 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
     if ((uint64_t)o.instance + (uint64_t)n_inst > (1ULL << 32))
         return fail(SU_EINVAL, "instance ids exceed 32 bits");
     if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "the batched path samples the exact bridge only");
+    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the batched path takes the collapsed-table models only");
     for (int64_t i = 0; i < n_inst; ++i) {
         int rc = validate(model, params, n_params, inst[i].a, inst[i].b, inst[i].T, p, inst[i].s, n_mc, o);
         if (rc) {
@@ -1481,6 +1591,7 @@ extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_
     if (opt) o = *opt;
     int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
     if (rc) return rc;
+    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the allocation-free path takes the collapsed-table models only");
     Effective E;
     std::string err;
     rc = build_effective(model, params, n_params, p, E, err);

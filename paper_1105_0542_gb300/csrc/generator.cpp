@@ -29,7 +29,9 @@
 // so that the error-free transformations stay error-free on every host.
 #include "generator.h"
 
+#include <algorithm>
 #include <cmath>
+#include <map>
 #include <cstdio>
 
 #include "../../include/speedup.h"
@@ -358,6 +360,278 @@ double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, doub
         acc = acc * y + h;
     }
     return acc;
+}
+
+// ---------------------------------------------------- general potentials
+namespace {
+
+using Mono = std::vector<unsigned char>;   // exponents of V_0..V_{2p-1}
+using GPoly = std::map<Mono, DD>;
+
+// acc += s * b, dropping sums that cancel to rounding residue
+void gadd(GPoly &acc, const GPoly &b, DD s) {
+    for (const auto &kv : b) {
+        const DD v = mul(kv.second, s);
+        auto it = acc.find(kv.first);
+        if (it == acc.end()) {
+            acc.emplace(kv.first, v);
+        } else {
+            const double scale = std::max(std::fabs(it->second.hi), std::fabs(v.hi));
+            it->second = add(it->second, v);
+            if (std::fabs(it->second.hi) <= 1e-26 * scale) acc.erase(it);
+        }
+    }
+}
+
+GPoly gmul(const GPoly &a, const GPoly &b) {
+    GPoly out;
+    for (const auto &x : a)
+        for (const auto &y : b) {
+            Mono m(x.first.size());
+            for (size_t j = 0; j < m.size(); ++j) m[j] = (unsigned char)(x.first[j] + y.first[j]);
+            GPoly t;
+            t.emplace(std::move(m), mul(x.second, y.second));
+            gadd(out, t, dd(1.0));
+        }
+    return out;
+}
+
+// d/dx with d/dx V_j = V_{j+1}
+GPoly gD(const GPoly &a) {
+    GPoly out;
+    for (const auto &x : a)
+        for (size_t j = 0; j + 1 < x.first.size(); ++j) {
+            if (!x.first[j]) continue;
+            Mono m = x.first;
+            m[j] -= 1;
+            m[j + 1] += 1;
+            GPoly t;
+            t.emplace(std::move(m), mul_d(x.second, (double)x.first[j]));
+            gadd(out, t, dd(1.0));
+        }
+    return out;
+}
+
+}  // namespace
+
+int build_general(int p, GeneralEffective &G, std::string &err) {
+    if (p < 1 || p > kGenMaxP) {
+        err = "the general potential supports p in 1..12";
+        return SU_EINVAL;
+    }
+    const int nsym = 2 * p;   // V_0..V_{2p-1}; W_p uses up to V_{2p-2}
+    std::vector<std::vector<GPoly>> c(p, std::vector<GPoly>(p)), dc(p, std::vector<GPoly>(p));
+    DD inv_fact = dd(1.0);
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) inv_fact = div_d(div_d(inv_fact, 2.0 * m), 2.0 * m + 1.0);
+        Mono e(nsym, 0);
+        e[2 * m] = 1;
+        c[m][m].emplace(e, inv_fact);
+        dc[m][m] = gD(c[m][m]);
+        for (int k = m - 1; k >= 0; --k) {
+            GPoly acc;
+            gadd(acc, c[m][k + 1], dd((double)((2 * k + 2) * (2 * k + 1))));
+            gadd(acc, gD(dc[m - 1][k]), dd(1.0));
+            for (int l = 0; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r)
+                    gadd(acc, gmul(dc[l][r], dc[m - l - 2][k - r]), dd(-1.0));
+            for (int l = 1; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r) {
+                    const int fac = 2 * r * (2 * k - 2 * r + 2);
+                    if (fac) gadd(acc, gmul(c[l][r], c[m - l - 1][k - r + 1]), dd(-(double)fac));
+                }
+            GPoly ck;
+            gadd(ck, acc, div_d(dd(1.0), 8.0 * (m + k + 1)));
+            c[m][k] = std::move(ck);
+            if (m < p - 1) dc[m][k] = gD(c[m][k]);
+        }
+    }
+    // monomial -> per k: coefficients of eps^(m-k), m = k..p-1
+    std::map<Mono, std::map<int, std::vector<DD>>> terms;
+    int K = 1;
+    for (int m = 0; m < p; ++m)
+        for (int k = 0; k <= m; ++k)
+            for (const auto &kv : c[m][k]) {
+                auto &vec = terms[kv.first][k];
+                if (vec.empty()) vec.assign((size_t)(p - k), dd(0));
+                vec[(size_t)(m - k)] = kv.second;
+                K = std::max(K, k + 1);
+            }
+    // trie over non-decreasing symbol sequences, children ordered by symbol
+    struct TNode {
+        std::map<int, int> child;
+        const std::map<int, std::vector<DD>> *entries = nullptr;
+    };
+    std::vector<TNode> trie(1);
+    for (const auto &kv : terms) {
+        int node = 0;
+        for (int j = 0; j < nsym; ++j)
+            for (int r = 0; r < kv.first[(size_t)j]; ++r) {
+                auto it = trie[(size_t)node].child.find(j);
+                if (it == trie[(size_t)node].child.end()) {
+                    trie.emplace_back();
+                    const int nn = (int)trie.size() - 1;
+                    trie[(size_t)node].child.emplace(j, nn);
+                    node = nn;
+                } else {
+                    node = it->second;
+                }
+            }
+        trie[(size_t)node].entries = &kv.second;
+    }
+    G = GeneralEffective{};
+    G.p = p;
+    G.J = std::max(2 * p - 2, 0);
+    G.K = K;
+    // depth-first, pre-order
+    struct Frame {
+        int node, depth, sym;
+    };
+    std::vector<Frame> stack{{0, 0, -1}};
+    while (!stack.empty()) {
+        const Frame f = stack.back();
+        stack.pop_back();
+        G.depth.push_back(f.depth);
+        G.sym.push_back(std::max(f.sym, 0));
+        G.first.push_back((int)G.entry_k.size());
+        int cnt = 0;
+        if (trie[(size_t)f.node].entries)
+            for (const auto &e : *trie[(size_t)f.node].entries) {
+                G.entry_k.push_back(e.first);
+                std::vector<double> hi, lo;
+                for (const DD &v : e.second) {
+                    hi.push_back(v.hi);
+                    lo.push_back(v.lo);
+                }
+                G.entry_hi.push_back(std::move(hi));
+                G.entry_lo.push_back(std::move(lo));
+                ++cnt;
+            }
+        G.count.push_back(cnt);
+        const auto &ch = trie[(size_t)f.node].child;
+        for (auto it = ch.rbegin(); it != ch.rend(); ++it) stack.push_back({it->second, f.depth + 1, it->first});
+    }
+    for (int s2 : G.sym)
+        if (s2 > G.J) {
+            err = "internal: a symbol beyond V^(2p-2) in W_p";
+            return SU_EINVAL;
+        }
+    return SU_OK;
+}
+
+void general_table(const GeneralEffective &G, double eps, std::vector<double> &T) {
+    T.resize(G.entry_k.size());
+    for (size_t e = 0; e < G.entry_k.size(); ++e) {
+        const int k = G.entry_k[e];
+        DD acc = dd(0), pw = dd(1.0);
+        for (size_t q = 0; q < G.entry_hi[e].size(); ++q) {   // eps^(m-k), m = k + q
+            acc = add(acc, mul(DD{G.entry_hi[e][q], G.entry_lo[e][q]}, pw));
+            pw = mul_d(pw, eps);
+        }
+        T[e] = mul_d(mul_d(acc, -eps), std::ldexp(1.0, -2 * k)).hi;
+    }
+}
+
+int general_potential(const double *params, int n_params, GeneralPotential &V, std::string &err) {
+    if (n_params != kGenParams || !params) {
+        err = "SU_GENERAL takes 33 parameters (a_0..a_8, (A, beta, c) x 4, (B, alpha, d) x 4)";
+        return SU_EINVAL;
+    }
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) {
+            err = "non-finite potential parameter";
+            return SU_EINVAL;
+        }
+    V = GeneralPotential{};
+    for (int i = 0; i < 9; ++i) V.a[i] = params[i];
+    for (int g = 0; g < 4; ++g) {
+        const double *q = params + 9 + 3 * g;
+        if (q[0] == 0.0) continue;
+        if (!(q[1] > 0)) {
+            err = "a Gaussian term needs beta > 0";
+            return SU_EINVAL;
+        }
+        for (int r = 0; r < 3; ++r) V.gauss[V.ng][r] = q[r];
+        ++V.ng;
+    }
+    for (int t = 0; t < 4; ++t) {
+        const double *q = params + 21 + 3 * t;
+        if (q[0] == 0.0) continue;
+        if (q[1] == 0.0) {
+            err = "a sech^2 term needs alpha != 0";
+            return SU_EINVAL;
+        }
+        for (int r = 0; r < 3; ++r) V.sech[V.ns][r] = q[r];
+        ++V.ns;
+    }
+    return SU_OK;
+}
+
+void general_derivatives(const GeneralPotential &V, double x, int J, double *out) {
+    for (int j = 0; j <= J; ++j) {
+        double v = 0.0;   // sum_{i>=j} a_i i!/(i-j)! x^(i-j)
+        for (int i = 8; i >= j; --i) {
+            double f = 1.0;
+            for (int r = 0; r < j; ++r) f *= (double)(i - r);
+            v = v * x + V.a[i] * f;
+        }
+        out[j] = j <= 8 ? v : 0.0;
+    }
+    for (int g = 0; g < V.ng; ++g) {
+        const double A = V.gauss[g][0], beta = V.gauss[g][1], c = V.gauss[g][2];
+        const double sb = std::sqrt(beta), u = x - c, y = sb * u, e = A * std::exp(-beta * u * u);
+        double h0 = 1.0, h1 = 2.0 * y, f = 1.0;
+        for (int n = 0; n <= J; ++n) {
+            const double h = n == 0 ? h0 : h1;
+            out[n] += f * h * e;
+            f *= -sb;
+            if (n >= 1) {
+                const double h2 = 2.0 * y * h1 - 2.0 * n * h0;
+                h0 = h1;
+                h1 = h2;
+            }
+        }
+    }
+    // sech^2 = tanh': Taylor coefficients a_k of tanh at alpha (x - d),
+    // (n+1) a_{n+1} = -sum_k a_k a_{n-k} (n >= 1) from tanh' = 1 - tanh^2
+    std::vector<double> a((size_t)J + 2);
+    for (int s = 0; s < V.ns; ++s) {
+        const double B = V.sech[s][0], alpha = V.sech[s][1], d = V.sech[s][2];
+        const double w = alpha * (x - d), ch = std::cosh(w);
+        a[0] = std::tanh(w);
+        a[1] = 1.0 / (ch * ch);
+        double sc = B;   // B alpha^n (n+1)!
+        for (int n = 0; n <= J; ++n) {
+            if (n >= 1) {
+                double acc = 0.0;
+                for (int k = 0; k <= n; ++k) acc += a[(size_t)k] * a[(size_t)(n - k)];
+                a[(size_t)n + 1] = -acc / (double)(n + 1);
+            }
+            sc *= (double)(n + 1);
+            out[n] += sc * a[(size_t)n + 1];
+            sc *= alpha;
+        }
+    }
+}
+
+double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps) {
+    std::vector<double> T;
+    general_table(G, eps, T);   // -eps c / 4^k per entry
+    std::vector<double> D((size_t)G.J + 1);
+    general_derivatives(V, x, G.J, D.data());
+    std::vector<double> stk((size_t)G.J + 3 * G.p + 2, 1.0), Q((size_t)G.K, 0.0);
+    for (size_t t = 0; t < G.depth.size(); ++t) {
+        double mu = 1.0;
+        if (t) {
+            mu = stk[(size_t)G.depth[t] - 1] * D[(size_t)G.sym[t]];
+            stk[(size_t)G.depth[t]] = mu;
+        }
+        for (int e = G.first[t]; e < G.first[t] + G.count[t]; ++e) Q[(size_t)G.entry_k[(size_t)e]] += T[(size_t)e] * mu;
+    }
+    const double Y = 4.0 * xb * xb;   // vs^2
+    double w = Q[(size_t)G.K - 1];
+    for (int k = G.K - 2; k >= 0; --k) w = w * Y + Q[(size_t)k];
+    return -w / eps;                  // the table carries -eps
 }
 
 }  // namespace su

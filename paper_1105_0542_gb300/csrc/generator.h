@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,7 @@ enum Ring : int {
     RING_EVEN = 0,   // z = x^2            (even polynomial potentials)
     RING_X = 1,      // z = x              (general polynomial potentials)
     RING_TANH2 = 2,  // z = tanh^2(alpha x)  (modified Poeschl-Teller)
+    RING_GENERAL = 3,  // general potential: W_p in the derivative symbols V^(j)(x)
 };
 
 struct Shape {
@@ -57,5 +59,48 @@ double wp_host(const Effective &E, double x, double xb, double eps);
 
 // W_p(x, xb; eps) from a collapse P already made for that eps (double).
 double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, double xb);
+
+// ---- general potentials: W_p as a polynomial in the derivative symbols
+// V_j = V^(j)(x), j = 0..2p-2 (the same recursion with d/dx V_j = V_{j+1}).
+// The distinct monomials of W_p form a trie over their non-decreasing symbol
+// sequences; its nodes in depth-first order give an evaluation program in
+// which every monomial is its parent (one level up) times one symbol.
+constexpr int kGenMaxP = 12;
+
+struct GeneralEffective {
+    int p = 0;
+    int J = 0;                        // highest symbol in W_p: 2p - 2
+    int K = 0;                        // powers xb^(2k), k = 0..K-1
+    std::vector<int> depth, sym;      // DFS nodes; node 0 is the constant monomial
+    std::vector<int> first, count;    // node -> its entries [first, first + count)
+    std::vector<int> entry_k;         // entry -> k
+    // entry -> coefficient of eps^(m-k) for m = k..p-1 (hi, lo)
+    std::vector<std::vector<double>> entry_hi, entry_lo;
+};
+
+int build_general(int p, GeneralEffective &G, std::string &err);
+
+// The level table of the general program for one eps: entry e of power k
+// gets -eps * sum_m c_m eps^(m-k) / 4^k (xb^(2k) = vs^(2k) / 4^k).
+void general_table(const GeneralEffective &G, double eps, std::vector<double> &T);
+
+// The potential of the general mode (SU_GENERAL): a polynomial of degree <= 8,
+// up to four Gaussians A e^{-beta (x - c)^2} and four sech^2 terms
+// B sech^2(alpha (x - d)); parameters (a_0..a_8, (A, beta, c) x 4,
+// (B, alpha, d) x 4), terms with a zero amplitude absent.
+constexpr int kGenParams = 9 + 3 * 4 + 3 * 4;
+struct GeneralPotential {
+    double a[9] = {0};
+    int ng = 0, ns = 0;
+    double gauss[4][3] = {{0}};   // A, beta, c
+    double sech[4][3] = {{0}};    // B, alpha, d
+};
+int general_potential(const double *params, int n_params, GeneralPotential &V, std::string &err);
+
+// V^(j)(x), j = 0..J, on the host (double).
+void general_derivatives(const GeneralPotential &V, double x, int J, double *out);
+
+// W_p(x, xb; eps) of the general potential on the host (level 0 and tests).
+double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps);
 
 }  // namespace su

@@ -17,6 +17,7 @@ const void *sampler_entry_f64_2();
 const void *sampler_entry_f32_0();
 const void *sampler_entry_f32_1();
 const void *sampler_entry_f32_2();
+const void *sampler_entry_f64_3();
 const void *batch_entry_f64_0();
 const void *batch_entry_f64_1();
 const void *batch_entry_f64_2();
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_
 }
 
 const void *pick(const SamplerParams &P, int precision) {
+    if (P.ring == RING_GENERAL) return precision == SU_FP64 ? sampler_entry_f64_3() : nullptr;
     if (precision == SU_FP32)
         return P.ring == RING_EVEN ? sampler_entry_f32_0() : P.ring == RING_X ? sampler_entry_f32_1() : sampler_entry_f32_2();
     return P.ring == RING_EVEN ? sampler_entry_f64_0() : P.ring == RING_X ? sampler_entry_f64_1() : sampler_entry_f64_2();
@@ -150,7 +152,7 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     const int C = 1 << (P.S - P.F);
     size_t off = P.w_out ? 0 : rs * (size_t)P.levels * kThreads * P.rounds;
     off = (off + 15) & ~(size_t)15;
-    off += rs * (size_t)P.S * P.M;
+    if (P.ring != RING_GENERAL) off += rs * (size_t)P.S * P.M;   // general tables stay in global memory
     off += rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/speedup.h"
+#include "generator.h"
 
 namespace su {
 
@@ -13,6 +14,29 @@ constexpr int kThreads = 128;   // threads per CTA of the sampler: one path per 
 constexpr int kMaxFine = 5;     // depth of the register-resident bisection subtree
 
 // Everything the sampler needs, passed by value (it lives in the constant bank).
+// General potential (RING_GENERAL): the device image of the monomial program
+// and of the potential's families (built by the host from GeneralEffective
+// and GeneralPotential, in device memory).
+constexpr int kGenMaxSym = 2 * kGenMaxP - 1;   // V_0..V_{2p-2}
+constexpr int kGenMaxDepth = 16;               // deepest monomial (6 at p = 12; checked by the host)
+
+struct GeneralNode {
+    unsigned char depth, sym;                  // depth in the trie, symbol j of V_j
+    unsigned short count;                      // entries of this monomial
+    int first;                                 // its first entry
+};
+
+struct GeneralDev {
+    int J, K, n_nodes, n_entries, ng, ns;
+    const GeneralNode *nodes;                  // depth-first; node 0 = the constant monomial
+    const unsigned char *entry_k;              // power of vs^2 of each entry
+    double poly_der[kGenMaxSym][9];            // V^(j) polynomial part: sum_i poly_der[j][i] x^(i-j)
+    double gauss[4][4];                        // A, beta, c, sqrt(beta)
+    double sech[4][3];                         // B, alpha, d
+    double sech_scale[4][kGenMaxSym];          // B alpha^n (n+1)!
+    double inv[kGenMaxSym + 1];                // 1 / n
+};
+
 struct SamplerParams {
     // path: q_0 = a, q_N = b, N = 2^S, bisection widths sigma[n] (n = 1..S)
     double a, b;
@@ -43,6 +67,7 @@ struct SamplerParams {
     double *w_out;            // device: per-sample mode when non-null, [sample][S]
     float *q_out;             // device: per-sample mode, single precision only: path points [sample][N+1] (or null)
     int *flags;               // device: bit 0 = non-finite weight seen
+    const GeneralDev *general;  // device: RING_GENERAL only
 };
 
 // One instance of a batch (top level only).

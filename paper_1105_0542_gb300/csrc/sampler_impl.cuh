@@ -120,11 +120,84 @@ __device__ __forceinline__ R ring_var(R us, R alpha) {
     }
 }
 
+// -eps W_p of one slice for a general potential (double only): the
+// derivatives V_j at the midpoint from the potential's families (polynomial
+// table; Gaussians through the Hermite recurrence; sech^2 = tanh' through the
+// Taylor coefficients a_k of tanh, (n+1) a_{n+1} = -sum_k a_k a_{n-k} from
+// tanh' = 1 - tanh^2, which stay accurate where tanh is near +-1), then the
+// monomial program -- each monomial its parent's value times one V_j, the
+// entries of a monomial added into the accumulator of their power of vs^2 --
+// and Horner in vs^2.
+__device__ __noinline__ double slice_general(double ql, double qr, const double *__restrict__ coef,
+                                             const GeneralDev *__restrict__ G) {
+    const double x = 0.5 * (ql + qr);
+    const double vs = qr - ql, Y = vs * vs;
+    const int J = G->J;
+    double V[kGenMaxSym];
+    for (int j = 0; j <= J; ++j) {
+        double v = 0.0;
+        if (j <= 8)
+            for (int i = 8; i >= j; --i) v = fma(v, x, G->poly_der[j][i]);
+        V[j] = v;
+    }
+    for (int g = 0; g < G->ng; ++g) {
+        const double u = x - G->gauss[g][2], sb = G->gauss[g][3];
+        const double y = sb * u, e = G->gauss[g][0] * exp(-G->gauss[g][1] * u * u);
+        double h0 = 1.0, h1 = 2.0 * y, f = 1.0;
+        for (int n = 0; n <= J; ++n) {
+            V[n] = fma(f * (n == 0 ? h0 : h1), e, V[n]);
+            f *= -sb;
+            if (n >= 1) {
+                const double h2 = fma(2.0 * y, h1, -2.0 * n * h0);
+                h0 = h1;
+                h1 = h2;
+            }
+        }
+    }
+    for (int q = 0; q < G->ns; ++q) {
+        const double w = G->sech[q][1] * (x - G->sech[q][2]);
+        const double em = expm1(-2.0 * fabs(w)), e = exp(-2.0 * fabs(w));
+        const double den = 2.0 + em;               // 1 + e^{-2|w|}
+        double a[kGenMaxSym + 1];
+        a[0] = copysign(-em / den, w);             // tanh w
+        a[1] = 4.0 * e / (den * den);              // sech^2 w
+        V[0] = fma(G->sech_scale[q][0], a[1], V[0]);
+        for (int n = 1; n <= J; ++n) {
+            double acc = 0.0;
+            for (int k = 0; k < (n + 1) / 2; ++k) acc = fma(a[k], a[n - k], acc);
+            acc += acc;
+            if (!(n & 1)) acc = fma(a[n >> 1], a[n >> 1], acc);
+            a[n + 1] = -acc * G->inv[n + 1];
+            V[n] = fma(G->sech_scale[q][n], a[n + 1], V[n]);
+        }
+    }
+    double stk[kGenMaxDepth + 1];
+    double Q[kGenMaxP];
+    for (int k = 0; k < G->K; ++k) Q[k] = 0.0;
+    stk[0] = 1.0;
+    for (int t = 0; t < G->n_nodes; ++t) {
+        const GeneralNode nd = G->nodes[t];
+        double mu = 1.0;
+        if (t) {
+            mu = stk[nd.depth - 1] * V[nd.sym];
+            stk[nd.depth] = mu;
+        }
+        for (int e = nd.first; e < nd.first + (int)nd.count; ++e) Q[G->entry_k[e]] = fma(coef[e], mu, Q[G->entry_k[e]]);
+    }
+    double w = Q[G->K - 1];
+    for (int k = G->K - 2; k >= 0; --k) w = fma(w, Y, Q[k]);
+    return w;
+}
+
 // -eps W_p(x, xb; eps) of one slice, from the level's table in shared memory:
 // sum_j (vs^2)^j sum_i T_ij Z^i, nested Horner (columns, then powers of vs^2).
 template <typename R, int RING>
 __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const SamplerParams &P,
                                    R alpha) {
+    if constexpr (RING == RING_GENERAL) {
+        static_assert(sizeof(R) == 8, "the general potential is evaluated in double");
+        return slice_general(ql, qr, tab, P.general);
+    }
     const R us = ql + qr;
     const R vs = qr - ql;
     const R Y = vs * vs;
@@ -160,6 +233,11 @@ struct Batch {
 template <typename R, int RING, int NS, int STR, int NQ>
 __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab,
                                        const SamplerParams &P, R alpha) {
+    if constexpr (RING == RING_GENERAL) {
+        R total = 0;
+        for (int k = 0; k < NS; ++k) total += slice<R, RING>(q[k * STR], q[(k + 1) * STR], tab, P, alpha);
+        return total;
+    }
     constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
     constexpr bool kFold = sizeof(R) == 8;
     const int L0 = P.len[0];
@@ -552,8 +630,13 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
     R *sw = reinterpret_cast<R *>(smem_raw);
     size_t off = per_sample ? 0 : sizeof(R) * (size_t)L * chunk;
     off = (off + 15) & ~(size_t)15;
-    R *tab = reinterpret_cast<R *>(smem_raw + off);
-    off += sizeof(R) * (size_t)P.S * P.M;
+    // the general program's level tables (thousands of entries per level)
+    // stay in global memory: every lane reads the same entry, one broadcast
+    // load through L1
+    constexpr bool kStage = RING != RING_GENERAL;
+    R *tab_s = reinterpret_cast<R *>(smem_raw + off);
+    const R *tab = kStage ? tab_s : reinterpret_cast<const R *>(P.tables);
+    off += kStage ? sizeof(R) * (size_t)P.S * P.M : 0;
     R *sig = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
@@ -568,8 +651,8 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
     // the Box-Muller node tables of the double path)
     {
         const R *g = reinterpret_cast<const R *>(P.tables);
-        const int n = P.S * P.M;
-        for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
+        const int n = kStage ? P.S * P.M : 0;
+        for (int i = tid; i < n; i += kThreads) tab_s[i] = g[i];
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)P.sigma[i];
         if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
     }

@@ -1,14 +1,15 @@
 // One instantiation of the sampler and batched kernels, selected at compile time:
 //   SU_PREC = 64 or 32 (double / float path and W_p), SU_RING = 0, 1, 2
-//   (z = x^2, x, sech^2(alpha x)).  The build compiles this file once per
-// pair so the six kernels compile in parallel.
+//   (z = x^2, x, sech^2(alpha x)) or 3 (a general potential through its
+//   derivatives; double sampler only).  The build compiles this file once per
+// pair so the kernels compile in parallel.
 #include "sampler_impl.cuh"
 
 #ifndef SU_PREC
 #error "SU_PREC must be 64 or 32"
 #endif
 #ifndef SU_RING
-#error "SU_RING must be 0, 1 or 2"
+#error "SU_RING must be 0, 1, 2 or 3"
 #endif
 
 #define SU_CAT2(a, b, c) a##b##_##c
@@ -25,7 +26,9 @@ const void *SU_CAT(sampler_entry_f, SU_PREC, SU_RING)() {
     return (const void *)sampler_kernel<Real, SU_RING>;
 }
 
+#if SU_RING != 3
 const void *SU_CAT(batch_entry_f, SU_PREC, SU_RING)() {
     return (const void *)batch_kernel<Real, SU_RING>;
 }
+#endif
 }  // namespace su

@@ -172,3 +172,44 @@ def test_fault_hooks_validate_and_the_nan_table_fails_before_any_device_work():
     finally:
         su.su_fault_inject("clear")
 
+
+
+# ---- the general-potential mode: argument checks come before any device work
+P_GEN = su.general_params((0.0, 0.0, 0.5), [(1.5, 2.0, 0.3)], [(-1.0, 2.0, 0.0)])
+
+
+def test_general_params_layout():
+    p = su.general_params((1.0, 2.0), [(3.0, 4.0, 5.0)], [(6.0, 7.0, 8.0), (9.0, 10.0, 11.0)])
+    assert len(p) == 33
+    assert p[:3] == (1.0, 2.0, 0.0) and p[9:12] == (3.0, 4.0, 5.0) and p[12:21] == (0.0,) * 9
+    assert p[21:27] == (6.0, 7.0, 8.0, 9.0, 10.0, 11.0) and p[27:] == (0.0,) * 6
+    with pytest.raises(ValueError):
+        su.general_params(tuple(range(10)))
+
+
+@pytest.mark.parametrize("params,kw,code", [
+    (P_GEN, {"p": 13}, -6),                                  # above the general program's p <= 12
+    (P_GEN, {"precision": "fp32"}, -6),                      # double only
+    (P_GEN[:32], {}, -1),                                    # 32 parameters
+    (P_GEN[:9] + (1.0, 0.0, 0.0) + P_GEN[12:], {}, -1),      # a Gaussian with beta = 0
+    (P_GEN[:21] + (1.0, 0.0, 0.0) + P_GEN[24:], {}, -1),     # a sech^2 term with alpha = 0
+    (P_GEN[:4] + (float("nan"),) + P_GEN[5:], {}, -1),       # a non-finite parameter
+])
+def test_general_mode_rejects_bad_requests(params, kw, code):
+    args = {"p": 6, "precision": "fp64"}
+    args.update(kw)
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude("general", params, 0.0, 1.0, 1.0, args["p"], 4, 1000, 1, precision=args["precision"])
+    assert e.value.code == code
+
+
+def test_general_mode_is_refused_where_a_collapsed_table_is_needed():
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_evolution_matrix("general", P_GEN, 4, 0.1, 5.0, 100, 1 << 20)
+    assert e.value.code == -6
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude_batch("general", P_GEN, 4, [(0.0, 1.0, 1.0, 4)], 1000, 1)
+    assert e.value.code == -6
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude_noalloc("general", P_GEN, 0.0, 1.0, 1.0, 4, 4, 1000, 1)
+    assert e.value.code == -6
