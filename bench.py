@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal entry")
     ap.add_argument("--no-configs", action="store_true", help="skip the configuration 1 and 4 entries")
     ap.add_argument("--no-evolution", action="store_true", help="skip the evolution-operator (Fig. 3) entry")
+    ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -359,6 +360,9 @@ def run_ours(args):
     evolution = None
     if not args.no_evolution:
         evolution = run_evolution(su, torch, dev, stream, flush)
+    general = None
+    if not args.no_general:
+        general = run_general(su, torch, dev, stream, flush)
 
     if rank != 0:
         if dist is not None:
@@ -401,7 +405,7 @@ def run_ours(args):
         "fp32_vs_fp64_top_level": f32_vs_f64,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
         "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
-        "evolution_operator_fig3": evolution,
+        "evolution_operator_fig3": evolution, "general_potential": general,
         "clocks": clock_info,
     }
     print(json.dumps(line))
@@ -501,6 +505,39 @@ def run_evolution(su, torch, dev, stream, flush):
                     "energies": [float(-math.log(v) / t) for v in lam]})
     return {"cases": out, "note": "matrix: device time of one speedup_evolution_matrix; energies from torch's "
                                   "eigensolver (cuSOLVER) on the 4097-point grid"}
+
+
+def run_general(su, torch, dev, stream, flush):
+    """The general-potential mode (W_p in V's derivatives, evaluated per
+    slice through the monomial program) next to the collapsed-table mode on
+    the same potential and samples (AHO g = 10, p = 10, N = 1024), and a mixed
+    polynomial + Gaussian + sech^2 potential at p = 12, N = 64; 1e6 samples
+    each, double precision, device time of one plan execute (L2 flushed)."""
+    mixed = su.general_params((0.0, 0.0, 0.5), [(1.5, 2.0, 0.3)], [(-1.0, 2.0, 0.0)])
+    cases = (("aho g=10, model table", "aho", [1.0, 10.0], 0.0, 1.0, 1.0, 10, 10),
+             ("aho g=10, general mode", "general", list(su.general_params((0.0, 0.0, 0.5, 0.0, 10.0 / 24.0))),
+              0.0, 1.0, 1.0, 10, 10),
+             ("x^2/2 + 1.5 exp(-2(x-0.3)^2) - sech^2(2x), general mode", "general", list(mixed),
+              -0.5, 0.7, 1.0, 12, 6))
+    out = []
+    n_mc = 1_000_000
+    for name, model, params, a, b, T, p, s in cases:
+        pl = su.Plan(model, params, a, b, T, p, s, n_mc, 1234, precision="fp64", n_blocks=64)
+        t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device=dev)
+        sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device=dev)
+        pl.su_plan_execute(t, sc, stream)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.su_plan_execute(t, sc, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        top = pl.su_plan_finalize(t.cpu().numpy(), sc)[s]
+        out.append({"case": name, "p": p, "N": 1 << s, "samples": n_mc, "ms": ms,
+                    "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "amp": top["amp"],
+                    "rel_err": top["rel_err"]})
+    return {"cases": out, "note": "same Philox stream in the first two cases: their amplitudes agree to rounding"}
 
 
 def run_batched(su, torch, dev, stream, flush):

@@ -149,7 +149,7 @@ struct su_plan {
     int64_t slice_actions = 0;
     double cancel_ratio = 1;  // largest sum|terms| / |sum| in the table collapse
     // SU_GENERAL: the monomial program of W_p, the potential's families and
-    // their device image (GeneralDev | nodes | entry powers)
+    // their device image (GeneralDev | nodes)
     std::shared_ptr<const su::GeneralEffective> G;
     su::GeneralPotential V{};
     void *d_general = nullptr;
@@ -260,7 +260,7 @@ static int validate(int model, const double *params, int n_params, double a, dou
 }
 
 // Device image of the general program and potential: one allocation holding
-// GeneralDev, the depth-first nodes and the entries' powers of vs^2.
+// GeneralDev and the depth-first nodes.
 static int upload_general(su_plan &pl) {
     using namespace su;
     const GeneralEffective &G = *pl.G;
@@ -283,7 +283,10 @@ static int upload_general(su_plan &pl) {
         nodes[(size_t)t].count = (unsigned short)G.count[(size_t)t];
         nodes[(size_t)t].first = G.first[(size_t)t];
     }
-    std::vector<unsigned char> ek(G.entry_k.begin(), G.entry_k.end());
+    for (int t = 0; t < D.n_nodes; ++t)   // the device takes a node's entries as vs^0, vs^2, ..
+        for (int e = 0; e < G.count[(size_t)t]; ++e)
+            if (G.entry_k[(size_t)(G.first[(size_t)t] + e)] != e)
+                return fail(SU_EINVAL, "internal: general program entries out of order");
     for (int j = 0; j <= std::min(G.J, 8); ++j)   // V^(j) of the polynomial: a_i i!/(i-j)!
         for (int i = j; i <= 8; ++i) {
             double f = 1.0;
@@ -305,16 +308,13 @@ static int upload_general(su_plan &pl) {
     }
     for (int n = 1; n <= kGenMaxSym; ++n) D.inv[n] = 1.0 / (double)n;
     const size_t o_nodes = (sizeof(GeneralDev) + 15) & ~(size_t)15;
-    const size_t o_k = (o_nodes + nodes.size() * sizeof(GeneralNode) + 15) & ~(size_t)15;
-    const size_t bytes = o_k + ek.size();
+    const size_t bytes = o_nodes + nodes.size() * sizeof(GeneralNode);
     CU(dmalloc(&pl.d_general, bytes), "device allocation (general program)");
     char *base = static_cast<char *>(pl.d_general);
     D.nodes = reinterpret_cast<const GeneralNode *>(base + o_nodes);
-    D.entry_k = reinterpret_cast<const unsigned char *>(base + o_k);
     std::vector<unsigned char> blob(bytes, 0);
     std::memcpy(blob.data(), &D, sizeof D);
     std::memcpy(blob.data() + o_nodes, nodes.data(), nodes.size() * sizeof(GeneralNode));
-    std::memcpy(blob.data() + o_k, ek.data(), ek.size());
     CU(cudaMemcpy(pl.d_general, blob.data(), bytes, cudaMemcpyHostToDevice), "upload general program");
     return SU_OK;
 }

@@ -28,8 +28,8 @@ struct GeneralNode {
 
 struct GeneralDev {
     int J, K, n_nodes, n_entries, ng, ns;
-    const GeneralNode *nodes;                  // depth-first; node 0 = the constant monomial
-    const unsigned char *entry_k;              // power of vs^2 of each entry
+    const GeneralNode *nodes;                  // depth-first; node 0 = the constant monomial;
+                                               // a node's entries are vs^0, vs^2, .. in order
     double poly_der[kGenMaxSym][9];            // V^(j) polynomial part: sum_i poly_der[j][i] x^(i-j)
     double gauss[4][4];                        // A, beta, c, sqrt(beta)
     double sech[4][3];                         // B, alpha, d

@@ -120,20 +120,13 @@ __device__ __forceinline__ R ring_var(R us, R alpha) {
     }
 }
 
-// -eps W_p of one slice for a general potential (double only): the
-// derivatives V_j at the midpoint from the potential's families (polynomial
-// table; Gaussians through the Hermite recurrence; sech^2 = tanh' through the
-// Taylor coefficients a_k of tanh, (n+1) a_{n+1} = -sum_k a_k a_{n-k} from
-// tanh' = 1 - tanh^2, which stay accurate where tanh is near +-1), then the
-// monomial program -- each monomial its parent's value times one V_j, the
-// entries of a monomial added into the accumulator of their power of vs^2 --
-// and Horner in vs^2.
-__device__ __noinline__ double slice_general(double ql, double qr, const double *__restrict__ coef,
-                                             const GeneralDev *__restrict__ G) {
-    const double x = 0.5 * (ql + qr);
-    const double vs = qr - ql, Y = vs * vs;
+// V_j = V^(j)(x), j = 0..J, of a general potential from its families:
+// polynomial table; Gaussians through the Hermite recurrence; sech^2 = tanh'
+// through the Taylor coefficients a_k of tanh, (n+1) a_{n+1} = -sum_k a_k a_{n-k}
+// from tanh' = 1 - tanh^2, which stay accurate where tanh is near +-1.
+__device__ __forceinline__ void general_derivatives(double x, const GeneralDev *__restrict__ G,
+                                                    double (&V)[kGenMaxSym]) {
     const int J = G->J;
-    double V[kGenMaxSym];
     for (int j = 0; j <= J; ++j) {
         double v = 0.0;
         if (j <= 8)
@@ -171,22 +164,58 @@ __device__ __noinline__ double slice_general(double ql, double qr, const double 
             V[n] = fma(G->sech_scale[q][n], a[n + 1], V[n]);
         }
     }
-    double stk[kGenMaxDepth + 1];
-    double Q[kGenMaxP];
-    for (int k = 0; k < G->K; ++k) Q[k] = 0.0;
-    stk[0] = 1.0;
-    for (int t = 0; t < G->n_nodes; ++t) {
-        const GeneralNode nd = G->nodes[t];
-        double mu = 1.0;
-        if (t) {
-            mu = stk[nd.depth - 1] * V[nd.sym];
-            stk[nd.depth] = mu;
-        }
-        for (int e = nd.first; e < nd.first + (int)nd.count; ++e) Q[G->entry_k[e]] = fma(coef[e], mu, Q[G->entry_k[e]]);
+}
+
+// -eps W_p of B = 1 or 2 slices (ql[b], qr[b]) for a general potential
+// (double only).  The monomials of W_p in the V_j form a trie walked depth
+// first: each node's monomial is its parent's (the top of a stack of depth
+// <= 6 at p = 12) times one V_j, and its entries are the coefficients of
+// vs^0, vs^2, .., vs^(2 count - 2), combined by Horner in vs^2 and added
+// times the monomial.  Two slices share every node and coefficient load.
+template <int B>
+__device__ __noinline__ double2 slice_general(double ql0, double qr0, double ql1, double qr1,
+                                              const double *__restrict__ coef,
+                                              const GeneralDev *__restrict__ G) {
+    const double ql[2] = {ql0, ql1}, qr[2] = {qr0, qr1};
+    double V[B][kGenMaxSym], Y[B], stk[B][kGenMaxDepth + 1], w[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        general_derivatives(0.5 * (ql[b] + qr[b]), G, V[b]);
+        const double vs = qr[b] - ql[b];
+        Y[b] = vs * vs;
+        stk[b][0] = 1.0;
+        w[b] = 0.0;
     }
-    double w = Q[G->K - 1];
-    for (int k = G->K - 2; k >= 0; --k) w = fma(w, Y, Q[k]);
-    return w;
+    const int nn = G->n_nodes;
+    for (int t = 0; t < nn; ++t) {
+        const GeneralNode nd = G->nodes[t];
+        double mu[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            mu[b] = 1.0;
+            if (t) {
+                mu[b] = stk[b][nd.depth - 1] * V[b][nd.sym];
+                stk[b][nd.depth] = mu[b];
+            }
+        }
+        const int cnt = nd.count;
+        if (cnt) {
+            const double *c = coef + nd.first;
+            double h[B];
+            const double top = c[cnt - 1];
+#pragma unroll
+            for (int b = 0; b < B; ++b) h[b] = top;
+#pragma unroll 4
+            for (int e = cnt - 2; e >= 0; --e) {
+                const double ce = c[e];
+#pragma unroll
+                for (int b = 0; b < B; ++b) h[b] = fma(h[b], Y[b], ce);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) w[b] = fma(h[b], mu[b], w[b]);
+        }
+    }
+    return make_double2(w[0], B > 1 ? w[B - 1] : 0.0);
 }
 
 // -eps W_p(x, xb; eps) of one slice, from the level's table in shared memory:
@@ -196,7 +225,7 @@ __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const 
                                    R alpha) {
     if constexpr (RING == RING_GENERAL) {
         static_assert(sizeof(R) == 8, "the general potential is evaluated in double");
-        return slice_general(ql, qr, tab, P.general);
+        return slice_general<1>(ql, qr, ql, qr, tab, P.general).x;
     }
     const R us = ql + qr;
     const R vs = qr - ql;
@@ -235,7 +264,16 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                                        const SamplerParams &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
         R total = 0;
-        for (int k = 0; k < NS; ++k) total += slice<R, RING>(q[k * STR], q[(k + 1) * STR], tab, P, alpha);
+        if constexpr (NS == 1) {
+            total = slice_general<1>(q[0], q[STR], q[0], q[STR], tab, P.general).x;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NS; k += 2) {   // unrolled: q stays in registers
+                const double2 r = slice_general<2>(q[k * STR], q[(k + 1) * STR], q[(k + 1) * STR],
+                                                   q[(k + 2) * STR], tab, P.general);
+                total += r.x + r.y;
+            }
+        }
         return total;
     }
     constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
