@@ -319,6 +319,56 @@ int su_plan_create(int model, const double *params, int n_params,
 /* Release a plan and its device memory (NULL is a no-op). */
 int su_plan_destroy(su_plan *plan);
 
+/* ---- systems of several coordinates (Sec. 2.2) ----------------------------- */
+
+#define SU_MAX_D 4   /* d = D x M coordinates (D dimensions, M particles)      */
+
+/*
+ * A polynomial potential V(x_1..x_d) of total degree <= 6 and at most 256
+ * terms: term t is coefs[t] * prod_i x_i^exps[t d + i] (exps: host, n_terms x
+ * d ints in 0..6; coefs: host, n_terms doubles, finite).  The level-p
+ * effective potential W(x, xb; eps) = sum_{m<p} sum_{k<=m} eps^(m-k) W_{m,k}
+ * follows from the contracted recursion Eq. MBrec with the diagonal Eq. DIA
+ * (double-double on the host); every coordinate has unit mass, no quantum
+ * statistics (amplitudes are not symmetrised).  p <= 12, SU_FP64 only, the
+ * exact bridge only (width_factor 1), one launch shape (seg_log2 = 0,
+ * rounds <= 1); SU_ENOTSUP otherwise.
+ *
+ * su_plan_create_nd -- a plan for A_N^(p)(a, b; T), N = 2^s, with a and b
+ * (host, d doubles each) the endpoint vectors; it is executed, finalized and
+ * destroyed by the su_plan_* calls above.  A_free is the product of the d
+ * one-dimensional free amplitudes.  Coordinate c of bisection midpoint j
+ * takes normal j d + c of the sample's stream (speedup_normals layout).  The
+ * scratch (su_plan_sizes) also holds every resident thread's path:
+ * grid x 128 x (2^s + 1) x d doubles.
+ */
+int su_plan_create_nd(int d, const int *exps, const double *coefs, int n_terms,
+                      const double *a, const double *b, double T, int p, int s,
+                      int64_t n_mc, uint64_t seed, const su_options *opt, su_plan **plan);
+
+/* speedup_amplitude for a system of d coordinates (host in, host out). */
+int speedup_amplitude_nd(int d, const int *exps, const double *coefs, int n_terms,
+                         const double *a, const double *b, double T, int p, int s,
+                         int64_t n_mc, uint64_t seed, const su_options *opt,
+                         su_level_result *out);
+
+/* speedup_logweights for a system of d coordinates: d_w (device) receives
+ * n_samples x s doubles, w_n of sample sample0 + i at d_w[i s + n - 1]. */
+int speedup_logweights_nd(int d, const int *exps, const double *coefs, int n_terms,
+                          const double *a, const double *b, double T, int p, int s,
+                          int64_t sample0, int64_t n_samples, uint64_t seed,
+                          const su_options *opt, double *d_w);
+
+/*
+ * speedup_generate_nd -- W(x, xb; eps) of a system of d coordinates at one
+ * eps, as monomials (host only, no device): term t is
+ * out_w[t] * prod_i x_i^out_exps[2 d t + i] xb_i^out_exps[2 d t + d + i]
+ * (out_exps: capacity x 2d ints; out_w: capacity doubles).  *n_out = the
+ * number of terms; SU_ENOTSUP if it exceeds capacity.
+ */
+int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms, int p,
+                        double eps, int *out_exps, double *out_w, int capacity, int *n_out);
+
 /*
  * su_plan_sizes -- sizes of the caller-provided device buffers of
  * su_plan_execute, in bytes: *tuple_bytes for d_tuples, *scratch_bytes for

@@ -6,9 +6,11 @@ this package is its ctypes binding.  There is no CPU fallback: without the
 built library or a CUDA device the entry points raise.
 """
 from ._binding import (  # noqa: F401
-    BatchPlan, EXPORTS, GENERAL_MAX_P, MLP_PARAMS, MODELS, PRECISIONS, Plan, Proposal, SpeedupError, library_path, load,
-    general_params, options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_noalloc, speedup_amplitude_proposal,
-    speedup_evolution_matrix, speedup_generate_coeffs, speedup_logweights, speedup_normals, speedup_philox_words,
+    BatchPlan, EXPORTS, GENERAL_MAX_P, MAX_D, MLP_PARAMS, MODELS, PRECISIONS, Plan, PlanND, Proposal, SpeedupError, library_path, load,
+    general_params, options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_nd, speedup_amplitude_noalloc,
+    speedup_amplitude_proposal,
+    speedup_evolution_matrix, speedup_generate_coeffs, speedup_generate_nd, speedup_logweights,
+    speedup_logweights_nd, speedup_normals, speedup_philox_words,
     speedup_proposal_logweights, speedup_train_proposal, su_autotune, su_autotune_clear, su_fault_inject,
     su_fma_peak,
     su_last_error, su_mlp_loss_grad, su_version,

@@ -30,7 +30,9 @@ EXPORTS = [
     "speedup_amplitude_proposal", "speedup_proposal_logweights", "su_train_options_default",
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
+    "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
 ]
+MAX_D = 4
 MLP_PARAMS = 34178
 
 
@@ -120,6 +122,13 @@ def load(build_if_missing=True):
     L.speedup_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                      ctypes.POINTER(Options), vp]
     L.speedup_philox_words.argtypes = [u64, u32, i64, i64, i32, vp, vp]
+    L.su_plan_create_nd.argtypes = [i32, pi, pd, i32, pd, pd, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                    ctypes.POINTER(vp)]
+    L.speedup_amplitude_nd.argtypes = [i32, pi, pd, i32, pd, pd, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                       ctypes.POINTER(LevelResult)]
+    L.speedup_logweights_nd.argtypes = [i32, pi, pd, i32, pd, pd, d, i32, i32, i64, i64, u64,
+                                        ctypes.POINTER(Options), vp]
+    L.speedup_generate_nd.argtypes = [i32, pi, pd, i32, i32, d, pi, pd, i32, pi]
     L.su_fma_peak.argtypes = [i32, pd]
     pf = ctypes.POINTER(ctypes.c_float)
     L.su_proposal_create.argtypes = [pf, i32, ctypes.POINTER(vp)]
@@ -305,6 +314,55 @@ def speedup_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, o
     o = options(**kw)
     _check(load().speedup_logweights(_model(model), pr, npar, a, b, T, p, s, int(sample0), int(n_samples),
                                      int(seed), ctypes.byref(o), _ptr(out)))
+
+
+def _nd_potential(V):
+    """{exponent tuple: coefficient} -> (d, exps, coefs, n_terms) as ctypes arrays."""
+    items = [(tuple(int(e) for e in k), float(v)) for k, v in dict(V).items()]
+    if not items:
+        raise ValueError("the potential needs at least one term")
+    d = len(items[0][0])
+    if any(len(k) != d for k, _ in items):
+        raise ValueError("every exponent tuple needs the same length d")
+    exps = (ctypes.c_int * (d * len(items)))(*[e for k, _ in items for e in k])
+    coefs = (ctypes.c_double * len(items))(*[v for _, v in items])
+    return d, exps, coefs, len(items)
+
+
+def _vec(x, d):
+    x = [float(v) for v in x]
+    if len(x) != d:
+        raise ValueError(f"endpoints need {d} coordinates")
+    return (ctypes.c_double * d)(*x)
+
+
+def speedup_generate_nd(V, p, eps):
+    """W(x, xb; eps) of a system of d coordinates: {(e_x..., e_xb...): coefficient}."""
+    d, ex, co, n = _nd_potential(V)
+    cap = 1 << 14
+    oe = (ctypes.c_int * (cap * 2 * d))()
+    ow = (ctypes.c_double * cap)()
+    nn = ctypes.c_int(0)
+    _check(load().speedup_generate_nd(d, ex, co, n, int(p), float(eps), oe, ow, cap, ctypes.byref(nn)))
+    return {tuple(oe[t * 2 * d:(t + 1) * 2 * d]): ow[t] for t in range(nn.value)}
+
+
+def speedup_amplitude_nd(V, a, b, T, p, s, n_mc, seed, **kw):
+    """Amplitude and errors of a system of d coordinates for every level n = 0..s."""
+    d, ex, co, n = _nd_potential(V)
+    out = (LevelResult * (s + 1))()
+    o = options(**kw)
+    _check(load().speedup_amplitude_nd(d, ex, co, n, _vec(a, d), _vec(b, d), T, p, s, int(n_mc), int(seed),
+                                       ctypes.byref(o), out))
+    return [out[k].as_dict(k) for k in range(s + 1)]
+
+
+def speedup_logweights_nd(V, a, b, T, p, s, sample0, n_samples, seed, out, **kw):
+    """Per-sample log-weights of a system of d coordinates into the device buffer out (n_samples x s)."""
+    d, ex, co, n = _nd_potential(V)
+    o = options(**kw)
+    _check(load().speedup_logweights_nd(d, ex, co, n, _vec(a, d), _vec(b, d), T, p, s, int(sample0),
+                                        int(n_samples), int(seed), ctypes.byref(o), _ptr(out)))
 
 
 def speedup_normals(seed, instance, sample0, n_samples, n_normals, out, precision="fp64", stream=None):
@@ -526,3 +584,23 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class PlanND(Plan):
+    """su_plan_create_nd: a plan for a system of d coordinates (potential
+    {exponent tuple: coefficient}, endpoint vectors a and b); executed and
+    finalized like Plan."""
+
+    def __init__(self, V, a, b, T, p, s, n_mc, seed, **kw):
+        self.s = s
+        d, ex, co, n = _nd_potential(V)
+        o = options(**kw)
+        h = ctypes.c_void_p()
+        _check(load().su_plan_create_nd(d, ex, co, n, _vec(a, d), _vec(b, d), T, p, s, int(n_mc), int(seed),
+                                        ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        tb, sb, lv, sa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        _check(load().su_plan_sizes(h, ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(lv),
+                                    ctypes.byref(sa)))
+        self.tuple_bytes, self.scratch_bytes = tb.value, sb.value
+        self.levels, self.slice_actions = lv.value, sa.value

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libspeedup_gb300.so")
-SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu"]
+SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu", "nd.cu"]
 # the sampler kernel, once per (precision, ring): compiled in parallel
 INSTANCES = [(prec, ring) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3)]
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",

@@ -153,6 +153,13 @@ struct su_plan {
     std::shared_ptr<const su::GeneralEffective> G;
     su::GeneralPotential V{};
     void *d_general = nullptr;
+    // systems of several coordinates (su_plan_create_nd): d, the program, the
+    // kernel's parameters and the bytes of its path scratch
+    int nd = 0;
+    std::vector<double> nd_a, nd_b;
+    su::NdEffective N;
+    su::NdParams Q{};
+    int64_t path_bytes = 0;
 };
 
 namespace {
@@ -481,6 +488,143 @@ int su_plan_create(int model, const double *params, int n_params, double a, doub
     return SU_OK;
 }
 
+// Tables, program and launch shape of a system of several coordinates.
+static int configure_nd(su_plan &pl) {
+    using namespace su;
+    const int S = pl.s;
+    const int M = (int)pl.N.hi.size();
+    std::vector<double> tabd((size_t)std::max(S, 1) * M, 0.0);
+    for (int d = 0; d < S; ++d) {
+        const double eps = pl.T / std::ldexp(1.0, S - d);
+        std::vector<double> t;
+        nd_table(pl.N, eps, t);
+        if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
+        for (int i = 0; i < M; ++i) {
+            if (!std::isfinite(t[(size_t)i])) return fail(SU_ENONFINITE, "non-finite coefficient at level %d", S - d);
+            tabd[(size_t)d * M + i] = t[(size_t)i];
+        }
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    CU(cudaGetDevice(&pl.device), "cudaGetDevice");
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
+    CU(dmalloc(&pl.d_tables, tabd.size() * sizeof(double)), "device allocation (tables)");
+    CU(cudaMemcpy(pl.d_tables, tabd.data(), tabd.size() * sizeof(double), cudaMemcpyHostToDevice), "upload tables");
+    std::vector<GeneralNode> nodes(pl.N.depth.size());
+    for (size_t t = 0; t < nodes.size(); ++t) {
+        if (pl.N.count[t] > 65535) return fail(SU_ENOTSUP, "a monomial group has more than 65535 entries");
+        nodes[t].depth = (unsigned char)pl.N.depth[t];
+        nodes[t].sym = (unsigned char)pl.N.sym[t];
+        nodes[t].count = (unsigned short)pl.N.count[t];
+        nodes[t].first = pl.N.first[t];
+    }
+    CU(dmalloc(&pl.d_general, nodes.size() * sizeof(GeneralNode)), "device allocation (program)");
+    CU(cudaMemcpy(pl.d_general, nodes.data(), nodes.size() * sizeof(GeneralNode), cudaMemcpyHostToDevice),
+       "upload program");
+
+    SamplerParams &P = pl.P;
+    std::memset(&P, 0, sizeof P);
+    for (int n = 1; n <= S; ++n) P.sigma[n] = std::sqrt(pl.T / std::ldexp(1.0, n + 1));
+    P.S = S;
+    P.F = 0;
+    P.rounds = 1;
+    P.levels = pl.levels;
+    P.M = M;
+    P.tables = pl.d_tables;
+    P.seed = pl.seed;
+    P.instance = pl.opt.instance;
+    P.n_mc = pl.n_mc;
+    P.sample0 = pl.opt.sample0;
+    P.n_blocks = pl.n_blocks;
+    const int64_t bsz = (pl.n_mc + pl.n_blocks - 1) / pl.n_blocks;
+    P.items_per_block = (bsz + kThreads - 1) / kThreads;
+    P.n_items = P.items_per_block * pl.n_blocks;
+    NdParams &Q = pl.Q;
+    std::memset(&Q, 0, sizeof Q);
+    Q.base = P;
+    Q.D = pl.nd;
+    Q.H = pl.N.H;
+    Q.n_nodes = (int)nodes.size();
+    Q.nodes = static_cast<const GeneralNode *>(pl.d_general);
+    for (int c = 0; c < pl.nd; ++c) {
+        Q.a[c] = pl.nd_a[(size_t)c];
+        Q.b[c] = pl.nd_b[(size_t)c];
+    }
+    pl.smem = nd_smem_bytes(Q);
+    const int occ = nd_occupancy(Q, pl.smem);
+    if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
+    pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
+    Q.pstride = (int64_t)pl.grid * kThreads;
+    pl.path_bytes = Q.pstride * (((int64_t)1 << S) + 1) * pl.nd * (int64_t)sizeof(double);
+    pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
+    pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + ((pl.path_bytes + 255) / 256) * 256 + 256;
+    pl.tuple_bytes = pl.n_blocks * pl.levels * 4 * (int64_t)sizeof(double);
+    const int64_t N = (int64_t)1 << S;
+    pl.slice_actions = S == 0 ? 0 : pl.n_mc * (pl.levels > 1 ? 2 * N - 2 : N);
+    return SU_OK;
+}
+
+int su_plan_create_nd(int d, const int *exps, const double *coefs, int n_terms, const double *a, const double *b,
+                      double T, int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt, su_plan **out) {
+    if (!out) return fail(SU_EINVAL, "plan pointer missing");
+    *out = nullptr;
+    if (d < 1 || d > su::kNdMaxDim) return fail(SU_EINVAL, "d must be in 1..%d", su::kNdMaxDim);
+    if (!a || !b) return fail(SU_EINVAL, "endpoints missing");
+    for (int c = 0; c < d; ++c)
+        if (!std::isfinite(a[c]) || !std::isfinite(b[c])) return fail(SU_EINVAL, "a and b must be finite");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    int rc = validate(-1, nullptr, 0, a[0], b[0], T, p, s, n_mc, o);
+    if (rc) return rc;
+    if (p > su::kNdMaxP) return fail(SU_ENOTSUP, "systems of several coordinates support p <= %d", su::kNdMaxP);
+    if (o.precision != SU_FP64) return fail(SU_ENOTSUP, "systems of several coordinates run in double only");
+    if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "systems of several coordinates sample the exact bridge only");
+    if (o.seg_log2 != 0 || o.rounds > 1) return fail(SU_ENOTSUP, "systems of several coordinates have one launch shape");
+    std::unique_ptr<su_plan> pl(new (std::nothrow) su_plan);
+    if (!pl) return fail(SU_ENOMEM, "host allocation failed");
+    std::string err;
+    rc = su::build_nd(d, exps, coefs, n_terms, p, pl->N, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    pl->model = -1;
+    pl->nd = d;
+    pl->nd_a.assign(a, a + d);
+    pl->nd_b.assign(b, b + d);
+    pl->a = a[0];
+    pl->b = b[0];
+    pl->T = T;
+    pl->p = p;
+    pl->s = s;
+    pl->n_mc = n_mc;
+    pl->seed = seed;
+    pl->opt = o;
+    pl->levels = s == 0 ? 0 : (o.hierarchy ? s : 1);
+    pl->n_blocks = std::min<int64_t>(o.n_blocks, n_mc);
+    double xm[su::kNdMaxDim], xh[su::kNdMaxDim];
+    pl->laf = 0.0;
+    for (int c = 0; c < d; ++c) {
+        xm[c] = 0.5 * (a[c] + b[c]);
+        xh[c] = 0.5 * (b[c] - a[c]);
+        pl->laf += log_A_free(a[c], b[c], T);
+    }
+    pl->w0 = -T * su::nd_wp_host(pl->N, xm, xh, T);
+    if (!std::isfinite(pl->w0) && !(std::isinf(pl->w0) && pl->w0 < 0))
+        return fail(SU_ENONFINITE, "level-0 weight is not finite");
+    rc = configure_nd(*pl);
+    if (rc) {
+        if (pl->d_tables) cudaFree(pl->d_tables);
+        if (pl->d_general) cudaFree(pl->d_general);
+        return rc;
+    }
+    *out = pl.release();
+    return SU_OK;
+}
+
 int su_plan_destroy(su_plan *pl) {
     if (!pl) return SU_OK;
     if (pl->d_tables) cudaFree(pl->d_tables);
@@ -527,7 +671,14 @@ int su_plan_execute_range(su_plan *pl, int64_t b0, int64_t b1, void *d_tuples, v
     P.flags = reinterpret_cast<int *>(static_cast<char *>(d_scratch) + pl->scratch_bytes - 256);
     P.w_out = nullptr;
     CU(cudaMemsetAsync(P.flags, 0, sizeof(int), st), "clear flags");
-    CU(su::launch_sampler(P, pl->opt.precision, grid, pl->smem, st), "sampler launch");
+    if (pl->nd) {
+        su::NdParams Q = pl->Q;
+        Q.base = P;
+        Q.paths = reinterpret_cast<double *>(static_cast<char *>(d_scratch) + ((pl->partial_bytes + 255) / 256) * 256);
+        CU(su::launch_nd(Q, grid, pl->smem, st), "sampler launch");
+    } else {
+        CU(su::launch_sampler(P, pl->opt.precision, grid, pl->smem, st), "sampler launch");
+    }
     CU(su::launch_combine(P.partial, static_cast<double *>(d_tuples), b0, b1 - b0, pl->levels, P.items_per_block,
                           st),
        "combine launch");
@@ -633,15 +784,10 @@ int su_plan_finalize(const su_plan *pl, const double *h_tuples, const void *d_sc
     return SU_OK;
 }
 
-int speedup_amplitude(int model, const double *params, int n_params, double a, double b, double T,
-                      int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt,
-                      su_level_result *out) {
-    if (!out) return fail(SU_EINVAL, "output missing");
-    su_plan *pl = nullptr;
-    int rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, opt, &pl);
-    if (rc) return rc;
-    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
-    if (s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
+// Sample a plan once and finalize: scratch on the plan's stream, tuples and
+// the flag word back to the host, the plan destroyed by the caller.
+static int amplitude_of_plan(su_plan *pl, su_level_result *out) {
+    if (pl->s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
     cudaStream_t st = (cudaStream_t)pl->opt.stream;
     void *dbuf = nullptr;
     const int64_t tb = pl->tuple_bytes, sb = pl->scratch_bytes;
@@ -649,7 +795,7 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     std::vector<double> h((size_t)(tb / sizeof(double)) + 32);
     void *d_tup = dbuf;
     void *d_scr = static_cast<char *>(dbuf) + tb;
-    rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);
+    int rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);
     cudaError_t e = cudaSuccess;
     if (rc == SU_OK) {
         e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
@@ -665,6 +811,92 @@ int speedup_amplitude(int model, const double *params, int n_params, double a, d
     std::memcpy(&flags, h.data() + tb / sizeof(double), sizeof(int));
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+int speedup_amplitude(int model, const double *params, int n_params, double a, double b, double T,
+                      int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt,
+                      su_level_result *out) {
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_plan *pl = nullptr;
+    int rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, opt, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    return amplitude_of_plan(pl, out);
+}
+
+int speedup_amplitude_nd(int d, const int *exps, const double *coefs, int n_terms, const double *a, const double *b,
+                         double T, int p, int s, int64_t n_mc, uint64_t seed, const su_options *opt,
+                         su_level_result *out) {
+    if (!out) return fail(SU_EINVAL, "output missing");
+    su_plan *pl = nullptr;
+    int rc = su_plan_create_nd(d, exps, coefs, n_terms, a, b, T, p, s, n_mc, seed, opt, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    return amplitude_of_plan(pl, out);
+}
+
+int speedup_logweights_nd(int d, const int *exps, const double *coefs, int n_terms, const double *a, const double *b,
+                          double T, int p, int s, int64_t sample0, int64_t n_samples, uint64_t seed,
+                          const su_options *opt, double *d_w) {
+    if (s < 1) return fail(SU_EINVAL, "s must be >= 1 for per-sample weights");
+    if (!d_w) return fail(SU_EINVAL, "output missing");
+    if (sample0 < 0 || n_samples < 1 || sample0 + n_samples > kMaxSamples)
+        return fail(SU_EINVAL, "sample range out of bounds");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    o.hierarchy = 1;
+    o.n_blocks = 1;
+    su_plan *pl = nullptr;
+    int rc = su_plan_create_nd(d, exps, coefs, n_terms, a, b, T, p, s, n_samples, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    su::NdParams Q = pl->Q;
+    Q.base.w_out = d_w;
+    Q.base.sample0 = sample0;
+    Q.base.partial = nullptr;
+    const size_t smem = su::nd_smem_bytes(Q);
+    void *buf = nullptr;
+    const int64_t pb = ((pl->path_bytes + 255) / 256) * 256;
+    CU(dmalloc_async(&buf, (size_t)(pb + 256), st), "cudaMallocAsync");
+    Q.paths = static_cast<double *>(buf);
+    Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(buf) + pb);
+    cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = su::launch_nd(Q, pl->grid, smem, st);
+    int flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "per-sample weights");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return SU_OK;
+}
+
+int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms, int p, double eps, int *out_exps,
+                        double *out_w, int capacity, int *n_out) {
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");
+    if (!out_exps || !out_w || !n_out || capacity < 0) return fail(SU_EINVAL, "output missing");
+    su::NdEffective E;
+    std::string err;
+    int rc = su::build_nd(d, exps, coefs, n_terms, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    std::vector<double> T;
+    su::nd_table(E, eps, T);
+    int n = 0;
+    for (size_t e = 0; e < T.size(); ++e) {
+        bool any = false;
+        for (double v : E.hi[e]) any |= v != 0.0;
+        if (!any) continue;   // a zero pad of the Horner groups
+        if (n < capacity) {
+            for (int v = 0; v < 2 * d; ++v) out_exps[(size_t)n * 2 * d + (size_t)v] = E.mono[e][(size_t)v];
+            out_w[n] = -T[e] / eps;
+        }
+        ++n;
+    }
+    *n_out = n;
+    if (n > capacity) return fail(SU_ENOTSUP, "the effective potential has %d terms", n);
+    return SU_OK;
 }
 
 // ------------------------------------------------------ fault injection

@@ -30,6 +30,9 @@
 #include "generator.h"
 
 #include <algorithm>
+#include <array>
+#include <climits>
+#include <cstdint>
 #include <cmath>
 #include <map>
 #include <cstdio>
@@ -632,6 +635,292 @@ double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, dou
     double w = Q[(size_t)G.K - 1];
     for (int k = G.K - 2; k >= 0; --k) w = w * Y + Q[(size_t)k];
     return -w / eps;                  // the table carries -eps
+}
+
+// ------------------------------------------- systems of d coordinates
+namespace {
+
+using NM = std::array<unsigned char, 2 * kNdMaxDim>;   // exponents of x_1..x_d, xb_1..xb_d
+using NPoly = std::map<NM, DD>;
+
+// acc += s * b, dropping sums that cancel to rounding residue
+void nadd(NPoly &acc, const NPoly &b, DD s) {
+    for (const auto &kv : b) {
+        const DD v = mul(kv.second, s);
+        auto it = acc.find(kv.first);
+        if (it == acc.end()) {
+            acc.emplace(kv.first, v);
+        } else {
+            const double scale = std::max(std::fabs(it->second.hi), std::fabs(v.hi));
+            it->second = add(it->second, v);
+            if (std::fabs(it->second.hi) <= 1e-26 * scale) acc.erase(it);
+        }
+    }
+}
+
+void nadd_term(NPoly &acc, const NM &m, DD v) {
+    auto it = acc.find(m);
+    if (it == acc.end()) {
+        acc.emplace(m, v);
+    } else {
+        const double scale = std::max(std::fabs(it->second.hi), std::fabs(v.hi));
+        it->second = add(it->second, v);
+        if (std::fabs(it->second.hi) <= 1e-26 * scale) acc.erase(it);
+    }
+}
+
+NPoly nmul(const NPoly &a, const NPoly &b) {
+    NPoly out;
+    for (const auto &x : a)
+        for (const auto &y : b) {
+            NM m;
+            for (size_t j = 0; j < m.size(); ++j) m[j] = (unsigned char)(x.first[j] + y.first[j]);
+            nadd_term(out, m, mul(x.second, y.second));
+        }
+    return out;
+}
+
+// d/dz_i
+NPoly nder(const NPoly &a, int i) {
+    NPoly out;
+    for (const auto &x : a) {
+        if (!x.first[(size_t)i]) continue;
+        NM m = x.first;
+        m[(size_t)i] -= 1;
+        nadd_term(out, m, mul_d(x.second, (double)x.first[(size_t)i]));
+    }
+    return out;
+}
+
+}  // namespace
+
+int build_nd(int d, const int *exps, const double *coefs, int n_terms, int p, NdEffective &E, std::string &err) {
+    if (d < 1 || d > kNdMaxDim) {
+        err = "the dimension d = D x M must be in 1..4";
+        return SU_EINVAL;
+    }
+    if (p < 1 || p > kNdMaxP) {
+        err = "p must be in 1..12 for systems of several coordinates";
+        return SU_EINVAL;
+    }
+    if (!exps || !coefs || n_terms < 1 || n_terms > kNdMaxTerms) {
+        err = "the potential needs 1..256 terms";
+        return SU_EINVAL;
+    }
+    NPoly V;
+    for (int t = 0; t < n_terms; ++t) {
+        NM m{};
+        int deg = 0;
+        for (int i = 0; i < d; ++i) {
+            const int e = exps[t * d + i];
+            if (e < 0 || e > kNdMaxDeg) {
+                err = "potential exponents must be in 0..6";
+                return SU_EINVAL;
+            }
+            m[(size_t)i] = (unsigned char)e;
+            deg += e;
+        }
+        if (deg > kNdMaxDeg) {
+            err = "the potential's total degree must be <= 6";
+            return SU_EINVAL;
+        }
+        if (!std::isfinite(coefs[t])) {
+            err = "non-finite potential coefficient";
+            return SU_EINVAL;
+        }
+        if (coefs[t] != 0.0) nadd_term(V, m, dd(coefs[t]));
+    }
+    // W[m][k] and its gradients in x and in xb
+    std::vector<std::vector<NPoly>> W((size_t)p, std::vector<NPoly>((size_t)p));
+    std::vector<std::vector<std::vector<NPoly>>> gx((size_t)p, std::vector<std::vector<NPoly>>((size_t)p)),
+        gb((size_t)p, std::vector<std::vector<NPoly>>((size_t)p));
+    auto grads = [&](int m, int k) {
+        gx[(size_t)m][(size_t)k].resize((size_t)d);
+        gb[(size_t)m][(size_t)k].resize((size_t)d);
+        for (int i = 0; i < d; ++i) {
+            gx[(size_t)m][(size_t)k][(size_t)i] = nder(W[(size_t)m][(size_t)k], i);
+            gb[(size_t)m][(size_t)k][(size_t)i] = nder(W[(size_t)m][(size_t)k], d + i);
+        }
+    };
+    auto dot = [&](const std::vector<NPoly> &a, const std::vector<NPoly> &b, NPoly &acc, DD s) {
+        for (int i = 0; i < d; ++i) nadd(acc, nmul(a[(size_t)i], b[(size_t)i]), s);
+    };
+    NPoly diag = V;   // (xb . grad)^(2m) V
+    DD inv_fact = dd(1.0);
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+            for (int rep = 0; rep < 2; ++rep) {
+                NPoly nxt;
+                for (int i = 0; i < d; ++i) {
+                    NPoly t = nder(diag, i);
+                    for (const auto &x : t) {
+                        NM mm = x.first;
+                        mm[(size_t)(d + i)] += 1;
+                        nadd_term(nxt, mm, x.second);
+                    }
+                }
+                diag = std::move(nxt);
+            }
+            inv_fact = div_d(div_d(inv_fact, 2.0 * m), 2.0 * m + 1.0);
+        }
+        NPoly &wmm = W[(size_t)m][(size_t)m];
+        nadd(wmm, diag, inv_fact);
+        grads(m, m);
+        for (int k = m - 1; k >= 0; --k) {
+            NPoly acc;
+            for (int i = 0; i < d; ++i) {   // lap W_{m-1,k} + lapb W_{m,k+1}
+                nadd(acc, nder(gx[(size_t)m - 1][(size_t)k][(size_t)i], i), dd(1.0));
+                nadd(acc, nder(gb[(size_t)m][(size_t)k + 1][(size_t)i], d + i), dd(1.0));
+            }
+            for (int l = 0; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r)
+                    dot(gx[(size_t)l][(size_t)r], gx[(size_t)(m - l - 2)][(size_t)(k - r)], acc, dd(-1.0));
+            for (int l = 1; l <= m - 2; ++l)
+                for (int r = std::max(0, k - m + l + 2); r <= std::min(k, l); ++r)
+                    dot(gb[(size_t)l][(size_t)r], gb[(size_t)(m - l - 1)][(size_t)(k - r + 1)], acc, dd(-1.0));
+            nadd(W[(size_t)m][(size_t)k], acc, div_d(dd(1.0), 8.0 * (m + k + 1)));
+            grads(m, k);
+        }
+    }
+    // monomial -> coefficient of eps^q, q = m - k
+    std::map<NM, std::vector<DD>> terms;
+    for (int m = 0; m < p; ++m)
+        for (int k = 0; k <= m; ++k)
+            for (const auto &kv : W[(size_t)m][(size_t)k]) {
+                auto &v = terms[kv.first];
+                if (v.empty()) v.assign((size_t)p, dd(0));
+                v[(size_t)(m - k)] = add(v[(size_t)(m - k)], kv.second);
+            }
+    // the Horner variable: the shortest program (trie nodes + padded entries)
+    const int nv = 2 * d;
+    auto prefix_of = [&](const NM &m, int H) {
+        std::vector<int> seq;
+        for (int v = 0; v < nv; ++v)
+            if (v != H)
+                for (int r = 0; r < m[(size_t)v]; ++r) seq.push_back(v);
+        return seq;
+    };
+    int bestH = 0;
+    size_t best = SIZE_MAX;
+    for (int H = 0; H < nv; ++H) {
+        std::map<std::vector<int>, int> groups;   // prefix -> highest power of z_H
+        for (const auto &kv : terms) {
+            auto &g = groups[prefix_of(kv.first, H)];
+            g = std::max(g, (int)kv.first[(size_t)H]);
+        }
+        std::map<std::vector<int>, int> trie;   // every prefix of every prefix
+        size_t entries = 0;
+        for (const auto &g : groups) {
+            entries += (size_t)g.second + 1;
+            for (size_t len = 0; len <= g.first.size(); ++len)
+                trie.emplace(std::vector<int>(g.first.begin(), g.first.begin() + (long)len), 0);
+        }
+        if (trie.size() + entries < best) {
+            best = trie.size() + entries;
+            bestH = H;
+        }
+    }
+    // the program: trie over prefixes, depth first, children by variable
+    struct TNode {
+        std::map<int, int> child;
+        int jmax = -1;
+        std::vector<std::vector<DD>> coef;   // power of z_H -> per-q coefficients
+        std::vector<int> seq;
+    };
+    std::vector<TNode> trie(1);
+    for (const auto &kv : terms) {
+        const std::vector<int> seq = prefix_of(kv.first, bestH);
+        int node = 0;
+        for (size_t t = 0; t < seq.size(); ++t) {
+            auto it = trie[(size_t)node].child.find(seq[t]);
+            if (it == trie[(size_t)node].child.end()) {
+                trie.emplace_back();
+                const int nn = (int)trie.size() - 1;
+                trie[(size_t)nn].seq.assign(seq.begin(), seq.begin() + (long)t + 1);
+                trie[(size_t)node].child.emplace(seq[t], nn);
+                node = nn;
+            } else {
+                node = it->second;
+            }
+        }
+        TNode &tn = trie[(size_t)node];
+        const int j = kv.first[(size_t)bestH];
+        if (j > tn.jmax) {
+            tn.coef.resize((size_t)j + 1, std::vector<DD>((size_t)p, dd(0)));
+            tn.jmax = j;
+        }
+        tn.coef[(size_t)j] = kv.second;
+    }
+    E = NdEffective{};
+    E.d = d;
+    E.p = p;
+    E.H = bestH;
+    struct Frame {
+        int node, depth, sym;
+    };
+    std::vector<Frame> stack{{0, 0, -1}};
+    while (!stack.empty()) {
+        const Frame f = stack.back();
+        stack.pop_back();
+        if (f.depth > kNdMaxDepth) {
+            err = "the effective potential's degree exceeds the evaluation program's depth (32)";
+            return SU_ENOTSUP;
+        }
+        const TNode &tn = trie[(size_t)f.node];
+        E.depth.push_back(f.depth);
+        E.sym.push_back(std::max(f.sym, 0));
+        E.first.push_back((int)E.hi.size());
+        E.count.push_back(tn.jmax + 1);
+        for (int j = 0; j <= tn.jmax; ++j) {
+            std::vector<double> hi, lo;
+            for (const DD &v : tn.coef[(size_t)j]) {
+                hi.push_back(v.hi);
+                lo.push_back(v.lo);
+            }
+            E.hi.push_back(std::move(hi));
+            E.lo.push_back(std::move(lo));
+            std::vector<unsigned char> mono((size_t)nv, 0);
+            for (int v : tn.seq) mono[(size_t)v] += 1;
+            mono[(size_t)bestH] = (unsigned char)j;
+            E.mono.push_back(std::move(mono));
+        }
+        for (auto it = tn.child.rbegin(); it != tn.child.rend(); ++it) stack.push_back({it->second, f.depth + 1, it->first});
+    }
+    return SU_OK;
+}
+
+void nd_table(const NdEffective &E, double eps, std::vector<double> &T) {
+    T.resize(E.hi.size());
+    for (size_t e = 0; e < E.hi.size(); ++e) {
+        DD acc = dd(0);
+        for (size_t q = E.hi[e].size(); q-- > 0;) acc = add(mul_d(acc, eps), DD{E.hi[e][q], E.lo[e][q]});
+        T[e] = mul_d(acc, -eps).hi;
+    }
+}
+
+double nd_wp_host(const NdEffective &E, const double *x, const double *xb, double eps) {
+    std::vector<double> T;
+    nd_table(E, eps, T);
+    double z[2 * kNdMaxDim];
+    for (int i = 0; i < E.d; ++i) {
+        z[i] = x[i];
+        z[E.d + i] = xb[i];
+    }
+    const double Y = z[E.H];
+    std::vector<double> stk((size_t)kNdMaxDepth + 1, 1.0);
+    double w = 0.0;
+    for (size_t t = 0; t < E.depth.size(); ++t) {
+        double mu = 1.0;
+        if (t) {
+            mu = stk[(size_t)E.depth[t] - 1] * z[E.sym[t]];
+            stk[(size_t)E.depth[t]] = mu;
+        }
+        if (!E.count[t]) continue;
+        double h = T[(size_t)(E.first[t] + E.count[t] - 1)];
+        for (int j = E.count[t] - 2; j >= 0; --j) h = h * Y + T[(size_t)(E.first[t] + j)];
+        w += h * mu;
+    }
+    return -w / eps;   // the table carries -eps
 }
 
 }  // namespace su

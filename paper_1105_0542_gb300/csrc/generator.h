@@ -103,4 +103,35 @@ void general_derivatives(const GeneralPotential &V, double x, int J, double *out
 // W_p(x, xb; eps) of the general potential on the host (level 0 and tests).
 double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps);
 
+// ---- systems of d = D x M coordinates (Sec. 2.2): the level-p effective
+// potential W(x, xb; eps) of a polynomial potential V(x_1..x_d) by the
+// contracted recursion (Eq. MBrec, diagonal Eq. DIA, Fig. 1 order) over
+// polynomials in the 2d variables z = (x_1..x_d, xb_1..xb_d), in
+// double-double.  For evaluation the distinct monomials are grouped by their
+// part without one variable z_H (the one that makes the program shortest):
+// the groups' monomials form a trie over non-decreasing variable sequences,
+// walked depth first (each prefix its parent times one variable), and a
+// group's entries are the coefficients of z_H^0, z_H^1, .. (Horner in z_H;
+// missing powers are zero entries).
+constexpr int kNdMaxDim = 4;
+constexpr int kNdMaxP = 12;
+constexpr int kNdMaxDeg = 6;
+constexpr int kNdMaxTerms = 256;
+constexpr int kNdMaxDepth = 32;
+
+struct NdEffective {
+    int d = 0, p = 0, H = 0;
+    std::vector<int> depth, sym, first, count;          // depth-first nodes; node 0 = the empty prefix
+    std::vector<std::vector<double>> hi, lo;            // entry -> coefficient of eps^q, q = 0..p-1
+    std::vector<std::vector<unsigned char>> mono;       // entry -> exponents of z (2d)
+};
+
+int build_nd(int d, const int *exps, const double *coefs, int n_terms, int p, NdEffective &E, std::string &err);
+
+// The level table for one eps: entry e gets -eps * sum_q c_q eps^q.
+void nd_table(const NdEffective &E, double eps, std::vector<double> &T);
+
+// W(x, xb; eps) on the host (level 0 and checks): x, xb of d entries.
+double nd_wp_host(const NdEffective &E, const double *x, const double *xb, double eps);
+
 }  // namespace su

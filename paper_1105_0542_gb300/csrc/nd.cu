@@ -1,0 +1,191 @@
+// The amplitude estimator for systems of d = D x M coordinates (Sec. 2.2,
+// Eq. EXP / Eq. MBrec): bisection paths of every coordinate (Sec. 4.1), the
+// level-p effective potential W(x, xb; eps) of a polynomial potential per
+// slice, per-sample log-weights of every level, per-item log-sum-exp tuples.
+#include <cstdint>
+
+#include "sampler_impl.cuh"
+
+namespace su {
+namespace {
+
+// -eps W of two slices with variables za, zb = (x_1..x_D, xb_1..xb_D): the
+// monomial program walked depth first (each prefix its parent times one
+// variable, the parent the top of a per-slice stack), each prefix's entries
+// combined by Horner in z_H and added times the prefix; the two slices share
+// every node and coefficient load.
+template <int D>
+__device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double (&zb)[2 * D],
+                                        const double *__restrict__ coef, const NdParams &Q, double &wa,
+                                        double &wb) {
+    double sa[kNdMaxDepth + 1], sb[kNdMaxDepth + 1];
+    sa[0] = 1.0;
+    sb[0] = 1.0;
+    const double Ya = za[Q.H], Yb = zb[Q.H];
+    double acc_a = 0.0, acc_b = 0.0;
+    const GeneralNode *__restrict__ nodes = Q.nodes;
+    for (int t = 0; t < Q.n_nodes; ++t) {
+        const GeneralNode nd = nodes[t];
+        double ma = 1.0, mb = 1.0;
+        if (t) {
+            ma = sa[nd.depth - 1] * za[nd.sym];
+            mb = sb[nd.depth - 1] * zb[nd.sym];
+            sa[nd.depth] = ma;
+            sb[nd.depth] = mb;
+        }
+        const int cnt = nd.count;
+        if (cnt) {
+            const double *c = coef + nd.first;
+            double ha = c[cnt - 1], hb = ha;
+#pragma unroll 4
+            for (int e = cnt - 2; e >= 0; --e) {
+                const double ce = c[e];
+                ha = fma(ha, Ya, ce);
+                hb = fma(hb, Yb, ce);
+            }
+            acc_a = fma(ha, ma, acc_a);
+            acc_b = fma(hb, mb, acc_b);
+        }
+    }
+    wa = acc_a;
+    wb = acc_b;
+}
+
+// Shared memory: sw[levels][kThreads] (double, reduced runs) | Box-Muller node tables
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__ NdParams Q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SamplerParams &P = Q.base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int L = P.levels, S = P.S, N = 1 << S;
+    const bool per_sample = P.w_out != nullptr;
+    double *sw = reinterpret_cast<double *>(smem_raw);
+    size_t off = per_sample ? 0 : sizeof(double) * (size_t)L * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
+    bm::tables_init(bm_smem, tid, kThreads);
+    __syncthreads();
+
+    Stream<double> st;
+    st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+    st.inst = P.instance;
+    st.bm = bm_smem;
+    const int64_t ps = Q.pstride;
+    double *q = Q.paths + (int64_t)blockIdx.x * kThreads + tid;   // this slot's points
+    auto at = [&](int i, int c) -> double & { return q[((int64_t)i * D + c) * ps]; };
+
+    for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
+        const int64_t b = item / P.items_per_block;
+        const int64_t r = item - b * P.items_per_block;
+        const int64_t lo = b * P.n_mc / P.n_blocks;
+        const int64_t hi = (b + 1) * P.n_mc / P.n_blocks;
+        const int64_t start = lo + r * kThreads;
+        const int cnt = (int)max((int64_t)0, min((int64_t)kThreads, hi - start));
+        if (tid < cnt) {
+            const uint64_t sample = (uint64_t)(P.sample0 + start + tid);
+            st.slo = (uint32_t)sample;
+            st.shi = (uint32_t)(sample >> 32);
+            for (int c = 0; c < D; ++c) {
+                at(0, c) = Q.a[c];
+                at(N, c) = Q.b[c];
+            }
+            // bisection, level by level; normals in Box-Muller pairs
+            uint32_t have = 0xffffffffu;
+            double z0 = 0.0, z1 = 0.0;
+            for (int n = 1; n <= S; ++n) {
+                const double sg = P.sigma[n];
+                const int h = 1 << (S - n);
+                const int j0 = (1 << (n - 1)) - 1;
+                for (int i = 0; i < (1 << (n - 1)); ++i) {
+                    const int idx = (2 * i + 1) * h;
+                    for (int c = 0; c < D; ++c) {
+                        const uint32_t g = (uint32_t)((j0 + i) * D + c);
+                        if ((g >> 1) != have) {
+                            st.pair(g >> 1, z0, z1);
+                            have = g >> 1;
+                        }
+                        const double z = (g & 1u) ? z1 : z0;
+                        at(idx, c) = fma(sg, z, 0.5 * (at(idx - h, c) + at(idx + h, c)));
+                    }
+                }
+            }
+            // w_n = -eps_n sum_k W on the level-n subpath; level n = S - dl
+            double wloc[SU_MAX_S];
+            bool bad = false;
+            for (int dl = 0; dl < L; ++dl) {
+                const int stp = 1 << dl, ns = 1 << (S - dl);
+                const double *tab = reinterpret_cast<const double *>(P.tables) + (size_t)dl * P.M;
+                double w = 0.0;
+                for (int k = 0; k < ns; k += 2) {
+                    double za[2 * D], zb[2 * D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const double pl = at(k * stp, c), pm = at((k + 1) * stp, c), pr = at((k + 2) * stp, c);
+                        za[c] = 0.5 * (pl + pm);
+                        za[D + c] = 0.5 * (pm - pl);
+                        zb[c] = 0.5 * (pm + pr);
+                        zb[D + c] = 0.5 * (pr - pm);
+                    }
+                    double wa, wb;
+                    nd_pair<D>(za, zb, tab, Q, wa, wb);
+                    w += wa + wb;
+                }
+                wloc[dl] = w;
+                bad |= isnan(w) || (isinf(w) && w > 0);
+            }
+            if (bad) atomicOr(P.flags, 1);
+            if (per_sample) {
+                double *dst = P.w_out + (start + tid) * (int64_t)S;
+                for (int dl = 0; dl < L; ++dl) dst[S - dl - 1] = wloc[dl];
+            } else {
+                for (int dl = 0; dl < L; ++dl) sw[(size_t)dl * kThreads + tid] = wloc[dl];
+            }
+        }
+        if (per_sample) continue;
+        __syncthreads();
+        item_lse<double>(sw, L, kThreads, cnt, P.partial, item, warp, lane);
+        __syncthreads();
+    }
+}
+
+const void *nd_fn(int D) {
+    switch (D) {
+        case 1: return (const void *)nd_kernel<1>;
+        case 2: return (const void *)nd_kernel<2>;
+        case 3: return (const void *)nd_kernel<3>;
+        default: return (const void *)nd_kernel<4>;
+    }
+}
+
+}  // namespace
+
+size_t nd_smem_bytes(const NdParams &Q) {
+    size_t off = Q.base.w_out ? 0 : sizeof(double) * (size_t)Q.base.levels * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    return off + sizeof(bm::Tables);
+}
+
+int nd_occupancy(const NdParams &Q, size_t smem) {
+    const void *fn = nd_fn(Q.D);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_nd(const NdParams &Q, int grid, size_t smem, cudaStream_t st) {
+    const void *fn = nd_fn(Q.D);
+    cudaGetLastError();
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {const_cast<NdParams *>(&Q)};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, st);
+}
+
+}  // namespace su

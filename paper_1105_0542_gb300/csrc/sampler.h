@@ -104,6 +104,24 @@ int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
 cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
                              double t, double lognorm, double *U, cudaStream_t st);
 
+// Systems of d = D x M coordinates (Sec. 2.2): one bisection path per
+// thread, every coordinate an exact Brownian bridge (coordinate c of heap
+// midpoint j takes normal j D + c of the sample's stream), its points in a
+// global scratch array; W(x, xb; eps) per slice from the monomial program of
+// NdEffective (nodes as GeneralNode; entries = powers of z_H), two slices at
+// a time; weights and per-item tuples as the one-dimensional sampler's.
+struct NdParams {
+    SamplerParams base;       // S, levels, tables (per level, global), M, sigma, stream, items, outputs
+    int D, H, n_nodes;
+    const GeneralNode *nodes; // device
+    double a[kNdMaxDim], b[kNdMaxDim];
+    double *paths;            // device: point i, coordinate c of slot t at [(i D + c) pstride + t]
+    int64_t pstride;          // slots = grid x kThreads
+};
+size_t nd_smem_bytes(const NdParams &Q);
+int nd_occupancy(const NdParams &Q, size_t smem);
+cudaError_t launch_nd(const NdParams &Q, int grid, size_t smem, cudaStream_t st);
+
 cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
                            cudaStream_t st);
 size_t batch_smem_bytes(const BatchParams &B, int precision);

@@ -643,6 +643,37 @@ __device__ __forceinline__ void lse_merge(double &ma, double &sa, double &qa, do
     }
 }
 
+// The log-sum-exp tuple (M, sum e^{w-M}, sum e^{2(w-M)}, n) of one item's
+// cnt weights per level (sw[level][chunk]), one warp per level, written to
+// partial[4 (item L + level)]; a fixed order, so a rerun gives the same bits.
+template <typename R>
+__device__ __forceinline__ void item_lse(const R *sw, int L, int chunk, int cnt, double *partial, int64_t item,
+                                         int warp, int lane) {
+    for (int d = warp; d < L; d += kThreads / 32) {
+        const R *v = sw + (size_t)d * chunk;
+        R m = (R)-INFINITY;
+        for (int t = lane; t < cnt; t += 32) m = fmax(m, v[t]);
+        m = warp_max(m);
+        double s = 0, q = 0;
+        if (m > (R)-INFINITY) {
+            for (int t = lane; t < cnt; t += 32) {
+                const double e = lse_exp((R)(v[t] - m));
+                s += e;
+                q = fma(e, e, q);
+            }
+        }
+        s = warp_sum(s);
+        q = warp_sum(q);
+        if (lane == 0) {
+            double *o = partial + 4 * (item * L + d);
+            o[0] = (double)m;
+            o[1] = s;
+            o[2] = q;
+            o[3] = (double)cnt;
+        }
+    }
+}
+
 // ----------------------------------------------------------- the kernel
 // Shared memory: sw[levels][chunk] (R) | tables[levels][M] (R) | sigma[S+1] (R) |
 //                qc[(C+1)][kThreads] (R) | zz[S+1][kThreads] (double, if wf_on) |
@@ -737,29 +768,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
 
         // log-sum-exp tuple of this item, per level, in a fixed order
         __syncthreads();
-        for (int d = warp; d < L; d += kThreads / 32) {
-            const R *v = sw + (size_t)d * chunk;
-            R m = (R)-INFINITY;
-            for (int t = lane; t < cnt; t += 32) m = fmax(m, v[t]);
-            m = warp_max(m);
-            double s = 0, q = 0;
-            if (m > (R)-INFINITY) {
-                for (int t = lane; t < cnt; t += 32) {
-                    const double e = lse_exp((R)(v[t] - m));
-                    s += e;
-                    q = fma(e, e, q);
-                }
-            }
-            s = warp_sum(s);
-            q = warp_sum(q);
-            if (lane == 0) {
-                double *o = P.partial + 4 * (item * L + d);
-                o[0] = (double)m;
-                o[1] = s;
-                o[2] = q;
-                o[3] = (double)cnt;
-            }
-        }
+        item_lse<R>(sw, L, chunk, cnt, P.partial, item, warp, lane);
         __syncthreads();
     }
 }

@@ -213,3 +213,57 @@ def test_general_mode_is_refused_where_a_collapsed_table_is_needed():
     with pytest.raises(su.SpeedupError) as e:
         su.speedup_amplitude_noalloc("general", P_GEN, 0.0, 1.0, 1.0, 4, 4, 1000, 1)
     assert e.value.code == -6
+
+
+# ---- systems of several coordinates: the host generator against the oracle
+from fractions import Fraction as _F  # noqa: E402
+
+ND_GEN2 = {(2, 0): 0.5, (0, 2): 0.75, (1, 1): 0.2, (2, 1): 1 / 3, (0, 3): -1 / 7, (4, 0): 0.1, (1, 3): 0.05,
+           (0, 4): 1 / 12, (1, 0): -1 / 3}
+ND_GEN3 = {(2, 0, 0): 0.5, (0, 2, 0): 0.5, (0, 0, 2): 0.5, (1, 1, 0): 0.2, (0, 1, 1): 1 / 7, (2, 0, 2): 1 / 11,
+           (4, 0, 0): 1 / 24, (0, 4, 0): 1 / 24, (0, 0, 4): 1 / 30, (1, 1, 1): 1 / 9}
+ND_TWO_2D = {(2, 0, 0, 0): 0.5, (0, 2, 0, 0): 0.5, (0, 0, 2, 0): 0.5, (0, 0, 0, 2): 0.5,   # two particles in 2D
+             (2, 0, 2, 0): 0.1, (1, 0, 1, 0): -0.2, (0, 1, 0, 1): -0.2, (0, 2, 0, 2): 0.1, (4, 0, 0, 0): 0.05}
+
+
+@pytest.mark.parametrize("V,d,p", [(ND_GEN2, 2, 1), (ND_GEN2, 2, 5), (ND_GEN2, 2, 9), (ND_GEN3, 3, 6),
+                                   (ND_TWO_2D, 4, 4), ({(2,): 0.5, (4,): 1 / 24, (3,): -0.1}, 1, 10),
+                                   ({(6, 0): 0.01, (0, 2): 0.5, (3, 3): 0.02}, 2, 6)])
+def test_nd_generator_matches_the_oracle(V, d, p):
+    from oracle import many_body as mb
+    Vf = {k: _F(v) for k, v in V.items()}
+    for eps in (0.05, 0.4):
+        got = su.speedup_generate_nd(V, p, eps)
+        ref = mb.collapsed(Vf, d, p, _F(eps))
+        assert set(got) == set(ref)
+        for k, v in ref.items():
+            assert got[k] == pytest.approx(float(v), rel=1e-14, abs=1e-300), k
+
+
+@pytest.mark.parametrize("V,kw,code", [
+    ({(2, 0, 0, 0, 0): 1.0}, {}, -1),                 # d = 5
+    ({(7, 0): 1.0}, {}, -1),                          # degree 7
+    ({(4, 3): 1.0}, {}, -1),                          # total degree 7
+    ({(-1, 2): 1.0}, {}, -1),                         # negative exponent
+    ({(2, 0): float("inf")}, {}, -1),                 # non-finite coefficient
+    ({(2, 0): 1.0}, {"p": 13}, -6),
+    ({(2, 0): 1.0}, {"precision": "fp32"}, -6),
+    ({(2, 0): 1.0}, {"width_factor": 1.4}, -6),
+    ({(2, 0): 1.0}, {"a": (float("nan"), 0.0)}, -1),
+])
+def test_nd_rejects_bad_requests(V, kw, code):
+    d = len(next(iter(V)))
+    args = {"p": 4, "a": (0.0,) * d, "b": (1.0,) * d}
+    args.update({k: v for k, v in kw.items() if k in ("p", "a")})
+    opts = {k: v for k, v in kw.items() if k not in ("p", "a")}
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_amplitude_nd(V, args["a"], args["b"], 1.0, args["p"], 3, 1000, 1, **opts)
+    assert e.value.code == code
+
+
+def test_nd_generator_term_limit():
+    big = {(i, j): 1.0 for i in range(7) for j in range(7) if i + j <= 6}   # 28 terms: fine
+    assert len(su.speedup_generate_nd(big, 2, 0.1)) > 0
+    with pytest.raises(su.SpeedupError) as e:
+        su.speedup_generate_nd({(2,): 1.0}, 0, 0.1)
+    assert e.value.code == -1
