@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-configs", action="store_true", help="skip the configuration 1 and 4 entries")
     ap.add_argument("--no-evolution", action="store_true", help="skip the evolution-operator (Fig. 3) entry")
     ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
+    ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -363,6 +364,9 @@ def run_ours(args):
     general = None
     if not args.no_general:
         general = run_general(su, torch, dev, stream, flush)
+    several = None
+    if not args.no_nd:
+        several = run_nd(su, torch, dev, stream, flush)
 
     if rank != 0:
         if dist is not None:
@@ -405,7 +409,7 @@ def run_ours(args):
         "fp32_vs_fp64_top_level": f32_vs_f64,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
         "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
-        "evolution_operator_fig3": evolution, "general_potential": general,
+        "evolution_operator_fig3": evolution, "general_potential": general, "several_coordinates": several,
         "clocks": clock_info,
     }
     print(json.dumps(line))
@@ -538,6 +542,53 @@ def run_general(su, torch, dev, stream, flush):
                     "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "amp": top["amp"],
                     "rel_err": top["rel_err"]})
     return {"cases": out, "note": "same Philox stream in the first two cases: their amplitudes agree to rounding"}
+
+
+def run_nd(su, torch, dev, stream, flush):
+    """Systems of several coordinates (Sec. 2.2): the 2D anharmonic
+    oscillator of Sec. 3.3 (A = 1, g = 1) at p = 10, N = 1024, the 3D one at
+    p = 8, N = 256, and two coupled particles in 2D (d = 4) at p = 6, N = 64;
+    1e6 samples each, double precision, device time of one plan execute
+    (L2 flushed)."""
+    aho2 = {(2, 0): 0.5, (0, 2): 0.5, (4, 0): 1 / 24, (0, 4): 1 / 24, (2, 2): 1 / 12}
+    aho3 = {}
+    for i in range(3):
+        e = [0, 0, 0]
+        e[i] = 2
+        aho3[tuple(e)] = 0.5
+        e[i] = 4
+        aho3[tuple(e)] = 1 / 24
+        for j in range(i + 1, 3):
+            e = [0, 0, 0]
+            e[i] = e[j] = 2
+            aho3[tuple(e)] = 1 / 12
+    two = {(2, 0, 0, 0): 0.5, (0, 2, 0, 0): 0.5, (0, 0, 2, 0): 0.5, (0, 0, 0, 2): 0.5, (2, 0, 2, 0): 0.1,
+           (1, 0, 1, 0): -0.2, (0, 1, 0, 1): -0.2, (0, 2, 0, 2): 0.1}
+    cases = (("2D anharmonic oscillator A=1 g=1", aho2, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10),
+             ("3D anharmonic oscillator A=1 g=1", aho3, (0.0, 0.0, 0.0), (1.0, 0.5, -0.5), 1.0, 8, 8),
+             ("two particles in 2D, harmonic + coupling", two, (0.3, 0.0, -0.3, 0.1), (0.2, 0.4, -0.1, -0.2),
+              1.0, 6, 6))
+    out = []
+    n_mc = 1_000_000
+    for name, V, a, b, T, p, s in cases:
+        pl = su.PlanND(V, a, b, T, p, s, n_mc, 1234, n_blocks=64)
+        t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device=dev)
+        sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device=dev)
+        pl.su_plan_execute(t, sc, stream)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.su_plan_execute(t, sc, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        top = pl.su_plan_finalize(t.cpu().numpy(), sc)[s]
+        out.append({"case": name, "d": len(a), "p": p, "N": 1 << s, "samples": n_mc, "ms": ms,
+                    "terms": len(su.speedup_generate_nd(V, p, T / 2 ** s)),
+                    "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "amp": top["amp"],
+                    "rel_err": top["rel_err"]})
+        del t, sc
+    return {"cases": out, "note": "terms = monomials of W(x, xb; eps) in the 2d variables at the finest level"}
 
 
 def run_batched(su, torch, dev, stream, flush):

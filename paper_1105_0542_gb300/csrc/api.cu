@@ -549,6 +549,7 @@ static int configure_nd(su_plan &pl) {
     Q.base = P;
     Q.D = pl.nd;
     Q.H = pl.N.H;
+    Q.G = pl.N.G;
     Q.n_nodes = (int)nodes.size();
     Q.nodes = static_cast<const GeneralNode *>(pl.d_general);
     for (int c = 0; c < pl.nd; ++c) {

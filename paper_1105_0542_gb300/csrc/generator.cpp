@@ -791,45 +791,83 @@ int build_nd(int d, const int *exps, const double *coefs, int n_terms, int p, Nd
                 if (v.empty()) v.assign((size_t)p, dd(0));
                 v[(size_t)(m - k)] = add(v[(size_t)(m - k)], kv.second);
             }
-    // the Horner variable: the shortest program (trie nodes + padded entries)
+    // the Horner variable z_H and step G: a group (the monomials that agree
+    // in every other variable) is z_H^j0 sum_i c_i (z_H^G)^i, j0 its lowest
+    // power of z_H, which joins the group's prefix; G is the gcd of the power
+    // differences inside groups (2 where V has a parity).  Taken to make the
+    // program shortest (trie nodes + entries).
     const int nv = 2 * d;
-    auto prefix_of = [&](const NM &m, int H) {
+    auto others_of = [&](const NM &m, int H) {
+        NM o = m;
+        o[(size_t)H] = 0;
+        return o;
+    };
+    auto seq_of = [&](const NM &o, int H, int j0) {
         std::vector<int> seq;
-        for (int v = 0; v < nv; ++v)
-            if (v != H)
-                for (int r = 0; r < m[(size_t)v]; ++r) seq.push_back(v);
+        for (int v = 0; v < nv; ++v) {
+            const int reps = v == H ? j0 : (int)o[(size_t)v];
+            for (int r = 0; r < reps; ++r) seq.push_back(v);
+        }
         return seq;
     };
-    int bestH = 0;
+    struct Span {
+        int lo = INT_MAX, hi = -1, g = 0;
+    };
+    auto spans_of = [&](int H, int &G) {
+        std::map<NM, Span> grp;
+        for (const auto &kv : terms) {
+            Span &sp = grp[others_of(kv.first, H)];
+            const int e = kv.first[(size_t)H];
+            sp.lo = std::min(sp.lo, e);
+            sp.hi = std::max(sp.hi, e);
+        }
+        G = 0;
+        for (const auto &kv : terms) {
+            const Span &sp = grp[others_of(kv.first, H)];
+            int a = G, b = kv.first[(size_t)H] - sp.lo;
+            while (b) {
+                const int t = a % b;
+                a = b;
+                b = t;
+            }
+            G = a;
+        }
+        if (G == 0) G = 1;
+        return grp;
+    };
+    int bestH = 0, bestG = 1;
     size_t best = SIZE_MAX;
     for (int H = 0; H < nv; ++H) {
-        std::map<std::vector<int>, int> groups;   // prefix -> highest power of z_H
-        for (const auto &kv : terms) {
-            auto &g = groups[prefix_of(kv.first, H)];
-            g = std::max(g, (int)kv.first[(size_t)H]);
-        }
-        std::map<std::vector<int>, int> trie;   // every prefix of every prefix
+        int G = 1;
+        const auto grp = spans_of(H, G);
+        std::map<std::vector<int>, int> trie;   // every prefix of every group's prefix
         size_t entries = 0;
-        for (const auto &g : groups) {
-            entries += (size_t)g.second + 1;
-            for (size_t len = 0; len <= g.first.size(); ++len)
-                trie.emplace(std::vector<int>(g.first.begin(), g.first.begin() + (long)len), 0);
+        for (const auto &g : grp) {
+            entries += (size_t)((g.second.hi - g.second.lo) / G + 1);
+            const std::vector<int> seq = seq_of(g.first, H, g.second.lo);
+            for (size_t len = 0; len <= seq.size(); ++len)
+                trie.emplace(std::vector<int>(seq.begin(), seq.begin() + (long)len), 0);
         }
         if (trie.size() + entries < best) {
             best = trie.size() + entries;
             bestH = H;
+            bestG = G;
         }
     }
     // the program: trie over prefixes, depth first, children by variable
     struct TNode {
         std::map<int, int> child;
-        int jmax = -1;
-        std::vector<std::vector<DD>> coef;   // power of z_H -> per-q coefficients
+        int imax = -1, j0 = 0;
+        std::vector<std::vector<DD>> coef;   // power of z_H^G -> per-q coefficients
         std::vector<int> seq;
     };
+    int G0 = 1;
+    const auto groups = spans_of(bestH, G0);
     std::vector<TNode> trie(1);
     for (const auto &kv : terms) {
-        const std::vector<int> seq = prefix_of(kv.first, bestH);
+        const NM o = others_of(kv.first, bestH);
+        const int j0 = groups.at(o).lo;
+        const std::vector<int> seq = seq_of(o, bestH, j0);
         int node = 0;
         for (size_t t = 0; t < seq.size(); ++t) {
             auto it = trie[(size_t)node].child.find(seq[t]);
@@ -844,17 +882,19 @@ int build_nd(int d, const int *exps, const double *coefs, int n_terms, int p, Nd
             }
         }
         TNode &tn = trie[(size_t)node];
-        const int j = kv.first[(size_t)bestH];
-        if (j > tn.jmax) {
-            tn.coef.resize((size_t)j + 1, std::vector<DD>((size_t)p, dd(0)));
-            tn.jmax = j;
+        tn.j0 = j0;
+        const int i = (kv.first[(size_t)bestH] - j0) / bestG;
+        if (i > tn.imax) {
+            tn.coef.resize((size_t)i + 1, std::vector<DD>((size_t)p, dd(0)));
+            tn.imax = i;
         }
-        tn.coef[(size_t)j] = kv.second;
+        tn.coef[(size_t)i] = kv.second;
     }
     E = NdEffective{};
     E.d = d;
     E.p = p;
     E.H = bestH;
+    E.G = bestG;
     struct Frame {
         int node, depth, sym;
     };
@@ -870,18 +910,18 @@ int build_nd(int d, const int *exps, const double *coefs, int n_terms, int p, Nd
         E.depth.push_back(f.depth);
         E.sym.push_back(std::max(f.sym, 0));
         E.first.push_back((int)E.hi.size());
-        E.count.push_back(tn.jmax + 1);
-        for (int j = 0; j <= tn.jmax; ++j) {
+        E.count.push_back(tn.imax + 1);
+        for (int i = 0; i <= tn.imax; ++i) {
             std::vector<double> hi, lo;
-            for (const DD &v : tn.coef[(size_t)j]) {
+            for (const DD &v : tn.coef[(size_t)i]) {
                 hi.push_back(v.hi);
                 lo.push_back(v.lo);
             }
             E.hi.push_back(std::move(hi));
             E.lo.push_back(std::move(lo));
             std::vector<unsigned char> mono((size_t)nv, 0);
-            for (int v : tn.seq) mono[(size_t)v] += 1;
-            mono[(size_t)bestH] = (unsigned char)j;
+            for (int v : tn.seq) mono[(size_t)v] += 1;   // includes z_H^j0
+            mono[(size_t)bestH] = (unsigned char)(mono[(size_t)bestH] + bestG * i);
             E.mono.push_back(std::move(mono));
         }
         for (auto it = tn.child.rbegin(); it != tn.child.rend(); ++it) stack.push_back({it->second, f.depth + 1, it->first});
@@ -906,7 +946,8 @@ double nd_wp_host(const NdEffective &E, const double *x, const double *xb, doubl
         z[i] = x[i];
         z[E.d + i] = xb[i];
     }
-    const double Y = z[E.H];
+    double Y = 1.0;
+    for (int g = 0; g < E.G; ++g) Y *= z[E.H];
     std::vector<double> stk((size_t)kNdMaxDepth + 1, 1.0);
     double w = 0.0;
     for (size_t t = 0; t < E.depth.size(); ++t) {

@@ -109,10 +109,11 @@ double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, dou
 // polynomials in the 2d variables z = (x_1..x_d, xb_1..xb_d), in
 // double-double.  For evaluation the distinct monomials are grouped by their
 // part without one variable z_H (the one that makes the program shortest):
-// the groups' monomials form a trie over non-decreasing variable sequences,
-// walked depth first (each prefix its parent times one variable), and a
-// group's entries are the coefficients of z_H^0, z_H^1, .. (Horner in z_H;
-// missing powers are zero entries).
+// a group is z_H^j0 times a polynomial in z_H^G (G = 2 where V has a
+// parity); the groups' prefixes (the other variables and z_H^j0) form a trie
+// over non-decreasing variable sequences, walked depth first (each prefix its
+// parent times one variable), and a group's entries are the coefficients of
+// (z_H^G)^0, (z_H^G)^1, .. (Horner in z_H^G; missing powers are zero entries).
 constexpr int kNdMaxDim = 4;
 constexpr int kNdMaxP = 12;
 constexpr int kNdMaxDeg = 6;
@@ -120,7 +121,7 @@ constexpr int kNdMaxTerms = 256;
 constexpr int kNdMaxDepth = 32;
 
 struct NdEffective {
-    int d = 0, p = 0, H = 0;
+    int d = 0, p = 0, H = 0, G = 1;                     // Horner in z_H^G
     std::vector<int> depth, sym, first, count;          // depth-first nodes; node 0 = the empty prefix
     std::vector<std::vector<double>> hi, lo;            // entry -> coefficient of eps^q, q = 0..p-1
     std::vector<std::vector<unsigned char>> mono;       // entry -> exponents of z (2d)

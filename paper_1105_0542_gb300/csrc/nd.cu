@@ -12,8 +12,8 @@ namespace {
 // -eps W of two slices with variables za, zb = (x_1..x_D, xb_1..xb_D): the
 // monomial program walked depth first (each prefix its parent times one
 // variable, the parent the top of a per-slice stack), each prefix's entries
-// combined by Horner in z_H and added times the prefix; the two slices share
-// every node and coefficient load.
+// combined by Horner in z_H^G and added times the prefix; the two slices
+// share every node and coefficient load.
 template <int D>
 __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double (&zb)[2 * D],
                                         const double *__restrict__ coef, const NdParams &Q, double &wa,
@@ -21,7 +21,11 @@ __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double 
     double sa[kNdMaxDepth + 1], sb[kNdMaxDepth + 1];
     sa[0] = 1.0;
     sb[0] = 1.0;
-    const double Ya = za[Q.H], Yb = zb[Q.H];
+    double Ya = 1.0, Yb = 1.0;
+    for (int g = 0; g < Q.G; ++g) {
+        Ya *= za[Q.H];
+        Yb *= zb[Q.H];
+    }
     double acc_a = 0.0, acc_b = 0.0;
     const GeneralNode *__restrict__ nodes = Q.nodes;
     for (int t = 0; t < Q.n_nodes; ++t) {

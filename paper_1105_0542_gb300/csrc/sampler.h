@@ -112,7 +112,7 @@ cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *
 // a time; weights and per-item tuples as the one-dimensional sampler's.
 struct NdParams {
     SamplerParams base;       // S, levels, tables (per level, global), M, sigma, stream, items, outputs
-    int D, H, n_nodes;
+    int D, H, G, n_nodes;     // Horner in z_H^G
     const GeneralNode *nodes; // device
     double a[kNdMaxDim], b[kNdMaxDim];
     double *paths;            // device: point i, coordinate c of slot t at [(i D + c) pstride + t]
