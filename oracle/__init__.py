@@ -19,6 +19,12 @@ Calculation of Transition Amplitudes via the Effective Action Approach"):
   kernel, the exact Gaussian value of A_N^(p) for the harmonic oscillator,
   tensor-grid quadrature over the N-1 intermediate points for tiny N, and an
   exact-diagonalisation reference for the continuum amplitude.
+* ``evolution`` -- the evolution-operator matrix of Sec. 5 and its spectrum.
+* ``proposal`` -- the learned proposal's network, loss and paths in numpy.
+* ``general_v`` -- W_p of a general potential in the derivative symbols
+  V_j (Sec. 3.1) and the derivatives of its families.
+* ``many_body`` -- the contracted W_{m,k} of a system of d = D x M
+  coordinates (Sec. 2.2, Eq. MBrec, Eq. DIA) and its Monte Carlo weights.
 
 It shares no code with the CUDA path; only ``workloads`` (seeded input
 definitions, none of the method's arithmetic) serves both.
