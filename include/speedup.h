@@ -69,7 +69,7 @@ extern "C" {
 #define SU_FP64  0   /* everything in double                                   */
 #define SU_FP32  1   /* path and W_p in float, log-sum-exp reductions in double */
 
-#define SU_MAX_P 32  /* highest effective-action level                         */
+#define SU_MAX_P 144 /* highest effective-action level (Sec. 3.3: AHO to 144)   */
 #define SU_MAX_S 10  /* deepest bisection level, N <= 1024                     */
 
 typedef struct {

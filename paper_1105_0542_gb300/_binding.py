@@ -18,7 +18,7 @@ SU_OK, SU_EINVAL, SU_ENOMEM, SU_ECUDA, SU_ETIMEOUT, SU_ENONFINITE, SU_ENOTSUP = 
 MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4, "general": 5}
 GENERAL_MAX_P = 12
 PRECISIONS = {"fp64": 0, "fp32": 1}
-MAX_P, MAX_S = 32, 10
+MAX_P, MAX_S = 144, 10
 
 EXPORTS = [
     "su_options_default", "su_last_error", "su_version", "speedup_amplitude",
@@ -297,7 +297,7 @@ def speedup_amplitude_noalloc(model, params, a, b, T, p, s, n_mc, seed, **kw):
 def speedup_generate_coeffs(model, params, p, eps):
     """(P, ncol, ring, lens): W_p = sum_j xb^(2j) sum_i P_ij z^i (see speedup.h)."""
     pr, npar = _params(params)
-    cap = 4096
+    cap = 1 << 14
     tab = (ctypes.c_double * cap)()
     shape = (ctypes.c_int * (MAX_P + 2))()
     nt = ctypes.c_int(0)

@@ -416,6 +416,11 @@ static int configure(su_plan &pl) {
         pl.smem = sampler_smem_bytes(P, prec);
         return pl.smem > (size_t)smem_max ? 0 : sampler_occupancy(P, prec, pl.smem);
     };
+    // tables too large to stage next to the rest (the highest levels) are
+    // read from global memory instead
+    P.rounds = 1;
+    P.tab_global = 0;
+    if (sampler_smem_bytes(P, prec) > (size_t)smem_max) P.tab_global = 1;
     const int occ1 = shape(1);
     if (pl.smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);

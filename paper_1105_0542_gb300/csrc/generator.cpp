@@ -153,7 +153,7 @@ int build_effective(int model, const double *params, int n_params, int p, Effect
         err = m;
         return SU_EINVAL;
     };
-    if (p < 1 || p > SU_MAX_P) return bad("p must be in 1..32");
+    if (p < 1 || p > SU_MAX_P) return bad("p must be in 1..144");
     if (n_params < 0 || (n_params > 0 && !params)) return bad("params missing");
     for (int i = 0; i < n_params; ++i)
         if (!std::isfinite(params[i])) return bad("non-finite potential parameter");

@@ -152,7 +152,7 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     const int C = 1 << (P.S - P.F);
     size_t off = P.w_out ? 0 : rs * (size_t)P.levels * kThreads * P.rounds;
     off = (off + 15) & ~(size_t)15;
-    if (P.ring != RING_GENERAL) off += rs * (size_t)P.S * P.M;   // general tables stay in global memory
+    if (P.ring != RING_GENERAL && !P.tab_global) off += rs * (size_t)P.S * P.M;   // else read from global memory
     off += rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;

@@ -50,6 +50,7 @@ struct SamplerParams {
     // effective potential tables: row d (level n = S - d), M entries each
     int ring, ncol, M;
     int len[SU_MAX_P];
+    int tab_global;           // 1: the level tables are read from global memory (too large to stage)
     double alpha;
     const void *tables;       // device, levels * M elements of the kernel's precision
     // Philox stream

@@ -699,10 +699,10 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(co
     R *sw = reinterpret_cast<R *>(smem_raw);
     size_t off = per_sample ? 0 : sizeof(R) * (size_t)L * chunk;
     off = (off + 15) & ~(size_t)15;
-    // the general program's level tables (thousands of entries per level)
-    // stay in global memory: every lane reads the same entry, one broadcast
-    // load through L1
-    constexpr bool kStage = RING != RING_GENERAL;
+    // the general program's level tables (thousands of entries per level),
+    // and any tables too large to stage (levels p >~ 100), stay in global
+    // memory: every lane reads the same entry, one broadcast load through L1
+    const bool kStage = RING != RING_GENERAL && !P.tab_global;
     R *tab_s = reinterpret_cast<R *>(smem_raw + off);
     const R *tab = kStage ? tab_s : reinterpret_cast<const R *>(P.tables);
     off += kStage ? sizeof(R) * (size_t)P.S * P.M : 0;

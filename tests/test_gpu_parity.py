@@ -110,6 +110,7 @@ CASES = [
     ("mpt", [3.0, 1.0], -1.0, 1.0, 5.0, 6, 7, 150, 3, 0),
     ("aho", [1.0, 10.0], 0.0, 1.0, 1.0, 21, 10, 96, 1234, 0),     # levels above the convergence sweep
     ("aho", [1.0, 48.0], 0.0, 0.5, 0.5, 32, 8, 64, 7, 5000),
+    ("aho", [1.0, 48.0], 0.0, 0.5, 0.5, 48, 6, 64, 3, 0),         # p = 48: exact oracle in ~10 s
     ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], -0.5, 0.7, 0.8, 5, 5, 140, 8, 0),
     ("poly", [0.0, 1.0, 0.5], 0.3, -0.2, 1.5, 3, 9, 64, 8, 0),
     ("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 6, 1, 65, 2, 0),
@@ -289,3 +290,14 @@ def test_fp32_and_fp64_means_agree(name, params, T, levels):
         s = math.hypot(r64[lev]["err"], r32[lev]["err"])
         assert math.isfinite(r64[lev]["amp"]) and math.isfinite(s)
         assert abs(r64[lev]["amp"] - r32[lev]["amp"]) <= 4 * s, lev
+
+
+def test_highest_levels_read_their_tables_from_global_memory():
+    """p = 144 at s = 10 does not fit its tables in shared memory and reads
+    them from global memory; its converged levels (eps <= T/64) equal the
+    staged p = 96 ones sample by sample."""
+    wg = _gpu_w("aho", [1.0, 48.0], 0.0, 0.5, 1.0, 144, 10, 64, 5, precision="fp64")
+    ws = _gpu_w("aho", [1.0, 48.0], 0.0, 0.5, 1.0, 96, 10, 64, 5, precision="fp64")
+    top = slice(5, 10)
+    scale = np.maximum(np.abs(ws[:, top]), np.median(np.abs(ws[:, top]), axis=0))
+    assert float(np.max(np.abs(wg[:, top] - ws[:, top]) / scale)) <= 1e-12

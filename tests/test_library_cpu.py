@@ -78,6 +78,8 @@ def _exact_collapse(name, params, p, eps):
     ("aho", [-10.0, 12.0], 21, 0.1),
     ("aho", [1.0, 10.0], 32, 1.0 / 64),
     ("dw", [1.0], 24, 0.25),
+    ("aho", [1.0, 48.0], 48, 0.02),          # levels beyond the convergence sweep
+    ("mpt", [3.0, 1.0], 24, 1.0 / 64),
 ])
 def test_generator_matches_oracle_exact_collapse(name, params, p, eps):
     P, ncol, ring, lens = su.speedup_generate_coeffs(name, params, p, eps)
@@ -101,6 +103,46 @@ def test_generator_matches_oracle_exact_collapse(name, params, p, eps):
             assert j < ncol
 
 
+def _eval_table(P, ncol, ring, lens, x, xb, alpha=1.0):
+    import mpmath as mp
+    z = {0: mp.mpf(x) ** 2, 1: mp.mpf(x), 2: mp.tanh(alpha * mp.mpf(x)) ** 2}[ring]
+    tot, tabs, off = mp.mpf(0), mp.mpf(0), 0
+    for j in range(ncol):
+        for i in range(lens[j]):
+            t = mp.mpf(P[off + i]) * z ** i * mp.mpf(xb) ** (2 * j)
+            tot += t
+            tabs += abs(t)
+        off += lens[j]
+    return tot, tabs
+
+
+def test_generator_at_the_paper_s_highest_levels():
+    """p = 144 (the anharmonic oscillator's highest level of Sec. 3.3): the
+    harmonic oscillator's collapsed table equals its closed-form W (the
+    Mehler kernel, 50 digits) to the table's rounding; the anharmonic
+    oscillator's p = 144 table equals its p = 96 one where both have
+    converged; the Poeschl-Teller p = 41 table is finite."""
+    import mpmath as mp
+    mp.mp.dps = 50
+    w, eps = 1.3, 0.25
+    P, ncol, ring, lens = su.speedup_generate_coeffs("ho", [w], 144, eps)
+    for x, xb in ((0.3, 0.1), (-1.2, 0.4), (2.0, -0.05)):
+        got, scale = _eval_table(P, ncol, ring, lens, x, xb)
+        we = mp.mpf(w) * eps
+        sh, ch = mp.sinh(we), mp.cosh(we)
+        ref = ((w / sh) * (x * x * (ch - 1) + xb * xb * (ch + 1)) - 2 * mp.mpf(xb) ** 2 / eps) / eps \
+            + mp.log(sh / we) / (2 * eps)
+        assert abs(got - ref) <= 1e-14 * scale, (x, xb, got, ref)
+    a = su.speedup_generate_coeffs("aho", [1.0, 48.0], 144, 0.02)
+    b = su.speedup_generate_coeffs("aho", [1.0, 48.0], 96, 0.02)
+    for x, xb in ((0.4, 0.05), (-0.9, 0.1)):
+        ga, sa = _eval_table(*a, x, xb)
+        gb, sb = _eval_table(*b, x, xb)
+        assert abs(ga - gb) <= 1e-13 * max(sa, sb)
+    m = su.speedup_generate_coeffs("mpt", [3.0, 1.0], 41, 1.0 / 64)
+    assert np.isfinite(m[0]).all() and len(m[0]) > 1000
+
+
 def test_generator_term_counts_of_the_anharmonic_oscillator():
     counts = [len(su.speedup_generate_coeffs("aho", [1.0, 10.0], p, 0.1)[0]) for p in (4, 10, 12, 18)]
     assert counts == [8, 21, 27, 48]
@@ -108,7 +150,7 @@ def test_generator_term_counts_of_the_anharmonic_oscillator():
 
 @pytest.mark.parametrize("args,kw", [
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 0, 4, 100, 1), {}),        # p = 0
-    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 33, 4, 100, 1), {}),       # p = 33
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 145, 4, 100, 1), {}),      # p = 145
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 11, 100, 1), {}),       # s = 11
     (("aho", [1.0, 1.0], 0.0, 1.0, 0.0, 4, 4, 100, 1), {}),        # T = 0
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 0, 1), {}),          # n_mc = 0
@@ -147,7 +189,7 @@ def test_level_zero_needs_no_sampling_but_still_a_plan():
             su.speedup_amplitude("ho", [1.0], 0.0, 1.0, 1.0, 4, 0, 10, 1)
 
 
-@pytest.mark.parametrize("kw", [{"t": 0.0}, {"L": -1.0}, {"n": 1}, {"n": 70000}, {"p": 33}])
+@pytest.mark.parametrize("kw", [{"t": 0.0}, {"L": -1.0}, {"n": 1}, {"n": 70000}, {"p": 145}])
 def test_evolution_matrix_rejects_bad_arguments(kw):
     args = {"model": "aho", "params": [1.0, 1.0], "p": 4, "t": 0.1, "L": 5.0, "n": 100}
     args.update(kw)
