@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no FP64 tensor path); see DESIGN
 # DRAM bytes (read + write) of one double-sampler launch of the p = 10 sweep
 # point on 2e5 samples, from the ncu capture summarised in
 # profiles/sampler_fp64_aho-g10_p10_s10_2e5.md; scaled by samples per launch
-FP64_TRAFFIC_BYTES, FP64_TRAFFIC_SAMPLES = 318_208, 200_000
+FP64_TRAFFIC_BYTES, FP64_TRAFFIC_SAMPLES = 559_872, 200_000
 CPU_BUDGET_S = 15.0
 
 
@@ -58,11 +58,13 @@ def parse():
     ap.add_argument("--no-evolution", action="store_true", help="skip the evolution-operator (Fig. 3) entry")
     ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
     ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
-    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal"], default=None,
+    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "general"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
                          "every 16th instance of the amplitude matrix; proposal = the learned-proposal "
-                         "instance with a fixed random network (--profile-n samples)")
+                         "instance with a fixed random network (--profile-n samples); nd = the 2D anharmonic "
+                         "oscillator, p = 10, s = 10; general = AHO g = 10 through the general-potential mode, "
+                         "p = 10, s = 10 (--profile-n samples)")
     ap.add_argument("--profile-p", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=200_000)
     return ap.parse_args()
@@ -713,6 +715,21 @@ def run_profile(args):
             r = su.speedup_amplitude_proposal(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, args.profile_n,
                                               x.seed, P, n_blocks=100)
         print(f"profile case proposal n={args.profile_n}: A_64 = {r[x.s]['amp']:.6g}, ess {r[x.s]['ess']:.4g}")
+        return
+    if args.profile in ("nd", "general"):
+        if args.profile == "nd":
+            V = {(2, 0): 0.5, (0, 2): 0.5, (4, 0): 1 / 24, (0, 4): 1 / 24, (2, 2): 1 / 12}
+            pl = su.PlanND(V, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10, args.profile_n, 1234, n_blocks=64)
+        else:
+            gp = list(su.general_params((0.0, 0.0, 0.5, 0.0, 10.0 / 24.0)))
+            pl = su.Plan("general", gp, 0.0, 1.0, 1.0, 10, 10, args.profile_n, 1234, n_blocks=64)
+        t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device="cuda")
+        sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            pl.su_plan_execute(t, sc)
+        torch.cuda.synchronize()
+        res = pl.su_plan_finalize(t.cpu().numpy(), sc)
+        print(f"profile case {args.profile} n={args.profile_n}: A_1024 = {res[10]['amp']:.10g}")
         return
     inst = workloads.config2(args.profile_p)
     pl = su.Plan(inst.model, inst.params, inst.a, inst.b, inst.T, args.profile_p, inst.s, args.profile_n,
