@@ -617,10 +617,49 @@ def run_batched(su, torch, dev, stream, flush):
     ms = e0.elapsed_time(e1)
     res = pl.su_batch_plan_finalize(t.cpu().numpy(), sc)
     rel = sorted(r["rel_err"] for r in res if r["level"] > 0 and r["amp"] > 0)
+    med = rel[len(rel) // 2] if rel else None
+    # the plain GPU method on the same instances: one plan per instance (top
+    # level only, as the batch), executed one after another (every 256th
+    # instance, extrapolated by slice-actions), in single precision (batching
+    # alone) and in double precision (the plain method)
+    sub = inst[::256]
+    per = {}
+    for prec in ("fp32", "fp64"):
+        plans = [su.Plan("aho", [1.0, 1.0], x.a, x.b, x.T, 10, x.s, x.n_mc, x.seed, precision=prec,
+                         n_blocks=x.n_blocks, instance=x.instance, hierarchy=False) for x in sub]
+        bufs = [(torch.empty(q.tuple_bytes // 8, dtype=torch.float64, device=dev),
+                 torch.empty(q.scratch_bytes, dtype=torch.uint8, device=dev)) for q in plans]
+        for q, (tt, ss) in zip(plans, bufs):
+            q.su_plan_execute(tt, ss, stream)
+        flush.zero_()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for q, (tt, ss) in zip(plans, bufs):
+            q.su_plan_execute(tt, ss, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        sub_ms = f0.elapsed_time(f1)
+        sub_sa = sum(q.slice_actions for q in plans)
+        rr = sorted(q.su_plan_finalize(tt.cpu().numpy(), ss)[q.s]["rel_err"] for q, (tt, ss) in zip(plans, bufs)
+                    if q.s > 0)
+        per[prec] = {"sample_instances": len(sub), "sample_ms": sub_ms,
+                     "extrapolated_ms": sub_ms * pl.slice_actions / max(sub_sa, 1),
+                     "median_rel_err": rr[len(rr) // 2] if rr else None}
+        del plans, bufs
+    ttr = lambda t_ms, r: (t_ms / 1e3) * (r / 1e-4) ** 2 if r else None  # noqa: E731
+    t_b = ttr(ms, med)
+    t32 = ttr(per["fp32"]["extrapolated_ms"], per["fp32"]["median_rel_err"])
+    t64 = ttr(per["fp64"]["extrapolated_ms"], per["fp64"]["median_rel_err"])
     return {"instances": len(tup), "slice_actions": pl.slice_actions, "ms": ms,
             "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "graph_launches": n,
-            "plan_create_s": create_s, "median_rel_err": rel[len(rel) // 2] if rel else None,
-            "dtype": "f32 W_p, f64 reductions"}
+            "plan_create_s": create_s, "median_rel_err": med,
+            "dtype": "f32 W_p, f64 reductions",
+            "per_instance_plans": per,
+            "time_to_rel_1e-4_s": {"batched_fp32": t_b, "per_instance_fp32": t32, "plain_fp64": t64,
+                                   "speedup_batching": (t32 / t_b) if t_b and t32 else None,
+                                   "speedup_vs_plain": (t64 / t_b) if t_b and t64 else None,
+                                   "method": "matrix time x (median top-level rel_err / 1e-4)^2; per-instance "
+                                             "times from every 256th instance, scaled by slice-actions"}}
 
 
 def _init_theta(seed):
