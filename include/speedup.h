@@ -339,8 +339,8 @@ int su_plan_destroy(su_plan *plan);
  * destroyed by the su_plan_* calls above.  A_free is the product of the d
  * one-dimensional free amplitudes.  Coordinate c of bisection midpoint j
  * takes normal j d + c of the sample's stream (speedup_normals layout).  The
- * scratch (su_plan_sizes) also holds every resident thread's path:
- * grid x 128 x (2^s + 1) x d doubles.
+ * scratch (su_plan_sizes) also holds every resident thread's path segment
+ * endpoints: grid x 128 x (2^max(s-5, 0) + 1) x d doubles.
  */
 int su_plan_create_nd(int d, const int *exps, const double *coefs, int n_terms,
                       const double *a, const double *b, double T, int p, int s,

@@ -383,8 +383,9 @@ static int configure(su_plan &pl) {
     su_tuning tuned{};
     const bool have_tuned = tuned_shape(prec, pl.model, pl.p, S, tuned);
     // rule: 16-slice register segments in double (measured 1-5 % faster than
-    // 32 at 2 CTAs per SM), 32 in single precision
-    const int seg_rule = prec == SU_FP64 ? 4 : kMaxFine;
+    // 32 at 2 CTAs per SM), 32 in single precision and for the general
+    // potential (4 CTAs per SM; 32 beat 8 and 16 by 25 % and 11 % at N = 1024)
+    const int seg_rule = (general || prec != SU_FP64) ? kMaxFine : 4;
     int seg = pl.opt.seg_log2 > 0 ? pl.opt.seg_log2 : (have_tuned ? tuned.seg_log2 : seg_rule);
     P.S = S;
     P.F = std::min(S, std::max(1, seg));
@@ -566,7 +567,7 @@ static int configure_nd(su_plan &pl) {
     if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
     pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
     Q.pstride = (int64_t)pl.grid * kThreads;
-    pl.path_bytes = Q.pstride * (((int64_t)1 << S) + 1) * pl.nd * (int64_t)sizeof(double);
+    pl.path_bytes = Q.pstride * (((int64_t)1 << (S - std::min(S, kNdSeg))) + 1) * pl.nd * (int64_t)sizeof(double);
     pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
     pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + ((pl.path_bytes + 255) / 256) * 256 + 256;
     pl.tuple_bytes = pl.n_blocks * pl.levels * 4 * (int64_t)sizeof(double);

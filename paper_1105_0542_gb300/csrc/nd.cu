@@ -55,7 +55,8 @@ __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double 
     wb = acc_b;
 }
 
-// Shared memory: sw[levels][kThreads] (double, reduced runs) | Box-Muller node tables
+// Shared memory: sw[levels][kThreads] (double, reduced runs) | Box-Muller node tables.
+// Global scratch per slot: the 2^(S-F) + 1 segment endpoints (F = min(S, kNdSeg)).
 template <int D>
 __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__ NdParams Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,8 +76,13 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
     st.inst = P.instance;
     st.bm = bm_smem;
     const int64_t ps = Q.pstride;
-    double *q = Q.paths + (int64_t)blockIdx.x * kThreads + tid;   // this slot's points
-    auto at = [&](int i, int c) -> double & { return q[((int64_t)i * D + c) * ps]; };
+    // the path in segments of 2^F slices: the C + 1 segment endpoints (the
+    // coarse levels' points) in this slot of the global scratch, one
+    // segment's points at a time in local memory
+    const int F = min(S, kNdSeg), Cn = S - F, C = 1 << Cn, NF = 1 << F;
+    double *q = Q.paths + (int64_t)blockIdx.x * kThreads + tid;
+    auto co = [&](int i, int c) -> double & { return q[((int64_t)i * D + c) * ps]; };
+    double seg[((1 << kNdSeg) + 1) * D];
 
     for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t b = item / P.items_per_block;
@@ -89,42 +95,39 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
             const uint64_t sample = (uint64_t)(P.sample0 + start + tid);
             st.slo = (uint32_t)sample;
             st.shi = (uint32_t)(sample >> 32);
-            for (int c = 0; c < D; ++c) {
-                at(0, c) = Q.a[c];
-                at(N, c) = Q.b[c];
-            }
-            // bisection, level by level; normals in Box-Muller pairs
-            uint32_t have = 0xffffffffu;
+            uint32_t have = 0xffffffffu;   // the Box-Muller pair last drawn
             double z0 = 0.0, z1 = 0.0;
-            for (int n = 1; n <= S; ++n) {
+            auto normal = [&](uint32_t g) {
+                if ((g >> 1) != have) {
+                    st.pair(g >> 1, z0, z1);
+                    have = g >> 1;
+                }
+                return (g & 1u) ? z1 : z0;
+            };
+            // coarse levels n = 1..S-F: midpoint i at segment endpoint (2i+1) 2^(S-F-n)
+            for (int c = 0; c < D; ++c) {
+                co(0, c) = Q.a[c];
+                co(C, c) = Q.b[c];
+            }
+            for (int n = 1; n <= Cn; ++n) {
                 const double sg = P.sigma[n];
-                const int h = 1 << (S - n);
-                const int j0 = (1 << (n - 1)) - 1;
+                const int h = 1 << (Cn - n), j0 = (1 << (n - 1)) - 1;
                 for (int i = 0; i < (1 << (n - 1)); ++i) {
                     const int idx = (2 * i + 1) * h;
-                    for (int c = 0; c < D; ++c) {
-                        const uint32_t g = (uint32_t)((j0 + i) * D + c);
-                        if ((g >> 1) != have) {
-                            st.pair(g >> 1, z0, z1);
-                            have = g >> 1;
-                        }
-                        const double z = (g & 1u) ? z1 : z0;
-                        at(idx, c) = fma(sg, z, 0.5 * (at(idx - h, c) + at(idx + h, c)));
-                    }
+                    for (int c = 0; c < D; ++c)
+                        co(idx, c) = fma(sg, normal((uint32_t)((j0 + i) * D + c)), 0.5 * (co(idx - h, c) + co(idx + h, c)));
                 }
             }
-            // w_n = -eps_n sum_k W on the level-n subpath; level n = S - dl
+            // w_n = -eps_n sum_k W on the level-n subpath (level n = S - dl),
+            // slices in ascending order, two at a time
             double wloc[SU_MAX_S];
-            bool bad = false;
-            for (int dl = 0; dl < L; ++dl) {
-                const int stp = 1 << dl, ns = 1 << (S - dl);
-                const double *tab = reinterpret_cast<const double *>(P.tables) + (size_t)dl * P.M;
-                double w = 0.0;
+            for (int dl = 0; dl < L; ++dl) wloc[dl] = 0.0;
+            auto slices = [&](const double *tab, auto &&pt, int stp, int ns, double &w) {
                 for (int k = 0; k < ns; k += 2) {
                     double za[2 * D], zb[2 * D];
 #pragma unroll
                     for (int c = 0; c < D; ++c) {
-                        const double pl = at(k * stp, c), pm = at((k + 1) * stp, c), pr = at((k + 2) * stp, c);
+                        const double pl = pt(k * stp, c), pm = pt((k + 1) * stp, c), pr = pt((k + 2) * stp, c);
                         za[c] = 0.5 * (pl + pm);
                         za[D + c] = 0.5 * (pm - pl);
                         zb[c] = 0.5 * (pm + pr);
@@ -134,9 +137,32 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
                     nd_pair<D>(za, zb, tab, Q, wa, wb);
                     w += wa + wb;
                 }
-                wloc[dl] = w;
-                bad |= isnan(w) || (isinf(w) && w > 0);
+            };
+            const double *tabs = reinterpret_cast<const double *>(P.tables);
+            for (int dl = F; dl < L; ++dl)   // coarse levels: between segment endpoints
+                slices(tabs + (size_t)dl * P.M, co, 1 << (dl - F), 1 << (S - dl), wloc[dl]);
+            // fine levels n = S-F+1..S, one segment at a time
+            auto fp = [&](int i, int c) -> double & { return seg[i * D + c]; };
+            for (int sgi = 0; sgi < C; ++sgi) {
+                for (int c = 0; c < D; ++c) {
+                    fp(0, c) = co(sgi, c);
+                    fp(NF, c) = co(sgi + 1, c);
+                }
+                for (int n = Cn + 1; n <= S; ++n) {
+                    const double sg = P.sigma[n];
+                    const int h = 1 << (S - n), m = 1 << (n - Cn - 1);
+                    const int j0 = (1 << (n - 1)) - 1 + sgi * m;
+                    for (int il = 0; il < m; ++il) {
+                        const int idx = (2 * il + 1) * h;
+                        for (int c = 0; c < D; ++c)
+                            fp(idx, c) = fma(sg, normal((uint32_t)((j0 + il) * D + c)), 0.5 * (fp(idx - h, c) + fp(idx + h, c)));
+                    }
+                }
+                for (int dl = 0; dl < min(F, L); ++dl)
+                    slices(tabs + (size_t)dl * P.M, fp, 1 << dl, NF >> dl, wloc[dl]);
             }
+            bool bad = false;
+            for (int dl = 0; dl < L; ++dl) bad |= isnan(wloc[dl]) || (isinf(wloc[dl]) && wloc[dl] > 0);
             if (bad) atomicOr(P.flags, 1);
             if (per_sample) {
                 double *dst = P.w_out + (start + tid) * (int64_t)S;

@@ -107,16 +107,18 @@ cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *
 
 // Systems of d = D x M coordinates (Sec. 2.2): one bisection path per
 // thread, every coordinate an exact Brownian bridge (coordinate c of heap
-// midpoint j takes normal j D + c of the sample's stream), its points in a
-// global scratch array; W(x, xb; eps) per slice from the monomial program of
+// midpoint j takes normal j D + c of the sample's stream), built and weighed
+// in segments of 2^kNdSeg slices (segment endpoints in a global scratch, one
+// segment's points in local memory); W(x, xb; eps) per slice from the monomial program of
 // NdEffective (nodes as GeneralNode; entries = powers of z_H), two slices at
 // a time; weights and per-item tuples as the one-dimensional sampler's.
+constexpr int kNdSeg = 5;     // the several-coordinates path in segments of 2^5 slices
 struct NdParams {
     SamplerParams base;       // S, levels, tables (per level, global), M, sigma, stream, items, outputs
     int D, H, G, n_nodes;     // Horner in z_H^G
     const GeneralNode *nodes; // device
     double a[kNdMaxDim], b[kNdMaxDim];
-    double *paths;            // device: point i, coordinate c of slot t at [(i D + c) pstride + t]
+    double *paths;            // device: segment endpoint i, coordinate c of slot t at [(i D + c) pstride + t]
     int64_t pstride;          // slots = grid x kThreads
 };
 size_t nd_smem_bytes(const NdParams &Q);

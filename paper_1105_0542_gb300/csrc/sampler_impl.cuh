@@ -682,13 +682,19 @@ __device__ __forceinline__ void item_lse(const R *sw, int L, int chunk, int cnt,
 // (up to 255 registers: its segment, accumulators and Box-Muller state stay
 // in registers; three CTAs at 168 registers spill and run slower), four for
 // the single path (128 registers)
-template <typename R>
+template <typename R, int RING = RING_EVEN>
 struct MinCtas {
     static constexpr int value = sizeof(R) == 8 ? 2 : 4;
 };
+// the general-potential evaluator keeps its derivatives and monomial stacks in
+// local memory: more warps to hide their latency, shorter register segments
+template <>
+struct MinCtas<double, RING_GENERAL> {
+    static constexpr int value = 4;
+};
 
 template <typename R, int RING>
-__global__ void __launch_bounds__(kThreads, MinCtas<R>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
+__global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int L = P.levels;
