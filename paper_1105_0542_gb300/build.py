@@ -19,7 +19,9 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libspeedup_gb300.so")
 SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu", "nd.cu"]
 # the sampler kernel, once per (precision, ring): compiled in parallel
-INSTANCES = [(prec, ring) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3)]
+INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3, 0)]
+# double-precision samplers that read tables too large for shared memory from global memory
+INSTANCES += [(64, ring, 1) for ring in (0, 1, 2)]
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",
            "proposal.h", "train.h", "philox.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -67,7 +69,8 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    jobs = [(os.path.join(CSRC, "sampler_inst.cu"), {"SU_PREC": p, "SU_RING": r}) for p, r in INSTANCES]
+    jobs = [(os.path.join(CSRC, "sampler_inst.cu"), {"SU_PREC": p, "SU_RING": r, "SU_GTAB": g})
+            for p, r, g in INSTANCES]
     jobs += [(os.path.join(CSRC, f), {}) for f in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         results = list(ex.map(lambda j: _compile(j, verbose), jobs))

@@ -421,7 +421,10 @@ static int configure(su_plan &pl) {
     // read from global memory instead
     P.rounds = 1;
     P.tab_global = 0;
-    if (sampler_smem_bytes(P, prec) > (size_t)smem_max) P.tab_global = 1;
+    if (sampler_smem_bytes(P, prec) > (size_t)smem_max) {
+        if (prec != SU_FP64) return fail(SU_ENOTSUP, "the level tables do not fit shared memory in single precision");
+        P.tab_global = 1;
+    }
     const int occ1 = shape(1);
     if (pl.smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);

@@ -18,6 +18,9 @@ const void *sampler_entry_f32_0();
 const void *sampler_entry_f32_1();
 const void *sampler_entry_f32_2();
 const void *sampler_entry_f64_3();
+const void *sampler_entry_gt_f64_0();
+const void *sampler_entry_gt_f64_1();
+const void *sampler_entry_gt_f64_2();
 const void *batch_entry_f64_0();
 const void *batch_entry_f64_1();
 const void *batch_entry_f64_2();
@@ -123,6 +126,11 @@ __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_
 
 const void *pick(const SamplerParams &P, int precision) {
     if (P.ring == RING_GENERAL) return precision == SU_FP64 ? sampler_entry_f64_3() : nullptr;
+    if (P.tab_global) {
+        if (precision != SU_FP64) return nullptr;
+        return P.ring == RING_EVEN ? sampler_entry_gt_f64_0() : P.ring == RING_X ? sampler_entry_gt_f64_1()
+                                                                                  : sampler_entry_gt_f64_2();
+    }
     if (precision == SU_FP32)
         return P.ring == RING_EVEN ? sampler_entry_f32_0() : P.ring == RING_X ? sampler_entry_f32_1() : sampler_entry_f32_2();
     return P.ring == RING_EVEN ? sampler_entry_f64_0() : P.ring == RING_X ? sampler_entry_f64_1() : sampler_entry_f64_2();

@@ -693,7 +693,7 @@ struct MinCtas<double, RING_GENERAL> {
     static constexpr int value = 4;
 };
 
-template <typename R, int RING>
+template <typename R, int RING, bool GTAB = false>
 __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     // the general program's level tables (thousands of entries per level),
     // and any tables too large to stage (levels p >~ 100), stay in global
     // memory: every lane reads the same entry, one broadcast load through L1
-    const bool kStage = RING != RING_GENERAL && !P.tab_global;
+    constexpr bool kStage = RING != RING_GENERAL && !GTAB;
     R *tab_s = reinterpret_cast<R *>(smem_raw + off);
     const R *tab = kStage ? tab_s : reinterpret_cast<const R *>(P.tables);
     off += kStage ? sizeof(R) * (size_t)P.S * P.M : 0;

@@ -1,8 +1,10 @@
 // One instantiation of the sampler and batched kernels, selected at compile time:
 //   SU_PREC = 64 or 32 (double / float path and W_p), SU_RING = 0, 1, 2
 //   (z = x^2, x, sech^2(alpha x)) or 3 (a general potential through its
-//   derivatives; double sampler only).  The build compiles this file once per
-// pair so the kernels compile in parallel.
+//   derivatives; double sampler only); SU_GTAB = 1 for the double sampler
+//   that reads level tables too large for shared memory from global memory.
+// The build compiles this file once per combination so the kernels compile
+// in parallel.
 #include "sampler_impl.cuh"
 
 #ifndef SU_PREC
@@ -10,6 +12,9 @@
 #endif
 #ifndef SU_RING
 #error "SU_RING must be 0, 1, 2 or 3"
+#endif
+#ifndef SU_GTAB
+#define SU_GTAB 0
 #endif
 
 #define SU_CAT2(a, b, c) a##b##_##c
@@ -22,11 +27,18 @@ using Real = double;
 using Real = float;
 #endif
 
+#if SU_GTAB
+// the level tables read from global memory (too large to stage)
+const void *SU_CAT(sampler_entry_gt_f, SU_PREC, SU_RING)() {
+    return (const void *)sampler_kernel<Real, SU_RING, true>;
+}
+#else
 const void *SU_CAT(sampler_entry_f, SU_PREC, SU_RING)() {
     return (const void *)sampler_kernel<Real, SU_RING>;
 }
+#endif
 
-#if SU_RING != 3
+#if SU_RING != 3 && !SU_GTAB
 const void *SU_CAT(batch_entry_f, SU_PREC, SU_RING)() {
     return (const void *)batch_kernel<Real, SU_RING>;
 }
