@@ -136,3 +136,15 @@ def test_general_amplitude_matches_dvr():
     sig = max(top["err"], top["err_naive"])
     assert sig < 0.01 * ref
     assert abs(top["amp"] - ref) <= 4 * sig, (top["amp"], ref, sig)
+
+
+def test_general_edge_cases():
+    """s = 0 is the analytic level 0; the hierarchy off gives the same top
+    level as the hierarchy on (same stream)."""
+    a, b, T, p = -0.5, 0.7, 1.0, 8
+    r0 = su.speedup_amplitude("general", P_MIXED, a, b, T, p, 0, 10, 1)
+    w0 = -T * float(gv.wp(P_MIXED, p, 0.5 * (a + b), 0.5 * (b - a), T))
+    assert r0[0]["log_amp"] == pytest.approx(mc.log_A_free(a, b, T) + w0, rel=1e-13)
+    on = su.speedup_amplitude("general", P_MIXED, a, b, T, p, 6, 5000, 9, n_blocks=10)
+    off = su.speedup_amplitude("general", P_MIXED, a, b, T, p, 6, 5000, 9, n_blocks=10, hierarchy=False)
+    assert off[6]["amp"] == on[6]["amp"] and off[6]["err"] == on[6]["err"]

@@ -157,3 +157,18 @@ def test_separable_anharmonic_oscillator_matches_the_product_of_dvr_amplitudes()
     sig = max(top["err"], top["err_naive"])
     assert sig < 0.01 * Ax * Ay
     assert abs(top["amp"] - Ax * Ay) <= 4 * sig, (top["amp"], Ax * Ay, sig)
+
+
+def test_nd_edge_cases():
+    """s = 0 is the analytic level 0; a single sample; the hierarchy off
+    gives the same top level as the hierarchy on (same stream)."""
+    V, a, b, T, p = GEN2, (0.2, -0.1), (0.4, 0.3), 0.7, 6
+    r0 = su.speedup_amplitude_nd(V, a, b, T, p, 0, 10, 1)
+    w0 = mb.level0(_frac(V), 2, p, np.array(a), np.array(b), T)
+    laf = mb.log_A_free(np.array(a), np.array(b), T)
+    assert r0[0]["log_amp"] == pytest.approx(laf + w0, rel=1e-13)
+    r1 = su.speedup_amplitude_nd(V, a, b, T, p, 3, 1, 5)
+    assert r1[3]["n"] == 1 and np.isfinite(r1[3]["amp"])
+    on = su.speedup_amplitude_nd(V, a, b, T, p, 7, 5000, 9, n_blocks=10)
+    off = su.speedup_amplitude_nd(V, a, b, T, p, 7, 5000, 9, n_blocks=10, hierarchy=False)
+    assert off[7]["amp"] == on[7]["amp"] and off[7]["err"] == on[7]["err"]

@@ -309,3 +309,15 @@ def test_nd_generator_term_limit():
     with pytest.raises(su.SpeedupError) as e:
         su.speedup_generate_nd({(2,): 1.0}, 0, 0.1)
     assert e.value.code == -1
+
+
+def test_nd_table_fault_fails_before_any_device_work():
+    su.su_fault_inject("table_nan")
+    try:
+        with pytest.raises(su.SpeedupError) as e:
+            su.speedup_amplitude_nd({(2, 0): 0.5, (0, 2): 0.5}, (0.0, 0.0), (1.0, 1.0), 1.0, 4, 3, 100, 1)
+        assert e.value.code == -5
+    finally:
+        su.su_fault_inject("clear")
+    with pytest.raises(ValueError):
+        su.speedup_amplitude_nd({(2, 0): 0.5}, (0.0,), (1.0, 1.0), 1.0, 4, 3, 100, 1)
