@@ -14,6 +14,16 @@ namespace {
 // variable, the parent the top of a per-slice stack), each prefix's entries
 // combined by Horner in z_H^G and added times the prefix; the two slices
 // share every node and coefficient load.
+// z[sym] with z in registers: a chain of selects on the integer pipes
+// instead of a dynamically indexed local-memory load
+template <int D>
+__device__ __forceinline__ double pick(const double (&z)[2 * D], int sym) {
+    double v = z[0];
+#pragma unroll
+    for (int i = 1; i < 2 * D; ++i) v = sym == i ? z[i] : v;
+    return v;
+}
+
 template <int D>
 __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double (&zb)[2 * D],
                                         const double *__restrict__ coef, const NdParams &Q, double &wa,
@@ -22,9 +32,10 @@ __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double 
     sa[0] = 1.0;
     sb[0] = 1.0;
     double Ya = 1.0, Yb = 1.0;
+    const double ha = pick<D>(za, Q.H), hb = pick<D>(zb, Q.H);
     for (int g = 0; g < Q.G; ++g) {
-        Ya *= za[Q.H];
-        Yb *= zb[Q.H];
+        Ya *= ha;
+        Yb *= hb;
     }
     double acc_a = 0.0, acc_b = 0.0;
     const GeneralNode *__restrict__ nodes = Q.nodes;
@@ -32,8 +43,8 @@ __device__ __forceinline__ void nd_pair(const double (&za)[2 * D], const double 
         const GeneralNode nd = nodes[t];
         double ma = 1.0, mb = 1.0;
         if (t) {
-            ma = sa[nd.depth - 1] * za[nd.sym];
-            mb = sb[nd.depth - 1] * zb[nd.sym];
+            ma = sa[nd.depth - 1] * pick<D>(za, nd.sym);
+            mb = sb[nd.depth - 1] * pick<D>(zb, nd.sym);
             sa[nd.depth] = ma;
             sb[nd.depth] = mb;
         }
