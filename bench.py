@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-evolution", action="store_true", help="skip the evolution-operator (Fig. 3) entry")
     ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
     ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
+    ap.add_argument("--no-fig2", action="store_true", help="skip the Fig. 2 convergence and continuum-fit entry")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "general"], default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -369,6 +370,9 @@ def run_ours(args):
     several = None
     if not args.no_nd:
         several = run_nd(su, torch, dev, stream, flush)
+    fig2 = None
+    if not args.no_fig2 and rank == 0:
+        fig2 = run_fig2()
 
     if rank != 0:
         if dist is not None:
@@ -412,6 +416,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
         "batched_amplitude_matrix": batched, "learned_proposal": learned, "configs_1_4": small,
         "evolution_operator_fig3": evolution, "general_potential": general, "several_coordinates": several,
+        "fig2_convergence_fit": fig2,
         "clocks": clock_info,
     }
     print(json.dumps(line))
@@ -544,6 +549,24 @@ def run_general(su, torch, dev, stream, flush):
                     "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "amp": top["amp"],
                     "rel_err": top["rel_err"]})
     return {"cases": out, "note": "same Philox stream in the first two cases: their amplitudes agree to rounding"}
+
+
+def run_fig2():
+    """Fig. 2's convergence run: modified Poeschl-Teller lambda = alpha = 1,
+    A(-0.5, 0.5; 1) at every level of one s = 10 run of 1e6 samples for
+    p = 1, 2, 10 (double precision, host API), and the constant of Eq. fit
+    over N = 8..1024 (the GPU tests hold it against a sinc-DVR continuum
+    value)."""
+    import paper_1105_0542_gb300 as su
+    out = []
+    for p in (1, 2, 10):
+        t0 = time.perf_counter()
+        r = su.speedup_amplitude("mpt", [1.0, 1.0], -0.5, 0.5, 1.0, p, 10, 1_000_000, 2011, n_blocks=100)
+        dt = time.perf_counter() - t0
+        A, dA, chi2 = su.su_fit_continuum(r, p, n_min=3, n_terms=3)
+        out.append({"p": p, "s": dt, "levels": [[1 << x["level"], x["amp"], x["err"]] for x in r],
+                    "fit": {"A": A, "A_err": dA, "chi2": chi2, "levels": "N = 8..1024"}})
+    return {"runs": out}
 
 
 def run_nd(su, torch, dev, stream, flush):

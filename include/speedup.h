@@ -164,6 +164,21 @@ int speedup_generate_coeffs(int model, const double *params, int n_params, int p
                             double eps, double *table, int capacity, int *shape,
                             int *n_terms);
 
+/*
+ * su_fit_continuum -- the continuum estimate of Sec. 4 (Eq. fit) from one
+ * run's levels (host only): weighted least squares of
+ *   A_N = A + B / N^p  [+ C / N^(p+1) when n_terms = 3],   N = 2^n,
+ * over the levels n = n_min..s of levels[] (speedup_amplitude's output,
+ * s + 1 entries), weights 1 / err_n^2.  *A = the constant, *A_err its
+ * least-squares standard error (levels of one run share samples, so this
+ * treats them as independent), *chi2 = the weighted residual sum (either may
+ * be NULL).  n_min >= 1 (level 0 has no statistical error); SU_EINVAL when a
+ * used level has no finite positive error or there are fewer levels than
+ * terms.
+ */
+int su_fit_continuum(const su_level_result *levels, int s, int p, int n_min, int n_terms,
+                     double *A, double *A_err, double *chi2);
+
 /* ---- many instances in one persistent launch ------------------------------ */
 
 /* one amplitude A_N^(p)(a,b;T) with N = 2^s of a batch */

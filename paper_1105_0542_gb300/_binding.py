@@ -31,6 +31,7 @@ EXPORTS = [
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
+    "su_fit_continuum",
 ]
 MAX_D = 4
 MLP_PARAMS = 34178
@@ -129,6 +130,7 @@ def load(build_if_missing=True):
     L.speedup_logweights_nd.argtypes = [i32, pi, pd, i32, pd, pd, d, i32, i32, i64, i64, u64,
                                         ctypes.POINTER(Options), vp]
     L.speedup_generate_nd.argtypes = [i32, pi, pd, i32, i32, d, pi, pd, i32, pi]
+    L.su_fit_continuum.argtypes = [ctypes.POINTER(LevelResult), i32, i32, i32, i32, pd, pd, pd]
     L.su_fma_peak.argtypes = [i32, pd]
     pf = ctypes.POINTER(ctypes.c_float)
     L.su_proposal_create.argtypes = [pf, i32, ctypes.POINTER(vp)]
@@ -363,6 +365,21 @@ def speedup_logweights_nd(V, a, b, T, p, s, sample0, n_samples, seed, out, **kw)
     o = options(**kw)
     _check(load().speedup_logweights_nd(d, ex, co, n, _vec(a, d), _vec(b, d), T, p, s, int(sample0),
                                         int(n_samples), int(seed), ctypes.byref(o), _ptr(out)))
+
+
+def su_fit_continuum(levels, p, n_min=1, n_terms=3):
+    """(A, A_err, chi2) of Eq. fit from a list of level results (dicts as
+    speedup_amplitude returns them, levels 0..s)."""
+    s = len(levels) - 1
+    arr = (LevelResult * (s + 1))()
+    for n, r in enumerate(levels):
+        for k, _ in LevelResult._fields_:
+            if k in r:
+                setattr(arr[n], k, r[k])
+    a, da, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().su_fit_continuum(arr, s, int(p), int(n_min), int(n_terms), ctypes.byref(a), ctypes.byref(da),
+                                   ctypes.byref(c2)))
+    return a.value, da.value, c2.value
 
 
 def speedup_normals(seed, instance, sample0, n_samples, n_normals, out, precision="fp64", stream=None):

@@ -883,6 +883,77 @@ int speedup_logweights_nd(int d, const int *exps, const double *coefs, int n_ter
     return SU_OK;
 }
 
+int su_fit_continuum(const su_level_result *levels, int s, int p, int n_min, int n_terms, double *A, double *A_err,
+                     double *chi2) {
+    if (!levels || !A) return fail(SU_EINVAL, "levels or output missing");
+    if (s < 1 || s > SU_MAX_S) return fail(SU_EINVAL, "s must be in 1..%d", SU_MAX_S);
+    if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
+    if (n_terms != 2 && n_terms != 3) return fail(SU_EINVAL, "n_terms must be 2 or 3");
+    if (n_min < 1 || s - n_min + 1 < n_terms)
+        return fail(SU_EINVAL, "need levels n_min..s, n_min >= 1 (level 0 has no statistical error), at least n_terms");
+    const int m = s - n_min + 1, k = n_terms;
+    // weighted design matrix sqrt(w_n) (1, N^-p, N^-(p+1)), N = 2^n, each column
+    // scaled to unit maximum; modified Gram-Schmidt QR
+    double a[3][SU_MAX_S + 1], y[SU_MAX_S + 1], c[3];
+    for (int i = 0; i < m; ++i) {
+        const su_level_result &r = levels[n_min + i];
+        if (!(r.err > 0) || !std::isfinite(r.err) || !std::isfinite(r.amp))
+            return fail(SU_EINVAL, "level %d has no finite positive error", n_min + i);
+        const double sw = 1.0 / r.err, lN = (double)(n_min + i) * std::log(2.0);
+        a[0][i] = sw;
+        a[1][i] = sw * std::exp(-p * lN);
+        if (k == 3) a[2][i] = sw * std::exp(-(p + 1) * lN);
+        y[i] = sw * r.amp;
+    }
+    for (int j = 0; j < k; ++j) {
+        double mx = 0;
+        for (int i = 0; i < m; ++i) mx = std::max(mx, std::fabs(a[j][i]));
+        c[j] = 1.0 / mx;
+        for (int i = 0; i < m; ++i) a[j][i] *= c[j];
+    }
+    double R[3][3] = {{0}}, z[3];
+    for (int j = 0; j < k; ++j) {
+        for (int l = 0; l < j; ++l) {
+            double d = 0;
+            for (int i = 0; i < m; ++i) d += a[l][i] * a[j][i];
+            R[l][j] = d;
+            for (int i = 0; i < m; ++i) a[j][i] -= d * a[l][i];
+        }
+        double nn = 0;
+        for (int i = 0; i < m; ++i) nn += a[j][i] * a[j][i];
+        R[j][j] = std::sqrt(nn);
+        if (!(R[j][j] > 0)) return fail(SU_EINVAL, "the fit's columns are dependent");
+        for (int i = 0; i < m; ++i) a[j][i] /= R[j][j];
+        double d = 0;
+        for (int i = 0; i < m; ++i) d += a[j][i] * y[i];
+        z[j] = d;
+        for (int i = 0; i < m; ++i) y[i] -= d * a[j][i];
+    }
+    double res = 0;
+    for (int i = 0; i < m; ++i) res += y[i] * y[i];
+    // R beta = z, and the first row of R^-1 for the variance of the constant
+    double beta[3], Ri[3][3] = {{0}};
+    for (int j = k - 1; j >= 0; --j) {
+        double t = z[j];
+        for (int l = j + 1; l < k; ++l) t -= R[j][l] * beta[l];
+        beta[j] = t / R[j][j];
+    }
+    for (int j = 0; j < k; ++j) {
+        Ri[j][j] = 1.0 / R[j][j];
+        for (int l = j - 1; l >= 0; --l) {
+            double t = 0;
+            for (int q = l + 1; q <= j; ++q) t += R[l][q] * Ri[q][j];
+            Ri[l][j] = -t / R[l][l];
+        }
+    }
+    double v = 0;
+    for (int j = 0; j < k; ++j) v += Ri[0][j] * Ri[0][j];
+    *A = c[0] * beta[0];
+    if (A_err) *A_err = c[0] * std::sqrt(v);
+    if (chi2) *chi2 = res;
+    return SU_OK;
+}
+
 int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms, int p, double eps, int *out_exps,
                         double *out_w, int capacity, int *n_out) {
     if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");

@@ -301,3 +301,17 @@ def test_highest_levels_read_their_tables_from_global_memory():
     top = slice(5, 10)
     scale = np.maximum(np.abs(ws[:, top]), np.median(np.abs(ws[:, top]), axis=0))
     assert float(np.max(np.abs(wg[:, top] - ws[:, top]) / scale)) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2, 10])
+def test_continuum_fit_of_one_run_matches_dvr(p):
+    """Fig. 2's case (modified Poeschl-Teller, lambda = alpha = 1,
+    A(-0.5, 0.5; 1), s = 10, 1e6 samples): the constant of Eq. fit over the
+    levels N = 8..1024 equals the sinc-DVR continuum amplitude within 4 of
+    its standard errors (the levels share samples, so the error is taken as
+    the larger of the fit's and the top level's)."""
+    r = su.speedup_amplitude("mpt", [1.0, 1.0], -0.5, 0.5, 1.0, p, 10, 1_000_000, 2011, n_blocks=100)
+    A, dA, _ = su.su_fit_continuum(r, p, n_min=3, n_terms=3)
+    ref, _ = exact.dvr_amplitude(lambda y: -1.0 / np.cosh(y) ** 2, -0.5, 0.5, 1.0, L=25.0, dx=0.02)
+    sig = max(dA, r[10]["err"])
+    assert abs(A - ref) <= 4 * sig, (A, ref, dA, r[10]["err"])

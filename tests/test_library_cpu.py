@@ -321,3 +321,41 @@ def test_nd_table_fault_fails_before_any_device_work():
         su.su_fault_inject("clear")
     with pytest.raises(ValueError):
         su.speedup_amplitude_nd({(2, 0): 0.5}, (0.0,), (1.0, 1.0), 1.0, 4, 3, 100, 1)
+
+
+# ---- the continuum fit (Eq. fit): host only, against the oracle's
+def _levels(amps, errs):
+    return [{"amp": float(a), "err": float(e), "n": 1} for a, e in zip(amps, errs)]
+
+
+@pytest.mark.parametrize("p,n_min,n_terms", [(1, 1, 2), (2, 1, 3), (10, 2, 3), (4, 3, 2), (18, 1, 3)])
+def test_fit_continuum_matches_the_oracle(p, n_min, n_terms):
+    from oracle import fit
+    rng = np.random.default_rng(p)
+    s = 10
+    N = 2.0 ** np.arange(s + 1)
+    errs = rng.uniform(1e-5, 1e-4, s + 1)
+    amps = 0.2 + 0.3 / N ** min(p, 30) + errs * rng.normal(size=s + 1)
+    a, da, c2 = su.su_fit_continuum(_levels(amps, errs), p, n_min, n_terms)
+    ra, rda, rc2 = fit.fit_continuum(amps, errs, p, n_min, n_terms)
+    assert a == pytest.approx(ra, rel=1e-9, abs=1e-14)
+    assert da == pytest.approx(rda, rel=1e-6)
+    assert c2 == pytest.approx(rc2, rel=1e-6, abs=1e-12)
+
+
+def test_fit_continuum_recovers_exact_series_and_rejects_bad_input():
+    s, p = 8, 3
+    N = 2.0 ** np.arange(s + 1)
+    amps = 0.4 - 0.6 / N ** p + 0.25 / N ** (p + 1)
+    a, _, c2 = su.su_fit_continuum(_levels(amps, np.full(s + 1, 1e-3)), p, 1, 3)
+    assert a == pytest.approx(0.4, rel=1e-13) and c2 <= 1e-20
+    for kw in ({"n_min": 0}, {"n_terms": 4}, {"n_min": 7}):
+        args = {"n_min": 1, "n_terms": 3}
+        args.update(kw)
+        with pytest.raises(su.SpeedupError) as e:
+            su.su_fit_continuum(_levels(amps, np.full(s + 1, 1e-3)), p, args["n_min"], args["n_terms"])
+        assert e.value.code == -1
+    bad = np.full(s + 1, 1e-3)
+    bad[4] = 0.0
+    with pytest.raises(su.SpeedupError):
+        su.su_fit_continuum(_levels(amps, bad), p, 1, 3)
