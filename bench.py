@@ -59,13 +59,15 @@ def parse():
     ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
     ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
     ap.add_argument("--no-fig2", action="store_true", help="skip the Fig. 2 convergence and continuum-fit entry")
-    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "general"], default=None,
+    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "general", "evolution", "train"],
+                    default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
                          "every 16th instance of the amplitude matrix; proposal = the learned-proposal "
                          "instance with a fixed random network (--profile-n samples); nd = the 2D anharmonic "
                          "oscillator, p = 10, s = 10; general = AHO g = 10 through the general-potential mode, "
-                         "p = 10, s = 10 (--profile-n samples)")
+                         "p = 10, s = 10 (--profile-n samples); evolution = the Fig. 3 AHO matrix (n = 16385); "
+                         "train = 20 training steps of the learned proposal on --profile-n plain paths")
     ap.add_argument("--profile-p", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=200_000)
     return ap.parse_args()
@@ -777,6 +779,20 @@ def run_profile(args):
             r = su.speedup_amplitude_proposal(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, args.profile_n,
                                               x.seed, P, n_blocks=100)
         print(f"profile case proposal n={args.profile_n}: A_64 = {r[x.s]['amp']:.6g}, ess {r[x.s]['ess']:.4g}")
+        return
+    if args.profile == "evolution":
+        n = 16385
+        U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            su.speedup_evolution_matrix("aho", [1.0, 48.0], 21, 0.02, 8.0, n, U)
+        torch.cuda.synchronize()
+        print(f"profile case evolution: n = {n}, U[n/2, n/2] = {float(U[n // 2, n // 2]):.10g}")
+        return
+    if args.profile == "train":
+        x = workloads.CONFIG5
+        th, losses = su.speedup_train_proposal(x.model, list(x.params), x.a, x.b, x.T, x.p, x.s, x.seed,
+                                               _init_theta(0), n_train=args.profile_n, steps=20)
+        print(f"profile case train: {args.profile_n} paths, 20 steps, loss {losses[0]:.4f} -> {losses[-1]:.4f}")
         return
     if args.profile in ("nd", "general"):
         if args.profile == "nd":

@@ -247,18 +247,34 @@ __global__ void out_loss_kernel(const float *__restrict__ Y, const float *__rest
     if (threadIdx.x == 0) atomicAdd(loss, sb[0]);
 }
 
-// out[row] = sum_r XT[row][r] (bias gradients from transposed gradients)
-__global__ void rowsum_kernel(const __nv_bfloat16 *__restrict__ XT, int R, float *out) {
+// out[row] = sum_r XT[row][r] (bias gradients from transposed gradients):
+// one CTA of kRowsumThreads per row, 16-byte loads of eight bf16 (R is a
+// multiple of 32, so every row starts 16-byte aligned), warp shuffles, then
+// the warps in order: a fixed summation order.
+constexpr int kRowsumThreads = 512;
+__global__ void __launch_bounds__(kRowsumThreads) rowsum_kernel(const __nv_bfloat16 *__restrict__ XT, int R,
+                                                                float *out) {
+    const uint4 *row = reinterpret_cast<const uint4 *>(XT + (size_t)blockIdx.x * R);
     float s = 0.f;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) s += __bfloat162float(XT[(size_t)blockIdx.x * R + r]);
-    __shared__ float sb[256];
-    sb[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if (threadIdx.x < o) sb[threadIdx.x] += sb[threadIdx.x + o];
-        __syncthreads();
+    for (int i = threadIdx.x; i < R / 8; i += kRowsumThreads) {
+        const uint4 v = row[i];
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            s += f.x + f.y;
+        }
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = sb[0];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float sw[kRowsumThreads / 32];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kRowsumThreads / 32; ++w) t += sw[w];
+        out[blockIdx.x] = t;
+    }
 }
 
 // float master weights -> the bf16 operands of one step
@@ -517,13 +533,13 @@ cudaError_t loss_grad(Workspace &ws, int R, double inv_norm, bool use_rw, cudaSt
     // backward
     if ((e = cudaMemsetAsync(ws.dW1, 0, ws.gbytes, st))) return e;
     if ((e = gemm(ws.dYT, R, ws.HT[2], R, ws.dW4, kHid, kOut, kHid, Rp, st, true))) return e;
-    rowsum_kernel<<<kOut, 256, 0, st>>>(ws.dYT, R, ws.db + 3 * kHid);
+    rowsum_kernel<<<kOut, kRowsumThreads, 0, st>>>(ws.dYT, R, ws.db + 3 * kHid);
     if ((e = gemm(ws.dYp, kK1, ws.W4T, kK1, ws.dH, kHid, R, kHid, kK1, st, false))) return e;
     const __nv_bfloat16 *WT[3] = {nullptr, ws.W2T, ws.W3T};
     float *dW[3] = {ws.dW1, ws.dW2, ws.dW3};
     for (int l = 2; l >= 0; --l) {
         gelu_bwd_kernel<<<tg, tb, 0, st>>>(ws.dH, ws.pre[l], ws.dP, ws.dPT, R);
-        rowsum_kernel<<<kHid, 256, 0, st>>>(ws.dPT, R, ws.db + l * kHid);
+        rowsum_kernel<<<kHid, kRowsumThreads, 0, st>>>(ws.dPT, R, ws.db + l * kHid);
         if (l > 0) {
             if ((e = gemm(ws.dPT, R, ws.HT[l - 1], R, dW[l], kHid, kHid, kHid, Rp, st, true))) return e;
             if ((e = gemm(ws.dP, kHid, WT[l], kHid, ws.dH, kHid, R, kHid, kHid, st, false))) return e;
