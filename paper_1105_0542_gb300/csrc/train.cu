@@ -43,6 +43,24 @@ constexpr int kTK = 128;                         // K staged per MMA round
 // 66 KB, so at most 3 CTAs (384 tensor-memory columns) per SM
 constexpr int kGemmSmem = 128 * (kBN + 4) * 4 > 2 * 128 * kTK * 2 ? 128 * (kBN + 4) * 4 : 2 * 128 * kTK * 2;
 
+__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float v) {
+    return 0.5f * (1.0f + erff(v * 0.70710678118654752f)) + v * 0.39894228040143268f * __expf(-0.5f * v * v);
+}
+
+// What the GEMM's epilogue does with the accumulator tile acc[row][col]:
+//   EP_STORE  C = acc (float)             EP_ADD  C += acc (atomic; split K)
+//   EP_GELU   pre = acc + bias[col] (float), H = bf16(GELU(pre)) [M][N] and
+//             HT = its transpose [N][M] (the forward layers)
+//   EP_DGELU  P = bf16(acc * GELU'(pre)) [M][N] and PT = its transpose
+//             (the backward layers: acc = dL/dH, P = dL/dpre)
+enum Epilogue { EP_STORE = 0, EP_ADD = 1, EP_GELU = 2, EP_DGELU = 3 };
+struct EpArgs {
+    const float *bias;        // EP_GELU
+    float *pre;               // EP_GELU: written; EP_DGELU: read ([M][ldc])
+    __nv_bfloat16 *H, *HT;    // EP_GELU: H, HT; EP_DGELU: P, PT ([M][ldc], [N][M])
+};
+
 // C[M][N] (+)= sum_k A[m][k] B[n][k] over the K-range of blockIdx.z.
 // A: [M][lda], B: [N][ldb] bf16 (lda, ldb multiples of 8); K and the K-range
 // multiples of 32.  128 threads (one warp per tensor-memory lane quadrant).
@@ -55,7 +73,7 @@ constexpr int kGemmSmem = 128 * (kBN + 4) * 4 > 2 * 128 * kTK * 2 ? 128 * (kBN +
 __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restrict__ A, int lda,
                                                   const __nv_bfloat16 *__restrict__ B, int ldb,
                                                   float *__restrict__ C, int ldc, int M, int N, int K,
-                                                  int kchunk, int atomic, int *status) {
+                                                  int kchunk, int mode, EpArgs ep, int *status) {
     extern __shared__ __align__(16) unsigned char gsm[];
     unsigned char *sA = gsm, *sB = gsm + 128 * kTK * 2;
     __shared__ uint32_t tmem_slot;
@@ -120,18 +138,42 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
             for (int j = 0; j < 16; j += 4)
                 *reinterpret_cast<float4 *>(Ts + trow * ts + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
-        __syncthreads();
+        ok = __syncthreads_and(ok);   // one verdict for the CTA (the epilogue has a barrier)
         if (ok) {
             const int nq = NT / 4;
             for (int i = tid; i < 128 * nq; i += 128) {
                 const int r = i / nq, c = 4 * (i - r * nq);
                 const int row = m0 + r, col = n0 + c;
                 if (row >= M || col >= N) continue;
-                const float4 v = *reinterpret_cast<const float4 *>(Ts + r * ts + c);
-                float *dst = C + (size_t)row * ldc + col;
-                const float e[4] = {v.x, v.y, v.z, v.w};
+                float4 v = *reinterpret_cast<const float4 *>(Ts + r * ts + c);
                 const int cnt = min(4, N - col);
-                if (atomic) {
+                const size_t at = (size_t)row * ldc + col;
+                if (mode == EP_GELU || mode == EP_DGELU) {   // N = ldc = 128: whole float4 groups
+                    float e[4] = {v.x, v.y, v.z, v.w};
+                    if (mode == EP_GELU) {
+                        const float4 bb = *reinterpret_cast<const float4 *>(ep.bias + col);
+                        const float b4[4] = {bb.x, bb.y, bb.z, bb.w};
+                        float pr[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            pr[j] = e[j] + b4[j];
+                            e[j] = gelu(pr[j]);
+                        }
+                        *reinterpret_cast<float4 *>(ep.pre + at) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+                    } else {
+                        const float4 pv = *reinterpret_cast<const float4 *>(ep.pre + at);
+                        const float p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) e[j] *= gelu_grad(p4[j]);
+                    }
+                    __nv_bfloat162 h2[2] = {__floats2bfloat162_rn(e[0], e[1]), __floats2bfloat162_rn(e[2], e[3])};
+                    *reinterpret_cast<uint2 *>(ep.H + at) = *reinterpret_cast<const uint2 *>(h2);
+                    *reinterpret_cast<float4 *>(Ts + r * ts + c) = make_float4(e[0], e[1], e[2], e[3]);
+                    continue;
+                }
+                float *dst = C + at;
+                const float e[4] = {v.x, v.y, v.z, v.w};
+                if (mode == EP_ADD) {
                     for (int j = 0; j < cnt; ++j) atomicAdd(dst + j, e[j]);
                 } else if (cnt == 4 && ((ldc | col) & 3) == 0) {
                     *reinterpret_cast<float4 *>(dst) = v;
@@ -139,16 +181,28 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
                     for (int j = 0; j < cnt; ++j) dst[j] = e[j];
                 }
             }
+            if (mode == EP_GELU || mode == EP_DGELU) {
+                // the transpose: thread c takes column c, eight consecutive rows
+                // per 16-byte store (M is a multiple of 32, so a group of eight
+                // rows is wholly inside or outside; conflict-free reads of Ts)
+                __syncthreads();
+                const int c = tid;
+                if (c < nn)
+                    for (int r8 = 0; r8 < 128 && m0 + r8 < M; r8 += 8) {
+                        __nv_bfloat162 h[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            h[q] = __floats2bfloat162_rn(Ts[(r8 + 2 * q) * ts + c], Ts[(r8 + 2 * q + 1) * ts + c]);
+                        *reinterpret_cast<uint4 *>(ep.HT + (size_t)(n0 + c) * M + m0 + r8) =
+                            *reinterpret_cast<const uint4 *>(h);
+                    }
+            }
         }
     }
     if (!ok && tid == 0) atomicOr(status, 1);
     mlp::tc_end(tc);
 }
 
-__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float v) {
-    return 0.5f * (1.0f + erff(v * 0.70710678118654752f)) + v * 0.39894228040143268f * __expf(-0.5f * v * v);
-}
 
 // rows of a minibatch from stored paths: row r = path pb, heap index j
 __global__ void rows_kernel(const float *__restrict__ paths, int np1, const int *__restrict__ ids, int nb,
@@ -170,50 +224,6 @@ __global__ void rows_kernel(const float *__restrict__ paths, int np1, const int 
         XT[(size_t)c * R + r] = v;
     }
     u[r] = (q[k] - 0.5f * (qL + qR)) / sig[n];
-}
-
-// pre += bias; H = GELU(pre) row-major and transposed (32 x 32 tiles through smem)
-__global__ void bias_gelu_kernel(float *pre, const float *__restrict__ bias, __nv_bfloat16 *H,
-                                 __nv_bfloat16 *HT, int R) {
-    __shared__ float t[32][33];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int r = r0 + y, c = c0 + threadIdx.x;
-        float g = 0.f;
-        if (r < R) {
-            const float v = pre[(size_t)r * kHid + c] + bias[c];
-            pre[(size_t)r * kHid + c] = v;
-            g = gelu(v);
-            H[(size_t)r * kHid + c] = __float2bfloat16_rn(g);
-        }
-        t[y][threadIdx.x] = g;
-    }
-    __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int c = c0 + y, r = r0 + threadIdx.x;
-        if (r < R) HT[(size_t)c * R + r] = __float2bfloat16_rn(t[threadIdx.x][y]);
-    }
-}
-
-// dPre = dH * GELU'(pre), row-major and transposed
-__global__ void gelu_bwd_kernel(const float *__restrict__ dH, const float *__restrict__ pre,
-                                __nv_bfloat16 *dP, __nv_bfloat16 *dPT, int R) {
-    __shared__ float t[32][33];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int r = r0 + y, c = c0 + threadIdx.x;
-        float g = 0.f;
-        if (r < R) {
-            g = dH[(size_t)r * kHid + c] * gelu_grad(pre[(size_t)r * kHid + c]);
-            dP[(size_t)r * kHid + c] = __float2bfloat16_rn(g);
-        }
-        t[y][threadIdx.x] = g;
-    }
-    __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int c = c0 + y, r = r0 + threadIdx.x;
-        if (r < R) dPT[(size_t)c * R + r] = __float2bfloat16_rn(t[threadIdx.x][y]);
-    }
 }
 
 // loss and dL/dY per row; dY row-major padded to 32 columns and transposed [2][R]
@@ -433,7 +443,8 @@ cudaError_t Workspace::reserve(int R) {
         oHT[l] = take((size_t)kHid * R * 2);
     }
     const size_t oY = take((size_t)R * 2 * 4), odYp = take((size_t)R * kK1 * 2), odYT = take((size_t)2 * R * 2),
-                 odH = take((size_t)R * kHid * 4), odP = take((size_t)R * kHid * 2), odPT = take((size_t)kHid * R * 2);
+                 odP = take((size_t)R * kHid * 2), odPT = take((size_t)kHid * R * 2),
+                 odP2 = take((size_t)R * kHid * 2), odPT2 = take((size_t)kHid * R * 2);
     const size_t ow = take((size_t)(kHid * kK1 * 2 + 4 * kHid * kHid * 2 + kOut * kHid * 2 + kHid * kK1 * 2));
     const size_t og = take((size_t)(kHid * kK1 + 2 * kHid * kHid + kOut * kHid + 3 * kHid + kOut) * 4);
     const size_t oflat = take((size_t)mlp::kParams * 4 * 4);   // theta, grad, m, v
@@ -459,9 +470,10 @@ cudaError_t Workspace::reserve(int R) {
     Y = (float *)(p + oY);
     dYp = (__nv_bfloat16 *)(p + odYp);
     dYT = (__nv_bfloat16 *)(p + odYT);
-    dH = (float *)(p + odH);
     dP = (__nv_bfloat16 *)(p + odP);
     dPT = (__nv_bfloat16 *)(p + odPT);
+    dP2 = (__nv_bfloat16 *)(p + odP2);
+    dPT2 = (__nv_bfloat16 *)(p + odPT2);
     __nv_bfloat16 *w = (__nv_bfloat16 *)(p + ow);
     W1p = w;
     W2 = W1p + kHid * kK1;
@@ -493,7 +505,8 @@ cudaError_t Workspace::reserve(int R) {
 static int *g_status = nullptr;   // the workspace's timeout word, set by loss_grad
 
 static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, float *C, int ldc,
-                        int M, int N, int K, cudaStream_t st, bool split) {
+                        int M, int N, int K, cudaStream_t st, bool split, int mode = EP_STORE,
+                        EpArgs ep = EpArgs{nullptr, nullptr, nullptr, nullptr}) {
     // weight gradients (K = R): split K over enough CTAs to fill the GPU
     int splitk = 1, kchunk = K;
     if (split) {
@@ -502,7 +515,8 @@ static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
         splitk = (K + kchunk - 1) / kchunk;
     }
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splitk);
-    gemm_nt<<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? 1 : 0, g_status);
+    gemm_nt<<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? EP_ADD : mode, ep,
+                                          g_status);
     return cudaGetLastError();
 }
 
@@ -515,15 +529,16 @@ cudaError_t loss_grad(Workspace &ws, int R, double inv_norm, bool use_rw, cudaSt
     const float *b1 = th + kHid * kIn, *b2 = b1 + kHid + kHid * kHid, *b3 = b2 + kHid + kHid * kHid,
                 *b4 = b3 + kHid + kOut * kHid;
     prep_weights_kernel<<<kHid, kHid, 0, st>>>(th, ws.W1p, ws.W2, ws.W3, ws.W4, ws.W2T, ws.W3T, ws.W4T);
-    const dim3 tb(32, 8), tg((R + 31) / 32, kHid / 32);
-    // forward
-    cudaError_t e = gemm(ws.X, kK1, ws.W1p, kK1, ws.pre[0], kHid, R, kHid, kK1, st, false);
+    // forward: each hidden layer's GEMM adds the bias and applies GELU in its epilogue
+    cudaError_t e = gemm(ws.X, kK1, ws.W1p, kK1, nullptr, kHid, R, kHid, kK1, st, false, EP_GELU,
+                         EpArgs{b1, ws.pre[0], ws.H[0], ws.HT[0]});
     if (e) return e;
-    bias_gelu_kernel<<<tg, tb, 0, st>>>(ws.pre[0], b1, ws.H[0], ws.HT[0], R);
-    if ((e = gemm(ws.H[0], kHid, ws.W2, kHid, ws.pre[1], kHid, R, kHid, kHid, st, false))) return e;
-    bias_gelu_kernel<<<tg, tb, 0, st>>>(ws.pre[1], b2, ws.H[1], ws.HT[1], R);
-    if ((e = gemm(ws.H[1], kHid, ws.W3, kHid, ws.pre[2], kHid, R, kHid, kHid, st, false))) return e;
-    bias_gelu_kernel<<<tg, tb, 0, st>>>(ws.pre[2], b3, ws.H[2], ws.HT[2], R);
+    if ((e = gemm(ws.H[0], kHid, ws.W2, kHid, nullptr, kHid, R, kHid, kHid, st, false, EP_GELU,
+                  EpArgs{b2, ws.pre[1], ws.H[1], ws.HT[1]})))
+        return e;
+    if ((e = gemm(ws.H[1], kHid, ws.W3, kHid, nullptr, kHid, R, kHid, kHid, st, false, EP_GELU,
+                  EpArgs{b3, ws.pre[2], ws.H[2], ws.HT[2]})))
+        return e;
     if ((e = gemm(ws.H[2], kHid, ws.W4, kHid, ws.Y, 2, R, kOut, kHid, st, false))) return e;
     // loss and dY
     if ((e = cudaMemsetAsync(ws.loss, 0, 8, st))) return e;
@@ -534,17 +549,24 @@ cudaError_t loss_grad(Workspace &ws, int R, double inv_norm, bool use_rw, cudaSt
     if ((e = cudaMemsetAsync(ws.dW1, 0, ws.gbytes, st))) return e;
     if ((e = gemm(ws.dYT, R, ws.HT[2], R, ws.dW4, kHid, kOut, kHid, Rp, st, true))) return e;
     rowsum_kernel<<<kOut, kRowsumThreads, 0, st>>>(ws.dYT, R, ws.db + 3 * kHid);
-    if ((e = gemm(ws.dYp, kK1, ws.W4T, kK1, ws.dH, kHid, R, kHid, kK1, st, false))) return e;
+    // dL/dpre of the last hidden layer straight from the dL/dH GEMM's epilogue;
+    // the layers' dP, dPT alternate between two buffers (one GEMM reads the
+    // layer above's while writing the one below)
+    __nv_bfloat16 *dP[2] = {ws.dP, ws.dP2}, *dPT[2] = {ws.dPT, ws.dPT2};
+    if ((e = gemm(ws.dYp, kK1, ws.W4T, kK1, nullptr, kHid, R, kHid, kK1, st, false, EP_DGELU,
+                  EpArgs{nullptr, ws.pre[2], dP[0], dPT[0]})))
+        return e;
     const __nv_bfloat16 *WT[3] = {nullptr, ws.W2T, ws.W3T};
     float *dW[3] = {ws.dW1, ws.dW2, ws.dW3};
-    for (int l = 2; l >= 0; --l) {
-        gelu_bwd_kernel<<<tg, tb, 0, st>>>(ws.dH, ws.pre[l], ws.dP, ws.dPT, R);
-        rowsum_kernel<<<kHid, kRowsumThreads, 0, st>>>(ws.dPT, R, ws.db + l * kHid);
+    for (int l = 2, cur = 0; l >= 0; --l, cur ^= 1) {
+        rowsum_kernel<<<kHid, kRowsumThreads, 0, st>>>(dPT[cur], R, ws.db + l * kHid);
         if (l > 0) {
-            if ((e = gemm(ws.dPT, R, ws.HT[l - 1], R, dW[l], kHid, kHid, kHid, Rp, st, true))) return e;
-            if ((e = gemm(ws.dP, kHid, WT[l], kHid, ws.dH, kHid, R, kHid, kHid, st, false))) return e;
+            if ((e = gemm(dPT[cur], R, ws.HT[l - 1], R, dW[l], kHid, kHid, kHid, Rp, st, true))) return e;
+            if ((e = gemm(dP[cur], kHid, WT[l], kHid, nullptr, kHid, R, kHid, kHid, st, false, EP_DGELU,
+                          EpArgs{nullptr, ws.pre[l - 1], dP[cur ^ 1], dPT[cur ^ 1]})))
+                return e;
         } else {
-            if ((e = gemm(ws.dPT, R, ws.XT, R, ws.dW1, kK1, kHid, kK1, Rp, st, true))) return e;
+            if ((e = gemm(dPT[cur], R, ws.XT, R, ws.dW1, kK1, kHid, kK1, Rp, st, true))) return e;
         }
     }
     gather_grad_kernel<<<(mlp::kParams + 255) / 256, 256, 0, st>>>(ws.dW1, ws.db, ws.dW2, ws.db + kHid, ws.dW3,

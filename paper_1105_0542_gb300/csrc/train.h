@@ -21,8 +21,8 @@ struct Workspace {
     __nv_bfloat16 *HT[3] = {nullptr, nullptr, nullptr}; // transposed [128][R]
     float *Y = nullptr;                                  // outputs [R][2] (no bias)
     __nv_bfloat16 *dYp = nullptr, *dYT = nullptr;        // dL/dY [R][32], [2][R]
-    float *dH = nullptr;                                 // dL/dH [R][128]
     __nv_bfloat16 *dP = nullptr, *dPT = nullptr;         // dL/dpre [R][128], [128][R]
+    __nv_bfloat16 *dP2 = nullptr, *dPT2 = nullptr;       // the same, the other layer of a pair
     __nv_bfloat16 *W1p = nullptr, *W2 = nullptr, *W3 = nullptr, *W4 = nullptr;
     __nv_bfloat16 *W2T = nullptr, *W3T = nullptr, *W4T = nullptr;
     float *dW1 = nullptr, *dW2 = nullptr, *dW3 = nullptr, *dW4 = nullptr, *db = nullptr;
