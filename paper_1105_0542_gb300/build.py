@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libspeedup_gb300.so")
+CLI = os.path.join(LIBDIR, "speedup")
 SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu", "nd.cu"]
 # the sampler kernel, once per (precision, ring): compiled in parallel
 INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3, 0)]
@@ -37,12 +38,13 @@ def nvcc():
 def _inputs():
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "speedup.h"))
+    files.append(os.path.join(CSRC, "speedup_cli.c"))
     files.append(os.path.abspath(__file__))
     return files
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(CLI):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
@@ -84,6 +86,14 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    # the command-line front end, plain C over the C ABI, beside the library
+    cli = [os.environ.get("CC", "gcc"), "-O2", "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"),
+           os.path.join(CSRC, "speedup_cli.c"), "-o", CLI + f".tmp{os.getpid()}", "-L", LIBDIR, "-lspeedup_gb300",
+           "-Wl,-rpath,$ORIGIN"]
+    r = subprocess.run(cli, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"cli build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(CLI + f".tmp{os.getpid()}", CLI)
     return LIB
 
 

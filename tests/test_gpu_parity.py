@@ -315,3 +315,23 @@ def test_continuum_fit_of_one_run_matches_dvr(p):
     ref, _ = exact.dvr_amplitude(lambda y: -1.0 / np.cosh(y) ** 2, -0.5, 0.5, 1.0, L=25.0, dx=0.02)
     sig = max(dA, r[10]["err"])
     assert abs(A - ref) <= 4 * sig, (A, ref, dA, r[10]["err"])
+
+
+def test_cli_prints_the_library_levels():
+    """The command-line front end (T a b s Nmc seed par..., Sec. 4's argument
+    order) prints exactly speedup_amplitude's levels, negative endpoints and
+    the continuum fit included."""
+    import subprocess
+    from paper_1105_0542_gb300 import build as _b
+    out = subprocess.run([_b.CLI, "-m", "dw", "-p", "6", "-B", "20", "-t", "1.5", "-1.0", "0.5", "6", "20000",
+                          "77", "2.0"], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if not l.startswith("#")]
+    r = su.speedup_amplitude("dw", [2.0], -1.0, 0.5, 1.5, 6, 6, 20000, 77, n_blocks=20)
+    assert len(lines) == 7
+    for n, l in enumerate(lines):
+        k, N, amp, err = l.split()
+        assert int(k) == n and int(N) == 2 ** n
+        assert float(amp) == r[n]["amp"]
+        assert float(err) == pytest.approx(r[n]["err"], rel=1e-5)
+    assert any(l.startswith("# continuum fit") for l in out.stdout.splitlines())

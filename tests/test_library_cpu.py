@@ -359,3 +359,21 @@ def test_fit_continuum_recovers_exact_series_and_rejects_bad_input():
     bad[4] = 0.0
     with pytest.raises(su.SpeedupError):
         su.su_fit_continuum(_levels(amps, bad), p, 1, 3)
+
+
+# ---- the command-line front end (the paper's argument order)
+def _cli(*args):
+    import subprocess
+    from paper_1105_0542_gb300 import build as _b
+    return subprocess.run([_b.CLI, *map(str, args)], capture_output=True, text=True, timeout=120)
+
+
+def test_cli_usage_and_argument_errors():
+    r = _cli()
+    assert r.returncode == 0 and r.stdout.startswith("usage: speedup")
+    assert _cli("-m", "nope", 1, 0, 1, 4, 100, 1).returncode == 2
+    assert _cli(1, 0, 1).returncode == 2                      # fewer than six positional arguments
+    assert _cli(1, 0, "x", 4, 100, 1).returncode == 2         # not a number
+    assert _cli("-f", "fp16", 1, 0, 1, 4, 100, 1).returncode == 2
+    r = _cli("-m", "aho", 1, 0, 1, 4, 100, 1, 1.0)             # wrong parameter count: the library's check
+    assert r.returncode == 1 and "speedup:" in r.stderr
