@@ -40,7 +40,7 @@ constexpr int kK1 = 32;        // padded input width (K of the first layer)
 constexpr int kBM = 128, kBN = 128, kBK = 32;   // output tile; K granularity
 constexpr int kTK = 128;                         // K staged per MMA round
 // A and B stages (64 KB), reused for the 128 x (128 + 4) float output tile:
-// 66 KB, so at most 3 CTAs (384 tensor-memory columns) per SM
+// 66 KB; 2 CTAs of 256 threads per SM (registers), 256 tensor-memory columns
 constexpr int kGemmSmem = 128 * (kBN + 4) * 4 > 2 * 128 * kTK * 2 ? 128 * (kBN + 4) * 4 : 2 * 128 * kTK * 2;
 
 __device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
@@ -63,14 +63,16 @@ struct EpArgs {
 
 // C[M][N] (+)= sum_k A[m][k] B[n][k] over the K-range of blockIdx.z.
 // A: [M][lda], B: [N][ldb] bf16 (lda, ldb multiples of 8); K and the K-range
-// multiples of 32.  128 threads (one warp per tensor-memory lane quadrant).
+// multiples of 32.  kGemmThreads = 256 threads: warp w reads tensor-memory lane
+// quadrant w % 4, columns [64 (w / 4), 64 (w / 4) + 64) of the tile.
 // Per round, 128 x 128 of A and min(N - n0, 128) x 128 of B are staged in the
 // operand layout of mlp.cuh (zeros outside M, N and the K-range), thread 0
 // issues K/16 MMAs (M = 128, N = the tile's width rounded up to 16) and
 // commits them; all threads wait (bounded) before the next round overwrites
 // the stage.  Epilogue: tcgen05.ld of each thread's row, stored or added.
 // A wait that gives up sets *status.
-__global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restrict__ A, int lda,
+constexpr int kGemmThreads = 256;
+__global__ void __launch_bounds__(kGemmThreads, 2) gemm_nt(const __nv_bfloat16 *__restrict__ A, int lda,
                                                   const __nv_bfloat16 *__restrict__ B, int ldb,
                                                   float *__restrict__ C, int ldc, int M, int N, int K,
                                                   int kchunk, int mode, EpArgs ep, int *status) {
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
         const int kn = min(kTK, ke - k0);
         // 16-byte asynchronous copies, all in flight at once; a source size of
         // 0 fills the destination with zeros (rows past M or N, K past the range)
-        for (int idx = tid; idx < 128 * (kTK / 8); idx += 128) {
+        for (int idx = tid; idx < 128 * (kTK / 8); idx += kGemmThreads) {
             const int r = idx / (kTK / 8), q = idx % (kTK / 8);
             const bool kin = 8 * q < kn;
             const bool ain = kin && m0 + r < M, bin = kin && r < nn;
@@ -130,10 +132,10 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
         // rows of NT + 4 floats), then row-contiguous stores or adds to C
         float *Ts = reinterpret_cast<float *>(gsm);
         const int ts = NT + 4;
-        const int trow = 32 * warp + lane;
-        for (int c = 0; c < NT; c += 16) {
+        const int quad = warp & 3, trow = 32 * quad + lane, c_lo = 64 * (warp >> 2);
+        for (int c = c_lo; c < min(NT, c_lo + 64); c += 16) {
             float v[16];
-            mlp::tmem_ld16(tc.tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            mlp::tmem_ld16(tc.tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c, v);
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
                 *reinterpret_cast<float4 *>(Ts + trow * ts + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
         ok = __syncthreads_and(ok);   // one verdict for the CTA (the epilogue has a barrier)
         if (ok) {
             const int nq = NT / 4;
-            for (int i = tid; i < 128 * nq; i += 128) {
+            for (int i = tid; i < 128 * nq; i += kGemmThreads) {
                 const int r = i / nq, c = 4 * (i - r * nq);
                 const int row = m0 + r, col = n0 + c;
                 if (row >= M || col >= N) continue;
@@ -182,13 +184,14 @@ __global__ void __launch_bounds__(128, 3) gemm_nt(const __nv_bfloat16 *__restric
                 }
             }
             if (mode == EP_GELU || mode == EP_DGELU) {
-                // the transpose: thread c takes column c, eight consecutive rows
-                // per 16-byte store (M is a multiple of 32, so a group of eight
-                // rows is wholly inside or outside; conflict-free reads of Ts)
+                // the transpose: thread t takes column t % 128 of the tile's rows
+                // 64 (t / 128) .. + 63, eight consecutive rows per 16-byte store
+                // (M is a multiple of 32, so a group of eight rows is wholly
+                // inside or outside; conflict-free reads of Ts)
                 __syncthreads();
-                const int c = tid;
+                const int c = tid & 127, rh = 64 * (tid >> 7);
                 if (c < nn)
-                    for (int r8 = 0; r8 < 128 && m0 + r8 < M; r8 += 8) {
+                    for (int r8 = rh; r8 < rh + 64 && m0 + r8 < M; r8 += 8) {
                         __nv_bfloat162 h[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
@@ -517,8 +520,8 @@ static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
         splitk = (K + kchunk - 1) / kchunk;
     }
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, splitk);
-    gemm_nt<<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? EP_ADD : mode, ep,
-                                          g_status);
+    gemm_nt<<<grid, kGemmThreads, kGemmSmem, st>>>(A, lda, B, ldb, C, ldc, M, N, K, kchunk, split ? EP_ADD : mode,
+                                                   ep, g_status);
     return cudaGetLastError();
 }
 
