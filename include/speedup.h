@@ -55,9 +55,12 @@ extern "C" {
 #define SU_POLY  4   /* sum_i v_i q^i, degree <= 8             params: v_0..v_d   */
 /* A general potential (Eq. 1Drec in the derivatives V^(j)(x), j = 0..2p-2,
  * Sec. 3.1): V = sum_{i<=8} a_i q^i + sum_{g<4} A_g e^{-beta_g (q - c_g)^2}
- *              + sum_{t<4} B_t sech^2(alpha_t (q - d_t)).
- * params (33): a_0..a_8, (A, beta, c) x 4, (B, alpha, d) x 4; a term with a
- * zero amplitude is absent, beta > 0 and alpha != 0 otherwise (SU_EINVAL).
+ *              + sum_{t<4} B_t sech^2(alpha_t (q - d_t))
+ *              [+ sum_{e<4} E_e e^{-kappa_e (q - x0_e)}].
+ * params (33): a_0..a_8, (A, beta, c) x 4, (B, alpha, d) x 4; or 45: the same
+ * and (E, kappa, x0) x 4 (Morse potentials are sums of exponentials); a term
+ * with a zero amplitude is absent, beta > 0 and alpha != 0 otherwise
+ * (SU_EINVAL).
  * W_p is evaluated per slice from V's derivatives at the slice midpoint and
  * the monomials of W_p in them (1629 monomial-power entries at p = 12), so it
  * needs no collapsed table: p <= 12, SU_FP64 only, su_plan_* /

@@ -16,7 +16,9 @@ derivatives of every order are evaluated here directly:
     V(x) = sum_{i<=8} a_i x^i + sum_g A_g exp(-beta_g (x - c_g)^2)
            + sum_s B_s sech^2(alpha_s (x - d_s)),
 
-the Gaussian's through Hermite polynomials,
+(and, optionally, four exponentials E e^{-kappa (x - x0)}, whose
+derivatives are (-kappa)^n times themselves: Morse potentials are sums of
+them), the Gaussian's through Hermite polynomials,
 d^n/du^n e^{-beta u^2} = (-sqrt(beta))^n H_n(sqrt(beta) u) e^{-beta u^2},
 and sech^2's as derivatives of tanh: sech^2 = tanh' and tanh' = 1 - tanh^2,
 so by Leibniz's rule tanh^(n+1) = -sum_k C(n, k) tanh^(k) tanh^(n-k) for
@@ -125,19 +127,31 @@ def term_count(p):
 # potentials of the general mode and their derivatives
 # ---------------------------------------------------------------------------
 
-N_POLY, N_GAUSS, N_SECH = 9, 4, 4
+N_POLY, N_GAUSS, N_SECH, N_EXP = 9, 4, 4, 4
 N_PARAMS = N_POLY + 3 * N_GAUSS + 3 * N_SECH     # 33
+N_PARAMS_EXP = N_PARAMS + 3 * N_EXP               # 45: with the exponential terms
 
 
-def split_params(params):
-    """(a[9], gauss [(A, beta, c)] with A != 0, sech [(B, alpha, d)] with B != 0)."""
-    if len(params) != N_PARAMS:
-        raise ValueError(f"the general potential takes {N_PARAMS} parameters")
+def split_params_all(params):
+    """(a[9], gauss [(A, beta, c)], sech [(B, alpha, d)], exps [(E, kappa, x0)]),
+    the terms with a nonzero amplitude; 33 parameters (no exponential terms)
+    or 45."""
+    if len(params) not in (N_PARAMS, N_PARAMS_EXP):
+        raise ValueError(f"the general potential takes {N_PARAMS} or {N_PARAMS_EXP} parameters")
     a = [float(v) for v in params[:N_POLY]]
     g = [tuple(float(v) for v in params[N_POLY + 3 * i:N_POLY + 3 * i + 3]) for i in range(N_GAUSS)]
     o = N_POLY + 3 * N_GAUSS
     s = [tuple(float(v) for v in params[o + 3 * i:o + 3 * i + 3]) for i in range(N_SECH)]
-    return a, [t for t in g if t[0] != 0], [t for t in s if t[0] != 0]
+    o = N_PARAMS
+    e = [tuple(float(v) for v in params[o + 3 * i:o + 3 * i + 3]) for i in range(N_EXP)] \
+        if len(params) == N_PARAMS_EXP else []
+    return a, [t for t in g if t[0] != 0], [t for t in s if t[0] != 0], [t for t in e if t[0] != 0]
+
+
+def split_params(params):
+    """(a[9], gauss [(A, beta, c)] with A != 0, sech [(B, alpha, d)] with B != 0)."""
+    a, g, s, _ = split_params_all(params)
+    return a, g, s
 
 
 @lru_cache(maxsize=64)
@@ -158,7 +172,7 @@ def _sech2_polys(J):
 def derivatives(params, x, J):
     """V^(j)(x), j = 0..J, as an array (J+1, *x.shape) in float64."""
     x = np.asarray(x, dtype=np.float64)
-    a, gs, ss = split_params(params)
+    a, gs, ss, es = split_params_all(params)
     out = np.zeros((J + 1,) + x.shape)
     # polynomial
     for j in range(J + 1):
@@ -190,6 +204,11 @@ def derivatives(params, x, J):
             T.append(acc)
         for n in range(J + 1):
             out[n] += B * alpha ** n * T[n + 1]
+    # exponentials: d^n/dx^n E e^{-kappa (x - x0)} = (-kappa)^n E e^{-kappa (x - x0)}
+    for E, kappa, x0 in es:
+        e = E * np.exp(-kappa * (x - x0))
+        for n in range(J + 1):
+            out[n] += (-kappa) ** n * e
     return out
 
 

@@ -169,15 +169,16 @@ def _check(rc):
         raise SpeedupError(rc, load().su_last_error().decode())
 
 
-def general_params(poly=(), gauss=(), sech=()):
-    """The 33 parameters of the general potential (model "general"):
+def general_params(poly=(), gauss=(), sech=(), expo=()):
+    """The parameters of the general potential (model "general"):
     poly = (a_0, .., a_d), d <= 8; gauss = up to four (A, beta, c) for
     A e^{-beta (q - c)^2}; sech = up to four (B, alpha, d) for
-    B sech^2(alpha (q - d))."""
-    if len(poly) > 9 or len(gauss) > 4 or len(sech) > 4:
-        raise ValueError("degree <= 8, at most four Gaussian and four sech^2 terms")
+    B sech^2(alpha (q - d)); expo = up to four (E, kappa, x0) for
+    E e^{-kappa (q - x0)}.  33 values without exponential terms, else 45."""
+    if len(poly) > 9 or len(gauss) > 4 or len(sech) > 4 or len(expo) > 4:
+        raise ValueError("degree <= 8, at most four Gaussian, sech^2 and exponential terms")
     out = [float(v) for v in poly] + [0.0] * (9 - len(poly))
-    for terms in (gauss, sech):
+    for terms in ((gauss, sech, expo) if expo else (gauss, sech)):
         for t in terms:
             if len(t) != 3:
                 raise ValueError("each Gaussian or sech^2 term has three parameters")

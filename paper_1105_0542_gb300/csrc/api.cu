@@ -280,6 +280,9 @@ static int upload_general(su_plan &pl) {
     D.n_entries = (int)G.entry_k.size();
     D.ng = V.ng;
     D.ns = V.ns;
+    D.ne = V.ne;
+    for (int q = 0; q < V.ne; ++q)
+        for (int r = 0; r < 3; ++r) D.expo[q][r] = V.expo[q][r];
     if (G.J >= kGenMaxSym || G.K > kGenMaxP) return fail(SU_EINVAL, "internal: general program out of range");
     std::vector<GeneralNode> nodes((size_t)D.n_nodes);
     for (int t = 0; t < D.n_nodes; ++t) {

@@ -536,8 +536,9 @@ void general_table(const GeneralEffective &G, double eps, std::vector<double> &T
 }
 
 int general_potential(const double *params, int n_params, GeneralPotential &V, std::string &err) {
-    if (n_params != kGenParams || !params) {
-        err = "SU_GENERAL takes 33 parameters (a_0..a_8, (A, beta, c) x 4, (B, alpha, d) x 4)";
+    if ((n_params != kGenParams && n_params != kGenParamsExp) || !params) {
+        err = "SU_GENERAL takes 33 parameters (a_0..a_8, (A, beta, c) x 4, (B, alpha, d) x 4) or 45 "
+              "(then (E, kappa, x0) x 4)";
         return SU_EINVAL;
     }
     for (int i = 0; i < n_params; ++i)
@@ -566,6 +567,12 @@ int general_potential(const double *params, int n_params, GeneralPotential &V, s
         }
         for (int r = 0; r < 3; ++r) V.sech[V.ns][r] = q[r];
         ++V.ns;
+    }
+    for (int t = 0; n_params == kGenParamsExp && t < 4; ++t) {
+        const double *q = params + kGenParams + 3 * t;
+        if (q[0] == 0.0) continue;
+        for (int r = 0; r < 3; ++r) V.expo[V.ne][r] = q[r];
+        ++V.ne;
     }
     return SU_OK;
 }
@@ -613,6 +620,14 @@ void general_derivatives(const GeneralPotential &V, double x, int J, double *out
             sc *= (double)(n + 1);
             out[n] += sc * a[(size_t)n + 1];
             sc *= alpha;
+        }
+    }
+    // exponentials: (-kappa)^n E e^{-kappa (x - x0)}
+    for (int t = 0; t < V.ne; ++t) {
+        double e = V.expo[t][0] * std::exp(-V.expo[t][1] * (x - V.expo[t][2]));
+        for (int n = 0; n <= J; ++n) {
+            out[n] += e;
+            e *= -V.expo[t][1];
         }
     }
 }

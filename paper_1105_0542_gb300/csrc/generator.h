@@ -85,15 +85,18 @@ int build_general(int p, GeneralEffective &G, std::string &err);
 void general_table(const GeneralEffective &G, double eps, std::vector<double> &T);
 
 // The potential of the general mode (SU_GENERAL): a polynomial of degree <= 8,
-// up to four Gaussians A e^{-beta (x - c)^2} and four sech^2 terms
-// B sech^2(alpha (x - d)); parameters (a_0..a_8, (A, beta, c) x 4,
-// (B, alpha, d) x 4), terms with a zero amplitude absent.
+// up to four Gaussians A e^{-beta (x - c)^2}, four sech^2 terms
+// B sech^2(alpha (x - d)) and, optionally, four exponentials
+// E e^{-kappa (x - x0)}; parameters (a_0..a_8, (A, beta, c) x 4,
+// (B, alpha, d) x 4 [, (E, kappa, x0) x 4]), terms with a zero amplitude absent.
 constexpr int kGenParams = 9 + 3 * 4 + 3 * 4;
+constexpr int kGenParamsExp = kGenParams + 3 * 4;
 struct GeneralPotential {
     double a[9] = {0};
-    int ng = 0, ns = 0;
+    int ng = 0, ns = 0, ne = 0;
     double gauss[4][3] = {{0}};   // A, beta, c
     double sech[4][3] = {{0}};    // B, alpha, d
+    double expo[4][3] = {{0}};    // E, kappa, x0
 };
 int general_potential(const double *params, int n_params, GeneralPotential &V, std::string &err);
 

@@ -27,13 +27,14 @@ struct GeneralNode {
 };
 
 struct GeneralDev {
-    int J, K, n_nodes, n_entries, ng, ns;
+    int J, K, n_nodes, n_entries, ng, ns, ne;
     const GeneralNode *nodes;                  // depth-first; node 0 = the constant monomial;
                                                // a node's entries are vs^0, vs^2, .. in order
     double poly_der[kGenMaxSym][9];            // V^(j) polynomial part: sum_i poly_der[j][i] x^(i-j)
     double gauss[4][4];                        // A, beta, c, sqrt(beta)
     double sech[4][3];                         // B, alpha, d
     double sech_scale[4][kGenMaxSym];          // B alpha^n (n+1)!
+    double expo[4][3];                         // E, kappa, x0
     double inv[kGenMaxSym + 1];                // 1 / n
 };
 

@@ -164,6 +164,14 @@ __device__ __forceinline__ void general_derivatives(double x, const GeneralDev *
             V[n] = fma(G->sech_scale[q][n], a[n + 1], V[n]);
         }
     }
+    for (int q = 0; q < G->ne; ++q) {   // exponentials: (-kappa)^n E e^{-kappa (x - x0)}
+        const double kap = G->expo[q][1];
+        double e = G->expo[q][0] * exp(-kap * (x - G->expo[q][2]));
+        for (int n = 0; n <= J; ++n) {
+            V[n] += e;
+            e *= -kap;
+        }
+    }
 }
 
 // -eps W_p of B = 1 or 2 slices (ql[b], qr[b]) for a general potential

@@ -69,6 +69,8 @@ P_MIXED = su.general_params((0.1, -0.2, 0.5, 0.05, 0.04), [(1.5, 2.0, 0.3), (-0.
 P_MPT = su.general_params((), (), [(-3.0, 1.0, 0.0)])
 P_BARRIER = su.general_params((0.0, 0.0, 0.5), [(2.0, 1.0, 0.0)])
 P_SEXTIC = su.general_params((0.0, 0.3, -1.0, 0.0, 0.2, 0.0, 0.01))
+# Morse D (1 - e^{-a (x - x0)})^2, D = 4, a = 1, x0 = 0.3, plus a Gaussian bump
+P_MORSE = su.general_params((4.0,), [(0.5, 3.0, -0.2)], (), [(-8.0, 1.0, 0.3), (4.0, 2.0, 0.3)])
 
 CASES = [
     # name, params, a, b, T, p, s, n, seed, sample0
@@ -80,6 +82,7 @@ CASES = [
     ("barrier", P_BARRIER, -1.5, 1.5, 2.0, 8, 6, 100, 5, (1 << 32) - 7),
     ("sextic", P_SEXTIC, 0.2, -0.4, 0.5, 9, 7, 60, 9, 0),
     ("s0-edge", P_MIXED, 0.0, 0.0, 0.3, 12, 1, 33, 2, 0),
+    ("morse", P_MORSE, -0.2, 0.9, 1.0, 10, 6, 100, 31, 0),
 ]
 
 
@@ -148,3 +151,17 @@ def test_general_edge_cases():
     on = su.speedup_amplitude("general", P_MIXED, a, b, T, p, 6, 5000, 9, n_blocks=10)
     off = su.speedup_amplitude("general", P_MIXED, a, b, T, p, 6, 5000, 9, n_blocks=10, hierarchy=False)
     assert off[6]["amp"] == on[6]["amp"] and off[6]["err"] == on[6]["err"]
+
+
+def test_morse_amplitude_matches_dvr():
+    """A(a, b; T) of the Morse potential 4 (1 - e^{-(x - 0.3)})^2 through the
+    exponential family, p = 12, N = 32, against sinc-DVR."""
+    params = su.general_params((4.0,), (), (), [(-8.0, 1.0, 0.3), (4.0, 2.0, 0.3)])
+    a, b, T = 0.0, 0.6, 1.0
+    r = su.speedup_amplitude("general", params, a, b, T, 12, 5, 4_000_000, 77, n_blocks=64)
+    V = lambda x: 4.0 * (1.0 - np.exp(-(x - 0.3))) ** 2  # noqa: E731
+    ref, _ = exact.dvr_amplitude(V, a, b, T, L=12.0, dx=0.02)
+    top = r[5]
+    sig = max(top["err"], top["err_naive"])
+    assert sig < 0.01 * ref
+    assert abs(top["amp"] - ref) <= 4 * sig, (top["amp"], ref, sig)

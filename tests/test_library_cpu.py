@@ -227,6 +227,8 @@ def test_general_params_layout():
     assert p[21:27] == (6.0, 7.0, 8.0, 9.0, 10.0, 11.0) and p[27:] == (0.0,) * 6
     with pytest.raises(ValueError):
         su.general_params(tuple(range(10)))
+    q = su.general_params((1.0,), (), (), [(2.0, 0.5, 0.1)])
+    assert len(q) == 45 and q[33:36] == (2.0, 0.5, 0.1) and q[36:] == (0.0,) * 9
 
 
 @pytest.mark.parametrize("params,kw,code", [
@@ -236,6 +238,8 @@ def test_general_params_layout():
     (P_GEN[:9] + (1.0, 0.0, 0.0) + P_GEN[12:], {}, -1),      # a Gaussian with beta = 0
     (P_GEN[:21] + (1.0, 0.0, 0.0) + P_GEN[24:], {}, -1),     # a sech^2 term with alpha = 0
     (P_GEN[:4] + (float("nan"),) + P_GEN[5:], {}, -1),       # a non-finite parameter
+    (P_GEN + (1.0, 1.0, 0.0) * 3 + (1.0, 1.0), {}, -1),       # 44 parameters
+    (P_GEN + (1.0, float("inf"), 0.0) + (0.0,) * 9, {}, -1),  # a non-finite exponential parameter
 ])
 def test_general_mode_rejects_bad_requests(params, kw, code):
     args = {"p": 6, "precision": "fp64"}

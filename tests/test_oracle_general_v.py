@@ -168,3 +168,22 @@ def test_sech2_leibniz_rule_matches_the_tanh_polynomials():
 
 def test_term_counts():
     assert [gv.term_count(p) for p in (1, 2, 4, 6, 8, 10)] == [1, 3, 15, 58, 193, 585]
+
+
+def test_exponential_terms_derivatives_to_the_highest_order():
+    """A Morse potential D (1 - e^{-a (x - x0)})^2 = D - 2D e^{-a u} + D e^{-2a u}
+    through the exponential family (45 parameters): every order up to 22
+    against mpmath's numerical differentiation."""
+    mp.mp.dps = 60
+    D, a, x0 = 4.0, 1.0, 0.3
+    params = _params(poly=[D]) + [-2 * D, a, x0, D, 2 * a, x0] + [0.0] * 6
+    assert len(params) == gv.N_PARAMS_EXP
+    J = 22
+    f = lambda z: D * (1 - mp.exp(-a * (z - x0))) ** 2  # noqa: E731
+    for xq in (-0.8, 0.3, 1.9):
+        got = gv.derivatives(params, np.array([xq]), J)[:, 0]
+        for j in range(J + 1):
+            ref = float(mp.diff(f, mp.mpf(xq), j))
+            assert got[j] == pytest.approx(ref, rel=1e-12, abs=1e-12 * max(1.0, abs(ref))), (xq, j)
+    # 33 parameters are the same potential without exponential terms
+    assert gv.split_params_all(_params(poly=[D]))[3] == []
