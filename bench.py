@@ -393,6 +393,11 @@ def run_ours(args):
                 "kernel": "sampler_kernel<double, RING_EVEN> (+ its combine)",
                 "measured_fma_peak_tflops": {"fp64": 2 * fma64 / 1e12, "fp32": 2 * fma32 / 1e12},
                 "frac_of_measured_fp64": achieved / (2 * fma64 / 1e12),
+                "fp32_sampler": {"kernel": "sampler_kernel<float, RING_EVEN>",
+                                 "achieved": per["fp32"]["flops"] / (per["fp32"]["ms"] / 1e3) / 1e12,
+                                 "peak": 2 * fma32 / 1e12, "unit": "TFLOP/s",
+                                 "frac": per["fp32"]["flops"] / (per["fp32"]["ms"] / 1e3) / (2 * fma32),
+                                 "bound": "issue (ncu: 60 % of issue slots, FMA pipe 27 %)"},
                 "note": "algorithmic flops 2*M_p+8 per slice-action (W_p only); peak = nominal FP64 "
                         "(MEASURED_PEAKS.json has no FP64 figure); measured_fma_peak from su_fma_peak"}
     cpu = None
