@@ -300,33 +300,82 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
         }
         const int jlast = kFold ? 1 : 0;          // last column of the outer Horner
         if (P.ncol - 1 >= jlast) {
-            int off = P.M;
-            {   // last column starts the outer Horner in x-bar^2
-                const int L = P.len[P.ncol - 1];
-                off -= L;
-                const R c = tab[off + L - 1];
+            if constexpr (sizeof(R) == 4) {
+                // single precision (issue bound): the first step of every Horner
+                // chain peeled -- the chains start from fma(c_top, z, c_next), a
+                // one-entry column goes straight into the outer chain -- so no
+                // chain is seeded by register copies; the same operations in the
+                // same order.  (In double the copies cost no FP64 issue and the
+                // peeled form spills.)
+                int off = P.M;
+                {   // last column starts the outer Horner in x-bar^2
+                    const int L = P.len[P.ncol - 1];
+                    off -= L;
+                    const R c = tab[off + L - 1];
+                    if (L == 1) {
 #pragma unroll
-                for (int b = 0; b < B; ++b) acc[b] = c;
-                for (int i = L - 2; i >= 0; --i) {
-                    const R ci = tab[off + i];
+                        for (int b = 0; b < B; ++b) acc[b] = c;
+                    } else {
+                        const R c0 = tab[off + L - 2];
 #pragma unroll
-                    for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+                        for (int b = 0; b < B; ++b) acc[b] = fma(c, Z[b], c0);
+                    }
+                    for (int i = L - 3; i >= 0; --i) {
+                        const R ci = tab[off + i];
+#pragma unroll
+                        for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+                    }
                 }
-            }
-            for (int j = P.ncol - 2; j >= jlast; --j) {
-                const int L = P.len[j];
-                off -= L;
-                R h[B];
-                const R c = tab[off + L - 1];
+                for (int j = P.ncol - 2; j >= jlast; --j) {
+                    const int L = P.len[j];
+                    off -= L;
+                    const R c = tab[off + L - 1];
+                    if (L == 1) {
 #pragma unroll
-                for (int b = 0; b < B; ++b) h[b] = c;
-                for (int i = L - 2; i >= 0; --i) {
-                    const R ci = tab[off + i];
+                        for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], c);
+                        continue;
+                    }
+                    R h[B];
+                    const R c0 = tab[off + L - 2];
 #pragma unroll
-                    for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                    for (int b = 0; b < B; ++b) h[b] = fma(c, Z[b], c0);
+                    for (int i = L - 3; i >= 0; --i) {
+                        const R ci = tab[off + i];
+#pragma unroll
+                        for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                    }
+#pragma unroll
+                    for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
                 }
+            } else {
+                int off = P.M;
+                {   // last column starts the outer Horner in x-bar^2
+                    const int L = P.len[P.ncol - 1];
+                    off -= L;
+                    const R c = tab[off + L - 1];
 #pragma unroll
-                for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
+                    for (int b = 0; b < B; ++b) acc[b] = c;
+                    for (int i = L - 2; i >= 0; --i) {
+                        const R ci = tab[off + i];
+#pragma unroll
+                        for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
+                    }
+                }
+                for (int j = P.ncol - 2; j >= jlast; --j) {
+                    const int L = P.len[j];
+                    off -= L;
+                    R h[B];
+                    const R c = tab[off + L - 1];
+#pragma unroll
+                    for (int b = 0; b < B; ++b) h[b] = c;
+                    for (int i = L - 2; i >= 0; --i) {
+                        const R ci = tab[off + i];
+#pragma unroll
+                        for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
+                    }
+#pragma unroll
+                    for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], h[b]);
+                }
             }
             if constexpr (kFold) {
 #pragma unroll
