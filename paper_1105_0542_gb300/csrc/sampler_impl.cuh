@@ -320,6 +320,7 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = fma(c, Z[b], c0);
                     }
+#pragma unroll 4
                     for (int i = L - 3; i >= 0; --i) {
                         const R ci = tab[off + i];
 #pragma unroll
@@ -339,6 +340,7 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                     const R c0 = tab[off + L - 2];
 #pragma unroll
                     for (int b = 0; b < B; ++b) h[b] = fma(c, Z[b], c0);
+#pragma unroll 4
                     for (int i = L - 3; i >= 0; --i) {
                         const R ci = tab[off + i];
 #pragma unroll
