@@ -357,6 +357,7 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                     const R c = tab[off + L - 1];
 #pragma unroll
                     for (int b = 0; b < B; ++b) acc[b] = c;
+#pragma unroll 4
                     for (int i = L - 2; i >= 0; --i) {
                         const R ci = tab[off + i];
 #pragma unroll
@@ -370,6 +371,7 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                     const R c = tab[off + L - 1];
 #pragma unroll
                     for (int b = 0; b < B; ++b) h[b] = c;
+#pragma unroll 4
                     for (int i = L - 2; i >= 0; --i) {
                         const R ci = tab[off + i];
 #pragma unroll
