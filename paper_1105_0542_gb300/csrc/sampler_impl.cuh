@@ -245,6 +245,7 @@ __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const 
         const int L = P.len[j];
         off -= L;
         R h = tab[off + L - 1];
+#pragma unroll 4
         for (int i = L - 2; i >= 0; --i) h = fma(h, Z, tab[off + i]);
         acc = fma(acc, Y, h);
     }
@@ -395,6 +396,7 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                 const R c = tab[L0 - 1];
 #pragma unroll
                 for (int b = 0; b < B; ++b) h[b] = c;
+#pragma unroll 4
                 for (int i = L0 - 2; i >= 1; --i) {
                     const R ci = tab[i];
 #pragma unroll
