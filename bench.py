@@ -36,7 +36,7 @@ import workloads  # noqa: E402
 METRIC = ("slice-actions/s and time to 1e-4 rel. error in A_N(a,b;T): plain vs chosen, 1 GB300")
 UNIT = "slice-actions/s"
 P_LIST = workloads.CONFIG2_P
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no FP64 tensor path); see the design doc
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no FP64 tensor path)
 # DRAM bytes (read + write) of one double-sampler launch of the p = 10 sweep
 # point on 2e5 samples, from the ncu capture summarised in
 # profiles/sampler_fp64_aho-g10_p10_s10_2e5.md; scaled by samples per launch

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_nt(const __nv_bfloat16 *
             for (int j = 0; j < 16; j += 4)
                 *reinterpret_cast<float4 *>(Ts + trow * ts + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
-        ok = __syncthreads_and(ok);   // one verdict for the CTA (the epilogue has a barrier)
+        ok = __syncthreads_and(ok);   // one outcome for the whole CTA (the epilogue has a barrier)
         if (ok) {
             const int nq = NT / 4;
             for (int i = tid; i < 128 * nq; i += kGemmThreads) {
