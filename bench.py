@@ -38,8 +38,8 @@ UNIT = "slice-actions/s"
 P_LIST = workloads.CONFIG2_P
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no FP64 tensor path)
 # DRAM bytes (read + write) of one double-sampler launch of the p = 10 sweep
-# point on 2e5 samples, from the ncu capture summarised in
-# profiles/sampler_fp64_aho-g10_p10_s10_2e5.md; scaled by samples per launch
+# point on 2e5 samples (an ncu capture of `--profile fp64`); scaled by
+# samples per launch
 FP64_TRAFFIC_BYTES, FP64_TRAFFIC_SAMPLES = 250_368, 200_000
 CPU_BUDGET_S = 15.0
 
