@@ -581,7 +581,7 @@ def run_nd(su, torch, dev, stream, flush):
     oscillator of Sec. 3.3 (A = 1, g = 1) at p = 10, N = 1024, the 3D one at
     p = 8, N = 256, and two coupled particles in 2D (d = 4) at p = 6, N = 64;
     1e6 samples each, double precision, device time of one plan execute
-    (L2 flushed)."""
+    (L2 flushed); the two anharmonic oscillators also in single precision."""
     aho2 = {(2, 0): 0.5, (0, 2): 0.5, (4, 0): 1 / 24, (0, 4): 1 / 24, (2, 2): 1 / 12}
     aho3 = {}
     for i in range(3):
@@ -596,14 +596,18 @@ def run_nd(su, torch, dev, stream, flush):
             aho3[tuple(e)] = 1 / 12
     two = {(2, 0, 0, 0): 0.5, (0, 2, 0, 0): 0.5, (0, 0, 2, 0): 0.5, (0, 0, 0, 2): 0.5, (2, 0, 2, 0): 0.1,
            (1, 0, 1, 0): -0.2, (0, 1, 0, 1): -0.2, (0, 2, 0, 2): 0.1}
-    cases = (("2D anharmonic oscillator A=1 g=1", aho2, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10),
-             ("3D anharmonic oscillator A=1 g=1", aho3, (0.0, 0.0, 0.0), (1.0, 0.5, -0.5), 1.0, 8, 8),
+    cases = (("2D anharmonic oscillator A=1 g=1", aho2, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10, "fp64"),
+             ("2D anharmonic oscillator A=1 g=1, single precision", aho2, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10,
+              "fp32"),
+             ("3D anharmonic oscillator A=1 g=1", aho3, (0.0, 0.0, 0.0), (1.0, 0.5, -0.5), 1.0, 8, 8, "fp64"),
+             ("3D anharmonic oscillator A=1 g=1, single precision", aho3, (0.0, 0.0, 0.0), (1.0, 0.5, -0.5), 1.0, 8,
+              8, "fp32"),
              ("two particles in 2D, harmonic + coupling", two, (0.3, 0.0, -0.3, 0.1), (0.2, 0.4, -0.1, -0.2),
-              1.0, 6, 6))
+              1.0, 6, 6, "fp64"))
     out = []
     n_mc = 1_000_000
-    for name, V, a, b, T, p, s in cases:
-        pl = su.PlanND(V, a, b, T, p, s, n_mc, 1234, n_blocks=64)
+    for name, V, a, b, T, p, s, prec in cases:
+        pl = su.PlanND(V, a, b, T, p, s, n_mc, 1234, n_blocks=64, precision=prec)
         t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device=dev)
         sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device=dev)
         pl.su_plan_execute(t, sc, stream)
@@ -615,7 +619,7 @@ def run_nd(su, torch, dev, stream, flush):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         top = pl.su_plan_finalize(t.cpu().numpy(), sc)[s]
-        out.append({"case": name, "d": len(a), "p": p, "N": 1 << s, "samples": n_mc, "ms": ms,
+        out.append({"case": name, "d": len(a), "p": p, "N": 1 << s, "precision": prec, "samples": n_mc, "ms": ms,
                     "terms": len(su.speedup_generate_nd(V, p, T / 2 ** s)),
                     "slice_actions_per_s": pl.slice_actions / (ms / 1e3), "amp": top["amp"],
                     "rel_err": top["rel_err"]})

@@ -348,8 +348,9 @@ int su_plan_destroy(su_plan *plan);
  * effective potential W(x, xb; eps) = sum_{m<p} sum_{k<=m} eps^(m-k) W_{m,k}
  * follows from the contracted recursion Eq. MBrec with the diagonal Eq. DIA
  * (double-double on the host); every coordinate has unit mass, no quantum
- * statistics (amplitudes are not symmetrised).  p <= 12, SU_FP64 only, the
- * exact bridge only (width_factor 1), one launch shape (seg_log2 = 0,
+ * statistics (amplitudes are not symmetrised).  p <= 12; SU_FP64, or SU_FP32
+ * (path and W in float, the stream's float layout, log-sum-exp in double);
+ * the exact bridge only (width_factor 1), one launch shape (seg_log2 = 0,
  * rounds <= 1); SU_ENOTSUP otherwise.
  *
  * su_plan_create_nd -- a plan for A_N^(p)(a, b; T), N = 2^s, with a and b

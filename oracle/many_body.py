@@ -216,10 +216,11 @@ def path(a, b, T, s, seed, sample, instance=0, bits=53):
     return q
 
 
-def logweights(V, d, p, a, b, T, s, seed, n, sample0=0, instance=0):
+def logweights(V, d, p, a, b, T, s, seed, n, sample0=0, instance=0, bits=53):
     """(n, s) array of w_n = -eps_n sum_k W_p on the level-n subpath, and the
-    condition scales eps_n sum_k sum |terms|."""
-    q = np.stack([path(a, b, T, s, seed, sample0 + i, instance) for i in range(n)])
+    condition scales eps_n sum_k sum |terms|; bits = 53 or 24 selects the
+    uniforms (and normal layout) of the double or single-precision stream."""
+    q = np.stack([path(a, b, T, s, seed, sample0 + i, instance, bits) for i in range(n)])
     w = np.empty((n, s))
     wa = np.empty((n, s))
     for lev in range(1, s + 1):

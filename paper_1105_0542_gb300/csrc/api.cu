@@ -505,6 +505,7 @@ static int configure_nd(su_plan &pl) {
     using namespace su;
     const int S = pl.s;
     const int M = (int)pl.N.hi.size();
+    const int prec = pl.opt.precision;
     std::vector<double> tabd((size_t)std::max(S, 1) * M, 0.0);
     for (int d = 0; d < S; ++d) {
         const double eps = pl.T / std::ldexp(1.0, S - d);
@@ -512,10 +513,17 @@ static int configure_nd(su_plan &pl) {
         nd_table(pl.N, eps, t);
         if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
         for (int i = 0; i < M; ++i) {
-            if (!std::isfinite(t[(size_t)i])) return fail(SU_ENONFINITE, "non-finite coefficient at level %d", S - d);
+            if (!std::isfinite(t[(size_t)i]) || (prec == SU_FP32 && !std::isfinite((float)t[(size_t)i])))
+                return fail(SU_ENONFINITE, "non-finite coefficient at level %d", S - d);
             tabd[(size_t)d * M + i] = t[(size_t)i];
         }
     }
+    const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> blob(tabd.size() * rs);
+    if (prec == SU_FP32)
+        for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
+    else
+        std::memcpy(blob.data(), tabd.data(), blob.size());
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -525,8 +533,8 @@ static int configure_nd(su_plan &pl) {
     CU(cudaGetDevice(&pl.device), "cudaGetDevice");
     int sms = 0;
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
-    CU(dmalloc(&pl.d_tables, tabd.size() * sizeof(double)), "device allocation (tables)");
-    CU(cudaMemcpy(pl.d_tables, tabd.data(), tabd.size() * sizeof(double), cudaMemcpyHostToDevice), "upload tables");
+    CU(dmalloc(&pl.d_tables, blob.size()), "device allocation (tables)");
+    CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
     std::vector<GeneralNode> nodes(pl.N.depth.size());
     for (size_t t = 0; t < nodes.size(); ++t) {
         if (pl.N.count[t] > 65535) return fail(SU_ENOTSUP, "a monomial group has more than 65535 entries");
@@ -568,12 +576,12 @@ static int configure_nd(su_plan &pl) {
         Q.a[c] = pl.nd_a[(size_t)c];
         Q.b[c] = pl.nd_b[(size_t)c];
     }
-    pl.smem = nd_smem_bytes(Q);
-    const int occ = nd_occupancy(Q, pl.smem);
+    pl.smem = nd_smem_bytes(Q, prec);
+    const int occ = nd_occupancy(Q, prec, pl.smem);
     if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
     pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
     Q.pstride = (int64_t)pl.grid * kThreads;
-    pl.path_bytes = Q.pstride * (((int64_t)1 << (S - std::min(S, kNdSeg))) + 1) * pl.nd * (int64_t)sizeof(double);
+    pl.path_bytes = Q.pstride * (((int64_t)1 << (S - std::min(S, kNdSeg))) + 1) * pl.nd * (int64_t)rs;
     pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
     pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + ((pl.path_bytes + 255) / 256) * 256 + 256;
     pl.tuple_bytes = pl.n_blocks * pl.levels * 4 * (int64_t)sizeof(double);
@@ -596,7 +604,6 @@ int su_plan_create_nd(int d, const int *exps, const double *coefs, int n_terms, 
     int rc = validate(-1, nullptr, 0, a[0], b[0], T, p, s, n_mc, o);
     if (rc) return rc;
     if (p > su::kNdMaxP) return fail(SU_ENOTSUP, "systems of several coordinates support p <= %d", su::kNdMaxP);
-    if (o.precision != SU_FP64) return fail(SU_ENOTSUP, "systems of several coordinates run in double only");
     if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "systems of several coordinates sample the exact bridge only");
     if (o.seg_log2 != 0 || o.rounds > 1) return fail(SU_ENOTSUP, "systems of several coordinates have one launch shape");
     std::unique_ptr<su_plan> pl(new (std::nothrow) su_plan);
@@ -687,8 +694,8 @@ int su_plan_execute_range(su_plan *pl, int64_t b0, int64_t b1, void *d_tuples, v
     if (pl->nd) {
         su::NdParams Q = pl->Q;
         Q.base = P;
-        Q.paths = reinterpret_cast<double *>(static_cast<char *>(d_scratch) + ((pl->partial_bytes + 255) / 256) * 256);
-        CU(su::launch_nd(Q, grid, pl->smem, st), "sampler launch");
+        Q.paths = static_cast<char *>(d_scratch) + ((pl->partial_bytes + 255) / 256) * 256;
+        CU(su::launch_nd(Q, pl->opt.precision, grid, pl->smem, st), "sampler launch");
     } else {
         CU(su::launch_sampler(P, pl->opt.precision, grid, pl->smem, st), "sampler launch");
     }
@@ -869,14 +876,14 @@ int speedup_logweights_nd(int d, const int *exps, const double *coefs, int n_ter
     Q.base.w_out = d_w;
     Q.base.sample0 = sample0;
     Q.base.partial = nullptr;
-    const size_t smem = su::nd_smem_bytes(Q);
+    const size_t smem = su::nd_smem_bytes(Q, o.precision);
     void *buf = nullptr;
     const int64_t pb = ((pl->path_bytes + 255) / 256) * 256;
     CU(dmalloc_async(&buf, (size_t)(pb + 256), st), "cudaMallocAsync");
-    Q.paths = static_cast<double *>(buf);
+    Q.paths = buf;
     Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(buf) + pb);
     cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = su::launch_nd(Q, pl->grid, smem, st);
+    if (e == cudaSuccess) e = su::launch_nd(Q, o.precision, pl->grid, smem, st);
     int flags = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -119,12 +119,13 @@ struct NdParams {
     int D, H, G, n_nodes;     // Horner in z_H^G
     const GeneralNode *nodes; // device
     double a[kNdMaxDim], b[kNdMaxDim];
-    double *paths;            // device: segment endpoint i, coordinate c of slot t at [(i D + c) pstride + t]
+    void *paths;              // device (double or float): segment endpoint i, coordinate c of slot t
+                              // at [(i D + c) pstride + t]
     int64_t pstride;          // slots = grid x kThreads
 };
-size_t nd_smem_bytes(const NdParams &Q);
-int nd_occupancy(const NdParams &Q, size_t smem);
-cudaError_t launch_nd(const NdParams &Q, int grid, size_t smem, cudaStream_t st);
+size_t nd_smem_bytes(const NdParams &Q, int precision);
+int nd_occupancy(const NdParams &Q, int precision, size_t smem);
+cudaError_t launch_nd(const NdParams &Q, int precision, int grid, size_t smem, cudaStream_t st);
 
 cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size_t smem,
                            cudaStream_t st);

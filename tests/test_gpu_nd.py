@@ -28,7 +28,7 @@ from oracle import many_body as mb  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-U64 = 2.0 ** -53
+U64, U32 = 2.0 ** -53, 2.0 ** -24
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,9 +38,9 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _gpu_w(V, a, b, T, p, s, n, seed, sample0=0):
+def _gpu_w(V, a, b, T, p, s, n, seed, sample0=0, precision="fp64"):
     w = torch.full((n, s), float("nan"), dtype=torch.float64, device="cuda")
-    su.speedup_logweights_nd(V, a, b, T, p, s, sample0, n, seed, w)
+    su.speedup_logweights_nd(V, a, b, T, p, s, sample0, n, seed, w, precision=precision)
     torch.cuda.synchronize()
     return w.cpu().numpy()
 
@@ -86,6 +86,30 @@ def test_nd_logweights_match_oracle(case):
     wo, wabs = mb.logweights(_frac(V), d, p, np.array(a), np.array(b), T, s, seed, n, s0)
     assert np.isfinite(wg).all()
     assert _excess(wg, wo, wabs, 1e-12, U64) <= 1.0
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_nd_logweights_fp32_match_oracle(case):
+    """Single precision: path and W in float on the stream's float layout,
+    against the oracle fed the same 24-bit uniforms (1e-5 relative, or the
+    float summation bound where the terms cancel)."""
+    _, V, a, b, T, p, s, n, seed, s0 = case
+    d = len(a)
+    wg = _gpu_w(V, a, b, T, p, s, n, seed, s0, precision="fp32")
+    wo, wabs = mb.logweights(_frac(V), d, p, np.array(a), np.array(b), T, s, seed, n, s0, bits=24)
+    assert np.isfinite(wg).all()
+    assert _excess(wg, wo, wabs, 1e-5, U32) <= 1.0
+
+
+def test_nd_fp32_and_fp64_amplitudes_agree():
+    """Independent streams: the two precisions' amplitudes within 3 combined
+    sigma at every level."""
+    V, a, b, T, p, s = AHO2, (0.0, 0.2), (1.0, -0.3), 1.0, 10, 6
+    r64 = su.speedup_amplitude_nd(V, a, b, T, p, s, 1_000_000, 5, n_blocks=64)
+    r32 = su.speedup_amplitude_nd(V, a, b, T, p, s, 1_000_000, 5, n_blocks=64, precision="fp32")
+    for lev in range(1, s + 1):
+        sig = math.hypot(r64[lev]["err"], r32[lev]["err"])
+        assert abs(r64[lev]["amp"] - r32[lev]["amp"]) <= 3 * sig, lev
 
 
 def test_one_coordinate_equals_the_one_dimensional_model():

@@ -293,7 +293,6 @@ def test_nd_generator_matches_the_oracle(V, d, p):
     ({(-1, 2): 1.0}, {}, -1),                         # negative exponent
     ({(2, 0): float("inf")}, {}, -1),                 # non-finite coefficient
     ({(2, 0): 1.0}, {"p": 13}, -6),
-    ({(2, 0): 1.0}, {"precision": "fp32"}, -6),
     ({(2, 0): 1.0}, {"width_factor": 1.4}, -6),
     ({(2, 0): 1.0}, {"a": (float("nan"), 0.0)}, -1),
 ])
