@@ -24,45 +24,87 @@ __device__ __forceinline__ R pick(const R (&z)[2 * D], int sym) {
     return v;
 }
 
-template <typename R, int D>
-__device__ __forceinline__ void nd_pair(const R (&za)[2 * D], const R (&zb)[2 * D], const R *__restrict__ coef,
-                                        const NdParams &Q, R &wa, R &wb) {
-    R sa[kNdMaxDepth + 1], sb[kNdMaxDepth + 1];
-    sa[0] = 1;
-    sb[0] = 1;
-    R Ya = 1, Yb = 1;
-    const R ha = pick<R, D>(za, Q.H), hb = pick<R, D>(zb, Q.H);
-    for (int g = 0; g < Q.G; ++g) {
-        Ya *= ha;
-        Yb *= hb;
+// The monomial stack of B slices as one vector (one 8- or 16-byte local
+// access per node for all B slices).
+template <typename R, int B>
+struct alignas(sizeof(R) * B) Lanes {
+    R v[B];
+};
+
+// W(x, xb; eps) for B slices at once: the prefix-node program (each node
+// multiplies its parent's monomial by one variable, then adds its Horner
+// polynomial in z_H^G times that monomial); the node and coefficient loads
+// are shared by the B slices.
+template <typename R, int D, int B>
+__device__ __forceinline__ void nd_multi(const R (&z)[B][2 * D], const R *__restrict__ coef, const NdParams &Q,
+                                         R (&w)[B]) {
+    Lanes<R, B> stk[kNdMaxDepth + 1];
+    R Y[B], acc[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        stk[0].v[i] = 1;
+        acc[i] = 0;
+        Y[i] = 1;
     }
-    R acc_a = 0, acc_b = 0;
+    for (int g = 0; g < Q.G; ++g) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) Y[i] *= pick<R, D>(z[i], Q.H);
+    }
     const GeneralNode *__restrict__ nodes = Q.nodes;
     for (int t = 0; t < Q.n_nodes; ++t) {
         const GeneralNode nd = nodes[t];
-        R ma = 1, mb = 1;
+        Lanes<R, B> m;
         if (t) {
-            ma = sa[nd.depth - 1] * pick<R, D>(za, nd.sym);
-            mb = sb[nd.depth - 1] * pick<R, D>(zb, nd.sym);
-            sa[nd.depth] = ma;
-            sb[nd.depth] = mb;
+            const Lanes<R, B> par = stk[nd.depth - 1];
+#pragma unroll
+            for (int i = 0; i < B; ++i) m.v[i] = par.v[i] * pick<R, D>(z[i], nd.sym);
+            stk[nd.depth] = m;
+        } else {
+#pragma unroll
+            for (int i = 0; i < B; ++i) m.v[i] = 1;
         }
         const int cnt = nd.count;
         if (cnt) {
             const R *c = coef + nd.first;
-            R ha = c[cnt - 1], hb = ha;
+            R h[B];
+            const R top = c[cnt - 1];
+#pragma unroll
+            for (int i = 0; i < B; ++i) h[i] = top;
 #pragma unroll 4
             for (int e = cnt - 2; e >= 0; --e) {
                 const R ce = c[e];
-                ha = fma(ha, Ya, ce);
-                hb = fma(hb, Yb, ce);
+#pragma unroll
+                for (int i = 0; i < B; ++i) h[i] = fma(h[i], Y[i], ce);
             }
-            acc_a = fma(ha, ma, acc_a);
-            acc_b = fma(hb, mb, acc_b);
+#pragma unroll
+            for (int i = 0; i < B; ++i) acc[i] = fma(h[i], m.v[i], acc[i]);
         }
     }
-    wa = acc_a;
-    wb = acc_b;
+#pragma unroll
+    for (int i = 0; i < B; ++i) w[i] = acc[i];
+}
+
+// Slices k..k+B-1 of a level (points pt(k*stp) .. pt((k+B)*stp)), added to w
+// two at a time in ascending order.
+template <typename R, int D, int B, typename PT>
+__device__ __forceinline__ void nd_block(const R *__restrict__ tab, const NdParams &Q, PT &&pt, int k, int stp,
+                                         R &w) {
+    R z[B][2 * D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        R pl = pt(k * stp, c);
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const R pr = pt((k + i + 1) * stp, c);
+            z[i][c] = (R)0.5 * (pl + pr);
+            z[i][D + c] = (R)0.5 * (pr - pl);
+            pl = pr;
+        }
+    }
+    R wv[B];
+    nd_multi<R, D, B>(z, tab, Q, wv);
+#pragma unroll
+    for (int i = 0; i < B; i += 2) w += wv[i] + wv[i + 1];
 }
 
 // R = double or float (the path, W and the per-level sums; the item's
@@ -97,6 +139,7 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
     R *q = reinterpret_cast<R *>(Q.paths) + (int64_t)blockIdx.x * kThreads + tid;
     auto co = [&](int i, int c) -> R & { return q[((int64_t)i * D + c) * ps]; };
     R seg[((1 << kNdSeg) + 1) * D];
+    constexpr int kB = sizeof(R) == 8 ? 2 : 4;   // slices per pass of the program
 
     for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t b = item / P.items_per_block;
@@ -147,24 +190,15 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
                 }
             }
             // w_n = -eps_n sum_k W on the level-n subpath (level n = S - dl),
-            // slices in ascending order, two at a time
+            // slices in ascending order, kB at a time (two on a level of two)
             R wloc[SU_MAX_S];
             for (int dl = 0; dl < L; ++dl) wloc[dl] = 0;
             auto slices = [&](const R *tab, auto &&pt, int stp, int ns, R &w) {
-                for (int k = 0; k < ns; k += 2) {
-                    R za[2 * D], zb[2 * D];
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        const R pl = pt(k * stp, c), pm = pt((k + 1) * stp, c), pr = pt((k + 2) * stp, c);
-                        za[c] = (R)0.5 * (pl + pm);
-                        za[D + c] = (R)0.5 * (pm - pl);
-                        zb[c] = (R)0.5 * (pm + pr);
-                        zb[D + c] = (R)0.5 * (pr - pm);
-                    }
-                    R wa, wb;
-                    nd_pair<R, D>(za, zb, tab, Q, wa, wb);
-                    w += wa + wb;
+                if (ns < kB) {
+                    nd_block<R, D, 2>(tab, Q, pt, 0, stp, w);
+                    return;
                 }
+                for (int k = 0; k < ns; k += kB) nd_block<R, D, kB>(tab, Q, pt, k, stp, w);
             };
             const R *tabs = reinterpret_cast<const R *>(P.tables);
             for (int dl = F; dl < L; ++dl)   // coarse levels: between segment endpoints
