@@ -59,13 +59,14 @@ def parse():
     ap.add_argument("--no-general", action="store_true", help="skip the general-potential entry")
     ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
     ap.add_argument("--no-fig2", action="store_true", help="skip the Fig. 2 convergence and continuum-fit entry")
-    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "general", "evolution", "train"],
+    ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "nd32", "general", "evolution",
+                                          "train"],
                     default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
                          "every 16th instance of the amplitude matrix; proposal = the learned-proposal "
                          "instance with a fixed random network (--profile-n samples); nd = the 2D anharmonic "
-                         "oscillator, p = 10, s = 10; general = AHO g = 10 through the general-potential mode, "
+                         "oscillator, p = 10, s = 10 (nd32: in single precision); general = AHO g = 10 through the general-potential mode, "
                          "p = 10, s = 10 (--profile-n samples); evolution = the Fig. 3 AHO matrix (n = 16385); "
                          "train = 20 training steps of the learned proposal on --profile-n plain paths")
     ap.add_argument("--profile-p", type=int, default=10)
@@ -803,10 +804,11 @@ def run_profile(args):
                                                _init_theta(0), n_train=args.profile_n, steps=20)
         print(f"profile case train: {args.profile_n} paths, 20 steps, loss {losses[0]:.4f} -> {losses[-1]:.4f}")
         return
-    if args.profile in ("nd", "general"):
-        if args.profile == "nd":
+    if args.profile in ("nd", "nd32", "general"):
+        if args.profile != "general":
             V = {(2, 0): 0.5, (0, 2): 0.5, (4, 0): 1 / 24, (0, 4): 1 / 24, (2, 2): 1 / 12}
-            pl = su.PlanND(V, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10, args.profile_n, 1234, n_blocks=64)
+            pl = su.PlanND(V, (0.0, 0.0), (1.0, 0.5), 1.0, 10, 10, args.profile_n, 1234, n_blocks=64,
+                           precision="fp32" if args.profile == "nd32" else "fp64")
         else:
             gp = list(su.general_params((0.0, 0.0, 0.5, 0.0, 10.0 / 24.0)))
             pl = su.Plan("general", gp, 0.0, 1.0, 1.0, 10, 10, args.profile_n, 1234, n_blocks=64)

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
     R *q = reinterpret_cast<R *>(Q.paths) + (int64_t)blockIdx.x * kThreads + tid;
     auto co = [&](int i, int c) -> R & { return q[((int64_t)i * D + c) * ps]; };
     R seg[((1 << kNdSeg) + 1) * D];
-    constexpr int kB = sizeof(R) == 8 ? 2 : 4;   // slices per pass of the program
+    constexpr int kB = sizeof(R) == 8 ? 2 : 8;   // slices per pass of the program
 
     for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t b = item / P.items_per_block;
@@ -190,11 +190,17 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
                 }
             }
             // w_n = -eps_n sum_k W on the level-n subpath (level n = S - dl),
-            // slices in ascending order, kB at a time (two on a level of two)
+            // slices in ascending order, kB at a time (fewer on a level of two or four)
             R wloc[SU_MAX_S];
             for (int dl = 0; dl < L; ++dl) wloc[dl] = 0;
             auto slices = [&](const R *tab, auto &&pt, int stp, int ns, R &w) {
                 if (ns < kB) {
+                    if constexpr (kB > 4) {
+                        if (ns == 4) {
+                            nd_block<R, D, 4>(tab, Q, pt, 0, stp, w);
+                            return;
+                        }
+                    }
                     nd_block<R, D, 2>(tab, Q, pt, 0, stp, w);
                     return;
                 }
