@@ -19,7 +19,8 @@ Calculation of Transition Amplitudes via the Effective Action Approach"):
   kernel, the exact Gaussian value of A_N^(p) for the harmonic oscillator,
   tensor-grid quadrature over the N-1 intermediate points for tiny N, and an
   exact-diagonalisation reference for the continuum amplitude.
-* ``evolution`` -- the evolution-operator matrix of Sec. 5 and its spectrum.
+* ``evolution`` -- the evolution-operator matrix of Sec. 5 and its spectrum
+  (the model potentials and the general potentials).
 * ``proposal`` -- the learned proposal's network, loss and paths in numpy.
 * ``general_v`` -- W_p of a general potential in the derivative symbols
   V_j (Sec. 3.1) and the derivatives of its families.

@@ -30,6 +30,7 @@ import numpy as np
 
 from . import effective_action as ea
 from . import exact
+from . import general_v
 
 
 BAND = 40.0   # largest (x_j - x_i)^2/(2t) of a nonzero element (reading E-1)
@@ -50,6 +51,22 @@ def evolution_matrix(model_name, params, p, t, L, n):
     free = (xj - xi) ** 2 / (2.0 * t)
     band = free <= BAND
     expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - free - t * np.where(band, W, 0.0)
+    return np.where(band, np.exp(expo), 0.0)
+
+
+def evolution_matrix_general(params, p, t, x):
+    """U of the docstring for a general potential (``general_v`` parameters,
+    W_p from the derivative symbols) on the equally spaced grid x, which
+    need not be symmetric about 0."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    delta = (x[-1] - x[0]) / (n - 1)
+    xi, xj = np.meshgrid(x, x, indexing="ij")
+    free = (xj - xi) ** 2 / (2.0 * t)
+    band = free <= BAND
+    W = np.zeros((n, n))
+    W[band] = general_v.wp(params, p, 0.5 * (xi[band] + xj[band]), 0.5 * (xj[band] - xi[band]), t)
+    expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - free - t * W
     return np.where(band, np.exp(expo), 0.0)
 
 
