@@ -187,3 +187,29 @@ def test_exponential_terms_derivatives_to_the_highest_order():
             assert got[j] == pytest.approx(ref, rel=1e-12, abs=1e-12 * max(1.0, abs(ref))), (xq, j)
     # 33 parameters are the same potential without exponential terms
     assert gv.split_params_all(_params(poly=[D]))[3] == []
+
+
+def _read_golden_w3():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "w3_derivative_symbols.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            m, k, coef, mono = line.split()
+            e = [0] * 6
+            for factor in mono.split("*"):
+                sym, _, power = factor.partition("^")
+                e[int(sym[1:])] += int(power) if power else 1
+            out.setdefault((int(m), int(k)), {})[tuple(e)] = Fraction(coef)
+    return out
+
+
+def test_level_three_matches_the_hand_derivation():
+    golden = _read_golden_w3()
+    c = gv.coefficients(3)
+    assert set(c) == set(golden)
+    for key, poly in golden.items():
+        assert c[key] == poly, key
