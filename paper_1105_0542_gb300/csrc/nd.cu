@@ -9,11 +9,6 @@
 namespace su {
 namespace {
 
-// -eps W of two slices with variables za, zb = (x_1..x_D, xb_1..xb_D): the
-// monomial program walked depth first (each prefix its parent times one
-// variable, the parent the top of a per-slice stack), each prefix's entries
-// combined by Horner in z_H^G and added times the prefix; the two slices
-// share every node and coefficient load.
 // z[sym] with z in registers: a chain of selects on the integer pipes
 // instead of a dynamically indexed local-memory load
 template <typename R, int D>
@@ -24,17 +19,18 @@ __device__ __forceinline__ R pick(const R (&z)[2 * D], int sym) {
     return v;
 }
 
-// The monomial stack of B slices as one vector (one 8- or 16-byte local
-// access per node for all B slices).
+// One stack entry of B slices as one aligned vector (16 or 32 bytes: one or
+// two 16-byte local accesses per node for all B slices).
 template <typename R, int B>
 struct alignas(sizeof(R) * B) Lanes {
     R v[B];
 };
 
-// W(x, xb; eps) for B slices at once: the prefix-node program (each node
-// multiplies its parent's monomial by one variable, then adds its Horner
-// polynomial in z_H^G times that monomial); the node and coefficient loads
-// are shared by the B slices.
+// -eps W for B slices at once, each with variables z = (x_1..x_D, xb_1..xb_D):
+// the monomial program walked depth first (each prefix node its parent times
+// one variable, the parent the top of the stack), each node's entries
+// combined by Horner in z_H^G and added times its monomial; the B slices
+// share every node and coefficient load.
 template <typename R, int D, int B>
 __device__ __forceinline__ void nd_multi(const R (&z)[B][2 * D], const R *__restrict__ coef, const NdParams &Q,
                                          R (&w)[B]) {

@@ -111,8 +111,9 @@ cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *
 // midpoint j takes normal j D + c of the sample's stream), built and weighed
 // in segments of 2^kNdSeg slices (segment endpoints in a global scratch, one
 // segment's points in local memory); W(x, xb; eps) per slice from the monomial program of
-// NdEffective (nodes as GeneralNode; entries = powers of z_H), two slices at
-// a time; weights and per-item tuples as the one-dimensional sampler's.
+// NdEffective (nodes as GeneralNode; entries = powers of z_H), several
+// slices at a time (two in double, eight in single precision); weights and
+// per-item tuples as the one-dimensional sampler's.
 constexpr int kNdSeg = 5;     // the several-coordinates path in segments of 2^5 slices
 struct NdParams {
     SamplerParams base;       // S, levels, tables (per level, global), M, sigma, stream, items, outputs
