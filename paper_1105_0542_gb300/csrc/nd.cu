@@ -19,7 +19,7 @@ __device__ __forceinline__ R pick(const R (&z)[2 * D], int sym) {
     return v;
 }
 
-// One stack entry of B slices as one aligned vector (16 or 32 bytes: one or
+// One stack entry of B slices as one aligned vector (8 to 32 bytes: one or
 // two 16-byte local accesses per node for all B slices).
 template <typename R, int B>
 struct alignas(sizeof(R) * B) Lanes {
