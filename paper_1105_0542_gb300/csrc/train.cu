@@ -65,10 +65,10 @@ struct EpArgs {
 // A: [M][lda], B: [N][ldb] bf16 (lda, ldb multiples of 8); K and the K-range
 // multiples of 32.  kGemmThreads = 256 threads: warp w reads tensor-memory lane
 // quadrant w % 4, columns [64 (w / 4), 64 (w / 4) + 64) of the tile.
-// Per round, 128 x 128 of A and min(N - n0, 128) x 128 of B are staged in the
+// Per K-step, 128 x 128 of A and min(N - n0, 128) x 128 of B are staged in the
 // operand layout of mlp.cuh (zeros outside M, N and the K-range), thread 0
 // issues K/16 MMAs (M = 128, N = the tile's width rounded up to 16) and
-// commits them; all threads wait (bounded) before the next round overwrites
+// commits them; all threads wait (bounded) before the next K-step overwrites
 // the stage.  Epilogue: tcgen05.ld of each thread's row, stored or added.
 // A wait that gives up sets *status.
 constexpr int kGemmThreads = 256;
