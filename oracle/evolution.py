@@ -31,6 +31,7 @@ import numpy as np
 from . import effective_action as ea
 from . import exact
 from . import general_v
+from . import many_body
 
 
 BAND = 40.0   # largest (x_j - x_i)^2/(2t) of a nonzero element (reading E-1)
@@ -68,6 +69,23 @@ def evolution_matrix_general(params, p, t, x):
     W[band] = general_v.wp(params, p, 0.5 * (xi[band] + xj[band]), 0.5 * (xj[band] - xi[band]), t)
     expo = math.log(delta) - 0.5 * math.log(2.0 * math.pi * t) - free - t * W
     return np.where(band, np.exp(expo), 0.0)
+
+
+def evolution_matrix_nd(V, d, p, t, x1):
+    """U of the docstring for a system of d coordinates (``many_body``
+    polynomial V) on the tensor grid x1^d, points in C order: the element of
+    grid points q and q' is Delta^d (2 pi t)^(-d/2) exp(-|q' - q|^2/(2t) - t
+    W_p(x, xb; t)), zero where |q' - q|^2/(2t) > 40."""
+    x1 = np.asarray(x1, dtype=np.float64)
+    delta = (x1[-1] - x1[0]) / (x1.shape[0] - 1)
+    P = np.stack([g.ravel() for g in np.meshgrid(*([x1] * d), indexing="ij")], axis=1)
+    n = P.shape[0]
+    free = ((P[None, :, :] - P[:, None, :]) ** 2).sum(axis=-1) / (2.0 * t)
+    I, J = np.nonzero(free <= BAND)
+    W = many_body.wp(V, d, p, 0.5 * (P[I] + P[J]), 0.5 * (P[J] - P[I]), t)
+    U = np.zeros((n, n))
+    U[I, J] = np.exp(d * math.log(delta) - 0.5 * d * math.log(2.0 * math.pi * t) - free[I, J] - t * W)
+    return U
 
 
 def evolution_matrix_abs(model_name, params, p, t, L, n):

@@ -259,3 +259,29 @@ def dvr_amplitude(V, a, b, T, L=20.0, dx=0.02):
     H = K / (2 * dx * dx) + np.diag(V(x))
     E, U = np.linalg.eigh(H)
     return float(np.sum(U[ia] * U[ib] * np.exp(-E * T)) / dx), E
+
+
+def dvr_energies_2d(V, L, dx, k):
+    """The k lowest eigenvalues of H = -(d^2/dx^2 + d^2/dy^2)/2 + V(x, y) on
+    the two-dimensional sinc-DVR grid (x_i, y_j) = (i dx, j dx), |x|, |y| <= L:
+    the one-dimensional sinc kinetic matrix on each axis (Kronecker sum),
+    applied matrix-free, with scipy's Lanczos solver."""
+    import scipy.sparse.linalg as sla
+    m = int(round(L / dx))
+    x = dx * np.arange(-m, m + 1)
+    n = len(x)
+    d = np.arange(n)
+    D = d[:, None] - d[None, :]
+    with np.errstate(divide="ignore"):
+        K = np.where(D == 0, math.pi ** 2 / 3.0, 2.0 * (-1.0) ** np.abs(D) / np.where(D == 0, 1, D) ** 2)
+    K = K / (2 * dx * dx)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    Vd = V(X, Y)
+
+    def apply(v):
+        v = v.reshape(n, n)
+        return (K @ v + v @ K.T + Vd * v).ravel()
+
+    op = sla.LinearOperator((n * n, n * n), matvec=apply, dtype=np.float64)
+    E = sla.eigsh(op, k=k, which="SA", tol=1e-13)[0]
+    return np.sort(E)
