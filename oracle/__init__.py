@@ -17,10 +17,12 @@ Calculation of Transition Amplitudes via the Effective Action Approach"):
   fed by its own Philox4x32-10 and Box-Muller, one sample at a time.
 * ``exact`` -- closed forms and brute force that pin the oracle: the Mehler
   kernel, the exact Gaussian value of A_N^(p) for the harmonic oscillator,
-  tensor-grid quadrature over the N-1 intermediate points for tiny N, and an
-  exact-diagonalisation reference for the continuum amplitude.
+  tensor-grid quadrature over the N-1 intermediate points for tiny N, and
+  exact-diagonalisation references (harmonic basis, sinc-DVR in one and two
+  dimensions) for continuum amplitudes and spectra.
 * ``evolution`` -- the evolution-operator matrix of Sec. 5 and its spectrum
-  (the model potentials and the general potentials).
+  (the model potentials, the general potentials and systems of several
+  coordinates on a tensor grid).
 * ``proposal`` -- the learned proposal's network, loss and paths in numpy.
 * ``general_v`` -- W_p of a general potential in the derivative symbols
   V_j (Sec. 3.1) and the derivatives of its families.
