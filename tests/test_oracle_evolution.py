@@ -8,7 +8,9 @@ and its spectrum, CPU only.
   t = 0.1, L = 10): the lowest eight energies equal the sinc-DVR
   diagonalisation of the Hamiltonian (an independent method) within 1e-9;
 * the effective action's convergence: at p = 4 the short-time error is
-  visible (> 1e-7), at p = 8 it is below 1e-9.
+  visible (> 1e-7), at p = 8 it is below 1e-9;
+* the Poeschl-Teller model (tanh^2 ring): the three bound states of
+  -6/cosh^2 x equal the closed form -(3 - n)^2/2 within 1e-10 at p = 8.
 """
 import math
 
@@ -57,3 +59,16 @@ def test_spectrum_converges_with_the_level_p():
         U = ev.evolution_matrix("aho", [1.0, 48.0], p, 0.02, 8.0, 401)
         err[p] = np.abs(ev.energies(U, 0.02, 6) - Ed).max()
     assert err[4] > 1e-7 and err[8] < 1e-9, err
+
+
+def test_poeschl_teller_model_spectrum_is_the_closed_form():
+    """The model-specific Poeschl-Teller action (the tanh^2 ring) in the
+    evolution operator: V = -6/cosh^2 x = -l(l+1)/2 sech^2 x with l = 3 has
+    the bound states E_n = -(l - n)^2/2 = -4.5, -2, -0.5; p = 8 gives them
+    within 1e-10, p = 4 misses them by > 1e-8."""
+    exact_E = np.array([-4.5, -2.0, -0.5])
+    err = {}
+    for p in (8, 4):
+        U = ev.evolution_matrix("mpt", [6.0, 1.0], p, 0.02, 14.0, 1401)
+        err[p] = np.abs(ev.energies(U, 0.02, 3) - exact_E).max()
+    assert err[8] <= 1e-10 and err[4] > 1e-8, err
