@@ -389,6 +389,32 @@ int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms
                         double eps, int *out_exps, double *out_w, int capacity, int *n_out);
 
 /*
+ * speedup_wp -- the level-p effective potential W_p(x, xb; eps) of a
+ * one-dimensional model (Eq. ansatz, coefficients of Eq. 1Drec and Eq.
+ * diagonal) at n_points points, on the host (no device), as plans evaluate
+ * their level-0 weight: the collapsed table of speedup_generate_coeffs in
+ * double-double for the model potentials, the general mode's program in the
+ * derivative symbols V^(j)(x) for SU_GENERAL.  x, xb, w: host arrays of
+ * n_points doubles; w[i] = W_p(x[i], xb[i]; eps).  Errors: SU_EINVAL (unknown
+ * model, wrong parameters, p outside 1..SU_MAX_P, eps not finite and > 0,
+ * n_points < 0, a missing array), SU_ENOTSUP (SU_GENERAL above p = 12).
+ */
+int speedup_wp(int model, const double *params, int n_params, int p, double eps,
+               const double *x, const double *xb, int64_t n_points, double *w);
+
+/*
+ * speedup_wp_nd -- W(x, xb; eps) of a system of d coordinates (potential
+ * arguments as su_plan_create_nd; Sec. 2.2, Eq. MBrec, Eq. DIA) at n_points
+ * points, on the host, through the evaluation program of the
+ * several-coordinates kernel (prefix nodes, Horner in one variable, the
+ * level's rounded table).  x, xb: host arrays laid out [point][d]; w: host,
+ * n_points doubles.  Errors as speedup_generate_nd, and SU_EINVAL for eps not
+ * finite and > 0, n_points < 0 or a missing array.
+ */
+int speedup_wp_nd(int d, const int *exps, const double *coefs, int n_terms, int p, double eps,
+                  const double *x, const double *xb, int64_t n_points, double *w);
+
+/*
  * su_plan_sizes -- sizes of the caller-provided device buffers of
  * su_plan_execute, in bytes: *tuple_bytes for d_tuples, *scratch_bytes for
  * d_scratch; *levels = the number of levels sampled (s, or 1 without the

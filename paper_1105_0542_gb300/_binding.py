@@ -31,7 +31,7 @@ EXPORTS = [
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
-    "su_fit_continuum",
+    "su_fit_continuum", "speedup_wp", "speedup_wp_nd",
 ]
 MAX_D = 4
 MLP_PARAMS = 34178
@@ -130,6 +130,8 @@ def load(build_if_missing=True):
     L.speedup_logweights_nd.argtypes = [i32, pi, pd, i32, pd, pd, d, i32, i32, i64, i64, u64,
                                         ctypes.POINTER(Options), vp]
     L.speedup_generate_nd.argtypes = [i32, pi, pd, i32, i32, d, pi, pd, i32, pi]
+    L.speedup_wp.argtypes = [i32, pd, i32, i32, d, pd, pd, i64, pd]
+    L.speedup_wp_nd.argtypes = [i32, pi, pd, i32, i32, d, pd, pd, i64, pd]
     L.su_fit_continuum.argtypes = [ctypes.POINTER(LevelResult), i32, i32, i32, i32, pd, pd, pd]
     L.su_fma_peak.argtypes = [i32, pd]
     pf = ctypes.POINTER(ctypes.c_float)
@@ -348,6 +350,36 @@ def speedup_generate_nd(V, p, eps):
     nn = ctypes.c_int(0)
     _check(load().speedup_generate_nd(d, ex, co, n, int(p), float(eps), oe, ow, cap, ctypes.byref(nn)))
     return {tuple(oe[t * 2 * d:(t + 1) * 2 * d]): ow[t] for t in range(nn.value)}
+
+
+def _points(x, xb, shape_tail=()):
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    xb = np.ascontiguousarray(np.asarray(xb, dtype=np.float64))
+    if x.shape != xb.shape or x.shape[x.ndim - len(shape_tail):] != shape_tail:
+        raise ValueError("x and xb must have the same shape (points x coordinates)")
+    return x, xb
+
+
+def speedup_wp(model, params, p, eps, x, xb):
+    """W_p(x, xb; eps) of a one-dimensional model at the points x, xb (host, no device)."""
+    pr, npar = _params(params)
+    x, xb = _points(x, xb)
+    w = np.empty(x.shape)
+    pd = ctypes.POINTER(ctypes.c_double)
+    _check(load().speedup_wp(_model(model), pr, npar, int(p), float(eps), x.ctypes.data_as(pd),
+                             xb.ctypes.data_as(pd), int(x.size), w.ctypes.data_as(pd)))
+    return w
+
+
+def speedup_wp_nd(V, p, eps, x, xb):
+    """W(x, xb; eps) of a system of d coordinates at the points x, xb (shape (..., d); host, no device)."""
+    d, ex, co, n = _nd_potential(V)
+    x, xb = _points(x, xb, (d,))
+    w = np.empty(x.shape[:-1])
+    pd = ctypes.POINTER(ctypes.c_double)
+    _check(load().speedup_wp_nd(d, ex, co, n, int(p), float(eps), x.ctypes.data_as(pd), xb.ctypes.data_as(pd),
+                                int(w.size), w.ctypes.data_as(pd)))
+    return w
 
 
 def speedup_amplitude_nd(V, a, b, T, p, s, n_mc, seed, **kw):

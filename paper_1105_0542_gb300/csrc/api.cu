@@ -990,6 +990,44 @@ int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms
     return SU_OK;
 }
 
+int speedup_wp(int model, const double *params, int n_params, int p, double eps, const double *x, const double *xb,
+               int64_t n_points, double *w) {
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");
+    if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
+    if (n_points < 0) return fail(SU_EINVAL, "n_points must be >= 0");
+    if (n_points > 0 && (!x || !xb || !w)) return fail(SU_EINVAL, "points or output missing");
+    std::string err;
+    int rc = SU_OK;
+    if (model == SU_GENERAL) {
+        if (p > su::kGenMaxP) return fail(SU_ENOTSUP, "the general potential supports p <= %d", su::kGenMaxP);
+        su::GeneralPotential V;
+        rc = su::general_potential(params, n_params, V, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        const auto G = general_program(p, rc, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        su::general_wp_points(*G, V, eps, x, xb, n_points, w);
+        return SU_OK;
+    }
+    su::Effective E;
+    rc = su::build_effective(model, params, n_params, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    su::wp_host_points(E, eps, x, xb, n_points, w);
+    return SU_OK;
+}
+
+int speedup_wp_nd(int d, const int *exps, const double *coefs, int n_terms, int p, double eps, const double *x,
+                  const double *xb, int64_t n_points, double *w) {
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(SU_EINVAL, "eps must be finite and > 0");
+    if (n_points < 0) return fail(SU_EINVAL, "n_points must be >= 0");
+    if (n_points > 0 && (!x || !xb || !w)) return fail(SU_EINVAL, "points or output missing");
+    su::NdEffective E;
+    std::string err;
+    const int rc = su::build_nd(d, exps, coefs, n_terms, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    su::nd_wp_points(E, eps, x, xb, n_points, w);
+    return SU_OK;
+}
+
 // ------------------------------------------------------ fault injection
 int su_fault_inject(int kind, int64_t arg) {
     switch (kind) {

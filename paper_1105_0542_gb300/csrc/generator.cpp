@@ -330,10 +330,7 @@ double kernel_table(const Effective &E, double eps, std::vector<double> &T) {
     return ratio;
 }
 
-double wp_host(const Effective &E, double x, double xb, double eps) {
-    std::vector<DD> Pd;
-    collapse_dd(E, eps, Pd, nullptr);
-    const Shape &S = E.shape;
+static double wp_from_dd(const Shape &S, const std::vector<DD> &Pd, double x, double xb) {
     double z = S.ring == RING_EVEN ? x * x
                : S.ring == RING_X  ? x
                                    : std::tanh(S.alpha * x) * std::tanh(S.alpha * x);
@@ -347,6 +344,18 @@ double wp_host(const Effective &E, double x, double xb, double eps) {
         acc = add(mul(acc, y), h);
     }
     return acc.hi;
+}
+
+double wp_host(const Effective &E, double x, double xb, double eps) {
+    std::vector<DD> Pd;
+    collapse_dd(E, eps, Pd, nullptr);
+    return wp_from_dd(E.shape, Pd, x, xb);
+}
+
+void wp_host_points(const Effective &E, double eps, const double *x, const double *xb, int64_t n, double *w) {
+    std::vector<DD> Pd;
+    collapse_dd(E, eps, Pd, nullptr);
+    for (int64_t i = 0; i < n; ++i) w[i] = wp_from_dd(E.shape, Pd, x[i], xb[i]);
 }
 
 double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, double xb) {
@@ -632,9 +641,8 @@ void general_derivatives(const GeneralPotential &V, double x, int J, double *out
     }
 }
 
-double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps) {
-    std::vector<double> T;
-    general_table(G, eps, T);   // -eps c / 4^k per entry
+static double general_wp_from_table(const GeneralEffective &G, const GeneralPotential &V,
+                                    const std::vector<double> &T, double x, double xb, double eps) {
     std::vector<double> D((size_t)G.J + 1);
     general_derivatives(V, x, G.J, D.data());
     std::vector<double> stk((size_t)G.J + 3 * G.p + 2, 1.0), Q((size_t)G.K, 0.0);
@@ -650,6 +658,19 @@ double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, dou
     double w = Q[(size_t)G.K - 1];
     for (int k = G.K - 2; k >= 0; --k) w = w * Y + Q[(size_t)k];
     return -w / eps;                  // the table carries -eps
+}
+
+double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps) {
+    std::vector<double> T;
+    general_table(G, eps, T);   // -eps c / 4^k per entry
+    return general_wp_from_table(G, V, T, x, xb, eps);
+}
+
+void general_wp_points(const GeneralEffective &G, const GeneralPotential &V, double eps, const double *x,
+                       const double *xb, int64_t n, double *w) {
+    std::vector<double> T;
+    general_table(G, eps, T);
+    for (int64_t i = 0; i < n; ++i) w[i] = general_wp_from_table(G, V, T, x[i], xb[i], eps);
 }
 
 // ------------------------------------------- systems of d coordinates
@@ -953,9 +974,8 @@ void nd_table(const NdEffective &E, double eps, std::vector<double> &T) {
     }
 }
 
-double nd_wp_host(const NdEffective &E, const double *x, const double *xb, double eps) {
-    std::vector<double> T;
-    nd_table(E, eps, T);
+static double nd_wp_from_table(const NdEffective &E, const std::vector<double> &T, const double *x,
+                               const double *xb, double eps) {
     double z[2 * kNdMaxDim];
     for (int i = 0; i < E.d; ++i) {
         z[i] = x[i];
@@ -977,6 +997,18 @@ double nd_wp_host(const NdEffective &E, const double *x, const double *xb, doubl
         w += h * mu;
     }
     return -w / eps;   // the table carries -eps
+}
+
+double nd_wp_host(const NdEffective &E, const double *x, const double *xb, double eps) {
+    std::vector<double> T;
+    nd_table(E, eps, T);
+    return nd_wp_from_table(E, T, x, xb, eps);
+}
+
+void nd_wp_points(const NdEffective &E, double eps, const double *x, const double *xb, int64_t n, double *w) {
+    std::vector<double> T;
+    nd_table(E, eps, T);
+    for (int64_t i = 0; i < n; ++i) w[i] = nd_wp_from_table(E, T, x + i * E.d, xb + i * E.d, eps);
 }
 
 }  // namespace su

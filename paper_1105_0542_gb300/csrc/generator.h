@@ -54,8 +54,10 @@ void collapse(const Effective &E, double eps, std::vector<double> &P);
 // cancellation measure of the double-double sums).
 double kernel_table(const Effective &E, double eps, std::vector<double> &T);
 
-// W_p(x, xb; eps) evaluated on the host from the double-double collapse.
+// W_p(x, xb; eps) evaluated on the host from the double-double collapse;
+// the _points form collapses once for n points (w[i] at x[i], xb[i]).
 double wp_host(const Effective &E, double x, double xb, double eps);
+void wp_host_points(const Effective &E, double eps, const double *x, const double *xb, int64_t n, double *w);
 
 // W_p(x, xb; eps) from a collapse P already made for that eps (double).
 double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, double xb);
@@ -105,6 +107,8 @@ void general_derivatives(const GeneralPotential &V, double x, int J, double *out
 
 // W_p(x, xb; eps) of the general potential on the host (level 0 and tests).
 double general_wp_host(const GeneralEffective &G, const GeneralPotential &V, double x, double xb, double eps);
+void general_wp_points(const GeneralEffective &G, const GeneralPotential &V, double eps, const double *x,
+                       const double *xb, int64_t n, double *w);
 
 // ---- systems of d = D x M coordinates (Sec. 2.2): the level-p effective
 // potential W(x, xb; eps) of a polynomial potential V(x_1..x_d) by the
@@ -137,5 +141,7 @@ void nd_table(const NdEffective &E, double eps, std::vector<double> &T);
 
 // W(x, xb; eps) on the host (level 0 and checks): x, xb of d entries.
 double nd_wp_host(const NdEffective &E, const double *x, const double *xb, double eps);
+// The same at n points, x and xb laid out [point][d], the table made once.
+void nd_wp_points(const NdEffective &E, double eps, const double *x, const double *xb, int64_t n, double *w);
 
 }  // namespace su

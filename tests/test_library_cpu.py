@@ -6,7 +6,11 @@
   the oracle's exact-rational c_{m,k} collapsed by hand (Eq. ansatz at fixed
   eps), coefficient by coefficient, for every model family and p up to 18;
 * argument validation fails loudly with SU_EINVAL, and without a CUDA device
-  the compute entry points fail with SU_ECUDA instead of falling back.
+  the compute entry points fail with SU_ECUDA instead of falling back;
+* the host evaluators of W (speedup_wp, speedup_wp_nd: the collapsed tables,
+  the general mode's derivative-symbol program and the several-coordinates
+  program the kernels run) against the oracle's term-by-term W at random
+  points, within 1e-12 of the terms' absolute sum.
 """
 import math
 import os
@@ -380,3 +384,77 @@ def test_cli_usage_and_argument_errors():
     assert _cli("-f", "fp16", 1, 0, 1, 4, 100, 1).returncode == 2
     r = _cli("-m", "aho", 1, 0, 1, 4, 100, 1, 1.0)             # wrong parameter count: the library's check
     assert r.returncode == 1 and "speedup:" in r.stderr
+
+
+# ---- the host evaluators of W (speedup_wp, speedup_wp_nd)
+
+def _wp_points(rng, n, d=None, x_scale=1.5, xb_scale=0.4):
+    shape = (n,) if d is None else (n, d)
+    return rng.uniform(-x_scale, x_scale, shape), rng.uniform(-xb_scale, xb_scale, shape)
+
+
+@pytest.mark.parametrize("model,params,p", [("ho", [1.3], 6), ("aho", [1.0, 10.0], 10), ("dw", [5.0], 12),
+                                            ("mpt", [3.0, 1.0], 8), ("poly", [0.0, -0.3, 0.5, 0.2, 1 / 24], 7),
+                                            ("aho", [1.0, 48.0], 21)])
+def test_host_wp_matches_the_oracle(model, params, p):
+    from oracle import exact
+    rng = np.random.default_rng(11)
+    x, xb = _wp_points(rng, 64)
+    for eps in (0.02, 0.25):
+        got = su.speedup_wp(model, params, p, eps, x, xb)
+        mdl = ea.make_model(model, [_F(v) for v in params] if model != "mpt" else params)
+        ref = exact._wp_vec(mdl, p, x, xb, eps)
+        scale = exact._wp_abs_vec(mdl, p, x, np.abs(xb), eps)
+        assert np.all(np.abs(got - ref) <= 1e-13 * scale + 1e-300), (model, eps)
+
+
+def test_host_wp_of_the_general_mode_matches_the_oracle_and_the_model_tables():
+    from oracle import general_v as gv
+    rng = np.random.default_rng(12)
+    x, xb = _wp_points(rng, 48)
+    gp = su.general_params((0.1, -0.2, 0.5, 0.0, 0.05), [(1.5, 2.0, 0.3)], [(-1.0, 2.0, 0.0)], [(0.4, 1.2, 0.5)])
+    for p, eps in ((6, 0.1), (12, 0.02)):
+        got = su.speedup_wp("general", gp, p, eps, x, xb)
+        ref = gv.wp(gp, p, x, xb, eps)
+        scale = gv.wp_abs(gp, p, x, xb, eps)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale), p
+    # the same anharmonic oscillator through the derivative-symbol program and
+    # through the collapsed tables
+    aho = su.general_params((0.0, 0.0, 0.5, 0.0, 10.0 / 24.0))
+    for p in (4, 10):
+        a = su.speedup_wp("general", aho, p, 0.05, x, xb)
+        b = su.speedup_wp("aho", [1.0, 10.0], p, 0.05, x, xb)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14), p
+
+
+@pytest.mark.parametrize("V,d,p", [(ND_GEN2, 2, 9), (ND_GEN3, 3, 6), (ND_TWO_2D, 4, 4),
+                                   ({(2,): 0.5, (4,): 1 / 24, (3,): -0.1}, 1, 10),
+                                   ({(2, 0): 0.5, (0, 2): 0.5, (4, 0): 1 / 24, (0, 4): 1 / 24, (2, 2): 1 / 12}, 2, 10)])
+def test_host_wp_nd_program_matches_the_oracle(V, d, p):
+    from oracle import many_body as mb
+    rng = np.random.default_rng(13)
+    x, xb = _wp_points(rng, 40, d)
+    Vf = {k: _F(v) for k, v in V.items()}
+    for eps in (0.05, 0.3):
+        got = su.speedup_wp_nd(V, p, eps, x, xb)
+        ref = mb.wp(Vf, d, p, x, xb, eps)
+        scale = mb.wp_abs(Vf, d, p, x, xb, eps)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale), eps
+
+
+def test_host_wp_rejects_bad_requests():
+    x = np.zeros(3)
+    for call, code in [(lambda: su.speedup_wp("aho", [1.0, 1.0], 4, 0.0, x, x), -1),
+                       (lambda: su.speedup_wp("aho", [1.0, 1.0], 4, float("nan"), x, x), -1),
+                       (lambda: su.speedup_wp("aho", [1.0], 4, 0.1, x, x), -1),
+                       (lambda: su.speedup_wp("aho", [1.0, 1.0], 145, 0.1, x, x), -1),
+                       (lambda: su.speedup_wp("general", su.general_params((0, 0, 0.5)), 13, 0.1, x, x), -6),
+                       (lambda: su.speedup_wp_nd({(2, 0): 1.0}, 4, -1.0, np.zeros((3, 2)), np.zeros((3, 2))), -1),
+                       (lambda: su.speedup_wp_nd({(2, 0): 1.0}, 13, 0.1, np.zeros((3, 2)), np.zeros((3, 2))), -1)]:
+        with pytest.raises(su.SpeedupError) as e:
+            call()
+        assert e.value.code == code
+    with pytest.raises(ValueError):
+        su.speedup_wp_nd({(2, 0): 1.0}, 4, 0.1, np.zeros((3, 3)), np.zeros((3, 3)))
+    # no points: nothing to do
+    assert su.speedup_wp("ho", [1.0], 3, 0.1, np.zeros(0), np.zeros(0)).shape == (0,)
