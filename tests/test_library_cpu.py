@@ -458,3 +458,31 @@ def test_host_wp_rejects_bad_requests():
         su.speedup_wp_nd({(2, 0): 1.0}, 4, 0.1, np.zeros((3, 3)), np.zeros((3, 3)))
     # no points: nothing to do
     assert su.speedup_wp("ho", [1.0], 3, 0.1, np.zeros(0), np.zeros(0)).shape == (0,)
+
+
+def test_host_wp_nd_program_on_random_polynomials():
+    """Random sparse polynomials (d = 1..3, degree <= 6, with and without a
+    parity, so that the Horner variable, its step G and the groups' offsets
+    j0 vary): the program's W equals the oracle's at random points."""
+    from oracle import many_body as mb
+    rng = np.random.default_rng(2024)
+    for trial in range(20):
+        d = int(rng.integers(1, 4))
+        p = int(rng.integers(2, 7 if d < 3 else 5))
+        V = {}
+        for _ in range(int(rng.integers(3, 8))):
+            e = [0] * d
+            for _ in range(int(rng.integers(1, 7 if d < 3 else 5))):
+                e[int(rng.integers(0, d))] += 1
+            if trial % 3 == 0:                       # even in every coordinate
+                e = [2 * (k // 2) for k in e]
+            V[tuple(e)] = V.get(tuple(e), 0.0) + float(rng.integers(-8, 9)) / 8.0
+        V = {k: v for k, v in V.items() if v and sum(k) > 0}
+        if not V:
+            continue
+        x, xb = _wp_points(rng, 24, d, 1.0, 0.3)
+        Vf = {k: _F(v) for k, v in V.items()}
+        got = su.speedup_wp_nd(V, p, 0.1, x, xb)
+        ref = mb.wp(Vf, d, p, x, xb, 0.1)
+        scale = mb.wp_abs(Vf, d, p, x, xb, 0.1)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), (V, d, p)
