@@ -486,3 +486,27 @@ def test_host_wp_nd_program_on_random_polynomials():
         ref = mb.wp(Vf, d, p, x, xb, 0.1)
         scale = mb.wp_abs(Vf, d, p, x, xb, 0.1)
         assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), (V, d, p)
+
+
+def test_host_wp_general_program_on_random_potentials():
+    """Random general potentials (a polynomial and up to two terms of each
+    family, p = 1..12): the library's derivative-symbol program equals the
+    oracle's W_p at random points."""
+    from oracle import general_v as gv
+    rng = np.random.default_rng(77)
+    for trial in range(10):
+        p = int(rng.integers(1, 13))
+        poly = [float(v) for v in rng.integers(-4, 5, size=int(rng.integers(1, 6))) / 4.0]
+        gauss = [(float(rng.uniform(-2, 2)), float(rng.uniform(0.3, 3)), float(rng.uniform(-1, 1)))
+                 for _ in range(int(rng.integers(0, 3)))]
+        sech = [(float(rng.uniform(-2, 2)), float(rng.uniform(0.3, 2)), float(rng.uniform(-1, 1)))
+                for _ in range(int(rng.integers(0, 3)))]
+        expo = [(float(rng.uniform(-1, 1)), float(rng.uniform(0.2, 1.5)), float(rng.uniform(-1, 1)))
+                for _ in range(int(rng.integers(0, 3)))]
+        gp = su.general_params(poly, gauss, sech, expo)
+        x, xb = _wp_points(rng, 24, None, 1.2, 0.3)
+        eps = float(rng.uniform(0.01, 0.2))
+        got = su.speedup_wp("general", gp, p, eps, x, xb)
+        ref = gv.wp(gp, p, x, xb, eps)
+        scale = gv.wp_abs(gp, p, x, xb, eps)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), (trial, p)
