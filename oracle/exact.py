@@ -74,13 +74,18 @@ def mehler_mp(a, b, T, omega=1, dps=60):
         return +(mp.sqrt(w / (2 * mp.pi * sh)) * mp.exp(-w * ((a * a + b * b) * ch - 2 * a * b) / (2 * sh)))
 
 
-def ho_discretized(p, N, a, b, T, omega=1.0, dps=40, as_mp=False):
-    """Exact A_N^(p)(a,b;T) of the harmonic oscillator (Gaussian integral)."""
+def ho_discretized(p, N, a, b, T, omega=1.0, dps=40, as_mp=False, w_scale=1):
+    """Exact A_N^(p)(a,b;T) of the harmonic oscillator (Gaussian integral).
+
+    w_scale = k replaces W_p by k W_p (Eq. SNp otherwise unchanged): then
+    A_N[k W_p] / A_free = E[exp(k w)] under the bisection bridge, the k-th
+    moment of the estimator's per-sample factor exp(w) (Sec. 4.1), which
+    pins the error bars of the Monte Carlo estimate."""
     import mpmath as mp
     with mp.workdps(dps):
         eps = mp.mpf(T) / N
         al, be, ga = ho_quadratic_form(p, Fraction(T) / N, omega)
-        al, be, ga = (mp.mpf(v.numerator) / v.denominator for v in (al, be, ga))
+        al, be, ga = (mp.mpf(v.numerator) / v.denominator * w_scale for v in (al, be, ga))
         # per slice: (q'-q)^2/(2 eps) + eps (al x^2 + be xb^2 + ga)
         #          = Ac (q'-q)^2 + Bc (q'+q)^2 + eps ga
         Ac = 1 / (2 * eps) + eps * be / 4
