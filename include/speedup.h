@@ -184,26 +184,46 @@ int su_fit_continuum(const su_level_result *levels, int s, int p, int n_min, int
 
 /* ---- many instances in one persistent launch ------------------------------ */
 
-/* one amplitude A_N^(p)(a,b;T) with N = 2^s of a batch */
+/* One amplitude A_N^(p)(a,b;T), N = 2^s, of a batch.  A zero-initialised
+ * tail (p = 0, n_mc = 0, hierarchy = 0) takes the batch's p and n_mc and the
+ * top level only. */
 typedef struct {
     double a, b, T;
-    int s;               /* 0..SU_MAX_S */
+    int s;               /* 0..SU_MAX_S                                           */
+    int p;               /* effective-action level 1..SU_MAX_P; 0 = the batch's p  */
+    int64_t n_mc;        /* samples, >= 1; 0 = the batch's n_mc                    */
+    int hierarchy;       /* 0: the top level n = s only (one result);
+                            1: every level n = 0..s from the same paths (s + 1
+                            results, level 0 analytic)                           */
+    int reserved;        /* 0                                                     */
 } su_instance;
 
 /*
- * speedup_amplitude_batch -- the top-level amplitude A_N^(p)(a_i,b_i;T_i),
- * N = 2^(s_i), of every instance of one model and level p (Sec. 4; e.g. a
- * matrix of short-time amplitudes on an endpoint grid), from n_mc bisection
- * paths each, in one persistent launch of the batched kernel (work items =
- * (instance, block), deepest instances first, taken from an atomic queue),
- * replayed from a CUDA graph.
+ * speedup_amplitude_batch -- the amplitudes A_N^(p_i)(a_i,b_i;T_i), N = 2^(s_i),
+ * of every instance of one model (Sec. 4; e.g. a matrix of short-time
+ * amplitudes on an endpoint grid, or a convergence sweep over p), from n_mc_i
+ * bisection paths each, in one persistent launch of the batched kernel,
+ * replayed from a CUDA graph.  Work items are (instance, error block, chunk)
+ * triples ordered by their cost (samples x slices x table entries), taken
+ * from an atomic queue; each instance's tables (one per level p_i and
+ * slice width) are staged per item.
  *
+ *   p, n_mc      : the defaults for instances whose p or n_mc is 0.
  *   inst, n_inst : host, 1..2^24 instances.  Instance i draws from Philox
- *                  stream opt->instance + i (counter word 1), samples 0..n_mc-1.
- *   opt          : precision, n_blocks, stream (width_factor must be 1,
- *                  sample0 must be 0, hierarchy is ignored: top level only).
- *   out          : host, n_inst entries, out[i] for level n = s_i (the
- *                  analytic level-0 value with err 0 where s_i = 0).
+ *                  stream opt->instance + i (counter word 1), samples
+ *                  0..n_mc_i - 1.
+ *   opt          : precision, n_blocks (per instance, capped at its n_mc),
+ *                  stream; width_factor must be 1, sample0 0; hierarchy,
+ *                  seg_log2 and rounds are not used (per-instance hierarchy;
+ *                  the shape of each (p, s, hierarchy) class is the one
+ *                  su_batch_autotune stored, else the rule: 2^4-slice
+ *                  register segments in double, 2^5 in single precision,
+ *                  capped at s).
+ *   out          : host, one entry per instance with hierarchy 0 and s_i + 1
+ *                  (levels n = 0..s_i) per instance with hierarchy 1, in
+ *                  instance order (su_batch_plan_sizes gives the count).  An
+ *                  instance with s_i = 0 gets the analytic level-0 value with
+ *                  err 0.
  */
 int speedup_amplitude_batch(int model, const double *params, int n_params, int p,
                             const su_instance *inst, int64_t n_inst, int64_t n_mc,
@@ -217,19 +237,50 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p,
                          const su_instance *inst, int64_t n_inst, int64_t n_mc,
                          uint64_t seed, const su_options *opt, su_batch_plan **plan);
 int su_batch_plan_destroy(su_batch_plan *plan);
-/* *tuple_bytes: d_tuples size (n_inst * n_blocks * 4 doubles, [instance][block]
- * (M, S, Q, n)); *scratch_bytes: d_scratch size; *slice_actions per execute */
+/* *tuple_bytes: d_tuples size (per instance and work item, one tuple (M, S,
+ * Q, n) of 4 doubles per sampled level); *scratch_bytes: d_scratch size;
+ * *slice_actions per execute (hierarchy slices counted); *n_results (may be
+ * NULL): the entries of out. */
 int su_batch_plan_sizes(const su_batch_plan *plan, int64_t *tuple_bytes, int64_t *scratch_bytes,
-                        int64_t *slice_actions);
+                        int64_t *slice_actions, int64_t *n_results);
+/* The launch shape the plan chose for instance i: *seg_log2 = its register
+ * segment (2^seg_log2 slices), *chunks = work items per error block, *from
+ * = 0 (rule) or 1 (stored by su_batch_autotune). */
+int su_batch_plan_shape(const su_batch_plan *plan, int64_t i, int *seg_log2, int *chunks, int *from);
 /* asynchronous on stream; the first call builds the plan's CUDA graph (a
  * memset of the queue head and the persistent kernel), later calls replay it
  * (and rebuild it if the buffers change); *launches = graph launches made */
 int su_batch_plan_execute(su_batch_plan *plan, void *d_tuples, void *d_scratch, void *stream,
                           int *launches);
-/* host tuples in, out[n_inst] as speedup_amplitude_batch; d_scratch (may be
- * NULL) is read for the non-finite flag */
+/* host tuples in, out as speedup_amplitude_batch; d_scratch (may be NULL) is
+ * read for the non-finite flag.  SU_ECUDA if an instance's samples were not
+ * all reduced. */
 int su_batch_plan_finalize(const su_batch_plan *plan, const double *h_tuples,
                            const void *d_scratch, su_level_result *out);
+
+/* One timed shape of su_batch_autotune: class (p, s, hierarchy), shape, and
+ * the device time per slice-action of the probe batch. */
+typedef struct {
+    int p, s, hierarchy;
+    int seg_log2;
+    double ns_per_slice;
+} su_batch_tuning;
+
+/*
+ * su_batch_autotune -- for every (p, s, hierarchy) class of the batch with
+ * s >= 1, times the batched kernel on a probe of that class (its first
+ * max_probe instances with their own samples, one execute after a warm-up,
+ * best of two) for every register segment seg_log2 = 1..min(s, 5) whose
+ * shared memory fits, and stores the fastest in a process-wide table under
+ * (precision, model, p, s, hierarchy); later batch plans use it.  No
+ * counterpart in the paper.  Arguments as su_batch_plan_create;
+ *   best, cap, n_best : host, optional: the chosen shape of up to cap
+ *                       classes, *n_best = the number of classes.
+ * Synchronous.  su_autotune_clear forgets these shapes too.
+ */
+int su_batch_autotune(int model, const double *params, int n_params, int p, const su_instance *inst,
+                      int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt, int max_probe,
+                      su_batch_tuning *best, int cap, int *n_best);
 
 /* ---- learned bisection proposal -------------------------------------------- */
 
@@ -586,7 +637,10 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
  * the GPU's memory, inside a memory-capped or pre-partitioned process, or in
  * a loop where cudaMalloc/cudaFree and the synchronisation they imply are not
  * allowed.  The paper has no counterpart; the arguments, results and errors
- * are those of speedup_amplitude.
+ * are those of speedup_amplitude, and so are the tables and the launch shape
+ * (opt->seg_log2, opt->rounds, a shape stored by su_autotune, or the built-in
+ * rule; double-precision tables too large for shared memory are read from
+ * global memory).  SU_GENERAL is not served (SU_ENOTSUP).
  *
  * Device scratch (coefficient tables, per-item and per-block log-sum-exp
  * tuples, the non-finite flag) lives in one static device array of
@@ -594,12 +648,17 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
  * library holds until the process exits.  The call makes no cudaMalloc,
  * cudaFree or other device allocation (its host-side work arrays use ordinary
  * host memory).
- *  - Sizes whose tuples do not fit the array (n_mc * levels / 8192 items of
- *    32-byte tuples at the coarsest split, plus the tables) fail with
- *    SU_ENOTSUP.
- *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress (with that device current); make that first call
- *    before any stream capture.
+ *  - Size limit: the tables, the per-item tuples (items x levels x 32 bytes,
+ *    items = n_blocks x ceil(n_mc / n_blocks / (128 rounds))) and the
+ *    per-block tuples (n_blocks x levels x 32 bytes) must fit the array
+ *    together.  With automatic rounds the call raises rounds (up to 8, while
+ *    the sampler stays resident) until they fit; a request that still does
+ *    not fit fails with SU_ENOTSUP and a message naming the sizes.
+ *  - The array's device address is looked up (cudaGetSymbolAddress) on every
+ *    call, with the caller's device current.
+ *  - The call is synchronous: it copies the tables in and the tuples out
+ *    through pageable host memory and synchronises opt->stream before it
+ *    returns.
  *  - Every call shares the one array and leaves its contents behind; calls
  *    whose device work overlaps (other threads, other streams of the same
  *    device) race on it and must be serialised by the caller.

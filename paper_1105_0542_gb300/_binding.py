@@ -31,7 +31,7 @@ EXPORTS = [
     "su_mlp_loss_grad", "speedup_train_proposal", "su_autotune", "su_autotune_clear", "su_plan_shape",
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
-    "su_fit_continuum", "speedup_wp", "speedup_wp_nd",
+    "su_fit_continuum", "speedup_wp", "speedup_wp_nd", "su_batch_plan_shape", "su_batch_autotune",
 ]
 MAX_D = 4
 MLP_PARAMS = 34178
@@ -63,7 +63,17 @@ class TrainOptions(ctypes.Structure):
 
 
 class Instance(ctypes.Structure):
-    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("T", ctypes.c_double), ("s", ctypes.c_int)]
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("T", ctypes.c_double), ("s", ctypes.c_int),
+                ("p", ctypes.c_int), ("n_mc", ctypes.c_int64), ("hierarchy", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("s", ctypes.c_int), ("hierarchy", ctypes.c_int), ("seg_log2", ctypes.c_int),
+                ("ns_per_slice", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class LevelResult(ctypes.Structure):
@@ -156,7 +166,11 @@ def load(build_if_missing=True):
     L.su_batch_plan_create.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options),
                                        ctypes.POINTER(vp)]
     L.su_batch_plan_destroy.argtypes = [vp]
-    L.su_batch_plan_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.su_batch_plan_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64)]
+    L.su_batch_plan_shape.argtypes = [vp, i64, pi, pi, pi]
+    L.su_batch_autotune.argtypes = [i32, pd, i32, i32, pinst, i64, i64, u64, ctypes.POINTER(Options), i32,
+                                    ctypes.POINTER(BatchTuning), i32, pi]
     L.su_batch_plan_execute.argtypes = [vp, vp, vp, vp, pi]
     L.su_batch_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
     for name in EXPORTS:
@@ -436,22 +450,61 @@ def su_fma_peak(precision="fp64"):
 
 
 def _instances(instances):
+    """Instances as tuples (a, b, T, s[, p[, n_mc[, hierarchy]]]) or dicts with
+    those keys; p = 0 and n_mc = 0 take the batch's values."""
     n = len(instances)
     arr = (Instance * max(n, 1))()
-    for i, (a, b, T, s) in enumerate(instances):
+    for i, x in enumerate(instances):
+        if isinstance(x, dict):
+            x = (x["a"], x["b"], x["T"], x["s"], x.get("p", 0), x.get("n_mc", 0), x.get("hierarchy", 0))
+        x = tuple(x) + (0,) * (7 - len(x))
+        a, b, T, s, p, n_mc, hier = x
         arr[i].a, arr[i].b, arr[i].T, arr[i].s = float(a), float(b), float(T), int(s)
+        arr[i].p, arr[i].n_mc, arr[i].hierarchy = int(p), int(n_mc), 1 if hier else 0
     return arr, n
 
 
+def _batch_results(out, arr, n):
+    """Per instance: its top-level result (a dict), or with hierarchy the list
+    of its s + 1 levels."""
+    res, k = [], 0
+    for i in range(n):
+        s = arr[i].s
+        if arr[i].hierarchy:
+            res.append([out[k + lev].as_dict(lev) for lev in range(s + 1)])
+            k += s + 1
+        else:
+            res.append(out[k].as_dict(s))
+            k += 1
+    return res
+
+
 def speedup_amplitude_batch(model, params, p, instances, n_mc, seed, **kw):
-    """Top-level amplitude of every (a, b, T, s) instance (list of dicts)."""
+    """Amplitude of every instance (see _instances): a dict of its top level,
+    or the list of its levels where the instance asks for the hierarchy."""
     pr, npar = _params(params)
     arr, n = _instances(instances)
-    out = (LevelResult * max(n, 1))()
+    n_out = sum(arr[i].s + 1 if arr[i].hierarchy else 1 for i in range(n))
+    out = (LevelResult * max(n_out, 1))()
     o = options(**kw)
     _check(load().speedup_amplitude_batch(_model(model), pr, npar, p, arr, n, int(n_mc), int(seed),
                                           ctypes.byref(o), out))
-    return [out[i].as_dict(instances[i][3]) for i in range(n)]
+    return _batch_results(out, arr, n)
+
+
+def su_batch_autotune(model, params, p, instances, n_mc, seed, max_probe=64, **kw):
+    """Time every register segment per (p, s, hierarchy) class of the batch on
+    its first max_probe instances and store the fastest; returns the chosen
+    shapes (list of dicts)."""
+    pr, npar = _params(params)
+    arr, n = _instances(instances)
+    cap = 256
+    best = (BatchTuning * cap)()
+    nb = ctypes.c_int(0)
+    o = options(**kw)
+    _check(load().su_batch_autotune(_model(model), pr, npar, p, arr, n, int(n_mc), int(seed), ctypes.byref(o),
+                                    int(max_probe), best, cap, ctypes.byref(nb)))
+    return [best[i].as_dict() for i in range(min(nb.value, cap))]
 
 
 class BatchPlan:
@@ -460,16 +513,24 @@ class BatchPlan:
     def __init__(self, model, params, p, instances, n_mc, seed, **kw):
         pr, npar = _params(params)
         arr, n = _instances(instances)
+        self._arr = arr
         self.n_inst = n
-        self.levels_of = [int(t[3]) for t in instances]
         o = options(**kw)
         h = ctypes.c_void_p()
         _check(load().su_batch_plan_create(_model(model), pr, npar, p, arr, n, int(n_mc), int(seed),
                                            ctypes.byref(o), ctypes.byref(h)))
         self._h = h
-        tb, sb, sa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(load().su_batch_plan_sizes(h, ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(sa)))
+        tb, sb, sa, nr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().su_batch_plan_sizes(h, ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(sa),
+                                          ctypes.byref(nr)))
         self.tuple_bytes, self.scratch_bytes, self.slice_actions = tb.value, sb.value, sa.value
+        self.n_results = nr.value
+
+    def su_batch_plan_shape(self, i):
+        """(seg_log2, chunks per block, 1 if from su_batch_autotune else 0) of instance i."""
+        f, k, fr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().su_batch_plan_shape(self._h, int(i), ctypes.byref(f), ctypes.byref(k), ctypes.byref(fr)))
+        return f.value, k.value, fr.value
 
     def su_batch_plan_execute(self, d_tuples, d_scratch, stream=None):
         n = ctypes.c_int(0)
@@ -478,11 +539,11 @@ class BatchPlan:
         return n.value
 
     def su_batch_plan_finalize(self, h_tuples, d_scratch=None):
-        out = (LevelResult * max(self.n_inst, 1))()
+        out = (LevelResult * max(self.n_results, 1))()
         arr = np.ascontiguousarray(h_tuples, dtype=np.float64)
         _check(load().su_batch_plan_finalize(self._h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                              _ptr(d_scratch), out))
-        return [out[i].as_dict(self.levels_of[i]) for i in range(self.n_inst)]
+        return _batch_results(out, self._arr, self.n_inst)
 
     def close(self):
         if getattr(self, "_h", None):

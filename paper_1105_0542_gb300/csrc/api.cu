@@ -45,6 +45,15 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, su_tuning> g_tune;
 
+// register segments stored by su_batch_autotune, per (precision, model, p, s, hierarchy)
+struct BatchTuneKey {
+    int precision, model, p, s, hier;
+    bool operator<(const BatchTuneKey &o) const {
+        return std::tie(precision, model, p, s, hier) < std::tie(o.precision, o.model, o.p, o.s, o.hier);
+    }
+};
+std::map<BatchTuneKey, int> g_btune;
+
 bool tuned_shape(int precision, int model, int p, int s, su_tuning &out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find({precision, model, p, s});
@@ -329,12 +338,12 @@ static int upload_general(su_plan &pl) {
     return SU_OK;
 }
 
-static int configure(su_plan &pl) {
+// The level tables of a plan (rows d = 0..S-1 for levels n = S..1), each
+// scaled for the kernel and rounded to its precision: host work only.
+static int plan_tables(su_plan &pl, std::vector<unsigned char> &blob) {
     using namespace su;
-    SamplerParams &P = pl.P;
     const int S = pl.s;
     const int prec = pl.opt.precision;
-    // tables of levels n = S..1 (row d = S - n), each scaled for the kernel
     const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
     const bool general = pl.model == SU_GENERAL;
     const int M = general ? (int)pl.G->entry_k.size() : pl.E.shape.M;
@@ -354,30 +363,43 @@ static int configure(su_plan &pl) {
             tabd[(size_t)d * M + i] = t[i];
         }
     }
-    std::vector<unsigned char> blob(tabd.size() * rs);
+    blob.assign(tabd.size() * rs, 0);
     if (prec == SU_FP32)
         for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
     else
         std::memcpy(blob.data(), tabd.data(), blob.size());
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
-    }
-    CU(cudaGetDevice(&pl.device), "cudaGetDevice");
-    int sms = 0;
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
-    int smem_max = 0;
-    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl.device),
-       "smem limit");
-    CU(dmalloc(&pl.d_tables, blob.size()), "device allocation (tables)");
-    CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
-    if (general) {
-        const int rc = upload_general(pl);
-        if (rc) return rc;
-    }
+    return SU_OK;
+}
 
+// Work decomposition of a plan for `rounds` paths per thread per item:
+// items of 128 * rounds samples, the persistent grid and the buffer sizes.
+// Returns the resident CTAs per SM (0 when the shared memory does not fit).
+static int plan_rounds(su_plan &pl, int rounds, int sms, int smem_max) {
+    using namespace su;
+    SamplerParams &P = pl.P;
+    const int prec = pl.opt.precision;
+    P.rounds = rounds;
+    const int chunk = kThreads * rounds;
+    const int64_t bsz = (pl.n_mc + pl.n_blocks - 1) / pl.n_blocks;
+    P.items_per_block = (bsz + chunk - 1) / chunk;
+    P.n_items = P.items_per_block * pl.n_blocks;
+    pl.smem = sampler_smem_bytes(P, prec);
+    const int occ = pl.smem > (size_t)smem_max ? 0 : sampler_occupancy(P, prec, pl.smem);
+    pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * std::max(occ, 1));
+    pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
+    pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + 256;
+    return occ;
+}
+
+// The sampler's parameters and launch shape of a plan (everything but the
+// device pointers): host work and occupancy queries only, no allocation.
+static int plan_shape(su_plan &pl, int sms, int smem_max) {
+    using namespace su;
+    SamplerParams &P = pl.P;
+    const int S = pl.s;
+    const int prec = pl.opt.precision;
+    const bool general = pl.model == SU_GENERAL;
+    const int M = general ? (int)pl.G->entry_k.size() : pl.E.shape.M;
     std::memset(&P, 0, sizeof P);
     P.a = pl.a;
     P.b = pl.b;
@@ -401,25 +423,12 @@ static int configure(su_plan &pl) {
     P.M = M;
     for (int j = 0; j < P.ncol; ++j) P.len[j] = pl.E.shape.len[j];
     P.alpha = general ? 0.0 : pl.E.shape.alpha;
-    P.tables = pl.d_tables;
-    P.general = static_cast<const GeneralDev *>(pl.d_general);
     P.seed = pl.seed;
     P.instance = pl.opt.instance;
     P.n_mc = pl.n_mc;
     P.sample0 = pl.opt.sample0;
     P.n_blocks = pl.n_blocks;
 
-    // launch shape: one path per thread, persistent grid over items of
-    // 128 * rounds samples
-    auto shape = [&](int rounds) {
-        P.rounds = rounds;
-        const int chunk = kThreads * rounds;
-        const int64_t bsz = (pl.n_mc + pl.n_blocks - 1) / pl.n_blocks;
-        P.items_per_block = (bsz + chunk - 1) / chunk;
-        P.n_items = P.items_per_block * pl.n_blocks;
-        pl.smem = sampler_smem_bytes(P, prec);
-        return pl.smem > (size_t)smem_max ? 0 : sampler_occupancy(P, prec, pl.smem);
-    };
     // tables too large to stage next to the rest (the highest levels) are
     // read from global memory instead
     P.rounds = 1;
@@ -428,7 +437,9 @@ static int configure(su_plan &pl) {
         if (prec != SU_FP64) return fail(SU_ENOTSUP, "the level tables do not fit shared memory in single precision");
         P.tab_global = 1;
     }
-    const int occ1 = shape(1);
+    // launch shape: one path per thread, persistent grid over items of
+    // 128 * rounds samples
+    const int occ1 = plan_rounds(pl, 1, sms, smem_max);
     if (pl.smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", pl.smem, smem_max);
     if (occ1 < 1) return fail(SU_ECUDA, "sampler cannot be resident (%s)", cudaGetErrorString(cudaGetLastError()));
@@ -436,21 +447,86 @@ static int configure(su_plan &pl) {
     // to the sampling, and small items leave no tail), more only to keep the
     // per-item tuples under 512 MB, and only while as many CTAs stay resident
     int rounds = 1;
-    while (rounds < 8 && P.n_items * pl.levels * 32 > ((int64_t)512 << 20)) shape(rounds *= 2);
-    while (rounds > 1 && shape(rounds) < occ1) rounds /= 2;
+    while (rounds < 8 && P.n_items * pl.levels * 32 > ((int64_t)512 << 20)) plan_rounds(pl, rounds *= 2, sms, smem_max);
+    while (rounds > 1 && plan_rounds(pl, rounds, sms, smem_max) < occ1) rounds /= 2;
     if (pl.opt.rounds > 0 || (have_tuned && tuned.rounds > 0)) {
         rounds = pl.opt.rounds > 0 ? pl.opt.rounds : tuned.rounds;
-        if (shape(rounds) < 1)
+        if (plan_rounds(pl, rounds, sms, smem_max) < 1)
             return fail(SU_ENOTSUP, "rounds = %d does not fit (shared memory %zu bytes)", rounds, pl.smem);
     }
-    const int occ = shape(rounds);
-    pl.grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
-    pl.partial_bytes = P.n_items * pl.levels * 4 * (int64_t)sizeof(double);
-    pl.scratch_bytes = ((pl.partial_bytes + 255) / 256) * 256 + 256;
+    plan_rounds(pl, rounds, sms, smem_max);
     pl.tuple_bytes = pl.n_blocks * pl.levels * 4 * (int64_t)sizeof(double);
     const int64_t N = (int64_t)1 << S;
     pl.slice_actions = pl.n_mc * (pl.levels > 1 ? 2 * N - 2 : N);
     if (S == 0) pl.slice_actions = 0;
+    return SU_OK;
+}
+
+// The current device's SM count and opt-in shared memory per CTA.
+static int device_limits(int &dev, int &sms, int &smem_max) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    CU(cudaGetDevice(&dev), "cudaGetDevice");
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+    return SU_OK;
+}
+
+static int configure(su_plan &pl) {
+    std::vector<unsigned char> blob;
+    int rc = plan_tables(pl, blob);
+    if (rc) return rc;
+    int sms = 0, smem_max = 0;
+    rc = device_limits(pl.device, sms, smem_max);
+    if (rc) return rc;
+    rc = plan_shape(pl, sms, smem_max);
+    if (rc) return rc;
+    CU(dmalloc(&pl.d_tables, blob.size()), "device allocation (tables)");
+    CU(cudaMemcpy(pl.d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
+    if (pl.model == SU_GENERAL) {
+        rc = upload_general(pl);
+        if (rc) return rc;
+    }
+    pl.P.tables = pl.d_tables;
+    pl.P.general = static_cast<const su::GeneralDev *>(pl.d_general);
+    return SU_OK;
+}
+
+// Validated arguments, the effective action and the level-0 value of a plan
+// (host only).
+static int plan_init(su_plan &pl, int model, const double *params, int n_params, double a, double b, double T,
+                     int p, int s, int64_t n_mc, uint64_t seed, const su_options &o) {
+    int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
+    if (rc) return rc;
+    std::string err;
+    if (model == SU_GENERAL) {
+        rc = su::general_potential(params, n_params, pl.V, err);
+        if (!rc) pl.G = general_program(p, rc, err);
+    } else {
+        rc = su::build_effective(model, params, n_params, p, pl.E, err);
+    }
+    if (rc) return fail(rc, "%s", err.c_str());
+    pl.model = model;
+    pl.params.assign(params, params + n_params);
+    pl.a = a;
+    pl.b = b;
+    pl.T = T;
+    pl.p = p;
+    pl.s = s;
+    pl.n_mc = n_mc;
+    pl.seed = seed;
+    pl.opt = o;
+    pl.levels = s == 0 ? 0 : (o.hierarchy ? s : 1);
+    pl.n_blocks = std::min<int64_t>(o.n_blocks, n_mc);
+    pl.w0 = model == SU_GENERAL ? -T * su::general_wp_host(*pl.G, pl.V, 0.5 * (a + b), 0.5 * (b - a), T)
+                                : -T * su::wp_host(pl.E, 0.5 * (a + b), 0.5 * (b - a), T);
+    pl.laf = log_A_free(a, b, T);
+    if (!std::isfinite(pl.w0) && !(std::isinf(pl.w0) && pl.w0 < 0))
+        return fail(SU_ENONFINITE, "level-0 weight is not finite");
     return SU_OK;
 }
 
@@ -461,35 +537,10 @@ int su_plan_create(int model, const double *params, int n_params, double a, doub
     su_options o;
     su_options_default(&o);
     if (opt) o = *opt;
-    int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
-    if (rc) return rc;
     std::unique_ptr<su_plan> pl(new (std::nothrow) su_plan);
     if (!pl) return fail(SU_ENOMEM, "host allocation failed");
-    std::string err;
-    if (model == SU_GENERAL) {
-        rc = su::general_potential(params, n_params, pl->V, err);
-        if (!rc) pl->G = general_program(p, rc, err);
-    } else {
-        rc = su::build_effective(model, params, n_params, p, pl->E, err);
-    }
-    if (rc) return fail(rc, "%s", err.c_str());
-    pl->model = model;
-    pl->params.assign(params, params + n_params);
-    pl->a = a;
-    pl->b = b;
-    pl->T = T;
-    pl->p = p;
-    pl->s = s;
-    pl->n_mc = n_mc;
-    pl->seed = seed;
-    pl->opt = o;
-    pl->levels = s == 0 ? 0 : (o.hierarchy ? s : 1);
-    pl->n_blocks = std::min<int64_t>(o.n_blocks, n_mc);
-    pl->w0 = model == SU_GENERAL ? -T * su::general_wp_host(*pl->G, pl->V, 0.5 * (a + b), 0.5 * (b - a), T)
-                                 : -T * su::wp_host(pl->E, 0.5 * (a + b), 0.5 * (b - a), T);
-    pl->laf = log_A_free(a, b, T);
-    if (!std::isfinite(pl->w0) && !(std::isinf(pl->w0) && pl->w0 < 0))
-        return fail(SU_ENONFINITE, "level-0 weight is not finite");
+    int rc = plan_init(*pl, model, params, n_params, a, b, T, p, s, n_mc, seed, o);
+    if (rc) return rc;
     rc = configure(*pl);
     if (rc) {
         if (pl->d_tables) cudaFree(pl->d_tables);
@@ -1109,6 +1160,7 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
 int su_autotune_clear(void) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.clear();
+    g_btune.clear();
     return SU_OK;
 }
 
@@ -1242,14 +1294,17 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
 
 struct su_batch_plan {
     int p = 1;
+    int model = 0;
     int64_t n_inst = 0, n_mc = 1;
     su_options opt{};
-    su::Effective E;
+    std::map<int, su::Effective> E;   // per level p
     su::BatchParams B{};
-    void *d_inst = nullptr, *d_items = nullptr, *d_tables = nullptr;
-    std::vector<int> S;           // per instance
-    std::vector<double> laf, w0;  // log A_free and the level-0 weight per instance
-    int n_blocks = 1;
+    void *d_inst = nullptr, *d_items = nullptr, *d_tables = nullptr, *d_shapes = nullptr;
+    // per instance
+    std::vector<int> S, L, F, K, NB, hier, from;
+    std::vector<int64_t> N, tup, out_off;
+    std::vector<double> laf, w0;      // log A_free and the level-0 weight
+    int64_t n_results = 0;
     int grid = 0;
     size_t smem = 0;
     int64_t tuple_bytes = 0, scratch_bytes = 256, slice_actions = 0;
@@ -1266,14 +1321,38 @@ static void batch_free(su_batch_plan *pl) {
     if (pl->d_inst) cudaFree(pl->d_inst);
     if (pl->d_items) cudaFree(pl->d_items);
     if (pl->d_tables) cudaFree(pl->d_tables);
+    if (pl->d_shapes) cudaFree(pl->d_shapes);
     delete pl;
 }
 
-extern "C" {
+namespace {
 
-int su_batch_plan_create(int model, const double *params, int n_params, int p, const su_instance *inst,
-                         int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt,
-                         su_batch_plan **out) {
+// one instance's resolved arguments
+struct BatchArg {
+    double a, b, T;
+    int s, p, hier;
+    int64_t n;
+};
+
+int batch_args(int p, const su_instance *inst, int64_t n_inst, int64_t n_mc, std::vector<BatchArg> &out) {
+    out.resize((size_t)n_inst);
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const su_instance &q = inst[i];
+        if (q.hierarchy != 0 && q.hierarchy != 1)
+            return fail(SU_EINVAL, "instance %lld: hierarchy must be 0 or 1", (long long)i);
+        if (q.p < 0 || q.n_mc < 0) return fail(SU_EINVAL, "instance %lld: negative p or n_mc", (long long)i);
+        out[(size_t)i] = {q.a, q.b, q.T, q.s, q.p ? q.p : p, q.hierarchy, q.n_mc ? q.n_mc : n_mc};
+    }
+    return SU_OK;
+}
+
+}  // namespace
+
+// The batch plan with every instance's register segment either automatic
+// (force_F = 0: the stored shape of its class, else the rule) or force_F.
+static int batch_create(int model, const double *params, int n_params, int p, const su_instance *inst,
+                        int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt, int force_F,
+                        su_batch_plan **out) {
     using namespace su;
     if (!out) return fail(SU_EINVAL, "plan pointer missing");
     *out = nullptr;
@@ -1285,8 +1364,12 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
         return fail(SU_EINVAL, "instance ids exceed 32 bits");
     if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "the batched path samples the exact bridge only");
     if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the batched path takes the collapsed-table models only");
+    std::vector<BatchArg> arg;
+    int rc = batch_args(p, inst, n_inst, n_mc, arg);
+    if (rc) return rc;
     for (int64_t i = 0; i < n_inst; ++i) {
-        int rc = validate(model, params, n_params, inst[i].a, inst[i].b, inst[i].T, p, inst[i].s, n_mc, o);
+        const BatchArg &q = arg[(size_t)i];
+        rc = validate(model, params, n_params, q.a, q.b, q.T, q.p, q.s, q.n, o);
         if (rc) {
             const std::string why = g_err;
             return fail(rc, "instance %lld: %s", (long long)i, why.c_str());
@@ -1295,72 +1378,186 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
     if (o.sample0 != 0) return fail(SU_ENOTSUP, "sample0 must be 0 for a batch");
     std::unique_ptr<su_batch_plan, void (*)(su_batch_plan *)> pl(new (std::nothrow) su_batch_plan, batch_free);
     if (!pl) return fail(SU_ENOMEM, "host allocation failed");
-    std::string err;
-    int rc = build_effective(model, params, n_params, p, pl->E, err);
-    if (rc) return fail(rc, "%s", err.c_str());
     pl->p = p;
+    pl->model = model;
     pl->n_inst = n_inst;
     pl->n_mc = n_mc;
     pl->opt = o;
-    pl->n_blocks = (int)std::min<int64_t>(o.n_blocks, n_mc);
-    if ((int64_t)pl->n_blocks * n_inst > (1LL << 31) - 1) return fail(SU_ENOTSUP, "too many work items");
     const int prec = o.precision;
-    const int M = pl->E.shape.M;
 
-    // one table per distinct top-level eps; level-0 values from one collapse per distinct T
-    std::map<double, int> tab_of;
+    // effective actions and table shapes, one per distinct level p
+    std::map<int, int> shape_of;
+    std::vector<BatchShape> shapes;
+    for (const BatchArg &q : arg) {
+        if (shape_of.count(q.p)) continue;
+        std::string err;
+        Effective &E = pl->E[q.p];
+        rc = build_effective(model, params, n_params, q.p, E, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        BatchShape sh;
+        std::memset(&sh, 0, sizeof sh);
+        sh.ncol = E.shape.ncol;
+        sh.M = E.shape.M;
+        for (int j = 0; j < E.shape.ncol; ++j) sh.len[j] = E.shape.len[j];
+        shape_of[q.p] = (int)shapes.size();
+        shapes.push_back(sh);
+    }
+    const double alpha = pl->E.begin()->second.shape.alpha;
+    const int ring = pl->E.begin()->second.shape.ring;
+
+    int dev = 0, sms = 0, smem_max = 0;
+    rc = device_limits(dev, sms, smem_max);
+    if (rc) return rc;
+
+    // per instance: path, tables (one set per (p, T, s, levels)), level 0, shape
+    std::map<std::tuple<int, double, int, int>, int64_t> tab_of;
+    std::map<std::pair<int, double>, std::vector<double>> coll;
     std::vector<double> tabd;
-    std::map<double, std::vector<double>> coll;
     std::vector<BatchInstance> hin((size_t)n_inst);
-    pl->S.resize((size_t)n_inst);
-    pl->laf.resize((size_t)n_inst);
-    pl->w0.resize((size_t)n_inst);
-    int S_max = 0;
-    for (int64_t i = 0; i < n_inst; ++i) {
-        const su_instance &q = inst[i];
-        BatchInstance &h = hin[(size_t)i];
+    const size_t ni = (size_t)n_inst;
+    pl->S.resize(ni);
+    pl->L.resize(ni);
+    pl->F.resize(ni);
+    pl->K.resize(ni, 1);
+    pl->NB.resize(ni);
+    pl->hier.resize(ni);
+    pl->from.resize(ni, 0);
+    pl->N.resize(ni);
+    pl->tup.resize(ni, 0);
+    pl->out_off.resize(ni);
+    pl->laf.resize(ni);
+    pl->w0.resize(ni);
+    int S_max = 0, C_max = 1, L_max = 1;
+    int64_t tab_max = 1;
+    for (size_t i = 0; i < ni; ++i) {
+        const BatchArg &q = arg[i];
+        const Effective &E = pl->E[q.p];
+        BatchInstance &h = hin[i];
         std::memset(&h, 0, sizeof h);
         h.a = q.a;
         h.b = q.b;
         h.S = q.s;
-        h.F = std::min(q.s, kMaxFine);
+        h.L = q.s == 0 ? 0 : (q.hier ? q.s : 1);
+        h.shape = shape_of[q.p];
+        h.n_mc = q.n;
+        h.n_blocks = (int)std::min<int64_t>(o.n_blocks, q.n);
         for (int n = 1; n <= q.s; ++n) h.sigma[n] = std::sqrt(q.T / std::ldexp(1.0, n + 1));
-        pl->S[(size_t)i] = q.s;
-        pl->laf[(size_t)i] = log_A_free(q.a, q.b, q.T);
-        auto c = coll.find(q.T);
+        pl->S[i] = q.s;
+        pl->L[i] = h.L;
+        pl->NB[i] = h.n_blocks;
+        pl->hier[i] = q.hier;
+        pl->N[i] = q.n;
+        pl->out_off[i] = pl->n_results;
+        pl->n_results += q.hier ? q.s + 1 : 1;
+        pl->laf[i] = log_A_free(q.a, q.b, q.T);
+        auto c = coll.find({q.p, q.T});
         if (c == coll.end()) {
             std::vector<double> P;
-            collapse(pl->E, q.T, P);
-            c = coll.emplace(q.T, std::move(P)).first;
+            collapse(E, q.T, P);
+            c = coll.emplace(std::make_pair(q.p, q.T), std::move(P)).first;
         }
-        pl->w0[(size_t)i] = -q.T * wp_collapsed(pl->E.shape, c->second, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a));
-        if (q.s >= 1) {
-            const double eps = q.T / std::ldexp(1.0, q.s);
-            auto it = tab_of.find(eps);
-            if (it == tab_of.end()) {
-                std::vector<double> t;
-                kernel_table(pl->E, eps, t);
-                if (g_fault_table_nan.exchange(0)) t[0] = NAN;   // fault injection
-                for (double v : t)
-                    if (!std::isfinite(v) || (prec == SU_FP32 && !std::isfinite((float)v)))
-                        return fail(SU_ENONFINITE, "non-finite coefficient at eps = %g", eps);
-                it = tab_of.emplace(eps, (int)tab_of.size()).first;
-                tabd.insert(tabd.end(), t.begin(), t.end());
+        pl->w0[i] = -q.T * wp_collapsed(E.shape, c->second, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a));
+        if (!std::isfinite(pl->w0[i]) && !(std::isinf(pl->w0[i]) && pl->w0[i] < 0))
+            return fail(SU_ENONFINITE, "instance %lld: level-0 weight is not finite", (long long)i);
+        if (q.s == 0) continue;
+        // shape: forced, else stored for the class, else the rule
+        int F = prec == SU_FP64 ? 4 : kMaxFine;
+        if (force_F > 0) {
+            F = force_F;
+        } else {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_btune.find({prec, model, q.p, q.s, q.hier});
+            if (it != g_btune.end()) {
+                F = it->second;
+                pl->from[i] = 1;
             }
-            h.table = it->second;
-            S_max = std::max(S_max, q.s);
-            pl->slice_actions += n_mc * ((int64_t)1 << q.s);
         }
+        h.F = std::min(q.s, std::max(1, F));
+        pl->F[i] = h.F;
+        const auto key = std::make_tuple(q.p, q.T, q.s, h.L);
+        auto t = tab_of.find(key);
+        if (t == tab_of.end()) {
+            const int64_t offset = (int64_t)tabd.size();
+            for (int d = 0; d < h.L; ++d) {
+                std::vector<double> row;
+                kernel_table(E, q.T / std::ldexp(1.0, q.s - d), row);
+                if (g_fault_table_nan.exchange(0)) row[0] = NAN;   // fault injection
+                for (double v : row)
+                    if (!std::isfinite(v) || (prec == SU_FP32 && !std::isfinite((float)v)))
+                        return fail(SU_ENONFINITE, "non-finite coefficient at p = %d, eps = %g", q.p,
+                                    q.T / std::ldexp(1.0, q.s - d));
+                tabd.insert(tabd.end(), row.begin(), row.end());
+            }
+            t = tab_of.emplace(key, offset).first;
+        }
+        h.tab = t->second;
+        S_max = std::max(S_max, q.s);
+        C_max = std::max(C_max, 1 << (q.s - h.F));
+        L_max = std::max(L_max, h.L);
+        tab_max = std::max(tab_max, (int64_t)h.L * E.shape.M);
+        const int64_t Nn = (int64_t)1 << q.s;
+        pl->slice_actions += q.n * (h.L > 1 ? 2 * Nn - 2 : Nn);
     }
-    // work items (instance, block), costliest (deepest) first
+
+    BatchParams &B = pl->B;
+    std::memset(&B, 0, sizeof B);
+    SamplerParams &P = B.base;
+    P.levels = 1;
+    P.ring = ring;
+    P.alpha = alpha;
+    P.seed = seed;
+    P.instance = o.instance;
+    B.S_max = S_max;
+    B.C_max = C_max;
+    B.L_max = L_max;
+    B.tab_max = tab_max;
+    pl->smem = batch_smem_bytes(B, prec);
+    if (pl->smem > (size_t)smem_max)
+        return fail(SU_ENOTSUP, "shared memory %zu exceeds %d (tables of %lld entries, %d levels)", pl->smem, smem_max,
+                    (long long)tab_max, L_max);
+    const int occ = batch_occupancy(B, prec, pl->smem);
+    if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
+    const int64_t slots = (int64_t)sms * occ;
+
+    // work items (instance, block, chunk).  Cost of an instance's block:
+    // samples x slices x (table entries + the per-slice formation and RNG
+    // share); blocks are split into chunks where the whole batch has fewer
+    // than about eight items of the average cost per resident CTA
+    std::vector<double> bcost(ni, 0.0);
+    double total = 0;
+    for (size_t i = 0; i < ni; ++i) {
+        if (pl->S[i] == 0) continue;
+        const int64_t Nn = (int64_t)1 << pl->S[i];
+        const double slices = (double)(pl->L[i] > 1 ? 2 * Nn - 2 : Nn);
+        bcost[i] = ((double)pl->N[i] / pl->NB[i]) * slices * (double)(shapes[(size_t)hin[i].shape].M + 12);
+        total += bcost[i] * pl->NB[i];
+    }
+    const double target = total / (8.0 * (double)slots);
+    int64_t n_items = 0, n_tup = 0;
+    for (size_t i = 0; i < ni; ++i) {
+        if (pl->S[i] == 0) continue;
+        const int64_t bmin = pl->N[i] / pl->NB[i];                 // smallest block
+        int64_t k = target > 0 ? (int64_t)std::ceil(bcost[i] / target) : 1;
+        k = std::max<int64_t>(1, std::min<int64_t>(k, std::max<int64_t>(1, bmin / kThreads)));
+        pl->K[i] = (int)k;
+        hin[i].chunks = (int)k;
+        hin[i].tup = n_tup;
+        pl->tup[i] = n_tup;
+        n_tup += (int64_t)pl->NB[i] * k * pl->L[i];
+        n_items += (int64_t)pl->NB[i] * k;
+    }
+    if (n_items > (1LL << 31) - 1) return fail(SU_ENOTSUP, "too many work items");
+    // costliest items first: an instance's items are alike, so order the instances
+    std::vector<int64_t> order;
+    for (size_t i = 0; i < ni; ++i)
+        if (pl->S[i] >= 1) order.push_back((int64_t)i);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        return bcost[(size_t)x] / pl->K[(size_t)x] > bcost[(size_t)y] / pl->K[(size_t)y];
+    });
     std::vector<int2> items;
-    items.reserve((size_t)(n_inst * pl->n_blocks));
-    std::vector<int64_t> order((size_t)n_inst);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return pl->S[(size_t)x] > pl->S[(size_t)y]; });
+    items.reserve((size_t)n_items);
     for (int64_t i : order)
-        if (pl->S[(size_t)i] >= 1)
-            for (int bk = 0; bk < pl->n_blocks; ++bk) items.push_back(make_int2((int)i, bk));
+        for (int u = 0; u < pl->NB[(size_t)i] * pl->K[(size_t)i]; ++u) items.push_back(make_int2((int)i, u));
 
     const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
     std::vector<unsigned char> blob(std::max<size_t>(tabd.size(), 1) * rs, 0);
@@ -1368,55 +1565,37 @@ int su_batch_plan_create(int model, const double *params, int n_params, int p, c
         for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
     else if (!tabd.empty())
         std::memcpy(blob.data(), tabd.data(), tabd.size() * sizeof(double));
-
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
-    }
-    int dev = 0, sms = 0, smem_max = 0;
-    CU(cudaGetDevice(&dev), "cudaGetDevice");
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
     CU(dmalloc(&pl->d_tables, blob.size()), "device allocation (tables)");
     CU(cudaMemcpy(pl->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice), "upload tables");
     CU(dmalloc(&pl->d_inst, sizeof(BatchInstance) * hin.size()), "device allocation (instances)");
     CU(cudaMemcpy(pl->d_inst, hin.data(), sizeof(BatchInstance) * hin.size(), cudaMemcpyHostToDevice),
        "upload instances");
+    CU(dmalloc(&pl->d_shapes, sizeof(BatchShape) * shapes.size()), "device allocation (shapes)");
+    CU(cudaMemcpy(pl->d_shapes, shapes.data(), sizeof(BatchShape) * shapes.size(), cudaMemcpyHostToDevice),
+       "upload shapes");
     if (!items.empty()) {
         CU(dmalloc(&pl->d_items, sizeof(int2) * items.size()), "device allocation (items)");
         CU(cudaMemcpy(pl->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice),
            "upload items");
     }
-
-    BatchParams &B = pl->B;
-    std::memset(&B, 0, sizeof B);
-    SamplerParams &P = B.base;
-    P.levels = 1;
-    P.ring = pl->E.shape.ring;
-    P.ncol = pl->E.shape.ncol;
-    P.M = M;
-    for (int j = 0; j < pl->E.shape.ncol; ++j) P.len[j] = pl->E.shape.len[j];
-    P.alpha = pl->E.shape.alpha;
     P.tables = pl->d_tables;
-    P.seed = seed;
-    P.instance = o.instance;
     B.inst = static_cast<const BatchInstance *>(pl->d_inst);
+    B.shapes = static_cast<const BatchShape *>(pl->d_shapes);
     B.items = static_cast<const int2 *>(pl->d_items);
     B.n_items = (int)items.size();
-    B.S_max = S_max;
-    B.n_mc = n_mc;
-    B.n_blocks = pl->n_blocks;
-    pl->smem = batch_smem_bytes(B, prec);
-    if (pl->smem > (size_t)smem_max) return fail(SU_ENOTSUP, "shared memory %zu exceeds %d", pl->smem, smem_max);
-    const int occ = batch_occupancy(B, prec, pl->smem);
-    if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
-    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, std::max(B.n_items, 1)));
-    pl->tuple_bytes = n_inst * pl->n_blocks * 4 * (int64_t)sizeof(double);
+    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(slots, std::max(B.n_items, 1)));
+    pl->tuple_bytes = std::max<int64_t>(n_tup, 1) * 4 * (int64_t)sizeof(double);
     pl->scratch_bytes = 256;
     *out = pl.release();
     return SU_OK;
+}
+
+extern "C" {
+
+int su_batch_plan_create(int model, const double *params, int n_params, int p, const su_instance *inst,
+                         int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt,
+                         su_batch_plan **out) {
+    return batch_create(model, params, n_params, p, inst, n_inst, n_mc, seed, opt, 0, out);
 }
 
 int su_batch_plan_destroy(su_batch_plan *pl) {
@@ -1425,11 +1604,21 @@ int su_batch_plan_destroy(su_batch_plan *pl) {
 }
 
 int su_batch_plan_sizes(const su_batch_plan *pl, int64_t *tuple_bytes, int64_t *scratch_bytes,
-                        int64_t *slice_actions) {
+                        int64_t *slice_actions, int64_t *n_results) {
     if (!pl) return fail(SU_EINVAL, "plan missing");
     if (tuple_bytes) *tuple_bytes = pl->tuple_bytes;
     if (scratch_bytes) *scratch_bytes = pl->scratch_bytes;
     if (slice_actions) *slice_actions = pl->slice_actions;
+    if (n_results) *n_results = pl->n_results;
+    return SU_OK;
+}
+
+int su_batch_plan_shape(const su_batch_plan *pl, int64_t i, int *seg_log2, int *chunks, int *from) {
+    if (!pl) return fail(SU_EINVAL, "plan missing");
+    if (i < 0 || i >= pl->n_inst) return fail(SU_EINVAL, "instance %lld out of range", (long long)i);
+    if (seg_log2) *seg_log2 = pl->F[(size_t)i];
+    if (chunks) *chunks = pl->K[(size_t)i];
+    if (from) *from = pl->from[(size_t)i];
     return SU_OK;
 }
 
@@ -1438,8 +1627,7 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
     if (!d_tuples || !d_scratch) return fail(SU_EINVAL, "device buffers missing");
     if (launches) *launches = 0;
     cudaStream_t st = (cudaStream_t)stream;
-    // instances with s = 0 have no samples: their tuples stay zero
-    CU(cudaMemsetAsync(d_tuples, 0, (size_t)pl->tuple_bytes, st), "clear tuples");
+    // instances with s = 0 have no samples and no tuples
     if (pl->B.n_items == 0) return SU_OK;
     su::BatchParams B = pl->B;
     B.tuples = static_cast<double *>(d_tuples);
@@ -1450,6 +1638,7 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
     const int64_t stop = g_fault_queue.exchange(0);
     if (stop > 0) {   // fault injection: the queue ends after `stop` items
         B.n_items = (int)std::min<int64_t>(B.n_items, stop);
+        CU(cudaMemsetAsync(d_tuples, 0, (size_t)pl->tuple_bytes, st), "clear tuples");
         CU(cudaMemsetAsync(d_scratch, 0, 8, st), "clear queue");
         CU(cudaLaunchKernel(fn, dim3(pl->grid), dim3(su::kThreads), args, pl->smem, st), "batch launch");
         if (launches) *launches = 1;
@@ -1498,21 +1687,61 @@ int su_batch_plan_finalize(const su_batch_plan *pl, const double *h_tuples, cons
            "read flags");
         if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     }
+    std::vector<double> blk;
     for (int64_t i = 0; i < pl->n_inst; ++i) {
-        su_level_result &r = out[i];
-        if (pl->S[(size_t)i] == 0) {
-            r.amp = std::exp(pl->laf[(size_t)i] + pl->w0[(size_t)i]);
-            r.log_amp = pl->laf[(size_t)i] + pl->w0[(size_t)i];
-            r.err = r.err_naive = r.rel_err = 0;
-            r.ess = (double)pl->n_mc;
-            r.max_share = 1.0 / (double)pl->n_mc;
-            r.n = pl->n_mc;
-        } else {
-            level_result(pl->laf[(size_t)i], h_tuples + 4 * i * pl->n_blocks, pl->n_blocks, 1, 0, &r);
-            if (r.n != pl->n_mc)
-                return fail(SU_ECUDA, "instance %lld: %lld of %lld samples reduced (the work queue ended early)",
-                            (long long)i, (long long)r.n, (long long)pl->n_mc);
+        const size_t k = (size_t)i;
+        su_level_result *o = out + pl->out_off[k];
+        su_level_result r0;
+        r0.amp = std::exp(pl->laf[k] + pl->w0[k]);
+        r0.log_amp = pl->laf[k] + pl->w0[k];
+        r0.err = r0.err_naive = r0.rel_err = 0;
+        r0.ess = (double)pl->N[k];
+        r0.max_share = 1.0 / (double)pl->N[k];
+        r0.n = pl->N[k];
+        if (pl->S[k] == 0) {
+            o[0] = r0;
+            continue;
         }
+        // merge each block's chunks in order: tuples [block][level]
+        const int L = pl->L[k], K = pl->K[k], nb = pl->NB[k];
+        const double *t = h_tuples + 4 * pl->tup[k];
+        blk.assign((size_t)nb * L * 4, 0.0);
+        for (int b = 0; b < nb; ++b)
+            for (int d = 0; d < L; ++d) {
+                double M = -INFINITY, S = 0, Q = 0, n = 0;
+                for (int c = 0; c < K; ++c) {
+                    const double *x = t + 4 * (((int64_t)b * K + c) * L + d);
+                    n += x[3];
+                    if (!(x[0] > -INFINITY)) continue;
+                    if (x[0] > M) {
+                        const double f = std::exp(M - x[0]);
+                        S = S * f + x[1];
+                        Q = Q * f * f + x[2];
+                        M = x[0];
+                    } else {
+                        const double f = std::exp(x[0] - M);
+                        S += x[1] * f;
+                        Q += x[2] * f * f;
+                    }
+                }
+                double *y = blk.data() + 4 * ((int64_t)b * L + d);
+                y[0] = M;
+                y[1] = S;
+                y[2] = Q;
+                y[3] = n;
+            }
+        for (int d = 0; d < L; ++d) {
+            su_level_result r;
+            level_result(pl->laf[k], blk.data(), nb, L, d, &r);
+            if (r.n != pl->N[k])
+                return fail(SU_ECUDA, "instance %lld: %lld of %lld samples reduced (the work queue ended early)",
+                            (long long)i, (long long)r.n, (long long)pl->N[k]);
+            if (pl->hier[k])
+                o[pl->S[k] - d] = r;
+            else
+                o[0] = r;
+        }
+        if (pl->hier[k]) o[0] = r0;
     }
     return SU_OK;
 }
@@ -1533,7 +1762,7 @@ int speedup_amplitude_batch(int model, const double *params, int n_params, int p
     rc = su_batch_plan_execute(pl, dbuf, d_scr, st, nullptr);
     cudaError_t e = cudaSuccess;
     int flags = 0;
-    if (rc == SU_OK) {
+    if (rc == SU_OK && pl->B.n_items > 0) {
         e = cudaMemcpyAsync(h.data(), dbuf, (size_t)pl->tuple_bytes, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&flags, static_cast<int *>(d_scr) + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1544,6 +1773,98 @@ int speedup_amplitude_batch(int model, const double *params, int n_params, int p
     if (e != cudaSuccess) return cuda_fail(e, "batched sampling");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
     return su_batch_plan_finalize(pl, h.data(), nullptr, out);
+}
+
+int su_batch_autotune(int model, const double *params, int n_params, int p, const su_instance *inst,
+                      int64_t n_inst, int64_t n_mc, uint64_t seed, const su_options *opt, int max_probe,
+                      su_batch_tuning *best, int cap, int *n_best) {
+    using namespace su;
+    if (n_best) *n_best = 0;
+    if (max_probe < 1) return fail(SU_EINVAL, "max_probe must be >= 1");
+    if (cap < 0 || (cap > 0 && !best)) return fail(SU_EINVAL, "best and cap inconsistent");
+    if (!inst || n_inst < 1 || n_inst > (1LL << 24)) return fail(SU_EINVAL, "n_inst must be in 1..2^24");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    std::vector<BatchArg> arg;
+    int rc = batch_args(p, inst, n_inst, n_mc, arg);
+    if (rc) return rc;
+    // the classes (p, s, hierarchy) and their first max_probe instances
+    std::map<std::tuple<int, int, int>, std::vector<su_instance>> cls;
+    for (int64_t i = 0; i < n_inst; ++i) {
+        const BatchArg &q = arg[(size_t)i];
+        if (q.s < 1) continue;
+        auto &v = cls[std::make_tuple(q.p, q.s, q.hier)];
+        if ((int)v.size() < max_probe) {
+            su_instance x = inst[i];
+            x.p = q.p;
+            x.n_mc = q.n;
+            v.push_back(x);
+        }
+    }
+    cudaStream_t st = (cudaStream_t)o.stream;
+    struct Res {
+        void *buf = nullptr;
+        size_t cap = 0;
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Res() {
+            if (buf) cudaFree(buf);
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } res;
+    CU(cudaEventCreate(&res.e[0]), "event");
+    CU(cudaEventCreate(&res.e[1]), "event");
+    int done = 0;
+    for (auto &kv : cls) {
+        const int cp = std::get<0>(kv.first), cs = std::get<1>(kv.first), ch = std::get<2>(kv.first);
+        su_batch_tuning top{cp, cs, ch, 0, INFINITY};
+        for (int F = 1; F <= std::min(cs, kMaxFine); ++F) {
+            su_batch_plan *pl = nullptr;
+            rc = batch_create(model, params, n_params, p, kv.second.data(), (int64_t)kv.second.size(), n_mc, seed, &o,
+                              F, &pl);
+            if (rc == SU_ENOTSUP) continue;   // this segment's shared memory does not fit
+            if (rc) return rc;
+            std::unique_ptr<su_batch_plan, int (*)(su_batch_plan *)> guard(pl, su_batch_plan_destroy);
+            const size_t need = (size_t)(pl->tuple_bytes + pl->scratch_bytes);
+            if (need > res.cap) {
+                if (res.buf) cudaFree(res.buf);
+                res.buf = nullptr;
+                res.cap = 0;
+                CU(dmalloc(&res.buf, need), "device allocation (probe buffers)");
+                res.cap = need;
+            }
+            void *d_tup = res.buf, *d_scr = static_cast<char *>(res.buf) + pl->tuple_bytes;
+            rc = su_batch_plan_execute(pl, d_tup, d_scr, st, nullptr);   // warm-up (and the graph)
+            if (rc) return rc;
+            float ms_best = INFINITY;
+            for (int k = 0; k < 2; ++k) {
+                CU(cudaEventRecord(res.e[0], st), "event record");
+                rc = su_batch_plan_execute(pl, d_tup, d_scr, st, nullptr);
+                if (rc) return rc;
+                CU(cudaEventRecord(res.e[1], st), "event record");
+                CU(cudaEventSynchronize(res.e[1]), "probe");
+                float ms = 0;
+                CU(cudaEventElapsedTime(&ms, res.e[0], res.e[1]), "event time");
+                ms_best = std::min(ms_best, ms);
+            }
+            const double ns = (double)ms_best * 1e6 / (double)std::max<int64_t>(pl->slice_actions, 1);
+            if (ns < top.ns_per_slice) {
+                top.seg_log2 = F;
+                top.ns_per_slice = ns;
+            }
+        }
+        if (top.seg_log2 == 0) return fail(SU_ENOTSUP, "no register segment fits class p = %d, s = %d", cp, cs);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_btune[{o.precision, model, cp, cs, ch}] = top.seg_log2;
+        }
+        if (done < cap) best[done] = top;
+        ++done;
+    }
+    if (n_best) *n_best = done;
+    g_err.clear();
+    return SU_OK;
 }
 
 int speedup_philox_words(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n_samples,
@@ -1919,28 +2240,20 @@ extern "C" int speedup_train_proposal(int model, const double *params, int n_par
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SU_NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[256];   // device address of the array, per device ordinal
-
 // The array's name is a host-side stand-in in host code; its device address
-// comes from cudaGetSymbolAddress, looked up once per device with that device
-// current (the first call on a device).
-static int noalloc_scratch(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= 256) return fail(SU_ENOTSUP, "device ordinal %d beyond 255", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
-        }
-        g_noalloc_addr[dev] = p;
+// comes from cudaGetSymbolAddress with the caller's device current.  It is
+// looked up on every call, not cached: a context torn down and rebuilt (for
+// example after cudaDeviceReset) loads the module again, possibly elsewhere.
+static int noalloc_scratch(unsigned char **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
     }
-    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    *out = static_cast<unsigned char *>(p);
     return SU_OK;
 }
-
 
 extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_params, double a, double b,
                                          double T, int p, int s, int64_t n_mc, uint64_t seed,
@@ -1950,122 +2263,66 @@ extern "C" int speedup_amplitude_noalloc(int model, const double *params, int n_
     su_options o;
     su_options_default(&o);
     if (opt) o = *opt;
-    int rc = validate(model, params, n_params, a, b, T, p, s, n_mc, o);
-    if (rc) return rc;
     if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the allocation-free path takes the collapsed-table models only");
-    Effective E;
-    std::string err;
-    rc = build_effective(model, params, n_params, p, E, err);
-    if (rc) return fail(rc, "%s", err.c_str());
-    const double laf = log_A_free(a, b, T);
-    const double w0 = -T * wp_host(E, 0.5 * (a + b), 0.5 * (b - a), T);
-    su_level_result &r0 = out[0];
-    r0.amp = std::exp(laf + w0);
-    r0.log_amp = laf + w0;
-    r0.err = r0.err_naive = r0.rel_err = 0;
-    r0.ess = (double)n_mc;
-    r0.max_share = 1.0 / (double)n_mc;
-    r0.n = n_mc;
-    if (s == 0) return SU_OK;
-
-    // host tables of levels n = s..1 (row d = s - n)
-    const int prec = o.precision;
-    const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
-    const int M = E.shape.M;
-    std::vector<double> tabd((size_t)s * M);
-    for (int d = 0; d < s; ++d) {
-        std::vector<double> t;
-        kernel_table(E, T / std::ldexp(1.0, s - d), t);
-        for (int i = 0; i < M; ++i) {
-            if (!std::isfinite(t[i]) || (prec == SU_FP32 && !std::isfinite((float)t[i])))
-                return fail(SU_ENONFINITE, "non-finite coefficient at level %d", s - d);
-            tabd[(size_t)d * M + i] = t[i];
-        }
-    }
-    std::vector<unsigned char> blob(tabd.size() * rs);
-    if (prec == SU_FP32)
-        for (size_t i = 0; i < tabd.size(); ++i) reinterpret_cast<float *>(blob.data())[i] = (float)tabd[i];
-    else
-        std::memcpy(blob.data(), tabd.data(), blob.size());
-
-    SamplerParams P;
-    std::memset(&P, 0, sizeof P);
-    P.a = a;
-    P.b = b;
-    for (int n = 1; n <= s; ++n) P.sigma[n] = o.width_factor * std::sqrt(T / std::ldexp(1.0, n + 1));
-    P.S = s;
-    P.F = std::min(s, kMaxFine);
-    P.levels = o.hierarchy ? s : 1;
-    P.wf_on = o.width_factor != 1.0;
-    P.lwf = std::log(o.width_factor);
-    P.hcoef = 0.5 * (1.0 - o.width_factor * o.width_factor);
-    P.ring = E.shape.ring;
-    P.ncol = E.shape.ncol;
-    P.M = M;
-    for (int j = 0; j < E.shape.ncol; ++j) P.len[j] = E.shape.len[j];
-    P.alpha = E.shape.alpha;
-    P.seed = seed;
-    P.instance = o.instance;
-    P.n_mc = n_mc;
-    P.sample0 = o.sample0;
-    const int64_t nb = std::min<int64_t>(o.n_blocks, n_mc);
-    P.n_blocks = nb;
-
-    // the fewest rounds (samples per item / 128) whose tuples fit the array
-    const int64_t bsz = (n_mc + nb - 1) / nb;
-    const int64_t tab_bytes = up256((int64_t)blob.size());
-    const int64_t tup_bytes = up256(nb * P.levels * 4 * (int64_t)sizeof(double));
-    int64_t part_bytes = 0;
-    for (P.rounds = 1;; P.rounds *= 2) {
-        P.items_per_block = (bsz + (int64_t)kThreads * P.rounds - 1) / ((int64_t)kThreads * P.rounds);
-        P.n_items = P.items_per_block * nb;
-        part_bytes = up256(P.n_items * P.levels * 4 * (int64_t)sizeof(double));
-        if (tab_bytes + part_bytes + tup_bytes + 256 <= (int64_t)SU_NOALLOC_SCRATCH_BYTES) break;
-        if (P.rounds >= 64)
-            return fail(SU_ENOTSUP,
-                        "n_mc = %lld with %lld blocks needs more than the %u bytes of no-alloc scratch",
-                        (long long)n_mc, (long long)nb, (unsigned)SU_NOALLOC_SCRATCH_BYTES);
-    }
-
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return fail(SU_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
-    }
-    int dev = 0, sms = 0, smem_max = 0;
-    CU(cudaGetDevice(&dev), "cudaGetDevice");
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
-    unsigned char *base = nullptr;
-    rc = noalloc_scratch(dev, &base);
+    // the plan's host side (arguments, tables, launch shape) as su_plan_create
+    // builds it; only the device memory differs
+    su_plan pl;
+    int rc = plan_init(pl, model, params, n_params, a, b, T, p, s, n_mc, seed, o);
     if (rc) return rc;
+    if (s == 0) return su_plan_finalize(&pl, nullptr, nullptr, out);
+    std::vector<unsigned char> blob;
+    rc = plan_tables(pl, blob);
+    if (rc) return rc;
+    int dev = 0, sms = 0, smem_max = 0;
+    rc = device_limits(dev, sms, smem_max);
+    if (rc) return rc;
+    rc = plan_shape(pl, sms, smem_max);
+    if (rc) return rc;
+
+    // scratch layout: tables | per-item tuples | per-block tuples | flag word;
+    // where the per-item tuples do not fit, more paths per item (rounds up to
+    // 8, while the shape stays resident), unless the caller fixed rounds
+    const int64_t tab_bytes = up256((int64_t)blob.size());
+    const int64_t tup_bytes = up256(pl.tuple_bytes);
+    auto fits = [&] { return tab_bytes + up256(pl.partial_bytes) + tup_bytes + 256 <= (int64_t)SU_NOALLOC_SCRATCH_BYTES; };
+    if (!fits() && o.rounds == 0) {
+        int good = pl.P.rounds;
+        for (int r = good * 2; r <= 8 && !fits(); r *= 2) {
+            if (plan_rounds(pl, r, sms, smem_max) < 1) break;   // shared memory or residency
+            good = r;
+        }
+        plan_rounds(pl, good, sms, smem_max);
+    }
+    if (!fits())
+        return fail(SU_ENOTSUP,
+                    "n_mc = %lld with %lld blocks and %d levels needs more than the %u bytes of no-alloc scratch",
+                    (long long)n_mc, (long long)pl.n_blocks, pl.levels, (unsigned)SU_NOALLOC_SCRATCH_BYTES);
+
+    unsigned char *base = nullptr;
+    rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    SamplerParams P = pl.P;
     unsigned char *d_tab = base;
     double *d_part = reinterpret_cast<double *>(base + tab_bytes);
-    double *d_tup = reinterpret_cast<double *>(base + tab_bytes + part_bytes);
-    int *d_flag = reinterpret_cast<int *>(base + tab_bytes + part_bytes + tup_bytes);
+    double *d_tup = reinterpret_cast<double *>(base + tab_bytes + up256(pl.partial_bytes));
+    int *d_flag = reinterpret_cast<int *>(base + tab_bytes + up256(pl.partial_bytes) + tup_bytes);
     P.tables = d_tab;
     P.partial = d_part;
     P.flags = d_flag;
     P.w_out = nullptr;
-    const size_t smem = sampler_smem_bytes(P, prec);
-    if (smem > (size_t)smem_max) return fail(SU_ENOTSUP, "shared memory %zu exceeds %d bytes", smem, smem_max);
-    const int occ = sampler_occupancy(P, prec, smem);
-    if (occ < 1) return fail(SU_ECUDA, "sampler cannot be resident");
-    const int grid = (int)std::min<int64_t>(P.n_items, (int64_t)sms * occ);
+    P.item0 = 0;
 
     cudaStream_t st = (cudaStream_t)o.stream;
-    std::vector<double> h((size_t)(nb * P.levels * 4));
+    std::vector<double> h((size_t)(pl.tuple_bytes / sizeof(double)));
     int flags = 0;
     CU(cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "upload tables");
     CU(cudaMemsetAsync(d_flag, 0, sizeof(int), st), "clear flag");
-    CU(launch_sampler(P, prec, grid, smem, st), "sampler launch");
-    CU(launch_combine(d_part, d_tup, 0, nb, P.levels, P.items_per_block, st), "combine launch");
+    CU(launch_sampler(P, o.precision, pl.grid, pl.smem, st), "sampler launch");
+    CU(launch_combine(d_part, d_tup, 0, pl.n_blocks, pl.levels, P.items_per_block, st), "combine launch");
     CU(cudaMemcpyAsync(h.data(), d_tup, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read tuples");
     CU(cudaMemcpyAsync(&flags, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     CU(cudaStreamSynchronize(st), "sampling");
-    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
     if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
-    for (int d = 0; d < P.levels; ++d) level_result(laf, h.data(), nb, P.levels, d, &out[s - d]);
-    return SU_OK;
+    // the same completeness check as su_plan_finalize (every sample reduced)
+    return su_plan_finalize(&pl, h.data(), nullptr, out);
 }

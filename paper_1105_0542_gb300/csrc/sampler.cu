@@ -146,10 +146,12 @@ const void *batch_fn(int ring, int precision) {
 
 size_t batch_smem_bytes(const BatchParams &B, int precision) {
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
-    const int Cmax = 1 << (B.S_max > kMaxFine ? B.S_max - kMaxFine : 0);
-    size_t off = rs * (size_t)B.base.M + rs * (size_t)(SU_MAX_S + 1);
+    size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
+    off += rs * (size_t)B.tab_max + rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
-    off += rs * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
+    off += rs * (size_t)(B.C_max > 1 ? B.C_max + 1 : 0) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    off += (2 * sizeof(double) + rs) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
     if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;

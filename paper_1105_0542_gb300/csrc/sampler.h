@@ -72,27 +72,42 @@ struct SamplerParams {
     const GeneralDev *general;  // device: RING_GENERAL only
 };
 
-// One instance of a batch (top level only).
+// One instance of a batch: its path (a, b, N = 2^S, widths), its table
+// shape (one per distinct level p), its tables (L rows of M entries from
+// element tab: row d for level n = S - d), its samples and error blocks,
+// the chunks each block is split into (work items), and where its tuples go.
 struct BatchInstance {
     double a, b;
     int S, F;
-    int table;                // index of its table in the batch's table list
-    int pad;
+    int L;                    // sampled levels: 1 (top level only) or S (hierarchy)
+    int shape;                // index into BatchParams::shapes
+    int64_t tab;              // first table element of this instance
+    int64_t n_mc;             // samples
+    int n_blocks, chunks;     // error blocks; work items per block
+    int64_t tup;              // first tuple: [block][chunk][level], 4 doubles each
     double sigma[SU_MAX_S + 1];
 };
 
-// The batched kernel's parameters: the shape and stream fields of base are
-// shared by all instances (same model and p); the per-instance fields of
-// base are unused.
+// The Horner shape of one level p's tables (columns in x-bar^2, entries per column).
+struct BatchShape {
+    int ncol, M;
+    int len[SU_MAX_P];
+};
+
+// The batched kernel's parameters: the model fields of base (ring, alpha,
+// seed, stream id, tables, flags) are shared by all instances; the
+// per-instance fields of base are unused.
 struct BatchParams {
     SamplerParams base;
     const BatchInstance *inst;
-    const int2 *items;        // (instance, block), costliest first
+    const BatchShape *shapes;
+    const int2 *items;        // (instance, block * chunks + chunk), costliest first
     int n_items;
     int S_max;
-    int64_t n_mc;             // samples per instance
-    int n_blocks;             // blocks per instance
-    double *tuples;           // [instance][block] (M, S, Q, n)
+    int C_max;                // largest 2^(S - F): segment endpoints per path
+    int L_max;                // most sampled levels of an instance
+    int64_t tab_max;          // largest L * M: table elements staged per item
+    double *tuples;           // per instance from its tup offset
     int *counter;             // work-queue head, zeroed before every launch
 };
 

@@ -228,9 +228,8 @@ __device__ __noinline__ double2 slice_general(double ql0, double qr0, double ql1
 
 // -eps W_p(x, xb; eps) of one slice, from the level's table in shared memory:
 // sum_j (vs^2)^j sum_i T_ij Z^i, nested Horner (columns, then powers of vs^2).
-template <typename R, int RING>
-__device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const SamplerParams &P,
-                                   R alpha) {
+template <typename R, int RING, typename SP>
+__device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const SP &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
         static_assert(sizeof(R) == 8, "the general potential is evaluated in double");
         return slice_general<1>(ql, qr, ql, qr, tab, P.general).x;
@@ -268,9 +267,8 @@ struct Batch {
     static constexpr int B = 8;
 };
 
-template <typename R, int RING, int NS, int STR, int NQ>
-__device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab,
-                                       const SamplerParams &P, R alpha) {
+template <typename R, int RING, int NS, int STR, int NQ, typename SP>
+__device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab, const SP &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
         R total = 0;
         if constexpr (NS == 1) {
@@ -412,10 +410,9 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
 }
 
 // levels d = D..F of a segment (level n = S - d uses every 2^d-th point)
-template <typename R, int RING, int F, int D>
+template <typename R, int RING, int F, int D, typename SP>
 __device__ __forceinline__ void segment_levels(R (&acc)[F + 1], const R (&q)[(1 << F) + 1],
-                                               const R *__restrict__ tab, const SamplerParams &P,
-                                               R alpha, int S) {
+                                               const R *__restrict__ tab, const SP &P, R alpha, int S) {
     if constexpr (D <= F) {
         if (D < S) {
             acc[D] += level_sum<R, RING, ((1 << F) >> D), (1 << D)>(q, tab + D * P.M, P, alpha);
@@ -450,8 +447,8 @@ struct PathCfg {
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
-template <typename R, int RING, int F, bool WF>
-__device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCfg<R> &pc,
+template <typename R, int RING, int F, bool WF, typename SP>
+__device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
                                             const R *__restrict__ tab, R *__restrict__ qc,
                                             double *__restrict__ zz, const Stream<R> &st,
                                             R *__restrict__ wout, int wstride, float *qout = nullptr) {
@@ -622,8 +619,8 @@ __device__ __forceinline__ void sample_path(const SamplerParams &P, const PathCf
 // The width-factor weight is a template switch: as a run-time test inside
 // the midpoint loop the compiler predicates it, and its double conversions
 // and multiply-add then occupy the FP64 pipe on every midpoint.
-template <typename R, int RING, bool WF>
-__device__ __forceinline__ void sample_path_f(int F, const SamplerParams &P, const PathCfg<R> &pc,
+template <typename R, int RING, bool WF, typename SP>
+__device__ __forceinline__ void sample_path_f(int F, const SP &P, const PathCfg<R> &pc,
                                               const R *tab, R *qc, double *zz, const Stream<R> &st,
                                               R *wout, int wstride, float *qout) {
     switch (F) {
@@ -635,8 +632,8 @@ __device__ __forceinline__ void sample_path_f(int F, const SamplerParams &P, con
     }
 }
 
-template <typename R, int RING>
-__device__ __forceinline__ void sample_path_any(int F, const SamplerParams &P, const PathCfg<R> &pc,
+template <typename R, int RING, typename SP>
+__device__ __forceinline__ void sample_path_any(int F, const SP &P, const PathCfg<R> &pc,
                                                 const R *tab, R *qc, double *zz, const Stream<R> &st,
                                                 R *wout, int wstride, float *qout = nullptr) {
     if (P.wf_on)
@@ -645,10 +642,11 @@ __device__ __forceinline__ void sample_path_any(int F, const SamplerParams &P, c
         sample_path_f<R, RING, false>(F, P, pc, tab, qc, zz, st, wout, wstride, qout);
 }
 
-// batched kernel: no width factor
-template <typename R, int RING>
-__device__ __forceinline__ void sample_path_plain(int F, const SamplerParams &P, const PathCfg<R> &pc,
-                                                  const R *tab, R *qc, const Stream<R> &st, R *wout) {
+// batched kernel: no width factor; the per-item view of the instance's
+// table shape (BatchView, in shared memory) in place of SamplerParams
+template <typename R, int RING, typename SP>
+__device__ __forceinline__ void sample_path_plain(int F, const SP &P, const PathCfg<R> &pc, const R *tab, R *qc,
+                                                  const Stream<R> &st, R *wout) {
     sample_path_f<R, RING, false>(F, P, pc, tab, qc, nullptr, st, wout, 1, nullptr);
 }
 
@@ -671,24 +669,28 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ double lse_exp(double x) { return exp(x); }
 __device__ __forceinline__ double lse_exp(float x) { return (double)__expf(x); }
 
-// running log-sum-exp tuple (M, S = sum e^{w-M}, Q = sum e^{2(w-M)}) of one thread
+// running log-sum-exp tuple (M, S = sum e^{w-M}, Q = sum e^{2(w-M)}) of one
+// thread: add the weight w
+template <typename R>
+__device__ __forceinline__ void lse_push(R &m, double &s, double &q, R w) {
+    if (!(w > (R)-INFINITY)) return;          // zero weight
+    if (w > m) {
+        const double f = lse_exp((R)(m - w)); // 0 for the first weight
+        s = fma(s, f, 1.0);
+        q = fma(q, f * f, 1.0);
+        m = w;
+    } else {
+        const double e = lse_exp((R)(w - m));
+        s += e;
+        q = fma(e, e, q);
+    }
+}
+
 template <typename R>
 struct Lse {
     R m = -INFINITY;
     double s = 0, q = 0;
-    __device__ __forceinline__ void push(R w) {
-        if (!(w > (R)-INFINITY)) return;          // zero weight
-        if (w > m) {
-            const double f = lse_exp((R)(m - w)); // 0 for the first weight
-            s = fma(s, f, 1.0);
-            q = fma(q, f * f, 1.0);
-            m = w;
-        } else {
-            const double e = lse_exp((R)(w - m));
-            s += e;
-            q = fma(e, e, q);
-        }
-    }
+    __device__ __forceinline__ void push(R w) { lse_push(m, s, q, w); }
 };
 
 // merge b into a (same convention), in double
@@ -843,12 +845,16 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
 }
 
 // ---------------------------------------------------- the batched kernel
-// Many instances (a_i, b_i, T_i, s_i) of one model and level p, top level
-// only, in one persistent launch: CTAs take work items (instance, block) from
-// an atomic queue ordered costliest first; each item's samples are reduced
-// per thread and then across the CTA in a fixed order.
-// Shared memory: table[M] (R) | sigma[S_max+1] (R) | qc[(C_max+1)][kThreads] (R) |
-//                Box-Muller node tables (double path)
+// Many instances (a_i, b_i, T_i, s_i, p_i, n_i) of one model in one
+// persistent launch: CTAs take work items (instance, block, chunk) from an
+// atomic queue ordered costliest first; each item's samples are reduced per
+// thread (online log-sum-exp, one tuple per sampled level) and then across
+// the CTA in a fixed order, so the tuples do not depend on which CTA took
+// which item.  An instance samples its top level only, or (hierarchy) every
+// level n = 1..s_i from the same paths.
+// Shared memory: BatchView | tables[L_max * M_max] (R) | sigma[S_max+1] (R) |
+//                qc[(C_max+1)][kThreads] (R) | level states m (R), s, q
+//                (double) [L_max-1][kThreads] | Box-Muller node tables (double path)
 // CTAs per SM for the register budget: the float form fits 96 registers
 // without spills at 5 (the amplitude matrix 3 % faster than at 4).
 template <typename R>
@@ -856,23 +862,42 @@ struct BatchCtas {
     static constexpr int value = sizeof(R) == 8 ? 2 : 5;
 };
 
+// The table shape of the current item's instance (its level p), staged in
+// shared memory; the path code reads it where the single-instance sampler
+// reads SamplerParams.
+struct BatchView {
+    int ncol, M;
+    double alpha, lwf, hcoef;
+    int wf_on;
+    const GeneralDev *general;
+    int len[SU_MAX_P];
+};
+
 template <typename R, int RING>
 __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
-    __shared__ double s_red[kThreads / 32][3];
+    __shared__ double s_red[kThreads / 32][SU_MAX_S][3];
     const SamplerParams &P = B.base;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int Cmax = 1 << (B.S_max > kMaxFine ? B.S_max - kMaxFine : 0);
 
-    R *tab = reinterpret_cast<R *>(smem_raw);
-    size_t off = sizeof(R) * (size_t)P.M;
+    BatchView *view = reinterpret_cast<BatchView *>(smem_raw);
+    size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
+    R *tab = reinterpret_cast<R *>(smem_raw + off);
+    off += sizeof(R) * (size_t)B.tab_max;
     R *sig = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     R *qc = reinterpret_cast<R *>(smem_raw + off) + tid;
-    off += sizeof(R) * (size_t)(Cmax > 1 ? Cmax + 1 : 0) * kThreads;
+    off += sizeof(R) * (size_t)(B.C_max > 1 ? B.C_max + 1 : 0) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    double *ls = reinterpret_cast<double *>(smem_raw + off);          // [L_max-1][kThreads]
+    off += sizeof(double) * (size_t)(B.L_max - 1) * kThreads;
+    double *lq = reinterpret_cast<double *>(smem_raw + off);
+    off += sizeof(double) * (size_t)(B.L_max - 1) * kThreads;
+    R *lm = reinterpret_cast<R *>(smem_raw + off);
+    off += sizeof(R) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
     if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
@@ -880,6 +905,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
+    int cur_shape = -1;
 
     while (true) {
         __syncthreads();   // previous item's shared memory is free
@@ -889,44 +915,89 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
         if (item >= B.n_items) break;
         const int2 it = B.items[item];
         const BatchInstance &in = B.inst[it.x];
-        const R *g = reinterpret_cast<const R *>(P.tables) + (size_t)in.table * P.M;
-        for (int i = tid; i < P.M; i += kThreads) tab[i] = g[i];
+        const int L = in.L;
+        if (in.shape != cur_shape) {             // the same for every thread
+            cur_shape = in.shape;
+            const BatchShape &sh = B.shapes[cur_shape];
+            if (tid == 0) {
+                view->ncol = sh.ncol;
+                view->M = sh.M;
+                view->alpha = P.alpha;
+                view->lwf = 0;
+                view->hcoef = 0;
+                view->wf_on = 0;
+                view->general = nullptr;
+            }
+            for (int j = tid; j < sh.ncol; j += kThreads) view->len[j] = sh.len[j];
+        }
+        {
+            const int n = L * B.shapes[in.shape].M;
+            const R *g = reinterpret_cast<const R *>(P.tables) + in.tab;
+            for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
+        }
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)in.sigma[i];
+        for (int d = 1; d < L; ++d) {
+            lm[(d - 1) * kThreads + tid] = (R)-INFINITY;
+            ls[(d - 1) * kThreads + tid] = 0.0;
+            lq[(d - 1) * kThreads + tid] = 0.0;
+        }
         __syncthreads();
-        const PathCfg<R> pc{(R)in.a, (R)in.b, in.S, 1, sig};
+        const PathCfg<R> pc{(R)in.a, (R)in.b, in.S, L, sig};
         st.inst = P.instance + (uint32_t)it.x;
-        const int64_t lo = (int64_t)it.y * B.n_mc / B.n_blocks;
-        const int64_t hi = ((int64_t)it.y + 1) * B.n_mc / B.n_blocks;
+        const int blk = it.y / in.chunks, chk = it.y - blk * in.chunks;
+        const int64_t blo = (int64_t)blk * in.n_mc / in.n_blocks;
+        const int64_t bhi = ((int64_t)blk + 1) * in.n_mc / in.n_blocks;
+        const int64_t lo = blo + (bhi - blo) * chk / in.chunks;
+        const int64_t hi = blo + (bhi - blo) * (chk + 1) / in.chunks;
         Lse<R> acc;
         bool bad = false;
         for (int64_t smp = lo + tid; smp < hi; smp += kThreads) {
             st.slo = (uint32_t)smp;
             st.shi = (uint32_t)((uint64_t)smp >> 32);
-            R w;
-            sample_path_plain<R, RING>(in.F, P, pc, tab, qc, st, &w);
-            bad |= isnan(w) || (isinf(w) && w > 0);
-            acc.push(w);
+            R w[SU_MAX_S];
+            sample_path_plain<R, RING>(in.F, *view, pc, tab, qc, st, w);
+            bad |= isnan(w[0]) || (isinf(w[0]) && w[0] > 0);
+            acc.push(w[0]);
+            for (int d = 1; d < L; ++d) {
+                bad |= isnan(w[d]) || (isinf(w[d]) && w[d] > 0);
+                const int k = (d - 1) * kThreads + tid;
+                lse_push(lm[k], ls[k], lq[k], w[d]);
+            }
         }
         if (bad) atomicOr(P.flags, 1);
-        // CTA merge in a fixed order: lanes by butterfly, then warps in order
-        double m = (double)acc.m, s = acc.s, q = acc.q;
+        // CTA merge per level in a fixed order: lanes by butterfly, then warps in order
+        for (int d = 0; d < L; ++d) {
+            double m, s, q;
+            if (d == 0) {
+                m = (double)acc.m;
+                s = acc.s;
+                q = acc.q;
+            } else {
+                const int k = (d - 1) * kThreads + tid;
+                m = (double)lm[k];
+                s = ls[k];
+                q = lq[k];
+            }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const double mb = __shfl_xor_sync(0xffffffffu, m, o);
-            const double sb = __shfl_xor_sync(0xffffffffu, s, o);
-            const double qb = __shfl_xor_sync(0xffffffffu, q, o);
-            lse_merge(m, s, q, mb, sb, qb);
-        }
-        if (lane == 0) {
-            s_red[warp][0] = m;
-            s_red[warp][1] = s;
-            s_red[warp][2] = q;
+            for (int o = 16; o; o >>= 1) {
+                const double mb = __shfl_xor_sync(0xffffffffu, m, o);
+                const double sb = __shfl_xor_sync(0xffffffffu, s, o);
+                const double qb = __shfl_xor_sync(0xffffffffu, q, o);
+                lse_merge(m, s, q, mb, sb, qb);
+            }
+            if (lane == 0) {
+                s_red[warp][d][0] = m;
+                s_red[warp][d][1] = s;
+                s_red[warp][d][2] = q;
+            }
         }
         __syncthreads();
-        if (tid == 0) {
-            double M0 = s_red[0][0], S0 = s_red[0][1], Q0 = s_red[0][2];
-            for (int w2 = 1; w2 < kThreads / 32; ++w2) lse_merge(M0, S0, Q0, s_red[w2][0], s_red[w2][1], s_red[w2][2]);
-            double *o = B.tuples + 4 * ((int64_t)it.x * B.n_blocks + it.y);
+        if (tid < L) {
+            const int d = tid;
+            double M0 = s_red[0][d][0], S0 = s_red[0][d][1], Q0 = s_red[0][d][2];
+            for (int w2 = 1; w2 < kThreads / 32; ++w2)
+                lse_merge(M0, S0, Q0, s_red[w2][d][0], s_red[w2][d][1], s_red[w2][d][2]);
+            double *o = B.tuples + 4 * (in.tup + (int64_t)it.y * L + d);
             o[0] = M0;
             o[1] = S0;
             o[2] = Q0;
