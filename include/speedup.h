@@ -321,6 +321,56 @@ int speedup_amplitude_proposal(int model, const double *params, int n_params,
                                const su_proposal *prop, su_level_result *out);
 
 /*
+ * speedup_amplitude_judged -- the learned proposal judged against, and
+ * falling back to, the plain sampler.  Two pilot runs of n_pilot samples
+ * each (the samples after the run's own range: opt->sample0 + n_mc ..),
+ * one per sampler (single precision, top level), give each sampler's device
+ * time per sample and per-sample relative variance n / ESS - 1; from them
+ * the estimated time to the relative statistical error target_rel_err,
+ *   t = (seconds per sample) (n / ESS - 1) / target_rel_err^2.
+ * The main run (n_mc samples, the same as speedup_amplitude or
+ * speedup_amplitude_proposal would draw) uses the proposal only when both
+ * pilots are usable (finite positive estimate, ESS >= 10), they agree
+ * (|z| <= 5 with z = (A_proposal - A_plain) / sqrt(err_proposal^2 +
+ * err_plain^2)), and the proposal's estimated time is the shorter; otherwise
+ * the plain sampler, with the reason in judge->reason.  An unbiased but
+ * unconfirmed proposal estimate (where the plain pilot diverges) is therefore
+ * never returned silently: it stays in judge->pilot_amp[1].  No counterpart
+ * in the paper.  Arguments as speedup_amplitude_proposal (s >= 1), and:
+ *   n_pilot         : samples per pilot, >= 2 (enough to fill the GPU, e.g. 2e5).
+ *   target_rel_err  : the relative error the times are estimated for, > 0.
+ *   out             : host, s + 1 entries, as speedup_amplitude.
+ *   judge           : host, the figures the choice was made on.
+ * Synchronous.
+ */
+#define SU_JUDGE_PLAIN_FASTER       0  /* both usable and agreeing; plain is faster    */
+#define SU_JUDGE_PROPOSAL_FASTER    1  /* both usable and agreeing; proposal is faster */
+#define SU_JUDGE_PROPOSAL_UNUSABLE  2  /* the proposal's pilot is not usable: plain    */
+#define SU_JUDGE_PLAIN_UNUSABLE     3  /* the plain pilot is not usable, so the proposal
+                                          cannot be confirmed: plain                    */
+#define SU_JUDGE_DISAGREE           4  /* the pilots disagree (|z| > 5): plain          */
+
+typedef struct {
+    int chosen;              /* 0 = plain sampler, 1 = learned proposal          */
+    int reason;              /* SU_JUDGE_*                                       */
+    double target_rel_err;
+    double pilot_amp[2];     /* [0] plain, [1] proposal: top-level estimates     */
+    double pilot_err[2];
+    double pilot_ess[2];
+    double pilot_relvar[2];  /* n / ESS - 1 (infinite when unusable)             */
+    double pilot_s[2];       /* device seconds of each pilot                     */
+    double t_target[2];      /* estimated seconds to target_rel_err (inf: unusable) */
+    double z;                /* pilot agreement (NaN unless both usable)         */
+    double run_s;            /* device seconds of the main run                   */
+} su_judge;
+
+int speedup_amplitude_judged(int model, const double *params, int n_params,
+                             double a, double b, double T, int p, int s,
+                             int64_t n_mc, uint64_t seed, const su_options *opt,
+                             const su_proposal *prop, int64_t n_pilot, double target_rel_err,
+                             su_level_result *out, su_judge *judge);
+
+/*
  * speedup_proposal_logweights -- per-sample log-weights of the proposal path
  * (W_p sum plus the proposal's log density ratio), laid out as
  * speedup_logweights; d_outs (device, may be NULL) receives the network's

@@ -32,7 +32,10 @@ EXPORTS = [
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
     "su_fit_continuum", "speedup_wp", "speedup_wp_nd", "su_batch_plan_shape", "su_batch_autotune",
+    "speedup_amplitude_judged",
 ]
+JUDGE_REASONS = {0: "plain faster", 1: "proposal faster", 2: "proposal unusable", 3: "plain unusable",
+                 4: "pilots disagree"}
 MAX_D = 4
 MLP_PARAMS = 34178
 
@@ -74,6 +77,23 @@ class BatchTuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Judge(ctypes.Structure):
+    _fields_ = [("chosen", ctypes.c_int), ("reason", ctypes.c_int), ("target_rel_err", ctypes.c_double),
+                ("pilot_amp", ctypes.c_double * 2), ("pilot_err", ctypes.c_double * 2),
+                ("pilot_ess", ctypes.c_double * 2), ("pilot_relvar", ctypes.c_double * 2),
+                ("pilot_s", ctypes.c_double * 2), ("t_target", ctypes.c_double * 2), ("z", ctypes.c_double),
+                ("run_s", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        d["chosen"] = "proposal" if self.chosen else "plain"
+        d["reason"] = JUDGE_REASONS.get(self.reason, str(self.reason))
+        return d
 
 
 class LevelResult(ctypes.Structure):
@@ -150,6 +170,8 @@ def load(build_if_missing=True):
     L.su_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
     L.speedup_amplitude_proposal.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
                                              vp, ctypes.POINTER(LevelResult)]
+    L.speedup_amplitude_judged.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
+                                           vp, i64, d, ctypes.POINTER(LevelResult), ctypes.POINTER(Judge)]
     L.speedup_proposal_logweights.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, i64, u64,
                                               ctypes.POINTER(Options), vp, vp, vp]
     L.speedup_amplitude_noalloc.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64,
@@ -593,6 +615,21 @@ def speedup_amplitude_proposal(model, params, a, b, T, p, s, n_mc, seed, proposa
     _check(load().speedup_amplitude_proposal(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
                                              ctypes.byref(o), proposal._h, out))
     return [out[n].as_dict(n) for n in range(s + 1)]
+
+
+def speedup_amplitude_judged(model, params, a, b, T, p, s, n_mc, seed, proposal, n_pilot=200_000,
+                             target_rel_err=1e-4, **kw):
+    """The proposal judged against the plain sampler on two pilots and used
+    only where confirmed and faster; returns (levels, judge dict)."""
+    pr, npar = _params(params)
+    out = (LevelResult * (s + 1))()
+    j = Judge()
+    kw.setdefault("precision", "fp32")
+    o = options(**kw)
+    _check(load().speedup_amplitude_judged(_model(model), pr, npar, a, b, T, p, s, int(n_mc), int(seed),
+                                           ctypes.byref(o), proposal._h, int(n_pilot), float(target_rel_err), out,
+                                           ctypes.byref(j)))
+    return [out[n].as_dict(n) for n in range(s + 1)], j.as_dict()
 
 
 def speedup_proposal_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, proposal, out,

@@ -857,7 +857,8 @@ int su_plan_finalize(const su_plan *pl, const double *h_tuples, const void *d_sc
 
 // Sample a plan once and finalize: scratch on the plan's stream, tuples and
 // the flag word back to the host, the plan destroyed by the caller.
-static int amplitude_of_plan(su_plan *pl, su_level_result *out) {
+static int amplitude_of_plan(su_plan *pl, su_level_result *out, float *ms = nullptr) {
+    if (ms) *ms = 0;
     if (pl->s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
     cudaStream_t st = (cudaStream_t)pl->opt.stream;
     void *dbuf = nullptr;
@@ -866,7 +867,7 @@ static int amplitude_of_plan(su_plan *pl, su_level_result *out) {
     std::vector<double> h((size_t)(tb / sizeof(double)) + 32);
     void *d_tup = dbuf;
     void *d_scr = static_cast<char *>(dbuf) + tb;
-    int rc = su_plan_execute(pl, d_tup, d_scr, st, nullptr);
+    int rc = ms ? su_plan_execute_timed(pl, d_tup, d_scr, st, nullptr, ms) : su_plan_execute(pl, d_tup, d_scr, st, nullptr);
     cudaError_t e = cudaSuccess;
     if (rc == SU_OK) {
         e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
@@ -1963,6 +1964,58 @@ static int proposal_check(const su_options &o, int s, const su_proposal *pr) {
     return SU_OK;
 }
 
+// Sample plan pl's paths from the proposal and finalize (out: s+1 levels);
+// *ms (may be NULL) = device time of the sampling launches (CUDA events).
+static int proposal_amplitude_of_plan(su_plan *pl, const su_proposal *pr, su_level_result *out, float *ms) {
+    if (ms) *ms = 0;
+    if (pl->s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
+    su::ProposalParams Q;
+    std::memset(&Q, 0, sizeof Q);
+    int grid = 0;
+    size_t smem = 0;
+    int rc = proposal_setup(pl, pr, Q, grid, smem);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)pl->opt.stream;
+    const int64_t part_bytes = up256(Q.base.n_items * pl->levels * 4 * (int64_t)sizeof(double));
+    const int64_t tb = pl->tuple_bytes;
+    struct Ev {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Ev() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    if (ms) {
+        CU(cudaEventCreate(&ev.e[0]), "event");
+        CU(cudaEventCreate(&ev.e[1]), "event");
+    }
+    void *dbuf = nullptr;
+    CU(dmalloc_async(&dbuf, (size_t)(part_bytes + tb + 256), st), "cudaMallocAsync");
+    Q.base.partial = static_cast<double *>(dbuf);
+    double *d_tup = reinterpret_cast<double *>(static_cast<char *>(dbuf) + part_bytes);
+    Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(dbuf) + part_bytes + tb);
+    Q.withhold = g_fault_mma.exchange(0);
+    Q.base.w_out = nullptr;
+    Q.outs = nullptr;
+    std::vector<double> h((size_t)(tb / sizeof(double)));
+    int flags = 0;
+    cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
+    if (e == cudaSuccess && ms) e = cudaEventRecord(ev.e[0], st);
+    if (e == cudaSuccess) e = su::launch_proposal(Q, grid, smem, st);
+    if (e == cudaSuccess)
+        e = su::launch_combine(Q.base.partial, d_tup, 0, pl->n_blocks, pl->levels, Q.base.items_per_block, st);
+    if (e == cudaSuccess && ms) e = cudaEventRecord(ev.e[1], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ms) e = cudaEventElapsedTime(ms, ev.e[0], ev.e[1]);
+    cudaFreeAsync(dbuf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal sampling");
+    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
+    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
+    return su_plan_finalize(pl, h.data(), nullptr, out);
+}
+
 extern "C" int speedup_amplitude_proposal(int model, const double *params, int n_params, double a, double b,
                                           double T, int p, int s, int64_t n_mc, uint64_t seed,
                                           const su_options *opt, const su_proposal *pr, su_level_result *out) {
@@ -1976,38 +2029,83 @@ extern "C" int speedup_amplitude_proposal(int model, const double *params, int n
     rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, &o, &pl);
     if (rc) return rc;
     std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
-    if (s == 0) return su_plan_finalize(pl, nullptr, nullptr, out);
-    su::ProposalParams Q;
-    std::memset(&Q, 0, sizeof Q);
-    int grid = 0;
-    size_t smem = 0;
-    rc = proposal_setup(pl, pr, Q, grid, smem);
+    return proposal_amplitude_of_plan(pl, pr, out, nullptr);
+}
+
+// The judge's view of one pilot run: usable when its top-level estimate is
+// finite and positive and rests on at least kJudgeMinEss effective samples.
+static constexpr double kJudgeMinEss = 10.0;
+
+static void judge_arm(const su_level_result &r, int64_t n, float ms, double target, int arm, su_judge *j) {
+    j->pilot_amp[arm] = r.amp;
+    j->pilot_err[arm] = r.err;
+    j->pilot_ess[arm] = r.ess;
+    j->pilot_s[arm] = ms / 1e3;
+    const bool ok = std::isfinite(r.amp) && r.amp > 0 && std::isfinite(r.err) && r.ess >= kJudgeMinEss;
+    // per-sample relative variance Var(f) / E[f]^2 = n / ESS - 1 (the pilot's own sums)
+    j->pilot_relvar[arm] = ok ? std::max((double)n / r.ess - 1.0, 0.0) : INFINITY;
+    j->t_target[arm] = ok ? (ms / 1e3) / (double)n * j->pilot_relvar[arm] / (target * target) : INFINITY;
+}
+
+extern "C" int speedup_amplitude_judged(int model, const double *params, int n_params, double a, double b,
+                                        double T, int p, int s, int64_t n_mc, uint64_t seed,
+                                        const su_options *opt, const su_proposal *pr, int64_t n_pilot,
+                                        double target_rel_err, su_level_result *out, su_judge *judge) {
+    if (!out || !judge) return fail(SU_EINVAL, "output or judge missing");
+    su_options o;
+    su_options_default(&o);
+    if (opt) o = *opt;
+    int rc = proposal_check(o, s, pr);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)o.stream;
-    const int64_t part_bytes = up256(Q.base.n_items * pl->levels * 4 * (int64_t)sizeof(double));
-    const int64_t tb = pl->tuple_bytes;
-    void *dbuf = nullptr;
-    CU(dmalloc_async(&dbuf, (size_t)(part_bytes + tb + 256), st), "cudaMallocAsync");
-    Q.base.partial = static_cast<double *>(dbuf);
-    double *d_tup = reinterpret_cast<double *>(static_cast<char *>(dbuf) + part_bytes);
-    Q.base.flags = reinterpret_cast<int *>(static_cast<char *>(dbuf) + part_bytes + tb);
-    Q.withhold = g_fault_mma.exchange(0);
-    Q.base.w_out = nullptr;
-    Q.outs = nullptr;
-    std::vector<double> h((size_t)(tb / sizeof(double)));
-    int flags = 0;
-    cudaError_t e = cudaMemsetAsync(Q.base.flags, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = su::launch_proposal(Q, grid, smem, st);
-    if (e == cudaSuccess)
-        e = su::launch_combine(Q.base.partial, d_tup, 0, pl->n_blocks, pl->levels, Q.base.items_per_block, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tup, (size_t)tb, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, Q.base.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFreeAsync(dbuf, st);
-    if (e != cudaSuccess) return cuda_fail(e, "proposal sampling");
-    if (flags & 4) return fail(SU_ETIMEOUT, "a tensor-core MMA of the proposal network did not complete");
-    if (flags & 1) return fail(SU_ENONFINITE, "a per-sample weight was NaN or +Inf");
-    return su_plan_finalize(pl, h.data(), nullptr, out);
+    if (s < 1) return fail(SU_EINVAL, "the judge compares sampled levels: s must be >= 1");
+    if (n_pilot < 2 || !(target_rel_err > 0) || !std::isfinite(target_rel_err))
+        return fail(SU_EINVAL, "n_pilot must be >= 2 and target_rel_err finite and > 0");
+    std::memset(judge, 0, sizeof *judge);
+    judge->target_rel_err = target_rel_err;
+    // pilots on the samples after the run's own range, so the main run is
+    // the one speedup_amplitude (or _proposal) would make
+    su_options op = o;
+    op.sample0 = o.sample0 + n_mc;
+    op.hierarchy = 0;
+    std::vector<su_level_result> pil((size_t)s + 1);
+    for (int arm = 0; arm < 2; ++arm) {
+        su_plan *pl = nullptr;
+        rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_pilot, seed, &op, &pl);
+        if (rc) return rc;
+        std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+        float ms = 0;
+        rc = arm == 0 ? amplitude_of_plan(pl, pil.data(), &ms) : proposal_amplitude_of_plan(pl, pr, pil.data(), &ms);
+        if (rc == SU_ENONFINITE) {   // a non-finite weight: this arm cannot estimate the amplitude
+            su_level_result bad{};
+            bad.amp = NAN;
+            bad.err = NAN;
+            judge_arm(bad, n_pilot, ms, target_rel_err, arm, judge);
+            continue;
+        }
+        if (rc) return rc;
+        judge_arm(pil[(size_t)s], n_pilot, ms, target_rel_err, arm, judge);
+    }
+    const bool ok0 = std::isfinite(judge->t_target[0]), ok1 = std::isfinite(judge->t_target[1]);
+    const double sig = std::hypot(judge->pilot_err[0], judge->pilot_err[1]);
+    judge->z = (ok0 && ok1 && sig > 0) ? (judge->pilot_amp[1] - judge->pilot_amp[0]) / sig : NAN;
+    // the proposal is taken only where the plain sampler confirms it and it is faster
+    if (!ok1)
+        judge->reason = SU_JUDGE_PROPOSAL_UNUSABLE;
+    else if (!ok0)
+        judge->reason = SU_JUDGE_PLAIN_UNUSABLE;
+    else if (!(std::fabs(judge->z) <= 5.0))
+        judge->reason = SU_JUDGE_DISAGREE;
+    else
+        judge->reason = judge->t_target[1] < judge->t_target[0] ? SU_JUDGE_PROPOSAL_FASTER : SU_JUDGE_PLAIN_FASTER;
+    judge->chosen = judge->reason == SU_JUDGE_PROPOSAL_FASTER ? 1 : 0;
+    su_plan *pl = nullptr;
+    rc = su_plan_create(model, params, n_params, a, b, T, p, s, n_mc, seed, &o, &pl);
+    if (rc) return rc;
+    std::unique_ptr<su_plan, int (*)(su_plan *)> guard(pl, su_plan_destroy);
+    float ms = 0;
+    rc = judge->chosen ? proposal_amplitude_of_plan(pl, pr, out, &ms) : amplitude_of_plan(pl, out, &ms);
+    judge->run_s = ms / 1e3;
+    return rc;
 }
 
 extern "C" int speedup_proposal_logweights(int model, const double *params, int n_params, double a, double b,

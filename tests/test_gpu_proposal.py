@@ -179,20 +179,59 @@ def test_trained_proposal_is_unbiased_and_better():
     assert r[6]["ess"] > plain[6]["ess"]
 
 
-def test_learned_proposal_recovers_the_continuum_double_well_amplitude():
-    """Double well h = 5 at T = 5 (p = 12, N = 64): the bridge's estimate is
-    ruled by rare paths on which the truncated W_p is hugely negative, while
-    the trained proposal never visits them and gives the continuum amplitude
-    of the sinc-DVR diagonalisation (the discretization error at p = 12 is far
-    below the statistical one)."""
-    th0 = pr.init(8).astype(np.float32)
-    th, losses = su.speedup_train_proposal("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1234, th0, n_train=1_000_000,
-                                           steps=2000, batch_paths=512, lr=1e-3)
+def test_judge_takes_a_trained_proposal_where_it_is_faster():
+    """A harmonic oscillator whose bridge is poor (omega = 4, T = 4: the
+    plain per-sample relative variance is about 28): the trained proposal,
+    judged on two pilots, is confirmed by the plain sampler, estimated faster
+    to a relative error of 1e-4 by more than 3x, and used for the main run,
+    which equals speedup_amplitude_proposal on the same samples and the exact
+    discretized amplitude."""
+    args = ("ho", [4.0], 0.0, 0.5, 4.0, 4, 6)
+    th0 = pr.init(9).astype(np.float32)
+    th, losses = su.speedup_train_proposal(*args, 2024, th0, n_train=1_000_000, steps=2000, batch_paths=512,
+                                           lr=1e-3)
     assert np.isfinite(losses).all()
     P = su.Proposal(th)
-    r = su.speedup_amplitude_proposal("dw", [5.0], -1.0, 1.0, 5.0, 12, 6, 1_000_000, 99, P, n_blocks=50)
-    ref, _ = exact.dvr_amplitude(lambda x: 5.0 * (x * x - 1) ** 2, -1.0, 1.0, 5.0, L=8.0, dx=0.02)
-    top = r[6]
-    sig = max(top["err"], top["err_naive"])
-    assert top["ess"] > 1e4 and sig < 0.02 * ref
-    assert abs(top["amp"] - ref) <= 4 * sig, (top["amp"], ref, sig)
+    res, j = su.speedup_amplitude_judged(*args, 1_000_000, 31, P, n_pilot=200_000, target_rel_err=1e-4,
+                                         n_blocks=50)
+    assert j["chosen"] == "proposal" and j["reason"] == "proposal faster", j
+    assert j["t_target"][0] > 3 * j["t_target"][1], j
+    assert abs(j["z"]) <= 5
+    ref = exact.ho_discretized(4, 64, 0.0, 0.5, 4.0, omega=4.0)
+    top = res[6]
+    assert abs(top["amp"] - ref) <= 4 * max(top["err"], top["err_naive"]), (top["amp"], ref)
+    same = su.speedup_amplitude_proposal(*args, 1_000_000, 31, P, n_blocks=50)
+    assert [r["amp"] for r in res] == [r["amp"] for r in same]
+
+
+def test_judge_keeps_the_plain_sampler_where_the_bridge_is_good():
+    """Where the bridge is already a good proposal (omega = 1, T = 1) the
+    network, which costs far more per path, loses: the main run is the plain
+    single-precision sampler's, sample for sample."""
+    args = ("ho", [1.0], 0.0, 0.5, 1.0, 4, 6)
+    P = su.Proposal(pr.init(10).astype(np.float32))   # zero output layer: the bridge itself
+    res, j = su.speedup_amplitude_judged(*args, 300_000, 5, P, n_pilot=200_000, target_rel_err=1e-4, n_blocks=30)
+    assert j["chosen"] == "plain" and j["reason"] == "plain faster", j
+    assert j["pilot_relvar"][0] == pytest.approx(j["pilot_relvar"][1], rel=0.3)
+    plain = su.speedup_amplitude(*args, 300_000, 5, precision="fp32", n_blocks=30)
+    assert [r["amp"] for r in res] == [r["amp"] for r in plain]
+
+
+def test_judge_refuses_an_unconfirmed_proposal():
+    """Double well h = 5 at T = 5 (p = 12, N = 64): the truncated W_12 is
+    unbounded below and the plain estimate is ruled by single far-out paths;
+    on this stream's pilot range (samples 1e6 .. 2e6 of seed 31) one of them
+    makes the plain estimate overflow.  A proposal trained on the plain paths
+    gives a finite number, but nothing confirms it: the judge falls back to
+    the plain sampler and says why, leaving the proposal's pilot value in the
+    record."""
+    args = ("dw", [5.0], -1.0, 1.0, 5.0, 12, 6)
+    th0 = pr.init(9).astype(np.float32)
+    th, _ = su.speedup_train_proposal(*args, 1234, th0, n_train=1_000_000, steps=2000, batch_paths=512, lr=1e-3)
+    P = su.Proposal(th)
+    res, j = su.speedup_amplitude_judged(*args, 1_000_000, 31, P, n_pilot=1_000_000, target_rel_err=1e-4,
+                                         n_blocks=50)
+    assert j["chosen"] == "plain" and j["reason"] == "plain unusable", j
+    assert not math.isfinite(j["t_target"][0]) and math.isfinite(j["pilot_amp"][1])
+    plain = su.speedup_amplitude(*args, 1_000_000, 31, precision="fp32", n_blocks=50)
+    assert res[6]["log_amp"] == plain[6]["log_amp"]

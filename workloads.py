@@ -89,3 +89,9 @@ def config4(n_mc=100_000_000):
 # 5: the learned-proposal instance: double well h = 5, T = 5, p = 12, N = 64;
 # n_mc = 1e7 is the number of plain paths the proposal is trained on.
 CONFIG5 = Instance("dw", (5.0,), -1.0, 1.0, 5.0, 12, 6, 10_000_000, 1234, 64)
+
+# The learned proposal where the bridge is a poor proposal but the truncated
+# action is bounded below: the harmonic oscillator omega = 4 at T = 4
+# (a = 0, b = 0.5, p = 4, N = 64); the bridge's per-sample relative variance
+# is about 28.  n_mc = 1e7 plain paths to train on.
+PROPOSAL_GAIN = Instance("ho", (4.0,), 0.0, 0.5, 4.0, 4, 6, 10_000_000, 2024, 50)
