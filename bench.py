@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-nd", action="store_true", help="skip the several-coordinates entry")
     ap.add_argument("--no-fig2", action="store_true", help="skip the Fig. 2 convergence and continuum-fit entry")
     ap.add_argument("--profile", choices=["fp64", "fp32", "batch", "proposal", "nd", "nd32", "general", "evolution",
-                                          "train"],
+                                          "spectrum", "train"],
                     default=None,
                     help="profiling case, one warm-up and one profiled launch, no JSON line: fp64/fp32 = "
                          "a plan of level --profile-p of the sweep (s = 10, --profile-n samples); batch = "
@@ -73,6 +73,7 @@ def parse():
                          "instance with a fixed random network (--profile-n samples); nd = the 2D anharmonic "
                          "oscillator, p = 10, s = 10 (nd32: in single precision); general = AHO g = 10 through the general-potential mode, "
                          "p = 10, s = 10 (--profile-n samples); evolution = the Fig. 3 AHO matrix (n = 16385); "
+                         "spectrum = the band eigensolver on it (ten energies); "
                          "train = 20 training steps of the learned proposal on --profile-n plain paths")
     ap.add_argument("--profile-p", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=200_000)
@@ -530,12 +531,14 @@ def run_small_configs(su, torch, dev, stream, flush):
 
 
 def run_evolution(su, torch, dev, stream, flush):
-    """The evolution-operator spectra of Fig. 3 (Sec. 5): the matrix
-    U_ij = Delta A_1^(21)(x_i, x_j; t) on the figure's grid (anharmonic A = 1,
-    g = 48, t = 0.02, L = 8, Delta = 9.77e-4; double well A = -10, g = 12,
-    t = 0.1, L = 10, Delta = 1.22e-3) built on the device (CUDA events), and
-    the lowest ten energies -ln(lambda)/t from torch's symmetric eigensolver
-    on a 4097-point grid of the same L."""
+    """The evolution-operator spectra of Fig. 3 (Sec. 5) on the figure's grids
+    (anharmonic A = 1, g = 48, t = 0.02, L = 8; double well A = -10, g = 12,
+    t = 0.1, L = 10; n = 16385, p = 21): the band of U_ij = Delta
+    A_1^(21)(x_i, x_j; t) built on the device and the lowest ten energies
+    -ln(lambda)/t from the band eigensolver (Chebyshev-filtered subspace
+    iteration in double precision; CUDA events around the band and around
+    every band matrix-block product), after one warm-up solve; the dense
+    n x n build is timed beside it for comparison."""
     out = []
     for name, params, t, L, n in (("aho A=1 g=48", [1.0, 48.0], 0.02, 8.0, 16385),
                                   ("double well A=-10 g=12", [-10.0, 12.0], 0.1, 10.0, 16385)):
@@ -547,25 +550,29 @@ def run_evolution(su, torch, dev, stream, flush):
         su.speedup_evolution_matrix("aho", params, 21, t, L, n, U, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        band = int((U > 0).sum().item())
+        dense_ms = e0.elapsed_time(e1)
         del U
-        m = 4097
-        Us = torch.empty((m, m), dtype=torch.float64, device=dev)
-        su.speedup_evolution_matrix("aho", params, 21, t, L, m, Us, stream=stream)
+        su.speedup_evolution_spectrum("aho", params, 21, t, L, n, 10, stream=stream)
+        flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lam = torch.linalg.eigvalsh(Us)
-        torch.cuda.synchronize()
-        eig_s = time.perf_counter() - t0
-        lam = lam.flip(0)[:10].cpu().numpy()
-        del Us
+        E, R, info = su.speedup_evolution_spectrum("aho", params, 21, t, L, n, 10, stream=stream)
+        wall = time.perf_counter() - t0
+        w = info["half_width"]
+        fma_block = info["block"] * (n * (2 * w + 1) - w * (w + 1))
+        per = info["block_matvec_ms"] / max(info["block_matvecs"], 1)
         out.append({"potential": name, "p": 21, "t": t, "L": L, "n": n, "delta": 2 * L / (n - 1),
-                    "matrix_ms": ms, "elements_per_s": n * n / (ms / 1e3), "band_elements": band,
-                    "spectrum_grid": m, "eigvalsh_s": eig_s,
-                    "energies": [float(-math.log(v) / t) for v in lam]})
-    return {"cases": out, "note": "matrix: device time of one speedup_evolution_matrix; energies from torch's "
-                                  "eigensolver (cuSOLVER) on the 4097-point grid"}
+                    "dense_matrix_ms": dense_ms, "dense_bytes": n * n * 8,
+                    "band_ms": info["band_ms"], "band_bytes": info["band_bytes"], "half_width": w,
+                    "solve_ms": info["solve_ms"], "wall_s": wall, "iterations": info["iterations"],
+                    "block": info["block"], "block_matvecs": info["block_matvecs"],
+                    "block_matvec_ms": per, "block_matvec_fp64_tflops": 2 * fma_block / (per / 1e3) / 1e12,
+                    "block_matvec_frac_of_fp64_peak": 2 * fma_block / (per / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                    "max_residual": max(R), "converged": info["converged"], "energies": E})
+    return {"cases": out,
+            "note": "band: device time of speedup_evolution_band (upper band, diagonal-major); solve: the band "
+                    "eigensolver (no library eigensolver); block_matvec: one band matrix-block product (B columns, "
+                    "FP64 multiply-add bound: B (n (2w+1) - w (w+1)) multiply-adds)"}
 
 
 def run_general(su, torch, dev, stream, flush):
@@ -868,6 +875,12 @@ def run_profile(args):
             su.speedup_evolution_matrix("aho", [1.0, 48.0], 21, 0.02, 8.0, n, U)
         torch.cuda.synchronize()
         print(f"profile case evolution: n = {n}, U[n/2, n/2] = {float(U[n // 2, n // 2]):.10g}")
+        return
+    if args.profile == "spectrum":
+        n = 16385
+        for _ in range(2):
+            E, R, info = su.speedup_evolution_spectrum("aho", [1.0, 48.0], 21, 0.02, 8.0, n, 10)
+        print(f"profile case spectrum: n = {n}, E_0 = {E[0]:.12g}, {info['block_matvecs']} block products")
         return
     if args.profile == "train":
         x = workloads.CONFIG5

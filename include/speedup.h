@@ -577,6 +577,67 @@ int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_
 int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
                              int precision, double *d_U, void *stream);
 
+/*
+ * su_evolution_band_size -- the geometry of the band storage below: the
+ * half width w (U_ij = 0 for |i - j| > w: the band of reading "free factor
+ * below e^-40") and the row pitch (n rounded up to 32).  Host only.
+ */
+int su_evolution_band_size(double t, double L, int n, int *half_width, int64_t *pitch);
+
+/*
+ * speedup_evolution_band -- the upper band of the evolution operator of
+ * speedup_evolution_matrix (Sec. 5, Fig. 3), diagonal-major:
+ *   d_band[k * pitch + i] = U_{i,i+k},  k = 0..w,  i = 0..n-1
+ * (zero where i + k >= n and outside the band; U is symmetric, so this is
+ * all of it).  About (w + 1) n doubles instead of n^2: 170 MB instead of
+ * 2.1 GB on the 16 385-point grid of Fig. 3.
+ *   d_band   : device, capacity bytes >= (w + 1) * pitch * 8.
+ * Arguments otherwise as speedup_evolution_matrix; returns after the band is
+ * written.
+ */
+int speedup_evolution_band(int model, const double *params, int n_params, int p, double t, double L, int n,
+                           int precision, double *d_band, int64_t capacity, void *stream);
+
+/* What speedup_evolution_spectrum did. */
+typedef struct {
+    int half_width;       /* w of the band                                      */
+    int block;            /* columns of the subspace block (8, 16 or 32)        */
+    int iterations;       /* filter and Rayleigh-Ritz rounds after the first    */
+    int converged;        /* 1: every residual within 1e-11 theta_0             */
+    int64_t band_bytes;   /* device bytes of the band                           */
+    int64_t matvecs;      /* products of U with one vector (a block counts B)   */
+    double lower, upper;  /* spectrum bounds of U from 40 Lanczos steps         */
+    double band_ms;       /* device time: the band                              */
+    double solve_ms;      /* device and host time of the eigensolver            */
+    int block_matvecs;    /* band matrix-block products U X                     */
+    double block_matvec_ms; /* their device time (CUDA events)                  */
+} su_spectrum_info;
+
+/*
+ * speedup_evolution_spectrum -- the lowest nev energies E_k = -ln(lambda_k)/t
+ * (ascending) of the evolution operator (Sec. 5, Fig. 3) from the nev largest
+ * eigenvalues lambda_k of the band matrix: Chebyshev-filtered block subspace
+ * iteration with Rayleigh-Ritz in double precision on the device (band
+ * matrix-block products, Gram products and rotations in this library's
+ * kernels; B x B Cholesky and Jacobi on the host), no dense matrix and no
+ * library eigensolver.
+ *   nev        : 1..26 (and <= n/2).
+ *   energies   : host, nev doubles.
+ *   residuals  : host, nev doubles or NULL: |U x_k - lambda_k x_k| of the
+ *                unit Ritz vectors (the eigenvalue error is at most about
+ *                residual^2 / gap).
+ *   d_vectors  : device, n * nev doubles or NULL: eigenfunction k on the grid,
+ *                psi_k(x_i) = d_vectors[k * n + i] (unit L2 norm in x; sign
+ *                arbitrary).
+ *   info       : host or NULL.
+ * Synchronous; allocates the band and the work buffers itself.  Errors as
+ * speedup_evolution_band, SU_EINVAL for nev, SU_ENOTSUP if the residuals do
+ * not reach 1e-11 lambda_0 within 60 rounds (energies and info still written).
+ */
+int speedup_evolution_spectrum(int model, const double *params, int n_params, int p, double t, double L, int n,
+                               int precision, int nev, double *energies, double *residuals, double *d_vectors,
+                               su_spectrum_info *info, void *stream);
+
 /* ---- fault injection (test support) ---------------------------------------- */
 
 /* No counterpart in the paper: host-side hooks for the failure-detection tests.

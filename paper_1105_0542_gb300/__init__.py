@@ -9,7 +9,7 @@ from ._binding import (  # noqa: F401
     BatchPlan, EXPORTS, GENERAL_MAX_P, MAX_D, MLP_PARAMS, MODELS, PRECISIONS, Plan, PlanND, Proposal, SpeedupError, library_path, load,
     general_params, options, speedup_amplitude, speedup_amplitude_batch, speedup_amplitude_nd, speedup_amplitude_noalloc,
     speedup_amplitude_proposal, speedup_amplitude_judged,
-    speedup_evolution_matrix, speedup_generate_coeffs, speedup_generate_nd, speedup_logweights,
+    speedup_evolution_matrix, speedup_evolution_band, speedup_evolution_spectrum, su_evolution_band_size, speedup_generate_coeffs, speedup_generate_nd, speedup_logweights,
     speedup_logweights_nd, speedup_normals, speedup_philox_words,
     speedup_proposal_logweights, speedup_train_proposal, speedup_wp, speedup_wp_nd, su_autotune, su_autotune_clear, su_batch_autotune,
     su_fault_inject, su_fit_continuum,

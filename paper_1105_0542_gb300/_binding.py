@@ -32,7 +32,7 @@ EXPORTS = [
     "speedup_evolution_matrix", "su_fault_inject", "su_plan_execute_timed", "su_plan_execute_range",
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
     "su_fit_continuum", "speedup_wp", "speedup_wp_nd", "su_batch_plan_shape", "su_batch_autotune",
-    "speedup_amplitude_judged",
+    "speedup_amplitude_judged", "su_evolution_band_size", "speedup_evolution_band", "speedup_evolution_spectrum",
 ]
 JUDGE_REASONS = {0: "plain faster", 1: "proposal faster", 2: "proposal unusable", 3: "plain unusable",
                  4: "pilots disagree"}
@@ -96,6 +96,16 @@ class Judge(ctypes.Structure):
         return d
 
 
+class SpectrumInfo(ctypes.Structure):
+    _fields_ = [("half_width", ctypes.c_int), ("block", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("converged", ctypes.c_int), ("band_bytes", ctypes.c_int64), ("matvecs", ctypes.c_int64),
+                ("lower", ctypes.c_double), ("upper", ctypes.c_double), ("band_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("block_matvecs", ctypes.c_int), ("block_matvec_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LevelResult(ctypes.Structure):
     _fields_ = [("amp", ctypes.c_double), ("log_amp", ctypes.c_double), ("err", ctypes.c_double),
                 ("rel_err", ctypes.c_double), ("err_naive", ctypes.c_double), ("ess", ctypes.c_double),
@@ -147,6 +157,10 @@ def load(build_if_missing=True):
                               ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
     L.su_autotune_clear.argtypes = []
     L.speedup_evolution_matrix.argtypes = [i32, pd, i32, i32, d, d, i32, i32, vp, vp]
+    L.su_evolution_band_size.argtypes = [d, d, i32, pi, ctypes.POINTER(i64)]
+    L.speedup_evolution_band.argtypes = [i32, pd, i32, i32, d, d, i32, i32, vp, i64, vp]
+    L.speedup_evolution_spectrum.argtypes = [i32, pd, i32, i32, d, d, i32, i32, i32, pd, pd, vp,
+                                             ctypes.POINTER(SpectrumInfo), vp]
     L.su_fault_inject.argtypes = [i32, i64]
     L.su_plan_execute_timed.argtypes = [vp, vp, vp, vp, pi, ctypes.POINTER(ctypes.c_float)]
     L.su_plan_execute_range.argtypes = [vp, i64, i64, vp, vp, vp, pi]
@@ -298,6 +312,37 @@ def speedup_evolution_matrix(model, params, p, t, L, n, out, precision="fp64", s
 
 
 FAULTS = {"clear": 0, "alloc": 1, "table_nan": 2, "queue_stop": 3, "withhold_mma": 4}
+
+
+def su_evolution_band_size(t, L, n):
+    """(half width w, row pitch) of the evolution operator's band storage."""
+    w, pitch = ctypes.c_int(0), ctypes.c_int64(0)
+    _check(load().su_evolution_band_size(float(t), float(L), int(n), ctypes.byref(w), ctypes.byref(pitch)))
+    return w.value, pitch.value
+
+
+def speedup_evolution_band(model, params, p, t, L, n, out, precision="fp64", stream=None):
+    """Upper band of U, diagonal-major, into out (a CUDA tensor of at least
+    (w + 1) * pitch doubles): out[k * pitch + i] = U[i, i + k]."""
+    pr, npar = _params(params)
+    cap = out.numel() * out.element_size() if hasattr(out, "numel") else 1 << 62
+    _check(load().speedup_evolution_band(_model(model), pr, npar, p, float(t), float(L), int(n),
+                                         PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                                         _ptr(out), int(cap), _stream(stream)))
+
+
+def speedup_evolution_spectrum(model, params, p, t, L, n, nev, vectors=None, precision="fp64", stream=None):
+    """The nev lowest energies of the evolution operator (band eigensolver);
+    returns (energies, residuals, info dict); vectors: optional CUDA tensor of
+    nev * n doubles for the eigenfunctions."""
+    pr, npar = _params(params)
+    E = (ctypes.c_double * nev)()
+    R = (ctypes.c_double * nev)()
+    info = SpectrumInfo()
+    _check(load().speedup_evolution_spectrum(_model(model), pr, npar, p, float(t), float(L), int(n),
+                                             PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                                             int(nev), E, R, _ptr(vectors), ctypes.byref(info), _stream(stream)))
+    return list(E), list(R), info.as_dict()
 
 
 def su_fault_inject(kind, arg=0):

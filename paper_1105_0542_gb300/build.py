@@ -18,13 +18,13 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libspeedup_gb300.so")
 CLI = os.path.join(LIBDIR, "speedup")
-SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu", "nd.cu"]
+SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "train.cu", "evolution.cu", "nd.cu", "spectrum.cu"]
 # the sampler kernel, once per (precision, ring): compiled in parallel
 INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3, 0)]
 # double-precision samplers that read tables too large for shared memory from global memory
 INSTANCES += [(64, ring, 1) for ring in (0, 1, 2)]
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",
-           "proposal.h", "train.h", "philox.cuh"]
+           "proposal.h", "train.h", "philox.cuh", "spectrum.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

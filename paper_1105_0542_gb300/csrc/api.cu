@@ -29,6 +29,7 @@
 #include "mlp.cuh"
 #include "proposal.h"
 #include "sampler.h"
+#include "spectrum.h"
 #include "train.h"
 
 namespace {
@@ -1109,9 +1110,10 @@ int su_fault_inject(int kind, int64_t arg) {
 }
 
 // ------------------------------------------------------- evolution operator
-int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
-                             int precision, double *d_U, void *stream) {
-    if (!d_U) return fail(SU_EINVAL, "output missing");
+// The level-p table of the single-slice weight at eps = t (kernel precision)
+// and the sampler parameters that evaluate it, for the evolution operator.
+static int evolution_setup(int model, const double *params, int n_params, int p, double t, double L, int n,
+                           int precision, std::vector<unsigned char> &blob, su::SamplerParams &P) {
     if (!(t > 0) || !std::isfinite(t)) return fail(SU_EINVAL, "t must be finite and > 0");
     if (!(L > 0) || !std::isfinite(L)) return fail(SU_EINVAL, "L must be finite and > 0");
     if (n < 2 || n > 65536) return fail(SU_EINVAL, "n must be in 2..65536");
@@ -1125,7 +1127,7 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
     std::vector<double> T;
     su::kernel_table(E, t, T);
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
-    std::vector<unsigned char> blob(T.size() * rs);
+    blob.assign(T.size() * rs, 0);
     for (size_t i = 0; i < T.size(); ++i) {
         if (!std::isfinite(T[i]) || (precision == SU_FP32 && !std::isfinite((float)T[i])))
             return fail(SU_ENONFINITE, "a coefficient of W_p is not representable at t = %g", t);
@@ -1136,13 +1138,22 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
             std::memcpy(blob.data() + i * rs, &T[i], rs);
         }
     }
-    su::SamplerParams P;
     std::memset(&P, 0, sizeof P);
     P.ring = E.shape.ring;
     P.ncol = E.shape.ncol;
     P.M = E.shape.M;
     for (int j = 0; j < E.shape.ncol; ++j) P.len[j] = E.shape.len[j];
     P.alpha = E.shape.alpha;
+    return SU_OK;
+}
+
+int speedup_evolution_matrix(int model, const double *params, int n_params, int p, double t, double L, int n,
+                             int precision, double *d_U, void *stream) {
+    if (!d_U) return fail(SU_EINVAL, "output missing");
+    std::vector<unsigned char> blob;
+    su::SamplerParams P;
+    int rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P);
+    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     void *d_tab = nullptr;
     CU(dmalloc_async(&d_tab, blob.size(), st), "device allocation (table)");
@@ -1154,6 +1165,106 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(d_tab, st);
     if (e != cudaSuccess) return cuda_fail(e, "evolution matrix");
+    return SU_OK;
+}
+
+int su_evolution_band_size(double t, double L, int n, int *half_width, int64_t *pitch) {
+    if (!(t > 0) || !std::isfinite(t) || !(L > 0) || !std::isfinite(L) || n < 2 || n > 65536)
+        return fail(SU_EINVAL, "t, L must be finite and > 0, n in 2..65536");
+    const double delta = 2.0 * L / (double)(n - 1);
+    // (x_j - x_i)^2 / (2t) <= 40 needs |j - i| Delta <= sqrt(80 t); two more
+    // diagonals cover the rounding of the grid points (zero there anyway)
+    const int w = (int)std::min<double>(n - 1, std::floor(std::sqrt(80.0 * t) / delta) + 2.0);
+    if (half_width) *half_width = w;
+    if (pitch) *pitch = ((int64_t)n + 31) / 32 * 32;
+    return SU_OK;
+}
+
+int speedup_evolution_band(int model, const double *params, int n_params, int p, double t, double L, int n,
+                           int precision, double *d_band, int64_t capacity, void *stream) {
+    int w = 0;
+    int64_t pitch = 0;
+    int rc = su_evolution_band_size(t, L, n, &w, &pitch);
+    if (rc) return rc;
+    if (!d_band) return fail(SU_EINVAL, "output missing");
+    const int64_t need = (int64_t)(w + 1) * pitch * (int64_t)sizeof(double);
+    if (capacity < need) return fail(SU_EINVAL, "the band needs %lld bytes, %lld given", (long long)need, (long long)capacity);
+    std::vector<unsigned char> blob;
+    su::SamplerParams P;
+    rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *d_tab = nullptr;
+    CU(dmalloc_async(&d_tab, blob.size(), st), "device allocation (table)");
+    cudaError_t e = cudaMemcpyAsync(d_tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+    const double delta = 2.0 * L / (double)(n - 1);
+    const double lognorm = std::log(delta) - 0.5 * std::log(2.0 * M_PI * t);
+    if (e == cudaSuccess) e = su::launch_band(P, precision, d_tab, L, delta, n, t, lognorm, w, pitch, d_band, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_tab, st);
+    if (e != cudaSuccess) return cuda_fail(e, "evolution band");
+    return SU_OK;
+}
+
+int speedup_evolution_spectrum(int model, const double *params, int n_params, int p, double t, double L, int n,
+                               int precision, int nev, double *energies, double *residuals, double *d_vectors,
+                               su_spectrum_info *info, void *stream) {
+    if (!energies) return fail(SU_EINVAL, "energies missing");
+    int w = 0;
+    int64_t pitch = 0;
+    int rc = su_evolution_band_size(t, L, n, &w, &pitch);
+    if (rc) return rc;
+    if (nev < 1 || nev > 26 || nev > n / 2) return fail(SU_EINVAL, "nev must be in 1..26 and at most n/2");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t bytes = (int64_t)(w + 1) * pitch * (int64_t)sizeof(double);
+    void *d_band = nullptr;
+    CU(dmalloc(&d_band, (size_t)bytes), "device allocation (band)");
+    std::unique_ptr<void, cudaError_t (*)(void *)> guard(d_band, cudaFree);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 3; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } eg{ev};
+    for (auto &x : ev) CU(cudaEventCreate(&x), "event");
+    CU(cudaEventRecord(ev[0], st), "event record");
+    rc = speedup_evolution_band(model, params, n_params, p, t, L, n, precision, static_cast<double *>(d_band), bytes,
+                                stream);
+    if (rc) return rc;
+    CU(cudaEventRecord(ev[1], st), "event record");
+    const double delta = 2.0 * L / (double)(n - 1);
+    su::SpectrumResult R;
+    std::string err;
+    rc = su::band_spectrum(static_cast<const double *>(d_band), pitch, n, w, nev, 12, 1e-11, 60, 20110505ULL,
+                           d_vectors, 1.0 / std::sqrt(delta), st, R, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    CU(cudaEventRecord(ev[2], st), "event record");
+    CU(cudaEventSynchronize(ev[2]), "event synchronize");
+    for (int k = 0; k < nev; ++k) {
+        energies[k] = R.theta[(size_t)k] > 0 ? -std::log(R.theta[(size_t)k]) / t : NAN;
+        if (residuals) residuals[k] = R.resid[(size_t)k];
+    }
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->half_width = w;
+        info->band_bytes = bytes;
+        info->block = R.block;
+        info->iterations = R.iterations;
+        info->matvecs = R.matvecs;
+        info->converged = R.converged;
+        info->block_matvecs = R.block_matvecs;
+        info->block_matvec_ms = R.block_matvec_ms;
+        info->lower = R.lower;
+        info->upper = R.upper;
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+        info->band_ms = ms;
+        CU(cudaEventElapsedTime(&ms, ev[1], ev[2]), "event time");
+        info->solve_ms = ms;
+    }
+    if (!R.converged) return fail(SU_ENOTSUP, "the eigensolver did not reach its residual tolerance in 60 rounds");
     return SU_OK;
 }
 

@@ -121,6 +121,23 @@ int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
 cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
                              double t, double lognorm, double *U, cudaStream_t st);
 
+// The upper band of the evolution operator, diagonal-major:
+// D[k * pitch + i] = U_{i,i+k}, k = 0..w (evolution.cu)
+cudaError_t launch_band(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
+                        double t, double lognorm, int w, int64_t pitch, double *D, cudaStream_t st);
+// part[split][i][c] = partial sums of (U X)[i][c] over the split's diagonals, B in {1, 8, 16, 32}
+cudaError_t launch_band_matvec(int B, const double *D, int64_t pitch, int n, int w, int splits, const double *X,
+                               double *part, cudaStream_t st);
+// Ynew = alpha * sum_split part + beta * Ycur + gamma * Yprev (nb = n * B elements)
+cudaError_t launch_cheb(const double *part, int splits, int64_t nb, const double *Ycur, const double *Yprev,
+                        double *Ynew, double alpha, double beta, double gamma, cudaStream_t st);
+// op 0: out[chunk][B][B] = A^T C over the chunk's rows; op 1: out = A Q (Q: B x B);
+// op 2: out[chunk][B] = sum (A - Q[c] C)^2 over the chunk's rows (Q: B Ritz values)
+cudaError_t launch_block_op(int op, int B, const double *A, const double *C, const double *Q, int n, int chunks,
+                            double *out, cudaStream_t st);
+// vec[k n + i] = scale X[i][k], k < nev
+cudaError_t launch_vectors(int B, const double *X, int n, int nev, double scale, double *vec, cudaStream_t st);
+
 // Systems of d = D x M coordinates (Sec. 2.2): one bisection path per
 // thread, every coordinate an exact Brownian bridge (coordinate c of heap
 // midpoint j takes normal j D + c of the sample's stream), built and weighed
