@@ -263,3 +263,103 @@ SU_BM_FN void rotate(double R, uint64_t b, const Tables *__restrict__ t, double 
 
 }  // namespace bm
 }  // namespace su
+
+// ---------------------------------------------------------------------------
+// Single-precision Box-Muller (the single-precision sampler's normals) for the
+// 24-bit uniforms u1 = fl(a + 1/2) 2^-24, u2 = fl(b + 1/2) 2^-24 (a, b the top
+// 24 bits of two Philox words), with the same structure as the double
+// routines above, in float:
+//  * -2 ln u1: u1 = 2^e m, m in [3/4, 3/2) from its bits; node c_j = 1 +
+//    (j - 16)/64 (j = 0..48) nearest to m, inv_j the float nearest 1/c_j,
+//    r = m inv_j - 1 in one fused multiply-add (|r| <= 1/96), and
+//      ln u1 = e ln2_hi + ln(1/inv_j) + [e ln2_lo + r (1 - r/2 + r^2/3 - r^3/4)]
+//    (truncation r^5/5 < 2^-34 relative to r; ln2_hi with trailing zeros so
+//    that e ln2_hi is exact; the node c = 1 has inv = 1 and ln 1 = 0 exactly,
+//    so u1 near 1 keeps its relative accuracy);
+//  * R = sqrt(v) from the hardware reciprocal-square-root estimate y and one
+//    correction s + (v - s^2) y/2 of s = v y (R = 0 where u1 rounds to 1);
+//  * cos/sin(2 pi u2): 8 u2 = 2q + g exactly (quadrant q, g in [0, 2)), g
+//    reflected to 2 - g above 1 (exact), phi = g pi/4 = i pi/128 + d pi/4 with
+//    i the nearest of 33 nodes and |d| <= 1/64 exact, then
+//      sin phi = S_i + (C_i sd - S_i h),  cos phi = C_i - (S_i sd + C_i h),
+//      sd = delta - delta^3/6,  h = delta^2/2,  delta = d pi/4
+//    (next terms below 2^-29 relative) and the quadrant's swap and signs.
+// Node values are computed once per CTA in double with the CUDA library
+// functions and rounded to float.  Accuracy: a few units in the last place of
+// float against R cos, R sin evaluated in double from the same uniforms
+// (GPU tests against the oracle's libm values, 1e-6 (1 + R)).
+namespace bm32 {
+
+constexpr int kLogNodes = 49;    // c_j = 1 + (j - 16)/64, j = 0..48: [3/4, 3/2]
+constexpr int kTrigNodes = 33;   // i pi/128, i = 0..32: [0, pi/4]
+
+struct Tables {
+    float2 lg[kLogNodes];        // (inv_j, ln(1/inv_j))
+    float2 sc[kTrigNodes];       // (sin, cos) of i pi/128
+};
+
+__device__ __forceinline__ void tables_init(Tables *t, int tid, int nthreads) {
+    for (int j = tid; j < kLogNodes; j += nthreads) {
+        const float inv = (float)(1.0 / (1.0 + (j - 16) * (1.0 / 64.0)));
+        t->lg[j] = make_float2(inv, (float)(-log((double)inv)));
+    }
+    for (int i = tid; i < kTrigNodes; i += nthreads) {
+        double s, c;
+        sincospi(i / 128.0, &s, &c);
+        t->sc[i] = make_float2((float)s, (float)c);
+    }
+}
+
+// z0 = R cos(2 pi u2), z1 = R sin(2 pi u2), R = sqrt(-2 ln u1)
+__device__ __forceinline__ void pair(uint32_t a, uint32_t b, const Tables *__restrict__ t, float &z0, float &z1) {
+    constexpr float kLn2Hi = 0.693145751953125f;         // 0x3F317200: 13 trailing zero bits
+    constexpr float kLn2Lo = 1.428606765330187e-06f;     // ln 2 - kLn2Hi
+    const float u1 = ((float)(a >> 8) + 0.5f) * 0x1p-24f;
+    const float u2 = ((float)(b >> 8) + 0.5f) * 0x1p-24f;
+
+    // ---- -2 ln u1 (u1 >= 2^-25: a normal float)
+    const int ib = __float_as_int(u1);
+    int e = (ib >> 23) - 127;
+    int mb = (ib & 0x7FFFFF) | 0x3F800000;                // m in [1, 2)
+    if (mb >= 0x3FC00000) {                               // m >= 3/2: halve m (exactly), raise e
+        mb -= 0x00800000;
+        e += 1;
+    }
+    const float m = __int_as_float(mb);
+    const int j = __float2int_rn((m - 1.0f) * 64.0f) + 16;
+    const float2 L = t->lg[j];
+    const float r = fmaf(m, L.x, -1.0f);
+    const float pl = r * fmaf(r, fmaf(r, fmaf(r, -0.25f, 0.333333343f), -0.5f), 1.0f);
+    const float fe = (float)e;
+    const float v = -2.0f * (fmaf(fe, kLn2Hi, L.y) + fmaf(fe, kLn2Lo, pl));
+
+    // ---- R = sqrt(v), v in {0} u [2^-24, 35] (u1 rounds to 1 for a >> 8 = 2^24 - 1)
+    const float y = rsqrtf(v);
+    const float s0 = v * y;
+    const float R = v > 0.0f ? fmaf(0.5f * y, fmaf(-s0, s0, v), s0) : 0.0f;
+
+    // ---- cos, sin of 2 pi u2
+    const float t8 = u2 * 8.0f;                            // exact, in (0, 8)
+    const int q = ((int)t8) >> 1;                          // quadrant
+    float g = t8 - (float)(2 * q);                         // [0, 2), exact
+    const bool refl = g > 1.0f;
+    g = refl ? 2.0f - g : g;                               // [0, 1], exact
+    const float fi = rintf(g * 32.0f);
+    const float d = fmaf(fi, -0.03125f, g);                // g - i/32, exact
+    const float dl = d * 0.785398163f;                     // delta = d pi/4
+    const float dl2 = dl * dl;
+    const float h = 0.5f * dl2;
+    const float sd = fmaf(dl2 * (-1.0f / 6.0f), dl, dl);
+    const float2 SC = t->sc[(int)fi];
+    const float sp = fmaf(SC.y, sd, fmaf(-SC.x, h, SC.x)); // sin phi
+    const float cp = fmaf(-SC.x, sd, fmaf(-SC.y, h, SC.y)); // cos phi
+    // psi = q pi/2 + (refl ? pi/2 - phi : phi): swap on refl xor odd q, then signs
+    const bool sw = refl != ((q & 1) != 0);
+    const float cq = sw ? sp : cp, sq = sw ? cp : sp;
+    const float cth = (q == 1 || q == 2) ? -cq : cq;
+    const float sth = (q >= 2) ? -sq : sq;
+    z0 = R * cth;
+    z1 = R * sth;
+}
+
+}  // namespace bm32

@@ -103,6 +103,9 @@ __global__ void __launch_bounds__(128) normals_kernel_f64(uint64_t seed, uint32_
 
 __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_t inst, int64_t sample0,
                                                           int64_t ns, int n, double *out) {
+    __shared__ bm32::Tables tabs;
+    bm32::tables_init(&tabs, threadIdx.x, blockDim.x);
+    __syncthreads();
     const int calls = n / 4 + 1;                 // j' = j + 1 runs over 1..n
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= ns * calls) return;
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_
     st.slo = (uint32_t)smp;
     st.shi = (uint32_t)(smp >> 32);
     st.bm = nullptr;
+    st.bm32 = &tabs;
     float z[4];
     st.quad(t, z);
 #pragma unroll
@@ -162,7 +166,8 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     const int C = 1 << (P.S - P.F);
     size_t off = P.w_out ? 0 : rs * (size_t)P.levels * kThreads * P.rounds;
     off = (off + 15) & ~(size_t)15;
-    if (P.ring != RING_GENERAL && !P.tab_global) off += rs * (size_t)P.S * P.M;   // else read from global memory
+    // staged tables (single precision: pairs {c, c}); else read from global memory
+    if (P.ring != RING_GENERAL && !P.tab_global) off += (precision == SU_FP32 ? 8 : rs) * (size_t)P.S * P.M;
     off += rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;

@@ -29,6 +29,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "boxmuller.cuh"
 #include "philox.cuh"
@@ -57,19 +58,11 @@ struct Normal<double> {
 template <>
 struct Normal<float> {
     // four normals per call: (z0, z1) from the 24-bit uniforms
-    // ((w >> 8) + 1/2) 2^-24 of (w0, w1), (z2, z3) from (w2, w3)
-    static __device__ __forceinline__ void bm24(uint32_t a, uint32_t b, float &z0, float &z1) {
-        const float u1 = ((float)(a >> 8) + 0.5f) * 0x1p-24f;
-        const float u2 = ((float)(b >> 8) + 0.5f) * 0x1p-24f;
-        const float r = sqrtf(-2.0f * logf(u1));
-        float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
-        z0 = r * cs;
-        z1 = r * sn;
-    }
-    static __device__ __forceinline__ void quad(uint4 w, float (&z)[4]) {
-        bm24(w.x, w.y, z[0], z[1]);
-        bm24(w.z, w.w, z[2], z[3]);
+    // ((w >> 8) + 1/2) 2^-24 of (w0, w1), (z2, z3) from (w2, w3), through the
+    // table-driven single-precision routine of boxmuller.cuh
+    static __device__ __forceinline__ void quad(uint4 w, const bm32::Tables *t, float (&z)[4]) {
+        bm32::pair(w.x, w.y, t, z[0], z[1]);
+        bm32::pair(w.z, w.w, t, z[2], z[3]);
     }
 };
 
@@ -82,6 +75,7 @@ struct Stream {
     uint2 key;
     uint32_t inst, slo, shi;
     const bm::Tables *bm;   // shared-memory node tables (double path)
+    const bm32::Tables *bm32;   // shared-memory node tables (single path)
     __device__ __forceinline__ uint4 words(uint32_t call) const {
         return philox4x32_10(make_uint4(call, inst, slo, shi), key);
     }
@@ -89,7 +83,7 @@ struct Stream {
         Normal<double>::pair(words(call), bm, z0, z1);
     }
     __device__ __forceinline__ void quad(uint32_t call, float (&z)[4]) const {
-        Normal<float>::quad(words(call), z);
+        Normal<float>::quad(words(call), bm32, z);
     }
 };
 
@@ -226,10 +220,16 @@ __device__ __noinline__ double2 slice_general(double ql0, double qr0, double ql1
     return make_double2(w[0], B > 1 ? w[B - 1] : 0.0);
 }
 
+// Entry i of a level table.  Tables hold scalars, or (the single-precision
+// sampler) pairs {c, c} that feed the packed two-slice multiply-adds.
+__device__ __forceinline__ float coef(const float *t, int i) { return t[i]; }
+__device__ __forceinline__ double coef(const double *t, int i) { return t[i]; }
+__device__ __forceinline__ float coef(const float2 *t, int i) { return t[i].x; }
+
 // -eps W_p(x, xb; eps) of one slice, from the level's table in shared memory:
 // sum_j (vs^2)^j sum_i T_ij Z^i, nested Horner (columns, then powers of vs^2).
-template <typename R, int RING, typename SP>
-__device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const SP &P, R alpha) {
+template <typename R, int RING, typename TT, typename SP>
+__device__ __forceinline__ R slice(R ql, R qr, const TT *__restrict__ tab, const SP &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
         static_assert(sizeof(R) == 8, "the general potential is evaluated in double");
         return slice_general<1>(ql, qr, ql, qr, tab, P.general).x;
@@ -243,9 +243,9 @@ __device__ __forceinline__ R slice(R ql, R qr, const R *__restrict__ tab, const 
     for (int j = P.ncol - 1; j >= 0; --j) {
         const int L = P.len[j];
         off -= L;
-        R h = tab[off + L - 1];
+        R h = coef(tab, off + L - 1);
 #pragma unroll 4
-        for (int i = L - 2; i >= 0; --i) h = fma(h, Z, tab[off + i]);
+        for (int i = L - 2; i >= 0; --i) h = fma(h, Z, coef(tab, off + i));
         acc = fma(acc, Y, h);
     }
     return acc;
@@ -267,8 +267,8 @@ struct Batch {
     static constexpr int B = 8;
 };
 
-template <typename R, int RING, int NS, int STR, int NQ, typename SP>
-__device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ tab, const SP &P, R alpha) {
+template <typename R, int RING, int NS, int STR, int NQ, typename TT, typename SP>
+__device__ __forceinline__ R level_sum(const R (&q)[NQ], const TT *__restrict__ tab, const SP &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
         R total = 0;
         if constexpr (NS == 1) {
@@ -285,6 +285,79 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
     }
     constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
     constexpr bool kFold = sizeof(R) == 8;
+    if constexpr (std::is_same<TT, float2>::value && B % 2 == 0) {
+        // single precision with paired tables: two slices per packed
+        // multiply-add (fma.rn.f32x2), the same operations in the same order
+        // as the scalar form below, so the same bits
+        constexpr int BP = B / 2;
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        R ty = 0;
+#pragma unroll
+        for (int k0 = 0; k0 < NS; k0 += B) {
+            float2 Z[BP], Y[BP], acc[BP];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) {
+                const float2 ql = make_float2(q[(k0 + 2 * m) * STR], q[(k0 + 2 * m + 1) * STR]);
+                const float2 qr = make_float2(q[(k0 + 2 * m + 1) * STR], q[(k0 + 2 * m + 2) * STR]);
+                const float2 vs = __ffma2_rn(ql, m1, qr);     // qr - ql, exactly as a subtraction
+                Y[m] = __fmul2_rn(vs, vs);
+                const float2 us = __fadd2_rn(ql, qr);
+                if constexpr (RING == RING_EVEN) {
+                    Z[m] = __fmul2_rn(us, us);
+                } else {
+                    Z[m] = make_float2(ring_var<float, RING>(us.x, alpha), ring_var<float, RING>(us.y, alpha));
+                }
+            }
+            int off = P.M;
+            {   // last column starts the outer Horner in x-bar^2
+                const int L = P.len[P.ncol - 1];
+                off -= L;
+                const float2 c = tab[off + L - 1];
+                if (L == 1) {
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) acc[m] = c;
+                } else {
+                    const float2 c0 = tab[off + L - 2];
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
+                }
+#pragma unroll 4
+                for (int i = L - 3; i >= 0; --i) {
+                    const float2 ci = tab[off + i];
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
+                }
+            }
+            for (int j = P.ncol - 2; j >= 0; --j) {
+                const int L = P.len[j];
+                off -= L;
+                const float2 c = tab[off + L - 1];
+                if (L == 1) {
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
+                    continue;
+                }
+                float2 h[BP];
+                const float2 c0 = tab[off + L - 2];
+#pragma unroll
+                for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
+#pragma unroll 4
+                for (int i = L - 3; i >= 0; --i) {
+                    const float2 ci = tab[off + i];
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
+                }
+#pragma unroll
+                for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
+            }
+#pragma unroll
+            for (int m = 0; m < BP; ++m) {
+                ty += acc[m].x;
+                ty += acc[m].y;
+            }
+        }
+        return ty;
+    } else {
     const int L0 = P.len[0];
     R ty = 0, tz = 0;
 #pragma unroll
@@ -310,18 +383,18 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                 {   // last column starts the outer Horner in x-bar^2
                     const int L = P.len[P.ncol - 1];
                     off -= L;
-                    const R c = tab[off + L - 1];
+                    const R c = coef(tab, off + L - 1);
                     if (L == 1) {
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = c;
                     } else {
-                        const R c0 = tab[off + L - 2];
+                        const R c0 = coef(tab, off + L - 2);
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = fma(c, Z[b], c0);
                     }
 #pragma unroll 4
                     for (int i = L - 3; i >= 0; --i) {
-                        const R ci = tab[off + i];
+                        const R ci = coef(tab, off + i);
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
                     }
@@ -329,19 +402,19 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                 for (int j = P.ncol - 2; j >= jlast; --j) {
                     const int L = P.len[j];
                     off -= L;
-                    const R c = tab[off + L - 1];
+                    const R c = coef(tab, off + L - 1);
                     if (L == 1) {
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Y[b], c);
                         continue;
                     }
                     R h[B];
-                    const R c0 = tab[off + L - 2];
+                    const R c0 = coef(tab, off + L - 2);
 #pragma unroll
                     for (int b = 0; b < B; ++b) h[b] = fma(c, Z[b], c0);
 #pragma unroll 4
                     for (int i = L - 3; i >= 0; --i) {
-                        const R ci = tab[off + i];
+                        const R ci = coef(tab, off + i);
 #pragma unroll
                         for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
                     }
@@ -353,12 +426,12 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                 {   // last column starts the outer Horner in x-bar^2
                     const int L = P.len[P.ncol - 1];
                     off -= L;
-                    const R c = tab[off + L - 1];
+                    const R c = coef(tab, off + L - 1);
 #pragma unroll
                     for (int b = 0; b < B; ++b) acc[b] = c;
 #pragma unroll 4
                     for (int i = L - 2; i >= 0; --i) {
-                        const R ci = tab[off + i];
+                        const R ci = coef(tab, off + i);
 #pragma unroll
                         for (int b = 0; b < B; ++b) acc[b] = fma(acc[b], Z[b], ci);
                     }
@@ -367,12 +440,12 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
                     const int L = P.len[j];
                     off -= L;
                     R h[B];
-                    const R c = tab[off + L - 1];
+                    const R c = coef(tab, off + L - 1);
 #pragma unroll
                     for (int b = 0; b < B; ++b) h[b] = c;
 #pragma unroll 4
                     for (int i = L - 2; i >= 0; --i) {
-                        const R ci = tab[off + i];
+                        const R ci = coef(tab, off + i);
 #pragma unroll
                         for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
                     }
@@ -391,12 +464,12 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
         if constexpr (kFold) {
             if (L0 > 1) {
                 R h[B];
-                const R c = tab[L0 - 1];
+                const R c = coef(tab, L0 - 1);
 #pragma unroll
                 for (int b = 0; b < B; ++b) h[b] = c;
 #pragma unroll 4
                 for (int i = L0 - 2; i >= 1; --i) {
-                    const R ci = tab[i];
+                    const R ci = coef(tab, i);
 #pragma unroll
                     for (int b = 0; b < B; ++b) h[b] = fma(h[b], Z[b], ci);
                 }
@@ -405,14 +478,15 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const R *__restrict__ t
             }
         }
     }
-    if constexpr (kFold) return fma((R)NS, tab[0], ty + tz);
+    if constexpr (kFold) return fma((R)NS, coef(tab, 0), ty + tz);
     return ty;
+    }
 }
 
 // levels d = D..F of a segment (level n = S - d uses every 2^d-th point)
-template <typename R, int RING, int F, int D, typename SP>
+template <typename R, int RING, int F, int D, typename TT, typename SP>
 __device__ __forceinline__ void segment_levels(R (&acc)[F + 1], const R (&q)[(1 << F) + 1],
-                                               const R *__restrict__ tab, const SP &P, R alpha, int S) {
+                                               const TT *__restrict__ tab, const SP &P, R alpha, int S) {
     if constexpr (D <= F) {
         if (D < S) {
             acc[D] += level_sum<R, RING, ((1 << F) >> D), (1 << D)>(q, tab + D * P.M, P, alpha);
@@ -447,9 +521,9 @@ struct PathCfg {
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
-template <typename R, int RING, int F, bool WF, typename SP>
+template <typename R, int RING, int F, bool WF, typename TT, typename SP>
 __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
-                                            const R *__restrict__ tab, R *__restrict__ qc,
+                                            const TT *__restrict__ tab, R *__restrict__ qc,
                                             double *__restrict__ zz, const Stream<R> &st,
                                             R *__restrict__ wout, int wstride, float *qout = nullptr) {
     constexpr int NF = 1 << F;
@@ -619,9 +693,9 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
 // The width-factor weight is a template switch: as a run-time test inside
 // the midpoint loop the compiler predicates it, and its double conversions
 // and multiply-add then occupy the FP64 pipe on every midpoint.
-template <typename R, int RING, bool WF, typename SP>
+template <typename R, int RING, bool WF, typename TT, typename SP>
 __device__ __forceinline__ void sample_path_f(int F, const SP &P, const PathCfg<R> &pc,
-                                              const R *tab, R *qc, double *zz, const Stream<R> &st,
+                                              const TT *tab, R *qc, double *zz, const Stream<R> &st,
                                               R *wout, int wstride, float *qout) {
     switch (F) {
         case 1: sample_path<R, RING, 1, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
@@ -632,9 +706,9 @@ __device__ __forceinline__ void sample_path_f(int F, const SP &P, const PathCfg<
     }
 }
 
-template <typename R, int RING, typename SP>
+template <typename R, int RING, typename TT, typename SP>
 __device__ __forceinline__ void sample_path_any(int F, const SP &P, const PathCfg<R> &pc,
-                                                const R *tab, R *qc, double *zz, const Stream<R> &st,
+                                                const TT *tab, R *qc, double *zz, const Stream<R> &st,
                                                 R *wout, int wstride, float *qout = nullptr) {
     if (P.wf_on)
         sample_path_f<R, RING, true>(F, P, pc, tab, qc, zz, st, wout, wstride, qout);
@@ -644,8 +718,8 @@ __device__ __forceinline__ void sample_path_any(int F, const SP &P, const PathCf
 
 // batched kernel: no width factor; the per-item view of the instance's
 // table shape (BatchView, in shared memory) in place of SamplerParams
-template <typename R, int RING, typename SP>
-__device__ __forceinline__ void sample_path_plain(int F, const SP &P, const PathCfg<R> &pc, const R *tab, R *qc,
+template <typename R, int RING, typename TT, typename SP>
+__device__ __forceinline__ void sample_path_plain(int F, const SP &P, const PathCfg<R> &pc, const TT *tab, R *qc,
                                                   const Stream<R> &st, R *wout) {
     sample_path_f<R, RING, false>(F, P, pc, tab, qc, nullptr, st, wout, 1, nullptr);
 }
@@ -761,6 +835,7 @@ struct MinCtas<double, RING_GENERAL> {
 template <typename R, int RING, bool GTAB = false>
 __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ bm32::Tables s_bm32;   // single path
     const int tid = threadIdx.x;
     const int L = P.levels;
     const int chunk = kThreads * P.rounds;
@@ -774,9 +849,12 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     // and any tables too large to stage (levels p >~ 100), stay in global
     // memory: every lane reads the same entry, one broadcast load through L1
     constexpr bool kStage = RING != RING_GENERAL && !GTAB;
-    R *tab_s = reinterpret_cast<R *>(smem_raw + off);
-    const R *tab = kStage ? tab_s : reinterpret_cast<const R *>(P.tables);
-    off += kStage ? sizeof(R) * (size_t)P.S * P.M : 0;
+    // single precision stages every entry as a pair {c, c} for the packed
+    // two-slice multiply-adds of level_sum
+    using TT = typename std::conditional<sizeof(R) == 4, float2, R>::type;
+    TT *tab_s = reinterpret_cast<TT *>(smem_raw + off);
+    const TT *tab = kStage ? tab_s : reinterpret_cast<const TT *>(P.tables);
+    off += kStage ? sizeof(TT) * (size_t)P.S * P.M : 0;
     R *sig = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
@@ -792,9 +870,15 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     {
         const R *g = reinterpret_cast<const R *>(P.tables);
         const int n = kStage ? P.S * P.M : 0;
-        for (int i = tid; i < n; i += kThreads) tab_s[i] = g[i];
+        for (int i = tid; i < n; i += kThreads) {
+            if constexpr (sizeof(R) == 4)
+                tab_s[i] = make_float2(g[i], g[i]);
+            else
+                tab_s[i] = g[i];
+        }
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)P.sigma[i];
         if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
+        if constexpr (sizeof(R) == 4) bm32::tables_init(&s_bm32, tid, kThreads);
     }
     __syncthreads();
     const PathCfg<R> pc{(R)P.a, (R)P.b, P.S, L, sig};
@@ -803,6 +887,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.inst = P.instance;
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
+    st.bm32 = &s_bm32;
 
     const int warp = tid >> 5, lane = tid & 31;
     for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
@@ -878,6 +963,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ double s_red[kThreads / 32][SU_MAX_S][3];
+    __shared__ bm32::Tables s_bm32;   // single path
     const SamplerParams &P = B.base;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -901,10 +987,12 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     off = (off + 15) & ~(size_t)15;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
     if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
+    if constexpr (sizeof(R) == 4) bm32::tables_init(&s_bm32, tid, kThreads);
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
+    st.bm32 = &s_bm32;
     int cur_shape = -1;
 
     while (true) {
