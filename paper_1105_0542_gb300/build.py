@@ -24,7 +24,7 @@ INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64,
 # double-precision samplers that read tables too large for shared memory from global memory
 INSTANCES += [(64, ring, 1) for ring in (0, 1, 2)]
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",
-           "proposal.h", "train.h", "philox.cuh", "spectrum.h"]
+           "proposal.h", "train.h", "philox.cuh", "spectrum.h", "erf_poly.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,10 +21,13 @@
 // [0, 128) (outputs: [128, 144)), a commit to an mbarrier, and an epilogue
 // in which warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows) and
 // a quarter of the columns of its quadrant's rows (16 warps: 32 columns each),
-// adds the bias, applies GELU and writes the bfloat16 activations back into
-// the A tile for the next layer.
+// adds the bias, applies GELU (erf by a polynomial, two values per packed
+// multiply-add) and writes the bfloat16 activations back into the A tile for
+// the next layer.
 #include <cuda_bf16.h>
 #include <cstdint>
+
+#include "erf_poly.h"
 
 namespace su {
 namespace mlp {
@@ -61,7 +64,31 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+// erf(v/sqrt 2) from the polynomial of erf_poly.h (one value)
+__device__ __forceinline__ float erf_sqrt2(float v) {
+    const float x = fminf(fmaxf(v, -kErfClamp), kErfClamp);
+    const float z = x * x;
+    float p = erf_poly(kErfTerms - 1);
+#pragma unroll
+    for (int k = kErfTerms - 2; k >= 0; --k) p = fmaf(p, z, erf_poly(k));
+    return x * p;
+}
+
+// GELU of two values, v (1 + erf(v/sqrt 2))/2, with erf(v/sqrt 2) from the
+// odd polynomial v Q(v^2) of erf_poly.h (v clamped to [-3 sqrt 2, 3 sqrt 2],
+// error <= 1e-4, below the bfloat16 rounding the epilogue applies) evaluated
+// on the pair by packed multiply-adds (fma.rn.f32x2): one instruction for
+// both values.
+__device__ __forceinline__ float2 gelu2(float2 v) {
+    const float2 x = make_float2(fminf(fmaxf(v.x, -kErfClamp), kErfClamp), fminf(fmaxf(v.y, -kErfClamp), kErfClamp));
+    const float2 z = __fmul2_rn(x, x);
+    float2 p = make_float2(erf_poly(kErfTerms - 1), erf_poly(kErfTerms - 1));
+#pragma unroll
+    for (int k = kErfTerms - 2; k >= 0; --k) p = __ffma2_rn(p, z, make_float2(erf_poly(k), erf_poly(k)));
+    const float2 e = __fmul2_rn(x, p);                                   // erf(v/sqrt 2)
+    const float2 h = __fmul2_rn(v, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(h, e, h);                                           // v/2 + v/2 erf
+}
 
 // ---- tcgen05 plumbing
 // shared-memory matrix descriptor: start address, leading (K) and stride
@@ -197,11 +224,19 @@ __device__ __forceinline__ void tc_store_gelu(const Tc &t, const float *bias, un
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int c = c0 + cc + 8 * half;
+            // the eight columns' biases (16-byte aligned: the blob's bias block is)
+            const float4 b0 = *reinterpret_cast<const float4 *>(bias + c);
+            const float4 b1 = *reinterpret_cast<const float4 *>(bias + c + 4);
+            const float *u = v + 8 * half;
+            const float2 g0 = gelu2(__fadd2_rn(make_float2(u[0], u[1]), make_float2(b0.x, b0.y)));
+            const float2 g1 = gelu2(__fadd2_rn(make_float2(u[2], u[3]), make_float2(b0.z, b0.w)));
+            const float2 g2 = gelu2(__fadd2_rn(make_float2(u[4], u[5]), make_float2(b1.x, b1.y)));
+            const float2 g3 = gelu2(__fadd2_rn(make_float2(u[6], u[7]), make_float2(b1.z, b1.w)));
             uint4 w;
-            w.x = pack_bf16(gelu(v[8 * half + 0] + bias[c + 0]), gelu(v[8 * half + 1] + bias[c + 1]));
-            w.y = pack_bf16(gelu(v[8 * half + 2] + bias[c + 2]), gelu(v[8 * half + 3] + bias[c + 3]));
-            w.z = pack_bf16(gelu(v[8 * half + 4] + bias[c + 4]), gelu(v[8 * half + 5] + bias[c + 5]));
-            w.w = pack_bf16(gelu(v[8 * half + 6] + bias[c + 6]), gelu(v[8 * half + 7] + bias[c + 7]));
+            w.x = pack_bf16(g0.x, g0.y);
+            w.y = pack_bf16(g1.x, g1.y);
+            w.z = pack_bf16(g2.x, g2.y);
+            w.w = pack_bf16(g3.x, g3.y);
             *reinterpret_cast<uint4 *>(H + cm_off(row, c, kHid)) = w;
         }
     }

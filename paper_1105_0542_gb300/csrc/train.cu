@@ -43,9 +43,12 @@ constexpr int kTK = 128;                         // K staged per MMA round
 // 66 KB; 2 CTAs of 256 threads per SM (registers), 256 tensor-memory columns
 constexpr int kGemmSmem = 128 * (kBN + 4) * 4 > 2 * 128 * kTK * 2 ? 128 * (kBN + 4) * 4 : 2 * 128 * kTK * 2;
 
-__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678118654752f)); }
+// GELU and its derivative with erf(v/sqrt 2) from the polynomial the
+// inference epilogue uses (mlp::erf_sqrt2): the same activations in training
+// and in the proposal kernel
+__device__ __forceinline__ float gelu(float v) { return 0.5f * v * (1.0f + mlp::erf_sqrt2(v)); }
 __device__ __forceinline__ float gelu_grad(float v) {
-    return 0.5f * (1.0f + erff(v * 0.70710678118654752f)) + v * 0.39894228040143268f * __expf(-0.5f * v * v);
+    return 0.5f * (1.0f + mlp::erf_sqrt2(v)) + v * 0.39894228040143268f * __expf(-0.5f * v * v);
 }
 
 // What the GEMM's epilogue does with the accumulator tile acc[row][col]:
