@@ -151,7 +151,7 @@ const void *batch_fn(int ring, int precision) {
 size_t batch_smem_bytes(const BatchParams &B, int precision) {
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
     size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
-    off += rs * (size_t)B.tab_max + rs * (size_t)(SU_MAX_S + 1);
+    off += (precision == SU_FP32 ? 8 : rs) * (size_t)B.tab_max + rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(B.C_max > 1 ? B.C_max + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;

@@ -970,8 +970,10 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
 
     BatchView *view = reinterpret_cast<BatchView *>(smem_raw);
     size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
-    R *tab = reinterpret_cast<R *>(smem_raw + off);
-    off += sizeof(R) * (size_t)B.tab_max;
+    // single precision stages the entries as pairs {c, c} (packed Horner)
+    using TT = typename std::conditional<sizeof(R) == 4, float2, R>::type;
+    TT *tab = reinterpret_cast<TT *>(smem_raw + off);
+    off += sizeof(TT) * (size_t)B.tab_max;
     R *sig = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
@@ -1021,7 +1023,12 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
         {
             const int n = L * B.shapes[in.shape].M;
             const R *g = reinterpret_cast<const R *>(P.tables) + in.tab;
-            for (int i = tid; i < n; i += kThreads) tab[i] = g[i];
+            for (int i = tid; i < n; i += kThreads) {
+                if constexpr (sizeof(R) == 4)
+                    tab[i] = make_float2(g[i], g[i]);
+                else
+                    tab[i] = g[i];
+            }
         }
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)in.sigma[i];
         for (int d = 1; d < L; ++d) {
