@@ -62,8 +62,8 @@ extern "C" {
  * with a zero amplitude is absent, beta > 0 and alpha != 0 otherwise
  * (SU_EINVAL).
  * W_p is evaluated per slice from V's derivatives at the slice midpoint and
- * the monomials of W_p in them (1629 monomial-power entries at p = 12), so it
- * needs no collapsed table: p <= 12, SU_FP64 only, su_plan_* /
+ * the monomials of W_p in them (1629 monomial-power entries at p = 12, 24 196
+ * at p = 18), so it needs no collapsed table: p <= 18, SU_FP64 only, su_plan_* /
  * speedup_amplitude / speedup_logweights / su_autotune only; everything else
  * answers SU_ENOTSUP. */
 #define SU_GENERAL 5
@@ -498,7 +498,7 @@ int speedup_generate_nd(int d, const int *exps, const double *coefs, int n_terms
  * derivative symbols V^(j)(x) for SU_GENERAL.  x, xb, w: host arrays of
  * n_points doubles; w[i] = W_p(x[i], xb[i]; eps).  Errors: SU_EINVAL (unknown
  * model, wrong parameters, p outside 1..SU_MAX_P, eps not finite and > 0,
- * n_points < 0, a missing array), SU_ENOTSUP (SU_GENERAL above p = 12).
+ * n_points < 0, a missing array), SU_ENOTSUP (SU_GENERAL above p = 18).
  */
 int speedup_wp(int model, const double *params, int n_params, int p, double eps,
                const double *x, const double *xb, int64_t n_points, double *w);

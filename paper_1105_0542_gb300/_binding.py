@@ -16,7 +16,7 @@ from . import build as _build
 
 SU_OK, SU_EINVAL, SU_ENOMEM, SU_ECUDA, SU_ETIMEOUT, SU_ENONFINITE, SU_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 MODELS = {"ho": 0, "aho": 1, "dw": 2, "mpt": 3, "poly": 4, "general": 5}
-GENERAL_MAX_P = 12
+GENERAL_MAX_P = 18
 PRECISIONS = {"fp64": 0, "fp32": 1}
 MAX_P, MAX_S = 144, 10
 

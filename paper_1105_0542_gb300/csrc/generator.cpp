@@ -428,7 +428,7 @@ GPoly gD(const GPoly &a) {
 
 int build_general(int p, GeneralEffective &G, std::string &err) {
     if (p < 1 || p > kGenMaxP) {
-        err = "the general potential supports p in 1..12";
+        err = "the general potential supports p in 1..18";
         return SU_EINVAL;
     }
     const int nsym = 2 * p;   // V_0..V_{2p-1}; W_p uses up to V_{2p-2}

@@ -67,7 +67,7 @@ double wp_collapsed(const Shape &S, const std::vector<double> &P, double x, doub
 // The distinct monomials of W_p form a trie over their non-decreasing symbol
 // sequences; its nodes in depth-first order give an evaluation program in
 // which every monomial is its parent (one level up) times one symbol.
-constexpr int kGenMaxP = 12;
+constexpr int kGenMaxP = 18;   // the paper's compiled W_p reaches p = 18 (Sec. 3.1)
 
 struct GeneralEffective {
     int p = 0;

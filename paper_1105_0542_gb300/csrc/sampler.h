@@ -18,7 +18,7 @@ constexpr int kMaxFine = 5;     // depth of the register-resident bisection subt
 // and of the potential's families (built by the host from GeneralEffective
 // and GeneralPotential, in device memory).
 constexpr int kGenMaxSym = 2 * kGenMaxP - 1;   // V_0..V_{2p-2}
-constexpr int kGenMaxDepth = 16;               // deepest monomial (6 at p = 12; checked by the host)
+constexpr int kGenMaxDepth = 16;               // deepest monomial (6 at p = 12, 9 at p = 18; checked by the host)
 
 struct GeneralNode {
     unsigned char depth, sym;                  // depth in the trie, symbol j of V_j

@@ -83,6 +83,8 @@ CASES = [
     ("sextic", P_SEXTIC, 0.2, -0.4, 0.5, 9, 7, 60, 9, 0),
     ("s0-edge", P_MIXED, 0.0, 0.0, 0.3, 12, 1, 33, 2, 0),
     ("morse", P_MORSE, -0.2, 0.9, 1.0, 10, 6, 100, 31, 0),
+    ("mixed-p16", P_MIXED, -0.5, 0.7, 1.0, 16, 3, 24, 13, 0),
+    ("aho10-p18", P_AHO10, 0.0, 1.0, 1.0, 18, 4, 24, 1234, 500),
 ]
 
 
@@ -98,6 +100,7 @@ def test_general_logweights_match_oracle(case):
 @pytest.mark.parametrize("model,mparams,gparams,p", [
     ("aho", [1.0, 10.0], P_AHO10, 10),
     ("aho", [1.0, 10.0], P_AHO10, 12),
+    ("aho", [1.0, 10.0], P_AHO10, 18),
     ("dw", [5.0], su.general_params((5.0, 0.0, -10.0, 0.0, 5.0)), 12),
     ("poly", [0.2, -0.5, 0.3, 0.25, 0.1], su.general_params((0.2, -0.5, 0.3, 0.25, 0.1)), 7),
     ("mpt", [3.0, 1.0], P_MPT, 12),

@@ -236,7 +236,7 @@ def test_general_params_layout():
 
 
 @pytest.mark.parametrize("params,kw,code", [
-    (P_GEN, {"p": 13}, -6),                                  # above the general program's p <= 12
+    (P_GEN, {"p": 19}, -6),                                  # above the general program's p <= 18
     (P_GEN, {"precision": "fp32"}, -6),                      # double only
     (P_GEN[:32], {}, -1),                                    # 32 parameters
     (P_GEN[:9] + (1.0, 0.0, 0.0) + P_GEN[12:], {}, -1),      # a Gaussian with beta = 0
@@ -448,7 +448,7 @@ def test_host_wp_rejects_bad_requests():
                        (lambda: su.speedup_wp("aho", [1.0, 1.0], 4, float("nan"), x, x), -1),
                        (lambda: su.speedup_wp("aho", [1.0], 4, 0.1, x, x), -1),
                        (lambda: su.speedup_wp("aho", [1.0, 1.0], 145, 0.1, x, x), -1),
-                       (lambda: su.speedup_wp("general", su.general_params((0, 0, 0.5)), 13, 0.1, x, x), -6),
+                       (lambda: su.speedup_wp("general", su.general_params((0, 0, 0.5)), 19, 0.1, x, x), -6),
                        (lambda: su.speedup_wp_nd({(2, 0): 1.0}, 4, -1.0, np.zeros((3, 2)), np.zeros((3, 2))), -1),
                        (lambda: su.speedup_wp_nd({(2, 0): 1.0}, 13, 0.1, np.zeros((3, 2)), np.zeros((3, 2))), -1)]:
         with pytest.raises(su.SpeedupError) as e:
@@ -486,6 +486,24 @@ def test_host_wp_nd_program_on_random_polynomials():
         ref = mb.wp(Vf, d, p, x, xb, 0.1)
         scale = mb.wp_abs(Vf, d, p, x, xb, 0.1)
         assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), (V, d, p)
+
+
+def test_host_wp_general_program_at_high_levels():
+    """p = 14, 16, 18 (the paper's compiled W_p reaches 18; 24 196
+    monomial-power entries at p = 18): the library's derivative-symbol
+    program equals the oracle's exact-rational W_p on a polynomial + Gaussian
+    + sech^2 potential at random points."""
+    from oracle import general_v as gv
+    rng = np.random.default_rng(78)
+    gp = su.general_params((0.1, -0.2, 0.5, 0.05, 0.04), [(1.5, 2.0, 0.3)], [(-1.0, 1.0, 0.1)])
+    for p in (14, 16, 18):
+        x, xb = _wp_points(rng, 16, None, 1.0, 0.2)
+        eps = 0.05
+        got = su.speedup_wp("general", gp, p, eps, x, xb)
+        ref = gv.wp(gp, p, x, xb, eps)
+        scale = gv.wp_abs(gp, p, x, xb, eps)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), (p, np.max(np.abs(got - ref) / scale))
+    assert gv.term_count(18) == 24196
 
 
 def test_host_wp_general_program_on_random_potentials():
