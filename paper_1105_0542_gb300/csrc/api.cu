@@ -278,10 +278,9 @@ static int validate(int model, const double *params, int n_params, double a, dou
 
 // Device image of the general program and potential: one allocation holding
 // GeneralDev and the depth-first nodes.
-static int upload_general(su_plan &pl) {
+static int general_image(const su::GeneralEffective &G, const su::GeneralPotential &V, void **d_out) {
     using namespace su;
-    const GeneralEffective &G = *pl.G;
-    const GeneralPotential &V = pl.V;
+    *d_out = nullptr;
     GeneralDev D;
     std::memset(&D, 0, sizeof D);
     D.J = G.J;
@@ -329,15 +328,17 @@ static int upload_general(su_plan &pl) {
     for (int n = 1; n <= kGenMaxSym; ++n) D.inv[n] = 1.0 / (double)n;
     const size_t o_nodes = (sizeof(GeneralDev) + 15) & ~(size_t)15;
     const size_t bytes = o_nodes + nodes.size() * sizeof(GeneralNode);
-    CU(dmalloc(&pl.d_general, bytes), "device allocation (general program)");
-    char *base = static_cast<char *>(pl.d_general);
+    CU(dmalloc(d_out, bytes), "device allocation (general program)");
+    char *base = static_cast<char *>(*d_out);
     D.nodes = reinterpret_cast<const GeneralNode *>(base + o_nodes);
     std::vector<unsigned char> blob(bytes, 0);
     std::memcpy(blob.data(), &D, sizeof D);
     std::memcpy(blob.data() + o_nodes, nodes.data(), nodes.size() * sizeof(GeneralNode));
-    CU(cudaMemcpy(pl.d_general, blob.data(), bytes, cudaMemcpyHostToDevice), "upload general program");
+    CU(cudaMemcpy(*d_out, blob.data(), bytes, cudaMemcpyHostToDevice), "upload general program");
     return SU_OK;
 }
+
+static int upload_general(su_plan &pl) { return general_image(*pl.G, pl.V, &pl.d_general); }
 
 // The level tables of a plan (rows d = 0..S-1 for levels n = S..1), each
 // scaled for the kernel and rounded to its precision: host work only.
@@ -1113,13 +1114,38 @@ int su_fault_inject(int kind, int64_t arg) {
 // The level-p table of the single-slice weight at eps = t (kernel precision)
 // and the sampler parameters that evaluate it, for the evolution operator.
 static int evolution_setup(int model, const double *params, int n_params, int p, double t, double L, int n,
-                           int precision, std::vector<unsigned char> &blob, su::SamplerParams &P) {
+                           int precision, std::vector<unsigned char> &blob, su::SamplerParams &P,
+                           void **d_general) {
+    *d_general = nullptr;
     if (!(t > 0) || !std::isfinite(t)) return fail(SU_EINVAL, "t must be finite and > 0");
     if (!(L > 0) || !std::isfinite(L)) return fail(SU_EINVAL, "L must be finite and > 0");
     if (n < 2 || n > 65536) return fail(SU_EINVAL, "n must be in 2..65536");
     if (p < 1 || p > SU_MAX_P) return fail(SU_EINVAL, "p must be in 1..%d", SU_MAX_P);
     if (precision != SU_FP64 && precision != SU_FP32) return fail(SU_EINVAL, "unknown precision");
-    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the evolution operator takes the collapsed-table models only");
+    if (model == SU_GENERAL) {
+        // the derivative-symbol program of W_p for a general potential (double only)
+        if (precision != SU_FP64) return fail(SU_ENOTSUP, "the general potential is evaluated in double only");
+        if (p > su::kGenMaxP) return fail(SU_ENOTSUP, "the general potential supports p <= %d", su::kGenMaxP);
+        su::GeneralPotential V;
+        std::string err;
+        int rc = su::general_potential(params, n_params, V, err);
+        std::shared_ptr<const su::GeneralEffective> G;
+        if (!rc) G = general_program(p, rc, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+        std::vector<double> T;
+        su::general_table(*G, t, T);
+        for (double v : T)
+            if (!std::isfinite(v)) return fail(SU_ENONFINITE, "a coefficient of W_p is not finite at t = %g", t);
+        blob.assign(T.size() * sizeof(double), 0);
+        std::memcpy(blob.data(), T.data(), blob.size());
+        std::memset(&P, 0, sizeof P);
+        P.ring = su::RING_GENERAL;
+        P.M = (int)T.size();
+        rc = general_image(*G, V, d_general);
+        if (rc) return rc;
+        P.general = static_cast<const su::GeneralDev *>(*d_general);
+        return SU_OK;
+    }
     su::Effective E;
     std::string err;
     int rc = su::build_effective(model, params, n_params, p, E, err);
@@ -1152,7 +1178,9 @@ int speedup_evolution_matrix(int model, const double *params, int n_params, int 
     if (!d_U) return fail(SU_EINVAL, "output missing");
     std::vector<unsigned char> blob;
     su::SamplerParams P;
-    int rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P);
+    void *d_gen = nullptr;
+    int rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P, &d_gen);
+    std::unique_ptr<void, cudaError_t (*)(void *)> gen_guard(d_gen, cudaFree);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     void *d_tab = nullptr;
@@ -1191,7 +1219,9 @@ int speedup_evolution_band(int model, const double *params, int n_params, int p,
     if (capacity < need) return fail(SU_EINVAL, "the band needs %lld bytes, %lld given", (long long)need, (long long)capacity);
     std::vector<unsigned char> blob;
     su::SamplerParams P;
-    rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P);
+    void *d_gen = nullptr;
+    rc = evolution_setup(model, params, n_params, p, t, L, n, precision, blob, P, &d_gen);
+    std::unique_ptr<void, cudaError_t (*)(void *)> gen_guard(d_gen, cudaFree);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     void *d_tab = nullptr;

@@ -35,9 +35,14 @@ __global__ void __launch_bounds__(256) evolution_kernel(const __grid_constant__ 
     if (ti > tj) return;
     extern __shared__ __align__(16) unsigned char esm[];
     __shared__ double tile[32][33];
-    R *tab = reinterpret_cast<R *>(esm);
+    // the general potential's program table (thousands of entries) is read
+    // from global memory, every lane the same entry; the others are staged
+    constexpr bool kStage = RING != RING_GENERAL;
+    R *tab_s = reinterpret_cast<R *>(esm);
+    const R *tab = kStage ? tab_s : gtab;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int k = tid; k < P.M; k += blockDim.x * blockDim.y) tab[k] = gtab[k];
+    if (kStage)
+        for (int k = tid; k < P.M; k += blockDim.x * blockDim.y) tab_s[k] = gtab[k];
     __syncthreads();
     const int j = tj * 32 + threadIdx.x;
     // grid points rounded as (k Delta) + (-L), the last one L itself
@@ -78,8 +83,11 @@ __global__ void __launch_bounds__(256) band_kernel(const __grid_constant__ Sampl
                                                    double t, double lognorm, int w, int64_t pitch,
                                                    double *__restrict__ D) {
     extern __shared__ __align__(16) unsigned char esm[];
-    R *tab = reinterpret_cast<R *>(esm);
-    for (int k = threadIdx.x; k < P.M; k += blockDim.x) tab[k] = gtab[k];
+    constexpr bool kStage = RING != RING_GENERAL;   // as in evolution_kernel
+    R *tab_s = reinterpret_cast<R *>(esm);
+    const R *tab = kStage ? tab_s : gtab;
+    if (kStage)
+        for (int k = threadIdx.x; k < P.M; k += blockDim.x) tab_s[k] = gtab[k];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -236,6 +244,9 @@ const void *pick_evolution(int ring) {
     switch (ring) {
         case RING_EVEN: return (const void *)evolution_kernel<R, RING_EVEN>;
         case RING_X: return (const void *)evolution_kernel<R, RING_X>;
+        case RING_GENERAL:
+            if constexpr (sizeof(R) == 8) return (const void *)evolution_kernel<double, RING_GENERAL>;
+            return nullptr;
         default: return (const void *)evolution_kernel<R, RING_TANH2>;
     }
 }
@@ -245,6 +256,9 @@ const void *pick_band(int ring) {
     switch (ring) {
         case RING_EVEN: return (const void *)band_kernel<R, RING_EVEN>;
         case RING_X: return (const void *)band_kernel<R, RING_X>;
+        case RING_GENERAL:
+            if constexpr (sizeof(R) == 8) return (const void *)band_kernel<double, RING_GENERAL>;
+            return nullptr;
         default: return (const void *)band_kernel<R, RING_TANH2>;
     }
 }
@@ -254,7 +268,8 @@ const void *pick_band(int ring) {
 cudaError_t launch_evolution(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
                              double t, double lognorm, double *U, cudaStream_t st) {
     const void *fn = precision == SU_FP32 ? pick_evolution<float>(P.ring) : pick_evolution<double>(P.ring);
-    const size_t smem = (size_t)P.M * (precision == SU_FP32 ? sizeof(float) : sizeof(double));
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = P.ring == RING_GENERAL ? 0 : (size_t)P.M * (precision == SU_FP32 ? sizeof(float) : sizeof(double));
     const dim3 block(32, 8), grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
     void *args[] = {(void *)&P, (void *)&tab, (void *)&L, (void *)&delta, (void *)&n, (void *)&t, (void *)&lognorm,
                     (void *)&U};
@@ -269,7 +284,8 @@ namespace su {
 cudaError_t launch_band(const SamplerParams &P, int precision, const void *tab, double L, double delta, int n,
                         double t, double lognorm, int w, int64_t pitch, double *D, cudaStream_t st) {
     const void *fn = precision == SU_FP32 ? pick_band<float>(P.ring) : pick_band<double>(P.ring);
-    const size_t smem = (size_t)P.M * (precision == SU_FP32 ? sizeof(float) : sizeof(double));
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = P.ring == RING_GENERAL ? 0 : (size_t)P.M * (precision == SU_FP32 ? sizeof(float) : sizeof(double));
     const dim3 block(256), grid((unsigned)((n + 255) / 256), (unsigned)((w + kKPerCta) / kKPerCta));
     void *args[] = {(void *)&P, (void *)&tab, (void *)&L, (void *)&delta, (void *)&n, (void *)&t,
                     (void *)&lognorm, (void *)&w, (void *)&pitch, (void *)&D};

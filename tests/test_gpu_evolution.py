@@ -154,3 +154,45 @@ def test_figure3_spectra_on_the_paper_grid(params, t, L, V):
     assert np.abs(G - np.eye(nev)).max() <= 1e-10
     g = vec[0].cpu().numpy()
     assert (g * np.sign(g[n // 2]) > -1e-12).all()      # the ground state has no node
+
+
+def _morse_params(D, a, x0):
+    """D (1 - e^{-a (x - x0)})^2 = D - 2D e^{-a (x - x0)} + D e^{-2a (x - x0)}"""
+    return list(su.general_params((D,), (), (), [(-2.0 * D, a, x0), (D, 2.0 * a, x0)]))
+
+
+def test_general_potential_band_equals_dense_and_oracle():
+    """The evolution operator of a general potential (W_p from the
+    derivative-symbol program): band storage equal to the dense matrix bit
+    for bit, and the dense matrix equal to the oracle's (general_v W_p) in
+    the exponent."""
+    gp = list(su.general_params((0.0, 0.0, 0.5), [(-4.0, 1.5, 0.4)], [(-1.0, 2.0, -0.3)]))
+    p, t, L, n = 8, 0.05, 5.0, 151
+    U = _device_matrix("general", gp, p, t, L, n).cpu().numpy()
+    w, pitch = su.su_evolution_band_size(t, L, n)
+    D = torch.full(((w + 1) * pitch,), float("nan"), dtype=torch.float64, device="cuda")
+    su.speedup_evolution_band("general", gp, p, t, L, n, D)
+    torch.cuda.synchronize()
+    Dh = D.cpu().numpy().reshape(w + 1, pitch)
+    for k in range(w + 1):
+        assert np.array_equal(Dh[k, :n - k], np.diagonal(U, k)), k
+    x = ev.grid(L, n)
+    ref = ev.evolution_matrix_general(gp, p, t, x)
+    live = (ref > 0) & (U > 0)
+    assert live.sum() > 3 * n
+    assert np.abs(np.log(U[live]) - np.log(ref[live])).max() <= 1e-11
+
+
+@pytest.mark.parametrize("name,params,p,t,L,n,ref", [
+    ("morse", _morse_params(12.5, 1.0, -5.1), 10, 0.02, 7.0, 701,
+     [5.0 * (k + 0.5) - 25.0 * (k + 0.5) ** 2 / 50.0 for k in range(4)]),
+    ("poeschl-teller", list(su.general_params((), (), [(-6.0, 1.0, 0.0)])), 8, 0.02, 20.0, 2001,
+     [-(3.0 - k) ** 2 / 2.0 for k in range(3)]),
+])
+def test_general_potential_spectrum_is_the_closed_form(name, params, p, t, L, n, ref):
+    """Sec. 5 with a general potential through the band eigensolver: the
+    Morse levels w (n + 1/2) - w^2 (n + 1/2)^2 / (4D) (w = a sqrt(2D)) and the
+    Poeschl-Teller levels -(l - n)^2 / 2 (l = 3), within 1e-9."""
+    E, R, info = su.speedup_evolution_spectrum("general", params, p, t, L, n, len(ref))
+    assert info["converged"] == 1
+    assert np.abs(np.array(E) - np.array(ref)).max() <= 1e-9, np.array(E) - np.array(ref)
