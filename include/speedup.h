@@ -64,8 +64,9 @@ extern "C" {
  * W_p is evaluated per slice from V's derivatives at the slice midpoint and
  * the monomials of W_p in them (1629 monomial-power entries at p = 12, 24 196
  * at p = 18), so it needs no collapsed table: p <= 18, SU_FP64 only, su_plan_* /
- * speedup_amplitude / speedup_logweights / su_autotune only; everything else
- * answers SU_ENOTSUP. */
+ * speedup_amplitude / speedup_logweights / su_autotune and the evolution
+ * operator (speedup_evolution_matrix / _band / _spectrum) only; everything
+ * else answers SU_ENOTSUP. */
 #define SU_GENERAL 5
 
 /* ---- arithmetic of the per-slice W_p evaluation --------------------------- */
@@ -568,7 +569,7 @@ int su_plan_finalize(const su_plan *plan, const double *h_tuples, const void *d_
  *   t     : propagation time of one slice, > 0.
  *   L     : grid half-width, > 0.   n : grid points, 2..65536.
  *   precision : SU_FP64 or SU_FP32 (W_p in float; the free factor and the
- *           output in double).
+ *           output in double); SU_GENERAL in SU_FP64 only.
  *   d_U   : device, n*n doubles, row-major.
  * Work on stream; returns after the matrix is written (the stream is
  * synchronised).  Errors: SU_EINVAL, SU_ENONFINITE (a coefficient is not
