@@ -98,6 +98,13 @@ typedef struct {
                              1, doubled while the per-item tuples would exceed
                              512 MB and as many CTAs stay resident).  The shape
                              changes the order of the floating-point sums only. */
+    int kernel;           /* 0 (default): a single-precision plan with 32-slice
+                             segments whose level tables have a shape compiled
+                             into the library (the even-ring shapes of the
+                             harmonic oscillator and of the quartic potentials
+                             at p <= 18, see su_fixed_shape) runs the sampler
+                             specialised for that shape; 1: always the generic
+                             sampler.  Both give the same results bit for bit. */
 } su_options;
 
 /* per bisection level n = 0..s (N = 2^n slices) */
@@ -703,6 +710,18 @@ int su_autotune_clear(void);
 
 /* The launch shape a plan uses. */
 int su_plan_shape(const su_plan *plan, int *seg_log2, int *rounds);
+
+/* The sampler a plan launches: *fixed_shape = the index of the table shape
+ * compiled into it (see su_fixed_shape), or -1 for the generic sampler. */
+int su_plan_kernel(const su_plan *plan, int *fixed_shape);
+
+/* Host only: the index of the compiled table shape (0..19) equal to the
+ * shape of the collapsed W_p tables of this model and level p (Eq. SNp in
+ * powers of xb^2 and z; the shape does not depend on eps), or -1 if none
+ * is.  A single-precision plan of that model and p with 32-slice segments
+ * and width_factor = 1 runs the sampler specialised for that shape unless
+ * opt->kernel = 1.  SU_ENOTSUP for the general potential (no table). */
+int su_fixed_shape(int model, const double *params, int n_params, int p, int *index);
 
 
 /*

@@ -12,7 +12,7 @@ from ._binding import (  # noqa: F401
     speedup_evolution_matrix, speedup_evolution_band, speedup_evolution_spectrum, su_evolution_band_size, speedup_generate_coeffs, speedup_generate_nd, speedup_logweights,
     speedup_logweights_nd, speedup_normals, speedup_philox_words,
     speedup_proposal_logweights, speedup_train_proposal, speedup_wp, speedup_wp_nd, su_autotune, su_autotune_clear, su_batch_autotune,
-    su_fault_inject, su_fit_continuum,
+    su_fault_inject, su_fit_continuum, su_fixed_shape,
     su_fma_peak,
     su_last_error, su_mlp_loss_grad, su_version,
 )

@@ -33,6 +33,7 @@ EXPORTS = [
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
     "su_fit_continuum", "speedup_wp", "speedup_wp_nd", "su_batch_plan_shape", "su_batch_autotune",
     "speedup_amplitude_judged", "su_evolution_band_size", "speedup_evolution_band", "speedup_evolution_spectrum",
+    "su_plan_kernel", "su_fixed_shape",
 ]
 JUDGE_REASONS = {0: "plain faster", 1: "proposal faster", 2: "proposal unusable", 3: "plain unusable",
                  4: "pilots disagree"}
@@ -50,7 +51,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_blocks", ctypes.c_int), ("hierarchy", ctypes.c_int),
                 ("instance", ctypes.c_uint32), ("width_factor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("sample0", ctypes.c_int64), ("seg_log2", ctypes.c_int),
-                ("rounds", ctypes.c_int)]
+                ("rounds", ctypes.c_int), ("kernel", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -153,6 +154,8 @@ def load(build_if_missing=True):
     L.su_plan_execute.argtypes = [vp, vp, vp, vp, pi]
     L.su_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
     L.su_plan_shape.argtypes = [vp, pi, pi]
+    L.su_plan_kernel.argtypes = [vp, pi]
+    L.su_fixed_shape.argtypes = [i32, pd, i32, i32, pi]
     L.su_autotune.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
                               ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
     L.su_autotune_clear.argtypes = []
@@ -269,7 +272,7 @@ def _stream(s):
 
 
 def options(precision="fp64", n_blocks=64, hierarchy=True, instance=0, width_factor=1.0, stream=None,
-            sample0=0, seg_log2=0, rounds=0):
+            sample0=0, seg_log2=0, rounds=0, kernel="auto"):
     o = Options()
     load().su_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -281,6 +284,7 @@ def options(precision="fp64", n_blocks=64, hierarchy=True, instance=0, width_fac
     o.sample0 = int(sample0)
     o.seg_log2 = int(seg_log2)
     o.rounds = int(rounds)
+    o.kernel = {"auto": 0, "generic": 1}[kernel] if isinstance(kernel, str) else int(kernel)
     return o
 
 
@@ -392,6 +396,14 @@ def speedup_generate_coeffs(model, params, p, eps):
     ncol = shape[0]
     lens = [shape[2 + j] for j in range(ncol)]
     return np.array(tab[:nt.value]), ncol, shape[1], lens
+
+
+def su_fixed_shape(model, params, p):
+    """Index of the compiled table shape of (model, p), or -1 (host only)."""
+    pr, npar = _params(params)
+    k = ctypes.c_int(0)
+    _check(load().su_fixed_shape(_model(model), pr, npar, int(p), ctypes.byref(k)))
+    return k.value
 
 
 def speedup_logweights(model, params, a, b, T, p, s, sample0, n_samples, seed, out, **kw):
@@ -738,6 +750,13 @@ class Plan:
         f, r = ctypes.c_int(0), ctypes.c_int(0)
         _check(load().su_plan_shape(self._h, ctypes.byref(f), ctypes.byref(r)))
         return f.value, r.value
+
+    def su_plan_kernel(self):
+        """Index of the table shape compiled into the sampler this plan
+        launches, or -1 for the generic sampler."""
+        k = ctypes.c_int(0)
+        _check(load().su_plan_kernel(self._h, ctypes.byref(k)))
+        return k.value
 
     def su_plan_execute_range(self, b0, b1, d_tuples, d_scratch, stream=None):
         """Sample error blocks [b0, b1) only (checkpoint / resume); returns launches."""

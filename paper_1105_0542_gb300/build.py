@@ -23,8 +23,11 @@ SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "
 INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3, 0)]
 # double-precision samplers that read tables too large for shared memory from global memory
 INSTANCES += [(64, ring, 1) for ring in (0, 1, 2)]
+# single-precision even-ring samplers with the table shapes of fixed_shapes.h
+# compiled in, spread over four units
+FIXED_GROUPS = 4
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",
-           "proposal.h", "train.h", "philox.cuh", "spectrum.h", "erf_poly.h"]
+           "proposal.h", "train.h", "philox.cuh", "spectrum.h", "erf_poly.h", "fixed_shapes.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -73,6 +76,7 @@ def build(force=False, verbose=False):
     os.makedirs(LIBDIR, exist_ok=True)
     jobs = [(os.path.join(CSRC, "sampler_inst.cu"), {"SU_PREC": p, "SU_RING": r, "SU_GTAB": g})
             for p, r, g in INSTANCES]
+    jobs += [(os.path.join(CSRC, "sampler_inst.cu"), {"SU_FIXED": g}) for g in range(FIXED_GROUPS)]
     jobs += [(os.path.join(CSRC, f), {}) for f in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         results = list(ex.map(lambda j: _compile(j, verbose), jobs))

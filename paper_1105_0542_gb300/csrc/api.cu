@@ -28,6 +28,7 @@
 #include "generator.h"
 #include "mlp.cuh"
 #include "proposal.h"
+#include "fixed_shapes.h"
 #include "sampler.h"
 #include "spectrum.h"
 #include "train.h"
@@ -269,6 +270,7 @@ static int validate(int model, const double *params, int n_params, double a, dou
     if (o.sample0 < 0 || o.sample0 + n_mc > kMaxSamples) return fail(SU_EINVAL, "sample0 out of range");
     if (o.seg_log2 < 0 || o.seg_log2 > su::kMaxFine) return fail(SU_EINVAL, "seg_log2 must be in 0..5");
     if (o.rounds < 0 || o.rounds > 8) return fail(SU_EINVAL, "rounds must be in 0..8");
+    if (o.kernel != 0 && o.kernel != 1) return fail(SU_EINVAL, "kernel must be 0 or 1");
     if (model == SU_GENERAL) {
         if (p > su::kGenMaxP) return fail(SU_ENOTSUP, "the general potential supports p <= %d", su::kGenMaxP);
         if (o.precision != SU_FP64) return fail(SU_ENOTSUP, "the general potential is evaluated in double only");
@@ -435,6 +437,7 @@ static int plan_shape(su_plan &pl, int sms, int smem_max) {
     // read from global memory instead
     P.rounds = 1;
     P.tab_global = 0;
+    P.generic = pl.opt.kernel == 1;
     if (sampler_smem_bytes(P, prec) > (size_t)smem_max) {
         if (prec != SU_FP64) return fail(SU_ENOTSUP, "the level tables do not fit shared memory in single precision");
         P.tab_global = 1;
@@ -720,6 +723,23 @@ int su_plan_shape(const su_plan *pl, int *seg_log2, int *rounds) {
     if (!pl) return fail(SU_EINVAL, "plan missing");
     if (seg_log2) *seg_log2 = pl->s > 0 ? pl->P.F : 0;
     if (rounds) *rounds = pl->s > 0 ? pl->P.rounds : 0;
+    return SU_OK;
+}
+
+int su_plan_kernel(const su_plan *pl, int *fixed_shape) {
+    if (!pl || !fixed_shape) return fail(SU_EINVAL, "plan or output missing");
+    *fixed_shape = pl->s > 0 ? su::sampler_fixed_shape(pl->P, pl->opt.precision) : -1;
+    return SU_OK;
+}
+
+int su_fixed_shape(int model, const double *params, int n_params, int p, int *index) {
+    if (!index) return fail(SU_EINVAL, "output missing");
+    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the general potential has no collapsed table");
+    su::Effective E;
+    std::string err;
+    const int rc = su::build_effective(model, params, n_params, p, E, err);
+    if (rc) return fail(rc, "%s", err.c_str());
+    *index = E.shape.ring == su::RING_EVEN ? su::fixed_shape_index(E.shape.ncol, E.shape.len.data()) : -1;
     return SU_OK;
 }
 

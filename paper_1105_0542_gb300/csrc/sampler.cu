@@ -27,6 +27,11 @@ const void *batch_entry_f64_2();
 const void *batch_entry_f32_0();
 const void *batch_entry_f32_1();
 const void *batch_entry_f32_2();
+const void *sampler_fixed_entry_0(int k);
+const void *sampler_fixed_entry_1(int k);
+const void *sampler_fixed_entry_2(int k);
+const void *sampler_fixed_entry_3(int k);
+static_assert(kFixedGroups == 4, "one sampler_fixed_entry_g per group");
 
 namespace {
 
@@ -128,7 +133,28 @@ __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_
     }
 }
 
+// the single-precision sampler with this plan's table shape compiled in, if
+// there is one (fixed_shapes.h): even ring, 2^kMaxFine-slice segments, no
+// width-factor weight
+int fixed_index(const SamplerParams &P, int precision) {
+    if (precision != SU_FP32 || P.generic || P.ring != RING_EVEN || P.tab_global || P.F != kMaxFine || P.wf_on)
+        return -1;
+    return fixed_shape_index(P.ncol, P.len);
+}
+
+const void *pick_fixed(const SamplerParams &P, int precision) {
+    const int k = fixed_index(P, precision);
+    if (k < 0) return nullptr;
+    switch (k % kFixedGroups) {
+        case 0: return sampler_fixed_entry_0(k);
+        case 1: return sampler_fixed_entry_1(k);
+        case 2: return sampler_fixed_entry_2(k);
+        default: return sampler_fixed_entry_3(k);
+    }
+}
+
 const void *pick(const SamplerParams &P, int precision) {
+    if (const void *fn = pick_fixed(P, precision)) return fn;
     if (P.ring == RING_GENERAL) return precision == SU_FP64 ? sampler_entry_f64_3() : nullptr;
     if (P.tab_global) {
         if (precision != SU_FP64) return nullptr;
@@ -147,6 +173,8 @@ const void *batch_fn(int ring, int precision) {
         return ring == RING_EVEN ? batch_entry_f32_0() : ring == RING_X ? batch_entry_f32_1() : batch_entry_f32_2();
     return ring == RING_EVEN ? batch_entry_f64_0() : ring == RING_X ? batch_entry_f64_1() : batch_entry_f64_2();
 }
+
+int sampler_fixed_shape(const SamplerParams &P, int precision) { return pick_fixed(P, precision) ? fixed_index(P, precision) : -1; }
 
 size_t batch_smem_bytes(const BatchParams &B, int precision) {
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);

@@ -52,6 +52,7 @@ struct SamplerParams {
     int ring, ncol, M;
     int len[SU_MAX_P];
     int tab_global;           // 1: the level tables are read from global memory (too large to stage)
+    int generic;              // 1: never the compiled-shape sampler (su_options.kernel = 1)
     double alpha;
     const void *tables;       // device, levels * M elements of the kernel's precision
     // Philox stream
@@ -113,6 +114,8 @@ struct BatchParams {
 
 // dynamic shared memory the sampler needs
 size_t sampler_smem_bytes(const SamplerParams &P, int precision);
+// the compiled table shape the sampler launch of P runs with, or -1 (generic)
+int sampler_fixed_shape(const SamplerParams &P, int precision);
 // max resident CTAs per SM for the sampler (after opting in to its smem)
 int sampler_occupancy(const SamplerParams &P, int precision, size_t smem);
 

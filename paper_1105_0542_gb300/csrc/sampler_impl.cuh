@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "boxmuller.cuh"
+#include "fixed_shapes.h"
 #include "philox.cuh"
 #include "generator.h"
 #include "sampler.h"
@@ -267,6 +268,87 @@ struct Batch {
     static constexpr int B = 8;
 };
 
+// The path code's view of the table shape when it is compiled in (shape K of
+// fixed_shapes.h): M and ncol are constants, the column lengths a run-time
+// copy for the few places that index them with a run-time column (the
+// coarse levels' single slices).  ShapeOf<SP>::value is K, or -1 for the
+// run-time shapes of SamplerParams and BatchView.
+template <int K>
+struct FixedView {
+    static constexpr int M = fixed_M(K);
+    static constexpr int ncol = fixed_ncol(K);
+    int len[SU_MAX_P];
+    double alpha, lwf, hcoef;
+    int wf_on;
+    const GeneralDev *general;
+};
+
+template <typename SP>
+struct ShapeOf {
+    static constexpr int value = -1;
+};
+template <int K>
+struct ShapeOf<FixedView<K>> {
+    static constexpr int value = K;
+};
+
+// Columns J, J-1, .., 0 of the packed nested Horner with shape K compiled
+// in: acc <- acc Y + H_j(Z), H_j the column's Horner in Z, the chains
+// started as in level_sum (fma(c_top, Z, c_next); a one-entry column goes
+// straight into acc).
+template <int K, int J, int BP>
+__device__ __forceinline__ void fixed_columns(float2 (&acc)[BP], const float2 (&Y)[BP], const float2 (&Z)[BP],
+                                              const float2 *__restrict__ tab) {
+    if constexpr (J >= 0) {
+        constexpr int L = fixed_len(K, J);
+        constexpr int off = fixed_off(K, J);
+        if constexpr (L == 1) {
+            const float2 c = tab[off];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
+        } else {
+            float2 h[BP];
+            const float2 c = tab[off + L - 1], c0 = tab[off + L - 2];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
+#pragma unroll
+            for (int i = L - 3; i >= 0; --i) {
+                const float2 ci = tab[off + i];
+#pragma unroll
+                for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
+            }
+#pragma unroll
+            for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
+        }
+        fixed_columns<K, J - 1, BP>(acc, Y, Z, tab);
+    }
+}
+
+// the whole table: the last column starts the outer Horner in xb^2
+template <int K, int BP>
+__device__ __forceinline__ void fixed_horner(float2 (&acc)[BP], const float2 (&Y)[BP], const float2 (&Z)[BP],
+                                             const float2 *__restrict__ tab) {
+    constexpr int J = fixed_ncol(K) - 1;
+    constexpr int L = fixed_len(K, J);
+    constexpr int off = fixed_off(K, J);
+    const float2 c = tab[off + L - 1];
+    if constexpr (L == 1) {
+#pragma unroll
+        for (int m = 0; m < BP; ++m) acc[m] = c;
+    } else {
+        const float2 c0 = tab[off + L - 2];
+#pragma unroll
+        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
+#pragma unroll
+        for (int i = L - 3; i >= 0; --i) {
+            const float2 ci = tab[off + i];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
+        }
+    }
+    fixed_columns<K, J - 1, BP>(acc, Y, Z, tab);
+}
+
 template <typename R, int RING, int NS, int STR, int NQ, typename TT, typename SP>
 __device__ __forceinline__ R level_sum(const R (&q)[NQ], const TT *__restrict__ tab, const SP &P, R alpha) {
     if constexpr (RING == RING_GENERAL) {
@@ -308,47 +390,51 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const TT *__restrict__ 
                     Z[m] = make_float2(ring_var<float, RING>(us.x, alpha), ring_var<float, RING>(us.y, alpha));
                 }
             }
-            int off = P.M;
-            {   // last column starts the outer Horner in x-bar^2
-                const int L = P.len[P.ncol - 1];
-                off -= L;
-                const float2 c = tab[off + L - 1];
-                if (L == 1) {
+            if constexpr (ShapeOf<SP>::value >= 0) {
+                fixed_horner<ShapeOf<SP>::value, BP>(acc, Y, Z, tab);
+            } else {
+                int off = P.M;
+                {   // last column starts the outer Horner in x-bar^2
+                    const int L = P.len[P.ncol - 1];
+                    off -= L;
+                    const float2 c = tab[off + L - 1];
+                    if (L == 1) {
 #pragma unroll
-                    for (int m = 0; m < BP; ++m) acc[m] = c;
-                } else {
+                        for (int m = 0; m < BP; ++m) acc[m] = c;
+                    } else {
+                        const float2 c0 = tab[off + L - 2];
+#pragma unroll
+                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
+                    }
+#pragma unroll 4
+                    for (int i = L - 3; i >= 0; --i) {
+                        const float2 ci = tab[off + i];
+#pragma unroll
+                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
+                    }
+                }
+                for (int j = P.ncol - 2; j >= 0; --j) {
+                    const int L = P.len[j];
+                    off -= L;
+                    const float2 c = tab[off + L - 1];
+                    if (L == 1) {
+#pragma unroll
+                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
+                        continue;
+                    }
+                    float2 h[BP];
                     const float2 c0 = tab[off + L - 2];
 #pragma unroll
-                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
-                }
+                    for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
 #pragma unroll 4
-                for (int i = L - 3; i >= 0; --i) {
-                    const float2 ci = tab[off + i];
+                    for (int i = L - 3; i >= 0; --i) {
+                        const float2 ci = tab[off + i];
 #pragma unroll
-                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
+                        for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
+                    }
+#pragma unroll
+                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
                 }
-            }
-            for (int j = P.ncol - 2; j >= 0; --j) {
-                const int L = P.len[j];
-                off -= L;
-                const float2 c = tab[off + L - 1];
-                if (L == 1) {
-#pragma unroll
-                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
-                    continue;
-                }
-                float2 h[BP];
-                const float2 c0 = tab[off + L - 2];
-#pragma unroll
-                for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
-#pragma unroll 4
-                for (int i = L - 3; i >= 0; --i) {
-                    const float2 ci = tab[off + i];
-#pragma unroll
-                    for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
-                }
-#pragma unroll
-                for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
             }
 #pragma unroll
             for (int m = 0; m < BP; ++m) {
@@ -832,7 +918,10 @@ struct MinCtas<double, RING_GENERAL> {
     static constexpr int value = 4;
 };
 
-template <typename R, int RING, bool GTAB = false>
+// KS >= 0: the single-precision sampler with table shape KS of
+// fixed_shapes.h compiled in, for plans with 2^kMaxFine-slice segments and
+// no width-factor weight (the host picks it only then).
+template <typename R, int RING, bool GTAB = false, int KS = -1>
 __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ bm32::Tables s_bm32;   // single path
@@ -889,6 +978,17 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
     st.bm32 = &s_bm32;
 
+    FixedView<(KS >= 0 ? KS : 0)> fv;
+    if constexpr (KS >= 0) {
+        static_assert(sizeof(R) == 4 && RING == RING_EVEN, "compiled shapes: single precision, even ring");
+        for (int j = 0; j < SU_MAX_P; ++j) fv.len[j] = P.len[j];
+        fv.alpha = P.alpha;
+        fv.lwf = P.lwf;
+        fv.hcoef = P.hcoef;
+        fv.wf_on = 0;
+        fv.general = nullptr;
+    }
+
     const int warp = tid >> 5, lane = tid & 31;
     for (int64_t item = P.item0 + blockIdx.x; item < P.n_items; item += gridDim.x) {
         const int64_t b = item / P.items_per_block;
@@ -908,7 +1008,10 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
             R *wout = per_sample ? wloc : sw + t;
             const int wstride = per_sample ? 1 : chunk;
             float *qout = (per_sample && P.q_out) ? P.q_out + (start + t) * (int64_t)((1 << P.S) + 1) : nullptr;
-            sample_path_any<R, RING>(P.F, P, pc, tab, qc, zz, st, wout, wstride, qout);
+            if constexpr (KS >= 0)
+                sample_path<R, RING, kMaxFine, false>(fv, pc, tab, qc, zz, st, wout, wstride, qout);
+            else
+                sample_path_any<R, RING>(P.F, P, pc, tab, qc, zz, st, wout, wstride, qout);
             bool bad = false;
             for (int d = 0; d < L; ++d) {
                 const R w = wout[d * wstride];

@@ -7,6 +7,28 @@
 // in parallel.
 #include "sampler_impl.cuh"
 
+#ifdef SU_FIXED
+// SU_FIXED = g: the single-precision even-ring samplers with the table shapes
+// k = g, g + kFixedGroups, .. of fixed_shapes.h compiled in
+namespace su {
+namespace {
+template <int K>
+const void *fixed_entry(int k) {
+    if constexpr (K >= kNumFixed) {
+        return nullptr;
+    } else {
+        if (k == K) return (const void *)sampler_kernel<float, RING_EVEN, false, K>;
+        return fixed_entry<K + kFixedGroups>(k);
+    }
+}
+}  // namespace
+
+#define SU_FIXED_NAME2(g) sampler_fixed_entry_##g
+#define SU_FIXED_NAME(g) SU_FIXED_NAME2(g)
+const void *SU_FIXED_NAME(SU_FIXED)(int k) { return fixed_entry<SU_FIXED>(k); }
+}  // namespace su
+#else
+
 #ifndef SU_PREC
 #error "SU_PREC must be 64 or 32"
 #endif
@@ -44,3 +66,4 @@ const void *SU_CAT(batch_entry_f, SU_PREC, SU_RING)() {
 }
 #endif
 }  // namespace su
+#endif  // SU_FIXED

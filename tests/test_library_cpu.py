@@ -152,6 +152,26 @@ def test_generator_term_counts_of_the_anharmonic_oscillator():
     assert counts == [8, 21, 27, 48]
 
 
+def test_compiled_shapes_cover_the_quartic_and_harmonic_tables():
+    """Every even-ring table of the harmonic oscillator and of the quartic
+    potentials at p = 1..18 has a compiled shape (the single-precision plans
+    of the convergence sweep all run specialised samplers); the shape is the
+    generator's, so the quartic shapes are distinct per p and shared by the
+    anharmonic oscillator and the double well; other rings and the polynomial
+    model keep the generic sampler."""
+    aho = [su.su_fixed_shape("aho", [1.0, 10.0], p) for p in range(1, 19)]
+    assert min(aho) >= 0 and len(set(aho)) == 18
+    assert aho == [su.su_fixed_shape("dw", [5.0], p) for p in range(1, 19)]
+    assert aho == [su.su_fixed_shape("aho", [0.0, 1.0], p) for p in range(1, 19)]
+    ho = {su.su_fixed_shape("ho", [1.0], p) for p in range(2, 19)}
+    assert len(ho) == 1 and min(ho) >= 0 and su.su_fixed_shape("ho", [1.0], 1) >= 0
+    assert su.su_fixed_shape("mpt", [3.0, 1.0], 10) == -1
+    assert su.su_fixed_shape("poly", [0.0, 1.0, 0.5], 4) == -1
+    with pytest.raises(su.SpeedupError) as e:
+        su.su_fixed_shape("general", su.general_params(poly=(0, 0, 1)), 4)
+    assert e.value.code == -6
+
+
 @pytest.mark.parametrize("args,kw", [
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 0, 4, 100, 1), {}),        # p = 0
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 145, 4, 100, 1), {}),      # p = 145
@@ -166,6 +186,7 @@ def test_generator_term_counts_of_the_anharmonic_oscillator():
     ((9, [1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {}),                  # unknown model
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"seg_log2": 6}),   # launch shape out of range
     (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"rounds": 9}),
+    (("aho", [1.0, 1.0], 0.0, 1.0, 1.0, 4, 4, 10, 1), {"kernel": 2}),
 ])
 def test_invalid_arguments_are_rejected(args, kw):
     with pytest.raises(su.SpeedupError) as e:
