@@ -201,6 +201,8 @@ size_t sampler_smem_bytes(const SamplerParams &P, int precision) {
     off += rs * (size_t)(C > 1 ? C + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;
     if (P.wf_on) off += sizeof(double) * (size_t)(P.S + 1) * kThreads;
+    off = (off + 15) & ~(size_t)15;
+    if (precision == SU_FP32) off += sizeof(float4) * (size_t)staged_quads(P.F) * kThreads;
     if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;
 }

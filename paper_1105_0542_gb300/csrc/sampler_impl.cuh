@@ -77,6 +77,8 @@ struct Stream {
     uint32_t inst, slo, shi;
     const bm::Tables *bm;   // shared-memory node tables (double path)
     const bm32::Tables *bm32;   // shared-memory node tables (single path)
+    float4 *zq;                 // single path: this thread's column (stride kThreads) of
+                                // staged quads, levels 3..F of a segment (see sample_path)
     __device__ __forceinline__ uint4 words(uint32_t call) const {
         return philox4x32_10(make_uint4(call, inst, slo, shi), key);
     }
@@ -604,6 +606,24 @@ struct PathCfg {
     const R *sigma;
 };
 
+// The single-path samplers stage a segment's normals of levels 3..F in shared
+// memory (Stream::zq) from one rolled loop before its bisection: the same
+// normals, but one copy of the Philox and Box-Muller code in the segment loop
+// instead of one per quad, which keeps that loop inside the instruction
+// cache.  The batched kernel (SP = BatchView) generates them in place.
+template <typename SP>
+struct StagesNormals {
+    static constexpr bool value = true;
+};
+struct BatchView;
+template <>
+struct StagesNormals<BatchView> {
+    static constexpr bool value = false;
+};
+
+// quads staged per thread for 2^F-slice segments
+__host__ __device__ constexpr int staged_quads(int F) { return F >= 3 ? (1 << (F - 2)) - 1 : 0; }
+
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
@@ -668,7 +688,24 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
 #pragma unroll
     for (int d = 0; d <= F; ++d) acc[d] = 0;
 
+    constexpr bool kStaged = sizeof(R) == 4 && StagesNormals<SP>::value && F >= 3;
     for (int c = 0; c < C; ++c) {
+        if constexpr (kStaged) {
+            // levels l = 3..F: normals j' = 2^(n-1) + c 2^(l-1) + il, whole quads
+            // from quad (2^(n-1) + c 2^(l-1)) / 4 on; slot 2^(l-3) - 1 + il / 4
+            int slot = 0;
+#pragma unroll 1
+            for (int l = 3; l <= F; ++l) {
+                const int n = S - F + l;
+                const uint32_t q0 = ((1u << (n - 1)) + ((uint32_t)c << (l - 1))) >> 2;
+#pragma unroll 1
+                for (int k = 0; k < (1 << (l - 3)); ++k, ++slot) {
+                    float z4[4];
+                    st.quad(q0 + (uint32_t)k, z4);
+                    st.zq[slot * kThreads] = make_float4(z4[0], z4[1], z4[2], z4[3]);
+                }
+            }
+        }
         R q[NF + 1];
         q[0] = C > 1 ? qc[c * kThreads] : pc.a;
         q[NF] = C > 1 ? qc[(c + 1) * kThreads] : pc.b;
@@ -706,7 +743,17 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
                     // j' = j + 1 = 2^(n-1) + c 2^(l-1) + il
                     const uint32_t jp = j + 1;
                     if (l >= 3) {               // aligned: whole quads inside the segment
-                        if ((il & 3) == 0) st.quad(jp >> 2, qq);
+                        if ((il & 3) == 0) {
+                            if constexpr (kStaged) {
+                                const float4 v = st.zq[((1 << (l - 3)) - 1 + (il >> 2)) * kThreads];
+                                qq[0] = v.x;
+                                qq[1] = v.y;
+                                qq[2] = v.z;
+                                qq[3] = v.w;
+                            } else {
+                                st.quad(jp >> 2, qq);
+                            }
+                        }
                         z = qq[il & 3];
                     } else if (l == 2) {
                         if (C == 1) {           // j' = 2, 3: the quad of level 1
@@ -902,6 +949,7 @@ __device__ __forceinline__ void item_lse(const R *sw, int L, int chunk, int cnt,
 // ----------------------------------------------------------- the kernel
 // Shared memory: sw[levels][chunk] (R) | tables[levels][M] (R) | sigma[S+1] (R) |
 //                qc[(C+1)][kThreads] (R) | zz[S+1][kThreads] (double, if wf_on) |
+//                staged quads[2^(F-2) - 1][kThreads] (float4, single path) |
 //                Box-Muller node tables (double path)
 // CTAs per SM the register allocation is sized for: two for the double path
 // (up to 255 registers: its segment, accumulators and Box-Muller state stay
@@ -952,6 +1000,9 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     off = (off + 15) & ~(size_t)15;
     double *zz = reinterpret_cast<double *>(smem_raw + off) + tid;
     off += P.wf_on ? sizeof(double) * (size_t)(P.S + 1) * kThreads : 0;
+    off = (off + 15) & ~(size_t)15;
+    float4 *zq = reinterpret_cast<float4 *>(smem_raw + off) + tid;           // single path only
+    off += sizeof(R) == 4 ? sizeof(float4) * (size_t)staged_quads(P.F) * kThreads : 0;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);   // double path only
 
     // stage the coefficient tables of every sampled level, the widths (and
@@ -977,6 +1028,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     st.inst = P.instance;
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
     st.bm32 = &s_bm32;
+    st.zq = zq;
 
     FixedView<(KS >= 0 ? KS : 0)> fv;
     if constexpr (KS >= 0) {
@@ -1098,6 +1150,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
     st.bm32 = &s_bm32;
+    st.zq = nullptr;
     int cur_shape = -1;
 
     while (true) {
