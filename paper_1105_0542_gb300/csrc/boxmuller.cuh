@@ -314,8 +314,9 @@ __device__ __forceinline__ void tables_init(Tables *t, int tid, int nthreads) {
 __device__ __forceinline__ void pair(uint32_t a, uint32_t b, const Tables *__restrict__ t, float &z0, float &z1) {
     constexpr float kLn2Hi = 0.693145751953125f;         // 0x3F317200: 13 trailing zero bits
     constexpr float kLn2Lo = 1.428606765330187e-06f;     // ln 2 - kLn2Hi
-    const float u1 = ((float)(a >> 8) + 0.5f) * 0x1p-24f;
-    const float u2 = ((float)(b >> 8) + 0.5f) * 0x1p-24f;
+    // ((w >> 8) + 1/2) 2^-24 in one rounding: the scaling is exact
+    const float u1 = fmaf((float)(a >> 8), 0x1p-24f, 0x1p-25f);
+    const float u2 = fmaf((float)(b >> 8), 0x1p-24f, 0x1p-25f);
 
     // ---- -2 ln u1 (u1 >= 2^-25: a normal float)
     const int ib = __float_as_int(u1);
