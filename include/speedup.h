@@ -255,6 +255,14 @@ int su_batch_plan_sizes(const su_batch_plan *plan, int64_t *tuple_bytes, int64_t
  * segment (2^seg_log2 slices), *chunks = work items per error block, *from
  * = 0 (rule) or 1 (stored by su_batch_autotune). */
 int su_batch_plan_shape(const su_batch_plan *plan, int64_t i, int *seg_log2, int *chunks, int *from);
+
+/* The batched kernel a plan launches: *fixed_shape = the index of the table
+ * shape compiled into it (single precision, every instance of one level p
+ * whose shape su_fixed_shape reports; its instances with 32-slice segments
+ * run the specialised path code), or -1.  opt->kernel = 1 forces -1; both
+ * give the same results bit for bit. */
+int su_batch_plan_kernel(const su_batch_plan *plan, int *fixed_shape);
+
 /* asynchronous on stream; the first call builds the plan's CUDA graph (a
  * memset of the queue head and the persistent kernel), later calls replay it
  * (and rebuild it if the buffers change); *launches = graph launches made */

@@ -33,7 +33,7 @@ EXPORTS = [
     "su_plan_create_nd", "speedup_amplitude_nd", "speedup_logweights_nd", "speedup_generate_nd",
     "su_fit_continuum", "speedup_wp", "speedup_wp_nd", "su_batch_plan_shape", "su_batch_autotune",
     "speedup_amplitude_judged", "su_evolution_band_size", "speedup_evolution_band", "speedup_evolution_spectrum",
-    "su_plan_kernel", "su_fixed_shape",
+    "su_plan_kernel", "su_fixed_shape", "su_batch_plan_kernel",
 ]
 JUDGE_REASONS = {0: "plain faster", 1: "proposal faster", 2: "proposal unusable", 3: "plain unusable",
                  4: "pilots disagree"}
@@ -155,6 +155,7 @@ def load(build_if_missing=True):
     L.su_plan_finalize.argtypes = [vp, pd, vp, ctypes.POINTER(LevelResult)]
     L.su_plan_shape.argtypes = [vp, pi, pi]
     L.su_plan_kernel.argtypes = [vp, pi]
+    L.su_batch_plan_kernel.argtypes = [vp, pi]
     L.su_fixed_shape.argtypes = [i32, pd, i32, i32, pi]
     L.su_autotune.argtypes = [i32, pd, i32, d, d, d, i32, i32, i64, u64, ctypes.POINTER(Options),
                               ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), i32, pi]
@@ -610,6 +611,12 @@ class BatchPlan:
         f, k, fr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         _check(load().su_batch_plan_shape(self._h, int(i), ctypes.byref(f), ctypes.byref(k), ctypes.byref(fr)))
         return f.value, k.value, fr.value
+
+    def su_batch_plan_kernel(self):
+        """Index of the table shape compiled into the batched kernel, or -1."""
+        k = ctypes.c_int(0)
+        _check(load().su_batch_plan_kernel(self._h, ctypes.byref(k)))
+        return k.value
 
     def su_batch_plan_execute(self, d_tuples, d_scratch, stream=None):
         n = ctypes.c_int(0)

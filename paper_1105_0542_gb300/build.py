@@ -23,9 +23,9 @@ SOURCES = ["sampler.cu", "api.cu", "generator.cpp", "peaks.cu", "proposal.cu", "
 INSTANCES = [(prec, ring, 0) for prec in (64, 32) for ring in (0, 1, 2)] + [(64, 3, 0)]
 # double-precision samplers that read tables too large for shared memory from global memory
 INSTANCES += [(64, ring, 1) for ring in (0, 1, 2)]
-# single-precision even-ring samplers with the table shapes of fixed_shapes.h
-# compiled in, spread over four units
-FIXED_GROUPS = 4
+# single-precision even-ring samplers and batched kernels with the table
+# shapes of fixed_shapes.h compiled in, spread over eight units (kFixedGroups)
+FIXED_GROUPS = 8
 HEADERS = ["sampler.h", "generator.h", "sampler_impl.cuh", "sampler_inst.cu", "boxmuller.cuh", "mlp.cuh",
            "proposal.h", "train.h", "philox.cuh", "spectrum.h", "erf_poly.h", "fixed_shapes.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1673,6 +1673,10 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     B.C_max = C_max;
     B.L_max = L_max;
     B.tab_max = tab_max;
+    // one table shape that the library has compiled in: the specialised kernel
+    B.fixed_shape = (prec == SU_FP32 && ring == RING_EVEN && shapes.size() == 1 && o.kernel != 1)
+                        ? fixed_shape_index(shapes[0].ncol, shapes[0].len)
+                        : -1;
     pl->smem = batch_smem_bytes(B, prec);
     if (pl->smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d (tables of %lld entries, %d levels)", pl->smem, smem_max,
@@ -1784,6 +1788,12 @@ int su_batch_plan_shape(const su_batch_plan *pl, int64_t i, int *seg_log2, int *
     return SU_OK;
 }
 
+int su_batch_plan_kernel(const su_batch_plan *pl, int *fixed_shape) {
+    if (!pl || !fixed_shape) return fail(SU_EINVAL, "plan or output missing");
+    *fixed_shape = pl->B.fixed_shape;
+    return SU_OK;
+}
+
 int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, void *stream, int *launches) {
     if (!pl) return fail(SU_EINVAL, "plan missing");
     if (!d_tuples || !d_scratch) return fail(SU_EINVAL, "device buffers missing");
@@ -1795,7 +1805,7 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
     B.tuples = static_cast<double *>(d_tuples);
     B.counter = static_cast<int *>(d_scratch);
     B.base.flags = static_cast<int *>(d_scratch) + 1;
-    const void *fn = su::batch_fn(B.base.ring, pl->opt.precision);
+    const void *fn = su::batch_fn(B, pl->opt.precision);
     void *args[] = {&B};
     const int64_t stop = g_fault_queue.exchange(0);
     if (stop > 0) {   // fault injection: the queue ends after `stop` items

@@ -8,7 +8,8 @@
 // double well) at p = 1..18; a plan whose level tables have one of them runs
 // a sampler instantiated for it, with every Horner loop unrolled and every
 // table offset a constant (the same operations in the same order, so the
-// same bits).  Any other shape runs the generic sampler.
+// same bits), and so does a batch plan whose instances all have it.  Any
+// other shape runs the generic kernels.
 //
 // Shape k is coded as nibbles: column j has (code >> 4 j) & 15 entries, the
 // columns run up to the first empty nibble.
@@ -17,7 +18,7 @@
 namespace su {
 
 constexpr int kNumFixed = 20;
-constexpr int kFixedGroups = 4;          // translation units the specialised samplers are spread over
+constexpr int kFixedGroups = 8;          // translation units the specialised kernels are spread over
 
 __host__ __device__ constexpr unsigned fixed_code(int k) {
     return k == 0 ? 0x2u :               // harmonic oscillator, p = 1

@@ -27,11 +27,27 @@ const void *batch_entry_f64_2();
 const void *batch_entry_f32_0();
 const void *batch_entry_f32_1();
 const void *batch_entry_f32_2();
-const void *sampler_fixed_entry_0(int k);
-const void *sampler_fixed_entry_1(int k);
-const void *sampler_fixed_entry_2(int k);
-const void *sampler_fixed_entry_3(int k);
-static_assert(kFixedGroups == 4, "one sampler_fixed_entry_g per group");
+// the compiled-shape kernels of group g = k % kFixedGroups (sampler_inst.cu, SU_FIXED = g)
+#define SU_FIXED_GROUP(g)                        \
+    const void *sampler_fixed_entry_##g(int k); \
+    const void *batch_fixed_entry_##g(int k);
+SU_FIXED_GROUP(0)
+SU_FIXED_GROUP(1)
+SU_FIXED_GROUP(2)
+SU_FIXED_GROUP(3)
+SU_FIXED_GROUP(4)
+SU_FIXED_GROUP(5)
+SU_FIXED_GROUP(6)
+SU_FIXED_GROUP(7)
+#undef SU_FIXED_GROUP
+static_assert(kFixedGroups == 8, "one entry pair per group");
+using FixedEntry = const void *(*)(int);
+static const FixedEntry kSamplerFixed[kFixedGroups] = {
+    sampler_fixed_entry_0, sampler_fixed_entry_1, sampler_fixed_entry_2, sampler_fixed_entry_3,
+    sampler_fixed_entry_4, sampler_fixed_entry_5, sampler_fixed_entry_6, sampler_fixed_entry_7};
+static const FixedEntry kBatchFixed[kFixedGroups] = {
+    batch_fixed_entry_0, batch_fixed_entry_1, batch_fixed_entry_2, batch_fixed_entry_3,
+    batch_fixed_entry_4, batch_fixed_entry_5, batch_fixed_entry_6, batch_fixed_entry_7};
 
 namespace {
 
@@ -144,13 +160,7 @@ int fixed_index(const SamplerParams &P, int precision) {
 
 const void *pick_fixed(const SamplerParams &P, int precision) {
     const int k = fixed_index(P, precision);
-    if (k < 0) return nullptr;
-    switch (k % kFixedGroups) {
-        case 0: return sampler_fixed_entry_0(k);
-        case 1: return sampler_fixed_entry_1(k);
-        case 2: return sampler_fixed_entry_2(k);
-        default: return sampler_fixed_entry_3(k);
-    }
+    return k < 0 ? nullptr : kSamplerFixed[k % kFixedGroups](k);
 }
 
 const void *pick(const SamplerParams &P, int precision) {
@@ -168,7 +178,12 @@ const void *pick(const SamplerParams &P, int precision) {
 
 }  // namespace
 
-const void *batch_fn(int ring, int precision) {
+const void *batch_fn(const BatchParams &B, int precision) {
+    const int ring = B.base.ring;
+    if (precision == SU_FP32 && ring == RING_EVEN && B.fixed_shape >= 0 && B.fixed_shape < kNumFixed) {
+        const int k = B.fixed_shape;
+        return kBatchFixed[k % kFixedGroups](k);
+    }
     if (precision == SU_FP32)
         return ring == RING_EVEN ? batch_entry_f32_0() : ring == RING_X ? batch_entry_f32_1() : batch_entry_f32_2();
     return ring == RING_EVEN ? batch_entry_f64_0() : ring == RING_X ? batch_entry_f64_1() : batch_entry_f64_2();
@@ -185,6 +200,7 @@ size_t batch_smem_bytes(const BatchParams &B, int precision) {
     off = (off + 15) & ~(size_t)15;
     off += (2 * sizeof(double) + rs) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
+    if (precision == SU_FP32) off += sizeof(float4) * (size_t)staged_quads(kMaxFine) * kThreads;
     if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;
 }
@@ -224,7 +240,7 @@ static cudaError_t allow_full_smem(const void *fn) {
 }
 
 int batch_occupancy(const BatchParams &B, int precision, size_t smem) {
-    const void *fn = batch_fn(B.base.ring, precision);
+    const void *fn = batch_fn(B, precision);
     if (allow_full_smem(fn) != cudaSuccess) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) {

@@ -110,6 +110,7 @@ struct BatchParams {
     int64_t tab_max;          // largest L * M: table elements staged per item
     double *tuples;           // per instance from its tup offset
     int *counter;             // work-queue head, zeroed before every launch
+    int fixed_shape;          // >= 0: every instance has this compiled table shape (fixed_shapes.h)
 };
 
 // dynamic shared memory the sampler needs
@@ -167,7 +168,7 @@ cudaError_t launch_sampler(const SamplerParams &P, int precision, int grid, size
                            cudaStream_t st);
 size_t batch_smem_bytes(const BatchParams &B, int precision);
 int batch_occupancy(const BatchParams &B, int precision, size_t smem);
-const void *batch_fn(int ring, int precision);
+const void *batch_fn(const BatchParams &B, int precision);
 // tuples of blocks [b0, b0 + n_blocks) from their items' partial tuples
 cudaError_t launch_combine(const double *partial, double *tuples, int64_t b0, int64_t n_blocks, int levels,
                            int64_t items_per_block, cudaStream_t st);

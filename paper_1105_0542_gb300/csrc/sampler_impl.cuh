@@ -606,20 +606,10 @@ struct PathCfg {
     const R *sigma;
 };
 
-// The single-path samplers stage a segment's normals of levels 3..F in shared
-// memory (Stream::zq) from one rolled loop before its bisection: the same
-// normals, but one copy of the Philox and Box-Muller code in the segment loop
-// instead of one per quad, which keeps that loop inside the instruction
-// cache.  The batched kernel (SP = BatchView) generates them in place.
-template <typename SP>
-struct StagesNormals {
-    static constexpr bool value = true;
-};
-struct BatchView;
-template <>
-struct StagesNormals<BatchView> {
-    static constexpr bool value = false;
-};
+// The single path stages a segment's normals of levels 3..F in shared memory
+// (Stream::zq) from one rolled loop before its bisection: the same normals,
+// but one copy of the Philox and Box-Muller code in the segment loop instead
+// of one per quad, which keeps that loop inside the instruction cache.
 
 // quads staged per thread for 2^F-slice segments
 __host__ __device__ constexpr int staged_quads(int F) { return F >= 3 ? (1 << (F - 2)) - 1 : 0; }
@@ -688,7 +678,7 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
 #pragma unroll
     for (int d = 0; d <= F; ++d) acc[d] = 0;
 
-    constexpr bool kStaged = sizeof(R) == 4 && StagesNormals<SP>::value && F >= 3;
+    constexpr bool kStaged = sizeof(R) == 4 && F >= 3;
     for (int c = 0; c < C; ++c) {
         if constexpr (kStaged) {
             // levels l = 3..F: normals j' = 2^(n-1) + c 2^(l-1) + il, whole quads
@@ -1094,7 +1084,8 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
 // level n = 1..s_i from the same paths.
 // Shared memory: BatchView | tables[L_max * M_max] (R) | sigma[S_max+1] (R) |
 //                qc[(C_max+1)][kThreads] (R) | level states m (R), s, q
-//                (double) [L_max-1][kThreads] | Box-Muller node tables (double path)
+//                (double) [L_max-1][kThreads] | staged quads[2^(kMaxFine-2) - 1]
+//                [kThreads] (float4, single path) | Box-Muller node tables (double path)
 // CTAs per SM for the register budget: the float form fits 96 registers
 // without spills at 5 (the amplitude matrix 3 % faster than at 4).
 template <typename R>
@@ -1113,7 +1104,10 @@ struct BatchView {
     int len[SU_MAX_P];
 };
 
-template <typename R, int RING>
+// KS >= 0: every instance has table shape KS of fixed_shapes.h (single
+// precision, even ring); items with 2^kMaxFine-slice segments run the path
+// code with that shape compiled in.
+template <typename R, int RING, int KS = -1>
 __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -1142,6 +1136,8 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     R *lm = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
+    float4 *zq = reinterpret_cast<float4 *>(smem_raw + off) + tid;           // single path only
+    off += sizeof(R) == 4 ? sizeof(float4) * (size_t)staged_quads(kMaxFine) * kThreads : 0;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
     if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
     if constexpr (sizeof(R) == 4) bm32::tables_init(&s_bm32, tid, kThreads);
@@ -1150,8 +1146,19 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
     st.bm32 = &s_bm32;
-    st.zq = nullptr;
+    st.zq = zq;
     int cur_shape = -1;
+
+    FixedView<(KS >= 0 ? KS : 0)> fv;
+    if constexpr (KS >= 0) {
+        static_assert(sizeof(R) == 4 && RING == RING_EVEN, "compiled shapes: single precision, even ring");
+        for (int j = 0; j < SU_MAX_P; ++j) fv.len[j] = B.shapes[0].len[j];
+        fv.alpha = P.alpha;
+        fv.lwf = 0;
+        fv.hcoef = 0;
+        fv.wf_on = 0;
+        fv.general = nullptr;
+    }
 
     while (true) {
         __syncthreads();   // previous item's shared memory is free
@@ -1206,7 +1213,14 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
             st.slo = (uint32_t)smp;
             st.shi = (uint32_t)((uint64_t)smp >> 32);
             R w[SU_MAX_S];
-            sample_path_plain<R, RING>(in.F, *view, pc, tab, qc, st, w);
+            if constexpr (KS >= 0) {
+                if (in.F == kMaxFine)
+                    sample_path<R, RING, kMaxFine, false>(fv, pc, tab, qc, nullptr, st, w, 1, nullptr);
+                else
+                    sample_path_plain<R, RING>(in.F, *view, pc, tab, qc, st, w);
+            } else {
+                sample_path_plain<R, RING>(in.F, *view, pc, tab, qc, st, w);
+            }
             bad |= isnan(w[0]) || (isinf(w[0]) && w[0] > 0);
             acc.push(w[0]);
             for (int d = 1; d < L; ++d) {

@@ -8,8 +8,9 @@
 #include "sampler_impl.cuh"
 
 #ifdef SU_FIXED
-// SU_FIXED = g: the single-precision even-ring samplers with the table shapes
-// k = g, g + kFixedGroups, .. of fixed_shapes.h compiled in
+// SU_FIXED = g: the single-precision even-ring samplers and batched kernels
+// with the table shapes k = g, g + kFixedGroups, .. of fixed_shapes.h
+// compiled in
 namespace su {
 namespace {
 template <int K>
@@ -21,11 +22,21 @@ const void *fixed_entry(int k) {
         return fixed_entry<K + kFixedGroups>(k);
     }
 }
+template <int K>
+const void *fixed_batch_entry(int k) {
+    if constexpr (K >= kNumFixed) {
+        return nullptr;
+    } else {
+        if (k == K) return (const void *)batch_kernel<float, RING_EVEN, K>;
+        return fixed_batch_entry<K + kFixedGroups>(k);
+    }
+}
 }  // namespace
 
-#define SU_FIXED_NAME2(g) sampler_fixed_entry_##g
-#define SU_FIXED_NAME(g) SU_FIXED_NAME2(g)
-const void *SU_FIXED_NAME(SU_FIXED)(int k) { return fixed_entry<SU_FIXED>(k); }
+#define SU_FIXED_NAME2(a, g) a##_##g
+#define SU_FIXED_NAME(a, g) SU_FIXED_NAME2(a, g)
+const void *SU_FIXED_NAME(sampler_fixed_entry, SU_FIXED)(int k) { return fixed_entry<SU_FIXED>(k); }
+const void *SU_FIXED_NAME(batch_fixed_entry, SU_FIXED)(int k) { return fixed_batch_entry<SU_FIXED>(k); }
 }  // namespace su
 #else
 

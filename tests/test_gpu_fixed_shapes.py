@@ -69,3 +69,35 @@ def test_plan_reports_the_sampler_it_launches(kw, expect_fixed):
     pl = su.Plan("aho", [1.0, 10.0], 0.0, 1.0, 1.0, 10, 10, 1000, 1, **kw)
     assert (pl.su_plan_kernel() >= 0) == expect_fixed
     assert su.Plan("mpt", [3.0, 1.0], 0.0, 1.0, 1.0, 10, 10, 1000, 1, precision="fp32").su_plan_kernel() == -1
+
+
+def _batch(inst, p, kernel, **kw):
+    pl = su.BatchPlan("aho", [1.0, 1.0], p, inst, 20_011, 9, precision="fp32", n_blocks=7, kernel=kernel, **kw)
+    t = torch.empty(pl.tuple_bytes // 8, dtype=torch.float64, device="cuda")
+    sc = torch.empty(pl.scratch_bytes, dtype=torch.uint8, device="cuda")
+    pl.su_batch_plan_execute(t, sc)
+    torch.cuda.synchronize()
+    return pl.su_batch_plan_kernel(), pl.su_batch_plan_finalize(t.cpu().numpy(), sc)
+
+
+def test_batched_kernel_with_the_shape_compiled_in_gives_the_generic_bits():
+    # one level p: the compiled shape; depths 2..8 (segments of 4..32 slices),
+    # the top level only and every level
+    inst = [(-1.0 + 0.3 * i, 0.5 - 0.2 * i, (0.25, 0.5, 1.0, 2.0)[i % 4], 2 + i % 7) for i in range(21)]
+    inst += [{"a": 0.2, "b": -0.4, "T": 1.0, "s": 8, "hierarchy": 1}, {"a": 0.0, "b": 1.0, "T": 0.5, "s": 6,
+                                                                        "hierarchy": 1}]
+    k_auto, got = _batch(inst, 12, "auto")
+    k_gen, ref = _batch(inst, 12, "generic")
+    assert k_auto == su.su_fixed_shape("aho", [1.0, 1.0], 12) and k_gen == -1
+    flat = lambda res: [lev for x in res for lev in (x if isinstance(x, list) else [x])]  # noqa: E731
+    got, ref = flat(got), flat(ref)
+    assert len(got) == len(ref) == 21 + 9 + 7
+    for g, r in zip(got, ref):
+        for key in ("amp", "log_amp", "err", "err_naive", "ess", "n"):
+            assert g[key] == r[key] or (np.isnan(g[key]) and np.isnan(r[key])), key
+
+
+def test_batched_kernel_with_several_levels_p_stays_generic():
+    inst = [{"a": 0.0, "b": 1.0, "T": 1.0, "s": 6, "p": p} for p in (4, 10)]
+    k, _ = _batch(inst, 10, "auto")
+    assert k == -1
