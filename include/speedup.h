@@ -63,10 +63,13 @@ extern "C" {
  * (SU_EINVAL).
  * W_p is evaluated per slice from V's derivatives at the slice midpoint and
  * the monomials of W_p in them (1629 monomial-power entries at p = 12, 24 196
- * at p = 18), so it needs no collapsed table: p <= 18, SU_FP64 only, su_plan_* /
- * speedup_amplitude / speedup_logweights / su_autotune and the evolution
- * operator (speedup_evolution_matrix / _band / _spectrum) only; everything
- * else answers SU_ENOTSUP. */
+ * at p = 18), so it needs no collapsed table: p <= 18, SU_FP64 only (the
+ * derivatives carry factors up to (2p-1)!, beyond the single-precision range),
+ * su_plan_* / speedup_amplitude / speedup_logweights / su_autotune, the batched
+ * launch (speedup_amplitude_batch / su_batch_plan_* / su_batch_autotune, one
+ * program per level p of the batch) and the evolution operator
+ * (speedup_evolution_matrix / _band / _spectrum) only; everything else
+ * answers SU_ENOTSUP. */
 #define SU_GENERAL 5
 
 /* ---- arithmetic of the per-slice W_p evaluation --------------------------- */
@@ -214,7 +217,8 @@ typedef struct {
  * replayed from a CUDA graph.  Work items are (instance, error block, chunk)
  * triples ordered by their cost (samples x slices x table entries), taken
  * from an atomic queue; each instance's tables (one per level p_i and
- * slice width) are staged per item.
+ * slice width) are staged per item (the general potential: its program per
+ * level p_i, read from device memory; double precision only).
  *
  *   p, n_mc      : the defaults for instances whose p or n_mc is 0.
  *   inst, n_inst : host, 1..2^24 instances.  Instance i draws from Philox
@@ -225,8 +229,8 @@ typedef struct {
  *                  seg_log2 and rounds are not used (per-instance hierarchy;
  *                  the shape of each (p, s, hierarchy) class is the one
  *                  su_batch_autotune stored, else the rule: 2^4-slice
- *                  register segments in double, 2^5 in single precision,
- *                  capped at s).
+ *                  register segments in double, 2^5 in single precision
+ *                  and for the general potential, capped at s).
  *   out          : host, one entry per instance with hierarchy 0 and s_i + 1
  *                  (levels n = 0..s_i) per instance with hierarchy 1, in
  *                  instance order (su_batch_plan_sizes gives the count).  An

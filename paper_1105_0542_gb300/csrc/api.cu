@@ -1460,6 +1460,10 @@ struct su_batch_plan {
     int64_t n_inst = 0, n_mc = 1;
     su_options opt{};
     std::map<int, su::Effective> E;   // per level p
+    // the general potential: its terms, and per level p the program and its device image
+    su::GeneralPotential V{};
+    std::map<int, std::shared_ptr<const su::GeneralEffective>> G;
+    std::vector<void *> d_general;
     su::BatchParams B{};
     void *d_inst = nullptr, *d_items = nullptr, *d_tables = nullptr, *d_shapes = nullptr;
     // per instance
@@ -1484,6 +1488,8 @@ static void batch_free(su_batch_plan *pl) {
     if (pl->d_items) cudaFree(pl->d_items);
     if (pl->d_tables) cudaFree(pl->d_tables);
     if (pl->d_shapes) cudaFree(pl->d_shapes);
+    for (void *g : pl->d_general)
+        if (g) cudaFree(g);
     delete pl;
 }
 
@@ -1525,7 +1531,7 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     if ((uint64_t)o.instance + (uint64_t)n_inst > (1ULL << 32))
         return fail(SU_EINVAL, "instance ids exceed 32 bits");
     if (o.width_factor != 1.0) return fail(SU_ENOTSUP, "the batched path samples the exact bridge only");
-    if (model == SU_GENERAL) return fail(SU_ENOTSUP, "the batched path takes the collapsed-table models only");
+    const bool general = model == SU_GENERAL;
     std::vector<BatchArg> arg;
     int rc = batch_args(p, inst, n_inst, n_mc, arg);
     if (rc) return rc;
@@ -1547,25 +1553,44 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     pl->opt = o;
     const int prec = o.precision;
 
-    // effective actions and table shapes, one per distinct level p
+    // effective actions and table shapes, one per distinct level p (the
+    // general potential: a monomial program per p, uploaded with the
+    // potential's terms; its shape has no columns, M = the program's entries)
     std::map<int, int> shape_of;
     std::vector<BatchShape> shapes;
+    if (general) {
+        std::string err;
+        rc = general_potential(params, n_params, pl->V, err);
+        if (rc) return fail(rc, "%s", err.c_str());
+    }
     for (const BatchArg &q : arg) {
         if (shape_of.count(q.p)) continue;
         std::string err;
-        Effective &E = pl->E[q.p];
-        rc = build_effective(model, params, n_params, q.p, E, err);
-        if (rc) return fail(rc, "%s", err.c_str());
         BatchShape sh;
         std::memset(&sh, 0, sizeof sh);
-        sh.ncol = E.shape.ncol;
-        sh.M = E.shape.M;
-        for (int j = 0; j < E.shape.ncol; ++j) sh.len[j] = E.shape.len[j];
+        if (general) {
+            auto G = general_program(q.p, rc, err);
+            if (rc) return fail(rc, "%s", err.c_str());
+            pl->G[q.p] = G;
+            void *d = nullptr;
+            rc = general_image(*G, pl->V, &d);
+            pl->d_general.push_back(d);
+            if (rc) return rc;
+            sh.M = (int)G->entry_k.size();
+            sh.general = static_cast<const GeneralDev *>(d);
+        } else {
+            Effective &E = pl->E[q.p];
+            rc = build_effective(model, params, n_params, q.p, E, err);
+            if (rc) return fail(rc, "%s", err.c_str());
+            sh.ncol = E.shape.ncol;
+            sh.M = E.shape.M;
+            for (int j = 0; j < E.shape.ncol; ++j) sh.len[j] = E.shape.len[j];
+        }
         shape_of[q.p] = (int)shapes.size();
         shapes.push_back(sh);
     }
-    const double alpha = pl->E.begin()->second.shape.alpha;
-    const int ring = pl->E.begin()->second.shape.ring;
+    const double alpha = general ? 0.0 : pl->E.begin()->second.shape.alpha;
+    const int ring = general ? RING_GENERAL : pl->E.begin()->second.shape.ring;
 
     int dev = 0, sms = 0, smem_max = 0;
     rc = device_limits(dev, sms, smem_max);
@@ -1593,7 +1618,8 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     int64_t tab_max = 1;
     for (size_t i = 0; i < ni; ++i) {
         const BatchArg &q = arg[i];
-        const Effective &E = pl->E[q.p];
+        const Effective *E = general ? nullptr : &pl->E[q.p];
+        const GeneralEffective *G = general ? pl->G[q.p].get() : nullptr;
         BatchInstance &h = hin[i];
         std::memset(&h, 0, sizeof h);
         h.a = q.a;
@@ -1612,18 +1638,24 @@ static int batch_create(int model, const double *params, int n_params, int p, co
         pl->out_off[i] = pl->n_results;
         pl->n_results += q.hier ? q.s + 1 : 1;
         pl->laf[i] = log_A_free(q.a, q.b, q.T);
-        auto c = coll.find({q.p, q.T});
-        if (c == coll.end()) {
-            std::vector<double> P;
-            collapse(E, q.T, P);
-            c = coll.emplace(std::make_pair(q.p, q.T), std::move(P)).first;
+        if (general) {
+            pl->w0[i] = -q.T * general_wp_host(*G, pl->V, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a), q.T);
+        } else {
+            auto c = coll.find({q.p, q.T});
+            if (c == coll.end()) {
+                std::vector<double> P;
+                collapse(*E, q.T, P);
+                c = coll.emplace(std::make_pair(q.p, q.T), std::move(P)).first;
+            }
+            pl->w0[i] = -q.T * wp_collapsed(E->shape, c->second, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a));
         }
-        pl->w0[i] = -q.T * wp_collapsed(E.shape, c->second, 0.5 * (q.a + q.b), 0.5 * (q.b - q.a));
         if (!std::isfinite(pl->w0[i]) && !(std::isinf(pl->w0[i]) && pl->w0[i] < 0))
             return fail(SU_ENONFINITE, "instance %lld: level-0 weight is not finite", (long long)i);
         if (q.s == 0) continue;
-        // shape: forced, else stored for the class, else the rule
-        int F = prec == SU_FP64 ? 4 : kMaxFine;
+        // shape: forced, else stored for the class, else the rule (as the
+        // single-instance plans: 16-slice segments in double, 32 in single
+        // precision and for the general potential)
+        int F = (prec == SU_FP64 && !general) ? 4 : kMaxFine;
         if (force_F > 0) {
             F = force_F;
         } else {
@@ -1642,7 +1674,11 @@ static int batch_create(int model, const double *params, int n_params, int p, co
             const int64_t offset = (int64_t)tabd.size();
             for (int d = 0; d < h.L; ++d) {
                 std::vector<double> row;
-                kernel_table(E, q.T / std::ldexp(1.0, q.s - d), row);
+                const double eps = q.T / std::ldexp(1.0, q.s - d);
+                if (general)
+                    general_table(*G, eps, row);
+                else
+                    kernel_table(*E, eps, row);
                 if (g_fault_table_nan.exchange(0)) row[0] = NAN;   // fault injection
                 for (double v : row)
                     if (!std::isfinite(v) || (prec == SU_FP32 && !std::isfinite((float)v)))
@@ -1656,7 +1692,7 @@ static int batch_create(int model, const double *params, int n_params, int p, co
         S_max = std::max(S_max, q.s);
         C_max = std::max(C_max, 1 << (q.s - h.F));
         L_max = std::max(L_max, h.L);
-        tab_max = std::max(tab_max, (int64_t)h.L * E.shape.M);
+        tab_max = std::max(tab_max, (int64_t)h.L * shapes[(size_t)h.shape].M);
         const int64_t Nn = (int64_t)1 << q.s;
         pl->slice_actions += q.n * (h.L > 1 ? 2 * Nn - 2 : Nn);
     }

@@ -24,6 +24,7 @@ const void *sampler_entry_gt_f64_2();
 const void *batch_entry_f64_0();
 const void *batch_entry_f64_1();
 const void *batch_entry_f64_2();
+const void *batch_entry_f64_3();
 const void *batch_entry_f32_0();
 const void *batch_entry_f32_1();
 const void *batch_entry_f32_2();
@@ -184,6 +185,7 @@ const void *batch_fn(const BatchParams &B, int precision) {
         const int k = B.fixed_shape;
         return kBatchFixed[k % kFixedGroups](k);
     }
+    if (ring == RING_GENERAL) return precision == SU_FP64 ? batch_entry_f64_3() : nullptr;
     if (precision == SU_FP32)
         return ring == RING_EVEN ? batch_entry_f32_0() : ring == RING_X ? batch_entry_f32_1() : batch_entry_f32_2();
     return ring == RING_EVEN ? batch_entry_f64_0() : ring == RING_X ? batch_entry_f64_1() : batch_entry_f64_2();
@@ -194,7 +196,9 @@ int sampler_fixed_shape(const SamplerParams &P, int precision) { return pick_fix
 size_t batch_smem_bytes(const BatchParams &B, int precision) {
     const size_t rs = precision == SU_FP32 ? sizeof(float) : sizeof(double);
     size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
-    off += (precision == SU_FP32 ? 8 : rs) * (size_t)B.tab_max + rs * (size_t)(SU_MAX_S + 1);
+    // staged tables (the general program's stay in global memory)
+    const size_t staged = B.base.ring == RING_GENERAL ? 0 : (size_t)B.tab_max;
+    off += (precision == SU_FP32 ? 8 : rs) * staged + rs * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
     off += rs * (size_t)(B.C_max > 1 ? B.C_max + 1 : 0) * kThreads;
     off = (off + 15) & ~(size_t)15;

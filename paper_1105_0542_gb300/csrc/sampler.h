@@ -89,10 +89,12 @@ struct BatchInstance {
     double sigma[SU_MAX_S + 1];
 };
 
-// The Horner shape of one level p's tables (columns in x-bar^2, entries per column).
+// The Horner shape of one level p's tables (columns in x-bar^2, entries per
+// column), or for the general potential its program (M = the program's entries).
 struct BatchShape {
     int ncol, M;
     int len[SU_MAX_P];
+    const GeneralDev *general;   // the general potential: this level's program (device), else null
 };
 
 // The batched kernel's parameters: the model fields of base (ring, alpha,

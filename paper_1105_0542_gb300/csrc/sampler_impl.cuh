@@ -1088,9 +1088,14 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
 //                [kThreads] (float4, single path) | Box-Muller node tables (double path)
 // CTAs per SM for the register budget: the float form fits 96 registers
 // without spills at 5 (the amplitude matrix 3 % faster than at 4).
-template <typename R>
+template <typename R, int RING>
 struct BatchCtas {
     static constexpr int value = sizeof(R) == 8 ? 2 : 5;
+};
+// the general potential: as the sampler (local-memory stacks, more warps)
+template <>
+struct BatchCtas<double, RING_GENERAL> {
+    static constexpr int value = 4;
 };
 
 // The table shape of the current item's instance (its level p), staged in
@@ -1108,7 +1113,7 @@ struct BatchView {
 // precision, even ring); items with 2^kMaxFine-slice segments run the path
 // code with that shape compiled in.
 template <typename R, int RING, int KS = -1>
-__global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(const __grid_constant__ BatchParams B) {
+__global__ void __launch_bounds__(kThreads, BatchCtas<R, RING>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ double s_red[kThreads / 32][SU_MAX_S][3];
@@ -1119,10 +1124,12 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
 
     BatchView *view = reinterpret_cast<BatchView *>(smem_raw);
     size_t off = (sizeof(BatchView) + 15) & ~(size_t)15;
-    // single precision stages the entries as pairs {c, c} (packed Horner)
+    // single precision stages the entries as pairs {c, c} (packed Horner);
+    // the general potential's program entries stay in global memory
     using TT = typename std::conditional<sizeof(R) == 4, float2, R>::type;
-    TT *tab = reinterpret_cast<TT *>(smem_raw + off);
-    off += sizeof(TT) * (size_t)B.tab_max;
+    constexpr bool kStage = RING != RING_GENERAL;
+    TT *tab_s = reinterpret_cast<TT *>(smem_raw + off);
+    off += kStage ? sizeof(TT) * (size_t)B.tab_max : 0;
     R *sig = reinterpret_cast<R *>(smem_raw + off);
     off += sizeof(R) * (size_t)(SU_MAX_S + 1);
     off = (off + 15) & ~(size_t)15;
@@ -1179,19 +1186,22 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R>::value) batch_kernel(co
                 view->lwf = 0;
                 view->hcoef = 0;
                 view->wf_on = 0;
-                view->general = nullptr;
+                view->general = sh.general;
             }
             for (int j = tid; j < sh.ncol; j += kThreads) view->len[j] = sh.len[j];
         }
-        {
+        const TT *tab = tab_s;
+        if constexpr (kStage) {
             const int n = L * B.shapes[in.shape].M;
             const R *g = reinterpret_cast<const R *>(P.tables) + in.tab;
             for (int i = tid; i < n; i += kThreads) {
                 if constexpr (sizeof(R) == 4)
-                    tab[i] = make_float2(g[i], g[i]);
+                    tab_s[i] = make_float2(g[i], g[i]);
                 else
-                    tab[i] = g[i];
+                    tab_s[i] = g[i];
             }
+        } else {
+            tab = reinterpret_cast<const TT *>(P.tables) + in.tab;
         }
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)in.sigma[i];
         for (int d = 1; d < L; ++d) {

@@ -71,7 +71,7 @@ const void *SU_CAT(sampler_entry_f, SU_PREC, SU_RING)() {
 }
 #endif
 
-#if SU_RING != 3 && !SU_GTAB
+#if !SU_GTAB && (SU_RING != 3 || SU_PREC == 64)
 const void *SU_CAT(batch_entry_f, SU_PREC, SU_RING)() {
     return (const void *)batch_kernel<Real, SU_RING>;
 }

@@ -10,6 +10,8 @@ Eq. 1Drec with V's derivatives as symbols) against the oracle, through the C ABI
   term the Poeschl-Teller model's: two independent device evaluations.
 * The amplitude of a mixed potential (polynomial + Gaussian + sech^2) against
   the sinc-DVR continuum value, within 4 sigma.
+* The batched launch with per-instance levels p against the oracle's
+  estimator on the same samples.
 """
 import numpy as np
 import pytest
@@ -39,11 +41,11 @@ def _gpu_w(model, params, a, b, T, p, s, n, seed, sample0=0, **kw):
     return w.cpu().numpy()
 
 
-def _oracle_w(params, a, b, T, p, s, n, seed, sample0=0):
+def _oracle_w(params, a, b, T, p, s, n, seed, sample0=0, instance=0):
     """w_n = -eps_n sum_k W_p over the level-n subpath of the oracle's path
     (Sec. 4.1), with W_p the oracle's general form; and eps_n sum_k sum|terms|."""
     paths = mc.Oracle("ho", [1.0], 1)   # the path does not depend on the potential
-    q = np.stack([paths.path(a, b, T, s, seed, sample0 + i)[0] for i in range(n)])
+    q = np.stack([paths.path(a, b, T, s, seed, sample0 + i, instance=instance)[0] for i in range(n)])
     w = np.empty((n, s))
     wabs = np.empty((n, s))
     for lev in range(1, s + 1):
@@ -127,6 +129,31 @@ def test_general_amplitude_estimator_matches_oracle_estimator():
         assert r[lev]["amp"] == pytest.approx(ref[lev]["amp"], rel=1e-11)
         if lev:
             assert r[lev]["err"] == pytest.approx(ref[lev]["err"], rel=1e-8)
+
+
+def test_general_batch_equals_oracle_per_instance():
+    """The batched launch with the general potential: instances of levels
+    p = 4, 10, 18 (one program each), depths 3..7, the top level alone or
+    every level, against the oracle's estimator applied to the oracle's
+    weights of the same samples (instance id = the batch's first id + i)."""
+    inst = [(-0.5, 0.7, 1.0, 5, 4, 900, 1), (0.2, -0.3, 0.5, 7, 10, 700, 0), (1.0, 0.0, 2.0, 3, 18, 500, 1),
+            (0.0, 0.4, 1.0, 6, 10, 800, 1)]
+    nb, seed = 5, 31
+    res = su.speedup_amplitude_batch("general", P_MIXED, 10, inst, 1000, seed, n_blocks=nb, instance=7)
+    for i, (a, b, T, s, p, n, hier) in enumerate(inst):
+        wo, _ = _oracle_w(P_MIXED, a, b, T, p, s, n, seed, instance=7 + i)
+        w0 = -T * float(gv.wp(P_MIXED, p, 0.5 * (a + b), 0.5 * (b - a), T))
+        ref = mc.estimate(wo, w0, a, b, T, nb)
+        got = res[i] if hier else [None] * s + [res[i]]
+        assert len(got) == s + 1
+        for lev in (range(s + 1) if hier else [s]):
+            g, r = got[lev], ref[lev]
+            assert g["n"] == n and g["level"] == lev
+            # (coarse levels at p = 18 sit far outside the expansion's radius:
+            # log-amplitudes of order 1e12, equal to 1e-10 relative)
+            assert abs(g["log_amp"] - r["log_amp"]) <= 1e-10 * max(1.0, abs(r["log_amp"])), (i, p, s, lev)
+            if lev:
+                assert g["err"] == pytest.approx(r["err"], rel=1e-7), (i, p, s, lev)
 
 
 def test_general_amplitude_matches_dvr():

@@ -275,12 +275,14 @@ def test_general_mode_rejects_bad_requests(params, kw, code):
 
 
 def test_general_mode_is_refused_where_a_collapsed_table_is_needed():
-    # the evolution operator takes the general potential in double precision only
+    # the evolution operator and the batched launch take the general potential
+    # in double precision only (its derivatives up to V^(2p-2) carry factors
+    # like (2p-1)!, beyond the single-precision range at p = 18)
     with pytest.raises(su.SpeedupError) as e:
         su.speedup_evolution_matrix("general", P_GEN, 4, 0.1, 5.0, 100, 1 << 20, precision="fp32")
     assert e.value.code == -6
     with pytest.raises(su.SpeedupError) as e:
-        su.speedup_amplitude_batch("general", P_GEN, 4, [(0.0, 1.0, 1.0, 4)], 1000, 1)
+        su.speedup_amplitude_batch("general", P_GEN, 4, [(0.0, 1.0, 1.0, 4)], 1000, 1, precision="fp32")
     assert e.value.code == -6
     with pytest.raises(su.SpeedupError) as e:
         su.speedup_amplitude_noalloc("general", P_GEN, 0.0, 1.0, 1.0, 4, 4, 1000, 1)
