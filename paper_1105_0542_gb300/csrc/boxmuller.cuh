@@ -276,37 +276,30 @@ SU_BM_FN void rotate(double R, uint64_t b, const Tables *__restrict__ t, double 
 //    (truncation r^5/5 < 2^-34 relative to r; ln2_hi with trailing zeros so
 //    that e ln2_hi is exact; the node c = 1 has inv = 1 and ln 1 = 0 exactly,
 //    so u1 near 1 keeps its relative accuracy);
-//  * R = sqrt(v) from the hardware reciprocal-square-root estimate y and one
-//    correction s + (v - s^2) y/2 of s = v y (R = 0 where u1 rounds to 1);
-//  * cos/sin(2 pi u2): 8 u2 = 2q + g exactly (quadrant q, g in [0, 2)), g
-//    reflected to 2 - g above 1 (exact), phi = g pi/4 = i pi/128 + d pi/4 with
-//    i the nearest of 33 nodes and |d| <= 1/64 exact, then
-//      sin phi = S_i + (C_i sd - S_i h),  cos phi = C_i - (S_i sd + C_i h),
-//      sd = delta - delta^3/6,  h = delta^2/2,  delta = d pi/4
-//    (next terms below 2^-29 relative) and the quadrant's swap and signs.
-// Node values are computed once per CTA in double with the CUDA library
-// functions and rounded to float.  Accuracy: a few units in the last place of
-// float against R cos, R sin evaluated in double from the same uniforms
-// (GPU tests against the oracle's libm values, 1e-6 (1 + R)).
+//  * R = sqrt(v) by the hardware approximation (sqrt.approx.f32; 0 where u1
+//    rounds to 1);
+//  * cos/sin(2 pi u2) = -(cos, sin)(2 pi (u2 - 1/2)) from the hardware
+//    approximations (__sincosf, absolute error about 2^-21 on (-pi, pi)).
+//    A table-driven form (quadrant and reflection, 33 nodes, a cubic
+//    correction) was a few units in the last place accurate but cost about
+//    35 instructions per pair, the largest item of the issue-bound sampler
+//    after the W_p Horner; the hardware form costs 4 and moves z by ~5e-7 R.
+// Log node values are computed once per CTA in double with the CUDA library
+// functions and rounded to float.  Accuracy: |dz| <~ 7e-7 (1 + R) against
+// R cos, R sin evaluated in double from the same uniforms (GPU tests against
+// the oracle's libm values, 1e-6 (1 + R)).
 namespace bm32 {
 
 constexpr int kLogNodes = 49;    // c_j = 1 + (j - 16)/64, j = 0..48: [3/4, 3/2]
-constexpr int kTrigNodes = 33;   // i pi/128, i = 0..32: [0, pi/4]
 
 struct Tables {
     float2 lg[kLogNodes];        // (inv_j, ln(1/inv_j))
-    float2 sc[kTrigNodes];       // (sin, cos) of i pi/128
 };
 
 __device__ __forceinline__ void tables_init(Tables *t, int tid, int nthreads) {
     for (int j = tid; j < kLogNodes; j += nthreads) {
         const float inv = (float)(1.0 / (1.0 + (j - 16) * (1.0 / 64.0)));
         t->lg[j] = make_float2(inv, (float)(-log((double)inv)));
-    }
-    for (int i = tid; i < kTrigNodes; i += nthreads) {
-        double s, c;
-        sincospi(i / 128.0, &s, &c);
-        t->sc[i] = make_float2((float)s, (float)c);
     }
 }
 
@@ -334,33 +327,19 @@ __device__ __forceinline__ void pair(uint32_t a, uint32_t b, const Tables *__res
     const float fe = (float)e;
     const float v = -2.0f * (fmaf(fe, kLn2Hi, L.y) + fmaf(fe, kLn2Lo, pl));
 
-    // ---- R = sqrt(v), v in {0} u [2^-24, 35] (u1 rounds to 1 for a >> 8 = 2^24 - 1)
-    const float y = rsqrtf(v);
-    const float s0 = v * y;
-    const float R = v > 0.0f ? fmaf(0.5f * y, fmaf(-s0, s0, v), s0) : 0.0f;
+    // ---- R = sqrt(v), v in {0} u [2^-24, 35] (u1 rounds to 1 for a >> 8 = 2^24 - 1):
+    // the hardware approximation (a few units in the last place; 0 at v = 0)
+    float R;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(R) : "f"(v));
 
-    // ---- cos, sin of 2 pi u2
-    const float t8 = u2 * 8.0f;                            // exact, in (0, 8)
-    const int q = ((int)t8) >> 1;                          // quadrant
-    float g = t8 - (float)(2 * q);                         // [0, 2), exact
-    const bool refl = g > 1.0f;
-    g = refl ? 2.0f - g : g;                               // [0, 1], exact
-    const float fi = rintf(g * 32.0f);
-    const float d = fmaf(fi, -0.03125f, g);                // g - i/32, exact
-    const float dl = d * 0.785398163f;                     // delta = d pi/4
-    const float dl2 = dl * dl;
-    const float h = 0.5f * dl2;
-    const float sd = fmaf(dl2 * (-1.0f / 6.0f), dl, dl);
-    const float2 SC = t->sc[(int)fi];
-    const float sp = fmaf(SC.y, sd, fmaf(-SC.x, h, SC.x)); // sin phi
-    const float cp = fmaf(-SC.x, sd, fmaf(-SC.y, h, SC.y)); // cos phi
-    // psi = q pi/2 + (refl ? pi/2 - phi : phi): swap on refl xor odd q, then signs
-    const bool sw = refl != ((q & 1) != 0);
-    const float cq = sw ? sp : cp, sq = sw ? cp : sp;
-    const float cth = (q == 1 || q == 2) ? -cq : cq;
-    const float sth = (q >= 2) ? -sq : sq;
-    z0 = R * cth;
-    z1 = R * sth;
+    // ---- cos, sin of 2 pi u2 = -(cos, sin) of 2 pi (u2 - 1/2): an argument in
+    // (-pi, pi) (u2 - 1/2 is exact) for the hardware approximations, whose
+    // absolute error (about 2^-21) moves z by ~5e-7 R -- the size of the
+    // single-precision W_p's own rounding, and inside the tested 1e-6 (1 + R)
+    float sn, cs;
+    __sincosf(6.28318530718f * (u2 - 0.5f), &sn, &cs);
+    z0 = -R * cs;
+    z1 = -R * sn;
 }
 
 }  // namespace bm32
