@@ -801,7 +801,7 @@ int speedup_normals(uint64_t seed, uint32_t instance, int64_t sample0, int64_t n
  *    call, with the caller's device current.
  *  - The call is synchronous: it copies the tables in and the tuples out
  *    through pageable host memory and synchronises opt->stream before it
- *    returns.
+ *    returns, so it cannot be recorded into a CUDA graph (stream capture).
  *  - Every call shares the one array and leaves its contents behind; calls
  *    whose device work overlaps (other threads, other streams of the same
  *    device) race on it and must be serialised by the caller.
