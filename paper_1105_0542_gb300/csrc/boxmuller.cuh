@@ -267,75 +267,47 @@ SU_BM_FN void rotate(double R, uint64_t b, const Tables *__restrict__ t, double 
 // ---------------------------------------------------------------------------
 // Single-precision Box-Muller (the single-precision sampler's normals) for the
 // 24-bit uniforms u1 = fl(a + 1/2) 2^-24, u2 = fl(b + 1/2) 2^-24 (a, b the top
-// 24 bits of two Philox words), with the same structure as the double
-// routines above, in float:
-//  * -2 ln u1: u1 = 2^e m, m in [3/4, 3/2) from its bits; node c_j = 1 +
-//    (j - 16)/64 (j = 0..48) nearest to m, inv_j the float nearest 1/c_j,
-//    r = m inv_j - 1 in one fused multiply-add (|r| <= 1/96), and
-//      ln u1 = e ln2_hi + ln(1/inv_j) + [e ln2_lo + r (1 - r/2 + r^2/3 - r^3/4)]
-//    (truncation r^5/5 < 2^-34 relative to r; ln2_hi with trailing zeros so
-//    that e ln2_hi is exact; the node c = 1 has inv = 1 and ln 1 = 0 exactly,
-//    so u1 near 1 keeps its relative accuracy);
-//  * R = sqrt(v) by the hardware approximation (sqrt.approx.f32; 0 where u1
-//    rounds to 1);
-//  * cos/sin(2 pi u2) = -(cos, sin)(2 pi (u2 - 1/2)) from the hardware
-//    approximations (__sincosf, absolute error about 2^-21 on (-pi, pi)).
-//    A table-driven form (quadrant and reflection, 33 nodes, a cubic
-//    correction) was a few units in the last place accurate but cost about
-//    35 instructions per pair, the largest item of the issue-bound sampler
-//    after the W_p Horner; the hardware form costs 4 and moves z by ~5e-7 R.
-// Log node values are computed once per CTA in double with the CUDA library
-// functions and rounded to float.  Accuracy: |dz| <~ 7e-7 (1 + R) against
-// R cos, R sin evaluated in double from the same uniforms (GPU tests against
-// the oracle's libm values, 1e-6 (1 + R)).
+// 24 bits of two Philox words), in float, from the hardware approximations:
+//  * -2 ln u1 = -2 ln 2 log2(u1) with lg2.approx.f32 (absolute error about
+//    2^-22.6), except for u1 > 15/16, where that absolute error would be large
+//    against ln u1 itself: there -ln(1 - t) = t (1 + t/2 + .. + t^6/7) with
+//    t = 1 - u1 exact (truncation t^7/8 < 2^-31 relative);
+//  * R = sqrt(v) by sqrt.approx.f32 (0 where u1 rounds to 1);
+//  * cos/sin(2 pi u2) = -(cos, sin)(2 pi (u2 - 1/2)) by __sincosf on an
+//    argument in (-pi, pi) (u2 - 1/2 is exact; absolute error about 2^-21).
+// Largest error: about 5e-7 R from the sine and cosine, at most 3e-7 from
+// the logarithm (at u1 = 15/16, where R = 0.36); the GPU tests hold the
+// normals to 1e-6 (1 + R) of the oracle's double-precision Box-Muller on the
+// same uniforms.  Earlier forms, table-driven like the double routines above
+// (a 49-node logarithm, quadrant-reduced 33-node sin/cos), were a few units
+// in the last place accurate but cost about 55 instructions per pair, the
+// largest item of the issue-bound single-precision sampler after the W_p
+// Horner; this one costs about 25.
 namespace bm32 {
 
-constexpr int kLogNodes = 49;    // c_j = 1 + (j - 16)/64, j = 0..48: [3/4, 3/2]
-
-struct Tables {
-    float2 lg[kLogNodes];        // (inv_j, ln(1/inv_j))
-};
-
-__device__ __forceinline__ void tables_init(Tables *t, int tid, int nthreads) {
-    for (int j = tid; j < kLogNodes; j += nthreads) {
-        const float inv = (float)(1.0 / (1.0 + (j - 16) * (1.0 / 64.0)));
-        t->lg[j] = make_float2(inv, (float)(-log((double)inv)));
-    }
-}
-
 // z0 = R cos(2 pi u2), z1 = R sin(2 pi u2), R = sqrt(-2 ln u1)
-__device__ __forceinline__ void pair(uint32_t a, uint32_t b, const Tables *__restrict__ t, float &z0, float &z1) {
-    constexpr float kLn2Hi = 0.693145751953125f;         // 0x3F317200: 13 trailing zero bits
-    constexpr float kLn2Lo = 1.428606765330187e-06f;     // ln 2 - kLn2Hi
+__device__ __forceinline__ void pair(uint32_t a, uint32_t b, float &z0, float &z1) {
     // ((w >> 8) + 1/2) 2^-24 in one rounding: the scaling is exact
     const float u1 = fmaf((float)(a >> 8), 0x1p-24f, 0x1p-25f);
     const float u2 = fmaf((float)(b >> 8), 0x1p-24f, 0x1p-25f);
 
-    // ---- -2 ln u1 (u1 >= 2^-25: a normal float)
-    const int ib = __float_as_int(u1);
-    int e = (ib >> 23) - 127;
-    int mb = (ib & 0x7FFFFF) | 0x3F800000;                // m in [1, 2)
-    if (mb >= 0x3FC00000) {                               // m >= 3/2: halve m (exactly), raise e
-        mb -= 0x00800000;
-        e += 1;
-    }
-    const float m = __int_as_float(mb);
-    const int j = __float2int_rn((m - 1.0f) * 64.0f) + 16;
-    const float2 L = t->lg[j];
-    const float r = fmaf(m, L.x, -1.0f);
-    const float pl = r * fmaf(r, fmaf(r, fmaf(r, -0.25f, 0.333333343f), -0.5f), 1.0f);
-    const float fe = (float)e;
-    const float v = -2.0f * (fmaf(fe, kLn2Hi, L.y) + fmaf(fe, kLn2Lo, pl));
+    // ---- v = -2 ln u1
+    const float t = 1.0f - u1;
+    float lg;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(lg) : "f"(u1));
+    float ser = fmaf(t, 1.0f / 7.0f, 1.0f / 6.0f);
+    ser = fmaf(t, ser, 0.2f);
+    ser = fmaf(t, ser, 0.25f);
+    ser = fmaf(t, ser, 0.333333343f);
+    ser = fmaf(t, ser, 0.5f);
+    ser = fmaf(t, ser, 1.0f);
+    const float v = t < 0.0625f ? 2.0f * t * ser : -1.38629436f * lg;   // -2 ln 2 = -1.38629436
 
-    // ---- R = sqrt(v), v in {0} u [2^-24, 35] (u1 rounds to 1 for a >> 8 = 2^24 - 1):
-    // the hardware approximation (a few units in the last place; 0 at v = 0)
+    // ---- R = sqrt(v), v in {0} u [2^-24, 35]
     float R;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(R) : "f"(v));
 
-    // ---- cos, sin of 2 pi u2 = -(cos, sin) of 2 pi (u2 - 1/2): an argument in
-    // (-pi, pi) (u2 - 1/2 is exact) for the hardware approximations, whose
-    // absolute error (about 2^-21) moves z by ~5e-7 R -- the size of the
-    // single-precision W_p's own rounding, and inside the tested 1e-6 (1 + R)
+    // ---- cos, sin of 2 pi u2
     float sn, cs;
     __sincosf(6.28318530718f * (u2 - 0.5f), &sn, &cs);
     z0 = -R * cs;

@@ -110,7 +110,6 @@ __device__ __forceinline__ void nd_block(const R *__restrict__ tab, const NdPara
 template <typename R, int D>
 __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__ NdParams Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ bm32::Tables s_bm32;   // single precision
     const SamplerParams &P = Q.base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int L = P.levels, S = P.S;
@@ -119,17 +118,13 @@ __global__ void __launch_bounds__(kThreads, 4) nd_kernel(const __grid_constant__
     size_t off = per_sample ? 0 : sizeof(R) * (size_t)L * kThreads;
     off = (off + 15) & ~(size_t)15;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
-    if constexpr (sizeof(R) == 8)
-        bm::tables_init(bm_smem, tid, kThreads);
-    else
-        bm32::tables_init(&s_bm32, tid, kThreads);
+    if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
     __syncthreads();
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.inst = P.instance;
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
-    st.bm32 = &s_bm32;
     const int64_t ps = Q.pstride;
     // the path in segments of 2^F slices: the C + 1 segment endpoints (the
     // coarse levels' points) in this slot of the global scratch, one

@@ -100,7 +100,6 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
     const int S = P.S, N = 1 << S, L = P.levels;
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mma_bar;
-    __shared__ bm32::Tables s_bm32;
     unsigned char *blob = smem_raw;
     size_t off = kBlobBytes;
     unsigned char *X0 = smem_raw + off;
@@ -125,7 +124,6 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
         for (int i = tid; i < S * P.M; i += kT) tab[i] = g[i];
         for (int i = tid; i <= SU_MAX_S; i += kT) sig[i] = (float)P.sigma[i];
         for (int i = tid; i < kX0Bytes / 16; i += kT) reinterpret_cast<uint4 *>(X0)[i] = make_uint4(0, 0, 0, 0);
-        bm32::tables_init(&s_bm32, tid, kT);
     }
     Tc tc = mlp::tc_begin(&tmem_slot, &mma_bar);   // contains __syncthreads
     bool alive = true;
@@ -139,7 +137,6 @@ __global__ void __launch_bounds__(mlp::kThreads, 1) proposal_kernel(const __grid
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.inst = P.instance;
     st.bm = nullptr;
-    st.bm32 = &s_bm32;
 
     for (int64_t item = blockIdx.x; alive && item < P.n_items; item += gridDim.x) {
         const int64_t bk = item / P.items_per_block;

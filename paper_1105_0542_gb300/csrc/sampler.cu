@@ -125,9 +125,6 @@ __global__ void __launch_bounds__(128) normals_kernel_f64(uint64_t seed, uint32_
 
 __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_t inst, int64_t sample0,
                                                           int64_t ns, int n, double *out) {
-    __shared__ bm32::Tables tabs;
-    bm32::tables_init(&tabs, threadIdx.x, blockDim.x);
-    __syncthreads();
     const int calls = n / 4 + 1;                 // j' = j + 1 runs over 1..n
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= ns * calls) return;
@@ -140,7 +137,6 @@ __global__ void __launch_bounds__(128) normals_kernel_f32(uint64_t seed, uint32_
     st.slo = (uint32_t)smp;
     st.shi = (uint32_t)(smp >> 32);
     st.bm = nullptr;
-    st.bm32 = &tabs;
     float z[4];
     st.quad(t, z);
 #pragma unroll

@@ -60,10 +60,10 @@ template <>
 struct Normal<float> {
     // four normals per call: (z0, z1) from the 24-bit uniforms
     // ((w >> 8) + 1/2) 2^-24 of (w0, w1), (z2, z3) from (w2, w3), through the
-    // table-driven single-precision routine of boxmuller.cuh
-    static __device__ __forceinline__ void quad(uint4 w, const bm32::Tables *t, float (&z)[4]) {
-        bm32::pair(w.x, w.y, t, z[0], z[1]);
-        bm32::pair(w.z, w.w, t, z[2], z[3]);
+    // single-precision routine of boxmuller.cuh (hardware approximations)
+    static __device__ __forceinline__ void quad(uint4 w, float (&z)[4]) {
+        bm32::pair(w.x, w.y, z[0], z[1]);
+        bm32::pair(w.z, w.w, z[2], z[3]);
     }
 };
 
@@ -76,9 +76,8 @@ struct Stream {
     uint2 key;
     uint32_t inst, slo, shi;
     const bm::Tables *bm;   // shared-memory node tables (double path)
-    const bm32::Tables *bm32;   // shared-memory node tables (single path)
-    float4 *zq;                 // single path: this thread's column (stride kThreads) of
-                                // staged quads, levels 3..F of a segment (see sample_path)
+    float4 *zq;             // single path: this thread's column (stride kThreads) of
+                            // staged quads, levels 3..F of a segment (see sample_path)
     __device__ __forceinline__ uint4 words(uint32_t call) const {
         return philox4x32_10(make_uint4(call, inst, slo, shi), key);
     }
@@ -86,7 +85,7 @@ struct Stream {
         Normal<double>::pair(words(call), bm, z0, z1);
     }
     __device__ __forceinline__ void quad(uint32_t call, float (&z)[4]) const {
-        Normal<float>::quad(words(call), bm32, z);
+        Normal<float>::quad(words(call), z);
     }
 };
 
@@ -962,7 +961,6 @@ struct MinCtas<double, RING_GENERAL> {
 template <typename R, int RING, bool GTAB = false, int KS = -1>
 __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ bm32::Tables s_bm32;   // single path
     const int tid = threadIdx.x;
     const int L = P.levels;
     const int chunk = kThreads * P.rounds;
@@ -1008,7 +1006,6 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
         }
         for (int i = tid; i <= SU_MAX_S; i += kThreads) sig[i] = (R)P.sigma[i];
         if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
-        if constexpr (sizeof(R) == 4) bm32::tables_init(&s_bm32, tid, kThreads);
     }
     __syncthreads();
     const PathCfg<R> pc{(R)P.a, (R)P.b, P.S, L, sig};
@@ -1017,7 +1014,6 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.inst = P.instance;
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
-    st.bm32 = &s_bm32;
     st.zq = zq;
 
     FixedView<(KS >= 0 ? KS : 0)> fv;
@@ -1117,7 +1113,6 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING>::value) batch_ker
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ double s_red[kThreads / 32][SU_MAX_S][3];
-    __shared__ bm32::Tables s_bm32;   // single path
     const SamplerParams &P = B.base;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -1147,12 +1142,10 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING>::value) batch_ker
     off += sizeof(R) == 4 ? sizeof(float4) * (size_t)staged_quads(kMaxFine) * kThreads : 0;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
     if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
-    if constexpr (sizeof(R) == 4) bm32::tables_init(&s_bm32, tid, kThreads);
 
     Stream<R> st;
     st.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
     st.bm = sizeof(R) == 8 ? bm_smem : nullptr;
-    st.bm32 = &s_bm32;
     st.zq = zq;
     int cur_shape = -1;
 
