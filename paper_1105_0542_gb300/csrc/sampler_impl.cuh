@@ -1082,15 +1082,17 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_ker
 //                qc[(C_max+1)][kThreads] (R) | level states m (R), s, q
 //                (double) [L_max-1][kThreads] | staged quads[2^(kMaxFine-2) - 1]
 //                [kThreads] (float4, single path) | Box-Muller node tables (double path)
-// CTAs per SM for the register budget: the float form fits 96 registers
-// without spills at 5 (the amplitude matrix 3 % faster than at 4).
-template <typename R, int RING>
+// CTAs per SM for the register budget: the generic float form runs the
+// amplitude matrix 2 % faster at 5 (96 registers) than at 4; with a table
+// shape compiled in (KS >= 0) it spills more at 96 registers and runs the
+// matrix 5 % faster at 4 (128 registers).
+template <typename R, int RING, int KS>
 struct BatchCtas {
-    static constexpr int value = sizeof(R) == 8 ? 2 : 5;
+    static constexpr int value = sizeof(R) == 8 ? 2 : (KS >= 0 ? 4 : 5);
 };
 // the general potential: as the sampler (local-memory stacks, more warps)
-template <>
-struct BatchCtas<double, RING_GENERAL> {
+template <int KS>
+struct BatchCtas<double, RING_GENERAL, KS> {
     static constexpr int value = 4;
 };
 
@@ -1109,7 +1111,7 @@ struct BatchView {
 // precision, even ring); items with 2^kMaxFine-slice segments run the path
 // code with that shape compiled in.
 template <typename R, int RING, int KS = -1>
-__global__ void __launch_bounds__(kThreads, BatchCtas<R, RING>::value) batch_kernel(const __grid_constant__ BatchParams B) {
+__global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     __shared__ double s_red[kThreads / 32][SU_MAX_S][3];
