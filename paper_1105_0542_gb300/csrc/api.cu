@@ -1720,6 +1720,17 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     const int occ = batch_occupancy(B, prec, pl->smem);
     if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
     const int64_t slots = (int64_t)sms * occ;
+    // the work items (and so the order of every sum) come from the generic
+    // kernel's residency, so that the compiled-shape kernel, which runs at
+    // another occupancy, gives the same bits
+    int occ_gen = occ;
+    if (B.fixed_shape >= 0) {
+        BatchParams G = B;
+        G.fixed_shape = -1;
+        occ_gen = batch_occupancy(G, prec, pl->smem);
+        if (occ_gen < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
+    }
+    const int64_t work_slots = (int64_t)sms * occ_gen;
 
     // work items (instance, block, chunk).  Cost of an instance's block:
     // samples x slices x (table entries + the per-slice formation and RNG
@@ -1734,7 +1745,7 @@ static int batch_create(int model, const double *params, int n_params, int p, co
         bcost[i] = ((double)pl->N[i] / pl->NB[i]) * slices * (double)(shapes[(size_t)hin[i].shape].M + 12);
         total += bcost[i] * pl->NB[i];
     }
-    const double target = total / (8.0 * (double)slots);
+    const double target = total / (8.0 * (double)work_slots);
     int64_t n_items = 0, n_tup = 0;
     for (size_t i = 0; i < ni; ++i) {
         if (pl->S[i] == 0) continue;

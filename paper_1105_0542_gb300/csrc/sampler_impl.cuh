@@ -368,83 +368,6 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const TT *__restrict__ 
     }
     constexpr int B = NS < Batch<R>::B ? NS : Batch<R>::B;
     constexpr bool kFold = sizeof(R) == 8;
-    if constexpr (std::is_same<TT, float2>::value && B % 2 == 0) {
-        // single precision with paired tables: two slices per packed
-        // multiply-add (fma.rn.f32x2), the same operations in the same order
-        // as the scalar form below, so the same bits
-        constexpr int BP = B / 2;
-        const float2 m1 = make_float2(-1.0f, -1.0f);
-        R ty = 0;
-#pragma unroll
-        for (int k0 = 0; k0 < NS; k0 += B) {
-            float2 Z[BP], Y[BP], acc[BP];
-#pragma unroll
-            for (int m = 0; m < BP; ++m) {
-                const float2 ql = make_float2(q[(k0 + 2 * m) * STR], q[(k0 + 2 * m + 1) * STR]);
-                const float2 qr = make_float2(q[(k0 + 2 * m + 1) * STR], q[(k0 + 2 * m + 2) * STR]);
-                const float2 vs = __ffma2_rn(ql, m1, qr);     // qr - ql, exactly as a subtraction
-                Y[m] = __fmul2_rn(vs, vs);
-                const float2 us = __fadd2_rn(ql, qr);
-                if constexpr (RING == RING_EVEN) {
-                    Z[m] = __fmul2_rn(us, us);
-                } else {
-                    Z[m] = make_float2(ring_var<float, RING>(us.x, alpha), ring_var<float, RING>(us.y, alpha));
-                }
-            }
-            if constexpr (ShapeOf<SP>::value >= 0) {
-                fixed_horner<ShapeOf<SP>::value, BP>(acc, Y, Z, tab);
-            } else {
-                int off = P.M;
-                {   // last column starts the outer Horner in x-bar^2
-                    const int L = P.len[P.ncol - 1];
-                    off -= L;
-                    const float2 c = tab[off + L - 1];
-                    if (L == 1) {
-#pragma unroll
-                        for (int m = 0; m < BP; ++m) acc[m] = c;
-                    } else {
-                        const float2 c0 = tab[off + L - 2];
-#pragma unroll
-                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
-                    }
-#pragma unroll 4
-                    for (int i = L - 3; i >= 0; --i) {
-                        const float2 ci = tab[off + i];
-#pragma unroll
-                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
-                    }
-                }
-                for (int j = P.ncol - 2; j >= 0; --j) {
-                    const int L = P.len[j];
-                    off -= L;
-                    const float2 c = tab[off + L - 1];
-                    if (L == 1) {
-#pragma unroll
-                        for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
-                        continue;
-                    }
-                    float2 h[BP];
-                    const float2 c0 = tab[off + L - 2];
-#pragma unroll
-                    for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
-#pragma unroll 4
-                    for (int i = L - 3; i >= 0; --i) {
-                        const float2 ci = tab[off + i];
-#pragma unroll
-                        for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
-                    }
-#pragma unroll
-                    for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < BP; ++m) {
-                ty += acc[m].x;
-                ty += acc[m].y;
-            }
-        }
-        return ty;
-    } else {
     const int L0 = P.len[0];
     R ty = 0, tz = 0;
 #pragma unroll
@@ -567,6 +490,116 @@ __device__ __forceinline__ R level_sum(const R (&q)[NQ], const TT *__restrict__ 
     }
     if constexpr (kFold) return fma((R)NS, coef(tab, 0), ty + tz);
     return ty;
+}
+
+// The packed nested Horner of BP pairs of slices: acc = sum_j (xb^2)^j sum_i
+// T_ij z^i for both slices of each pair (fma.rn.f32x2 on tables of pairs
+// {c, c}), the chains started from fma(c_top, Z, c_next) and a one-entry
+// column going straight into the outer chain; with the table shape compiled
+// in (ShapeOf<SP>) every loop unrolled (fixed_horner), the same operations
+// in the same order.
+template <int BP, typename SP>
+__device__ __forceinline__ void horner_packed(float2 (&acc)[BP], const float2 (&Y)[BP], const float2 (&Z)[BP],
+                                              const float2 *__restrict__ tab, const SP &P) {
+    if constexpr (ShapeOf<SP>::value >= 0) {
+        fixed_horner<ShapeOf<SP>::value, BP>(acc, Y, Z, tab);
+    } else {
+        int off = P.M;
+        {   // last column starts the outer Horner in x-bar^2
+            const int L = P.len[P.ncol - 1];
+            off -= L;
+            const float2 c = tab[off + L - 1];
+            if (L == 1) {
+#pragma unroll
+                for (int m = 0; m < BP; ++m) acc[m] = c;
+            } else {
+                const float2 c0 = tab[off + L - 2];
+#pragma unroll
+                for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(c, Z[m], c0);
+            }
+#pragma unroll 4
+            for (int i = L - 3; i >= 0; --i) {
+                const float2 ci = tab[off + i];
+#pragma unroll
+                for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Z[m], ci);
+            }
+        }
+        for (int j = P.ncol - 2; j >= 0; --j) {
+            const int L = P.len[j];
+            off -= L;
+            const float2 c = tab[off + L - 1];
+            if (L == 1) {
+#pragma unroll
+                for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], c);
+                continue;
+            }
+            float2 h[BP];
+            const float2 c0 = tab[off + L - 2];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(c, Z[m], c0);
+#pragma unroll 4
+            for (int i = L - 3; i >= 0; --i) {
+                const float2 ci = tab[off + i];
+#pragma unroll
+                for (int m = 0; m < BP; ++m) h[m] = __ffma2_rn(h[m], Z[m], ci);
+            }
+#pragma unroll
+            for (int m = 0; m < BP; ++m) acc[m] = __ffma2_rn(acc[m], Y[m], h[m]);
+        }
+    }
+}
+
+// Single precision: a segment's points as pairs Pq[m] = (q_m, q_{m+H}),
+// m = 0..H, H = 2^(F-1) (q_H in both Pq[0].y and Pq[H].x).  A level of NS >= 2
+// slices of the segment (stride STR = 2^F / NS) pairs slice k with slice
+// k + NS/2: both lie between Pq[k STR] and Pq[(k+1) STR], so the packed
+// two-slice Horner takes them without moves.  The sum runs over the pairs in
+// order, each pair's two slices in turn.  NS = 1: the one slice (q_0, q_2H).
+template <int RING, int NS, int STR, int H, typename TT, typename SP>
+__device__ __forceinline__ float level_sum_pairs(const float2 (&Pq)[H + 1], const TT *__restrict__ tab, const SP &P,
+                                                 float alpha) {
+    if constexpr (NS == 1) {
+        return slice<float, RING>(Pq[0].x, Pq[H].y, tab, P, alpha);
+    } else {
+        constexpr int NP = NS / 2;                 // pairs of slices
+        constexpr int BP = NP < 4 ? NP : 4;        // pairs per batch: each table entry feeds 2 BP slices
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        float ty = 0;
+#pragma unroll
+        for (int k0 = 0; k0 < NP; k0 += BP) {
+            float2 Z[BP], Y[BP], acc[BP];
+#pragma unroll
+            for (int m = 0; m < BP; ++m) {
+                const float2 ql = Pq[(k0 + m) * STR], qr = Pq[(k0 + m + 1) * STR];
+                const float2 vs = __ffma2_rn(ql, m1, qr);     // qr - ql, exactly as a subtraction
+                Y[m] = __fmul2_rn(vs, vs);
+                const float2 us = __fadd2_rn(ql, qr);
+                if constexpr (RING == RING_EVEN) {
+                    Z[m] = __fmul2_rn(us, us);
+                } else {
+                    Z[m] = make_float2(ring_var<float, RING>(us.x, alpha), ring_var<float, RING>(us.y, alpha));
+                }
+            }
+            horner_packed<BP>(acc, Y, Z, tab, P);
+#pragma unroll
+            for (int m = 0; m < BP; ++m) {
+                ty += acc[m].x;
+                ty += acc[m].y;
+            }
+        }
+        return ty;
+    }
+}
+
+// levels d = D..F of a single-precision segment held as pairs
+template <int RING, int F, int D, typename TT, typename SP>
+__device__ __forceinline__ void segment_levels_pairs(float (&acc)[F + 1], const float2 (&Pq)[(1 << (F - 1)) + 1],
+                                                     const TT *__restrict__ tab, const SP &P, float alpha, int S) {
+    if constexpr (D <= F) {
+        if (D < S) {
+            acc[D] += level_sum_pairs<RING, ((1 << F) >> D), (1 << D), (1 << (F - 1))>(Pq, tab + D * P.M, P, alpha);
+            segment_levels_pairs<RING, F, D + 1>(acc, Pq, tab, P, alpha, S);
+        }
     }
 }
 
@@ -677,39 +710,115 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
 #pragma unroll
     for (int d = 0; d <= F; ++d) acc[d] = 0;
 
-    constexpr bool kStaged = sizeof(R) == 4 && F >= 3;
     for (int c = 0; c < C; ++c) {
-        if constexpr (kStaged) {
-            // levels l = 3..F: normals j' = 2^(n-1) + c 2^(l-1) + il, whole quads
-            // from quad (2^(n-1) + c 2^(l-1)) / 4 on; slot 2^(l-3) - 1 + il / 4
-            int slot = 0;
+        if constexpr (sizeof(R) == 4) {
+            // ---- single precision: the segment as pairs Pq[m] = (q_m, q_{m+H})
+            constexpr int H = NF / 2;
+            if constexpr (F >= 3) {
+                // stage the normals of levels 3..F (level l: quads from
+                // (2^(n-1) + c 2^(l-1)) / 4 on, normal il at slot il & 3 of quad
+                // il / 4) in the order the paired bisection takes them: pair il
+                // of level l is (z_il, z_{il + 2^(l-2)}), float4 slot
+                // 2^(l-3) - 1 + il / 2 holds pairs il (even) and il + 1
+                {   // level 3: one quad, pairs (z0, z2), (z1, z3)
+                    const int n = S - F + 3;
+                    float za[4];
+                    st.quad(((1u << (n - 1)) + ((uint32_t)c << 2)) >> 2, za);
+                    st.zq[0] = make_float4(za[0], za[2], za[1], za[3]);
+                }
 #pragma unroll 1
-            for (int l = 3; l <= F; ++l) {
-                const int n = S - F + l;
-                const uint32_t q0 = ((1u << (n - 1)) + ((uint32_t)c << (l - 1))) >> 2;
+                for (int l = 4; l <= F; ++l) {   // levels 4..F: quad k pairs with quad k + 2^(l-4)
+                    const int n = S - F + l;
+                    const uint32_t q0 = ((1u << (n - 1)) + ((uint32_t)c << (l - 1))) >> 2;
+                    const int hq = 1 << (l - 4), base = (1 << (l - 3)) - 1;
 #pragma unroll 1
-                for (int k = 0; k < (1 << (l - 3)); ++k, ++slot) {
-                    float z4[4];
-                    st.quad(q0 + (uint32_t)k, z4);
-                    st.zq[slot * kThreads] = make_float4(z4[0], z4[1], z4[2], z4[3]);
+                    for (int k = 0; k < hq; ++k) {
+                        float za[4], zb[4];
+                        st.quad(q0 + (uint32_t)k, za);
+                        st.quad(q0 + (uint32_t)(k + hq), zb);
+                        st.zq[(base + 2 * k) * kThreads] = make_float4(za[0], zb[0], za[1], zb[1]);
+                        st.zq[(base + 2 * k + 1) * kThreads] = make_float4(za[2], zb[2], za[3], zb[3]);
+                    }
                 }
             }
-        }
-        R q[NF + 1];
-        q[0] = C > 1 ? qc[c * kThreads] : pc.a;
-        q[NF] = C > 1 ? qc[(c + 1) * kThreads] : pc.b;
-#pragma unroll
-        for (int l = 1; l <= F; ++l) {
-            const int n = S - F + l;
-            const uint32_t jbase = (1u << (n - 1)) - 1u + ((uint32_t)c << (l - 1));
-            const R sg = pc.sigma[n];
-            const int h = 1 << (F - l);
-            float qq[4];
-#pragma unroll
-            for (int il = 0; il < (1 << (l - 1)); ++il) {
-                const uint32_t j = jbase + (uint32_t)il;
+            float2 Pq[H + 1];
+            const R qa = C > 1 ? qc[c * kThreads] : pc.a;
+            const R qb = C > 1 ? qc[(c + 1) * kThreads] : pc.b;
+            {   // level 1: the midpoint q_H (normal j' = 2^(n-1) + c)
+                const int n = S - F + 1;
+                const uint32_t jp = (1u << (n - 1)) + (uint32_t)c;
                 R z;
-                if constexpr (sizeof(R) == 8) {
+                if (C == 1) {
+                    st.quad(0, Q1);
+                    z = Q1[1];
+                } else if (C == 2) {            // the endpoint levels' quad
+                    z = c ? Q1[3] : Q1[2];
+                } else {                        // a quad per four segments
+                    if ((c & 3) == 0) st.quad(jp >> 2, Q1);
+                    z = pick4(Q1, (uint32_t)c);
+                }
+                if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
+                const R qm = fma(pc.sigma[n], z, mid(qa, qb));
+                Pq[0] = make_float2(qa, qm);
+                Pq[H] = make_float2(qm, qb);
+            }
+            // levels 2..F: midpoints idx and idx + H together, pair il < 2^(l-2)
+#pragma unroll
+            for (int l = 2; l <= F; ++l) {
+                const int n = S - F + l;
+                const R sg = pc.sigma[n];
+                const float2 sg2 = make_float2(sg, sg), half2 = make_float2(0.5f, 0.5f);
+                const int h = 1 << (F - l);
+                float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int il = 0; il < (1 << (l - 2)); ++il) {
+                    float2 zp;
+                    if (l == 2) {                   // normals j' = 2^(n-1) + 2c + {0, 1}
+                        if (C == 1) {               // j' = 2, 3: the quad of level 1
+                            zp = make_float2(Q1[2], Q1[3]);
+                        } else {                    // a quad per two segments
+                            if ((c & 1) == 0) st.quad(((1u << (n - 1)) + 2u * (uint32_t)c) >> 2, Q2);
+                            zp = (c & 1) ? make_float2(Q2[2], Q2[3]) : make_float2(Q2[0], Q2[1]);
+                        }
+                    } else {
+                        if ((il & 1) == 0) v4 = st.zq[((1 << (l - 3)) - 1 + (il >> 1)) * kThreads];
+                        zp = (il & 1) ? make_float2(v4.z, v4.w) : make_float2(v4.x, v4.y);
+                    }
+                    if constexpr (WF) {
+                        zz[n * kThreads] += (double)zp.x * (double)zp.x;
+                        zz[n * kThreads] += (double)zp.y * (double)zp.y;
+                    }
+                    const int idx = (2 * il + 1) * h;
+                    // (0.5 (l + r), for both) then the widths: the scalar mid() and fma
+                    Pq[idx] = __ffma2_rn(sg2, zp, __fmul2_rn(half2, __fadd2_rn(Pq[idx - h], Pq[idx + h])));
+                }
+            }
+            if (qout) {   // path output (per-sample mode)
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    qout[c * NF + k] = Pq[k].x;
+                    qout[c * NF + H + k] = Pq[k].y;
+                }
+                if (c == C - 1) qout[C * NF] = Pq[H].y;
+            }
+            // top level: every slice of the segment; then the coarser levels
+            acc[0] += level_sum_pairs<RING, NF, 1, H>(Pq, tab, P, alpha);
+            if (hier) segment_levels_pairs<RING, F, 1>(acc, Pq, tab, P, alpha, S);
+        } else {
+            // ---- double precision: the segment's points in registers
+            R q[NF + 1];
+            q[0] = C > 1 ? qc[c * kThreads] : pc.a;
+            q[NF] = C > 1 ? qc[(c + 1) * kThreads] : pc.b;
+#pragma unroll
+            for (int l = 1; l <= F; ++l) {
+                const int n = S - F + l;
+                const uint32_t jbase = (1u << (n - 1)) - 1u + ((uint32_t)c << (l - 1));
+                const R sg = pc.sigma[n];
+                const int h = 1 << (F - l);
+#pragma unroll
+                for (int il = 0; il < (1 << (l - 1)); ++il) {
+                    const uint32_t j = jbase + (uint32_t)il;
+                    R z;
                     if ((j & 1u) == 0) {
                         R z0, z1;
                         st.pair(j >> 1, z0, z1);
@@ -728,56 +837,15 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
                     } else {
                         z = cz[l];
                     }
-                } else {
-                    // j' = j + 1 = 2^(n-1) + c 2^(l-1) + il
-                    const uint32_t jp = j + 1;
-                    if (l >= 3) {               // aligned: whole quads inside the segment
-                        if ((il & 3) == 0) {
-                            if constexpr (kStaged) {
-                                const float4 v = st.zq[((1 << (l - 3)) - 1 + (il >> 2)) * kThreads];
-                                qq[0] = v.x;
-                                qq[1] = v.y;
-                                qq[2] = v.z;
-                                qq[3] = v.w;
-                            } else {
-                                st.quad(jp >> 2, qq);
-                            }
-                        }
-                        z = qq[il & 3];
-                    } else if (l == 2) {
-                        if (C == 1) {           // j' = 2, 3: the quad of level 1
-                            z = Q1[2 + il];
-                        } else {                // a quad per two segments
-                            if (il == 0 && (c & 1) == 0) st.quad(jp >> 2, Q2);
-                            z = (c & 1) ? Q2[2 + il] : Q2[il];
-                        }
-                    } else {
-                        if (C == 1) {           // j' = 1
-                            st.quad(0, Q1);
-                            z = Q1[1];
-                        } else if (C == 2) {    // j' = 2 + c: the endpoint levels' quad
-                            z = c ? Q1[3] : Q1[2];
-                        } else {                // a quad per four segments
-                            if ((c & 3) == 0) st.quad(jp >> 2, Q1);
-                            z = pick4(Q1, (uint32_t)c);
-                        }
-                    }
+                    if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
+                    const int idx = (2 * il + 1) * h;
+                    q[idx] = fma(sg, z, mid(q[idx - h], q[idx + h]));
                 }
-                if constexpr (WF) zz[n * kThreads] += (double)z * (double)z;
-                const int idx = (2 * il + 1) * h;
-                q[idx] = fma(sg, z, mid(q[idx - h], q[idx + h]));
             }
+            // top level: every slice of the segment; then the coarser levels
+            acc[0] += level_sum<R, RING, NF, 1>(q, tab, P, alpha);
+            if (hier) segment_levels<R, RING, F, 1>(acc, q, tab, P, alpha, S);
         }
-        if constexpr (sizeof(R) == 4) {   // path output: single-precision paths only
-            if (qout) {
-#pragma unroll
-                for (int k = 0; k < NF; ++k) qout[c * NF + k] = (float)q[k];
-                if (c == C - 1) qout[C * NF] = (float)q[NF];
-            }
-        }
-        // top level: every slice of the segment; then the coarser levels
-        acc[0] += level_sum<R, RING, NF, 1>(q, tab, P, alpha);
-        if (hier) segment_levels<R, RING, F, 1>(acc, q, tab, P, alpha, S);
     }
 
     // ---- width-factor weight, cumulative over levels 1..n (stored in zz)
@@ -943,15 +1011,17 @@ __device__ __forceinline__ void item_lse(const R *sw, int L, int chunk, int cnt,
 // CTAs per SM the register allocation is sized for: two for the double path
 // (up to 255 registers: its segment, accumulators and Box-Muller state stay
 // in registers; three CTAs at 168 registers spill and run slower), four for
-// the single path (128 registers)
-template <typename R, int RING = RING_EVEN>
+// the single path (128 registers), three for single-path kernels with a
+// compiled table shape of more than 30 entries (p >= 14), whose unrolled
+// Horner spills at 128 registers (p = 18: 62.5 -> 57.6 ms at three)
+template <typename R, int RING = RING_EVEN, int KS = -1>
 struct MinCtas {
-    static constexpr int value = sizeof(R) == 8 ? 2 : 4;
+    static constexpr int value = sizeof(R) == 8 ? 2 : ((KS >= 0 && fixed_M(KS >= 0 ? KS : 0) > 30) ? 3 : 4);
 };
 // the general-potential evaluator keeps its derivatives and monomial stacks in
 // local memory: more warps to hide their latency, shorter register segments
-template <>
-struct MinCtas<double, RING_GENERAL> {
+template <int KS>
+struct MinCtas<double, RING_GENERAL, KS> {
     static constexpr int value = 4;
 };
 
@@ -959,7 +1029,7 @@ struct MinCtas<double, RING_GENERAL> {
 // fixed_shapes.h compiled in, for plans with 2^kMaxFine-slice segments and
 // no width-factor weight (the host picks it only then).
 template <typename R, int RING, bool GTAB = false, int KS = -1>
-__global__ void __launch_bounds__(kThreads, MinCtas<R, RING>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
+__global__ void __launch_bounds__(kThreads, MinCtas<R, RING, KS>::value) sampler_kernel(const __grid_constant__ SamplerParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
     const int L = P.levels;
