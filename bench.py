@@ -435,9 +435,10 @@ def run_ours(args):
                                "FP64 figure); measured_fma_peak_tflops is this GPU's FMA loop (su_fma_peak)",
                 "measured_fma_peak_tflops": {"fp64": peak64, "fp32": 2 * fma32 / 1e12},
                 "frac_of_measured_fp64": achieved / peak64,
-                "fp32_sampler": {"kernel": "sampler_kernel<float, RING_EVEN>", "achieved": achieved32,
+                "fp32_sampler": {"kernel": "sampler_kernel<float, RING_EVEN, false, K> (the compiled table shape K of each p)",
+                                 "achieved": achieved32,
                                  "peak": 2 * fma32 / 1e12, "unit": "TFLOP/s", "frac": achieved32 / (2 * fma32 / 1e12),
-                                 "bound": "issue (Philox, Box-Muller and table addressing beside the Horner FMAs)"},
+                                 "bound": "issue and the FMA pipe (the packed W_p Horner; Philox beside it)"},
                 "note": "algorithmic flops 2*M_p+8 per slice-action (W_p only), summed over the timed sweep points"}
     cpu = None
     if not args.no_cpu:
