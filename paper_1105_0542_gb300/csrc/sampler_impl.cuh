@@ -15,7 +15,11 @@
 // the C+1 segment endpoints (bisection levels 1..S-F) are generated first and
 // parked in shared memory; each segment's 2^F - 1 interior points (levels
 // S-F+1..S) are then generated in registers and all slices of the segment, at
-// every level, are evaluated before the next segment starts.
+// every level, are evaluated before the next segment starts.  The double path
+// keeps the segment's points as scalars; the single path as pairs
+// (q_m, q_{m+2^(F-1)}), so that two slices or two midpoints go through one
+// packed instruction (level_sum_pairs), and with its table shape compiled in
+// where the library has it (fixed_shapes.h).
 //
 // Normal j of a sample (heap order: level n, midpoint i -> j = 2^(n-1)-1+i).
 // Double path: Box-Muller branch (j & 1) of Philox call j >> 1; every call is
@@ -639,9 +643,10 @@ struct PathCfg {
 };
 
 // The single path stages a segment's normals of levels 3..F in shared memory
-// (Stream::zq) from one rolled loop before its bisection: the same normals,
-// but one copy of the Philox and Box-Muller code in the segment loop instead
-// of one per quad, which keeps that loop inside the instruction cache.
+// (Stream::zq) from one rolled loop before its bisection, in the order its
+// paired bisection takes them: the same normals, but few copies of the Philox
+// and Box-Muller code in the segment loop instead of one per quad, which keeps
+// that loop inside the instruction cache.
 
 // quads staged per thread for 2^F-slice segments
 __host__ __device__ constexpr int staged_quads(int F) { return F >= 3 ? (1 << (F - 2)) - 1 : 0; }
