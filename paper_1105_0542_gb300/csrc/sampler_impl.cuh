@@ -266,8 +266,8 @@ __device__ __forceinline__ R slice(R ql, R qr, const TT *__restrict__ tab, const
 // is column 0 without its constant and A the outer Horner over columns 1..;
 // the two products go straight into two running sums and the NS constants
 // are added once, one FP64 operation per slice fewer than summing whole
-// slice values.  (The single path sums whole slice values two at a time in
-// level_sum_pairs; here it serves only single slices.)
+// slice values.  (The single path sums its slices two at a time in
+// level_sum_pairs.)
 template <typename R>
 struct Batch {
     static constexpr int B = 8;
