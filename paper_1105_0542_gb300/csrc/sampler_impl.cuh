@@ -282,7 +282,7 @@ template <int K>
 struct FixedView {
     static constexpr int M = fixed_M(K);
     static constexpr int ncol = fixed_ncol(K);
-    int len[SU_MAX_P];
+    int len[fixed_ncol(K)];
     double alpha, lwf, hcoef;
     int wf_on;
     const GeneralDev *general;
@@ -1094,7 +1094,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING, KS>::value) sampler
     FixedView<(KS >= 0 ? KS : 0)> fv;
     if constexpr (KS >= 0) {
         static_assert(sizeof(R) == 4 && RING == RING_EVEN, "compiled shapes: single precision, even ring");
-        for (int j = 0; j < SU_MAX_P; ++j) fv.len[j] = P.len[j];
+        for (int j = 0; j < fixed_ncol(KS); ++j) fv.len[j] = P.len[j];
         fv.alpha = P.alpha;
         fv.lwf = P.lwf;
         fv.hcoef = P.hcoef;
@@ -1229,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
     FixedView<(KS >= 0 ? KS : 0)> fv;
     if constexpr (KS >= 0) {
         static_assert(sizeof(R) == 4 && RING == RING_EVEN, "compiled shapes: single precision, even ring");
-        for (int j = 0; j < SU_MAX_P; ++j) fv.len[j] = B.shapes[0].len[j];
+        for (int j = 0; j < fixed_ncol(KS); ++j) fv.len[j] = B.shapes[0].len[j];
         fv.alpha = P.alpha;
         fv.lwf = 0;
         fv.hcoef = 0;
