@@ -456,7 +456,8 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) before every step", "seed": inst.seed},
         "chosen_fp32": {"value": chosen["sa"] * world / (chosen["total_ms"] / 1e3), "unit": UNIT,
                         "ms_per_step": chosen["total_ms"] / max(args.steps, 1), "dtype": "f32 W_p, f64 reductions",
-                        "launches": chosen["launches"] * world, "clocks": chosen["clocks"]},
+                        "launches": chosen["launches"] * world, "clocks": chosen["clocks"],
+                        "compiled_shape_by_p": {str(p): plans[(p, "fp32")].su_plan_kernel() for p in ps}},
         "time_to_rel_1e-4_s": {"p": p_ref, "level": inst.s, "plain_fp64": ttr.get("fp64"),
                                "chosen_fp32": ttr.get("fp32"),
                                "speedup": (ttr["fp64"] / ttr["fp32"]) if ttr.get("fp64") and ttr.get("fp32") else None,
