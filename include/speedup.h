@@ -260,11 +260,15 @@ int su_batch_plan_sizes(const su_batch_plan *plan, int64_t *tuple_bytes, int64_t
  * = 0 (rule) or 1 (stored by su_batch_autotune). */
 int su_batch_plan_shape(const su_batch_plan *plan, int64_t i, int *seg_log2, int *chunks, int *from);
 
-/* The batched kernel a plan launches: *fixed_shape = the index of the table
- * shape compiled into it (single precision, every instance of one level p
- * whose shape su_fixed_shape reports; its instances with 32-slice segments
- * run the specialised path code), or -1.  opt->kernel = 1 forces -1; both
- * give the same results bit for bit. */
+/* The batched kernels a plan launches.  In single precision every level p of
+ * the batch whose table shape is compiled into the library (su_fixed_shape)
+ * runs a batched kernel with that shape compiled in (its instances with
+ * 32-slice segments take the specialised path code), the other levels the
+ * generic kernel, one persistent launch per kernel in the plan's graph.
+ * *fixed_shape = the compiled shape's index when the plan launches that one
+ * kernel only, -1 when it launches only the generic kernel, -2 when several.
+ * opt->kernel = 1 forces -1; every choice gives the same results bit for
+ * bit (the work items do not depend on it). */
 int su_batch_plan_kernel(const su_batch_plan *plan, int *fixed_shape);
 
 /* asynchronous on stream; the first call builds the plan's CUDA graph (a

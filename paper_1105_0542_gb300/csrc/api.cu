@@ -1476,8 +1476,16 @@ struct su_batch_plan {
     int64_t tuple_bytes = 0, scratch_bytes = 256, slice_actions = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t knode = nullptr;
     void *g_tuples = nullptr, *g_scratch = nullptr;
+    // the launches: the items [item0, item0 + n) of each group, one kernel per
+    // group (a compiled table shape, or the generic kernel: fixed = -1), each
+    // with its own queue head (scratch int `counter`)
+    struct Group {
+        int fixed, src, counter, grid;
+        int64_t item0;
+        int n;
+    };
+    std::vector<Group> groups;
 };
 
 static void batch_free(su_batch_plan *pl) {
@@ -1709,27 +1717,17 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     B.C_max = C_max;
     B.L_max = L_max;
     B.tab_max = tab_max;
-    // one table shape that the library has compiled in: the specialised kernel
-    B.fixed_shape = (prec == SU_FP32 && ring == RING_EVEN && shapes.size() == 1 && o.kernel != 1)
-                        ? fixed_shape_index(shapes[0].ncol, shapes[0].len)
-                        : -1;
+    B.fixed_shape = -1;   // the generic kernel; the compiled-shape groups are set up below
+    B.fixed_src = 0;
     pl->smem = batch_smem_bytes(B, prec);
     if (pl->smem > (size_t)smem_max)
         return fail(SU_ENOTSUP, "shared memory %zu exceeds %d (tables of %lld entries, %d levels)", pl->smem, smem_max,
                     (long long)tab_max, L_max);
-    const int occ = batch_occupancy(B, prec, pl->smem);
-    if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
-    const int64_t slots = (int64_t)sms * occ;
     // the work items (and so the order of every sum) come from the generic
-    // kernel's residency, so that the compiled-shape kernel, which runs at
-    // another occupancy, gives the same bits
-    int occ_gen = occ;
-    if (B.fixed_shape >= 0) {
-        BatchParams G = B;
-        G.fixed_shape = -1;
-        occ_gen = batch_occupancy(G, prec, pl->smem);
-        if (occ_gen < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
-    }
+    // kernel's residency, so that the compiled-shape kernels, which run at
+    // other occupancies, give the same bits
+    const int occ_gen = batch_occupancy(B, prec, pl->smem);
+    if (occ_gen < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
     const int64_t work_slots = (int64_t)sms * occ_gen;
 
     // work items (instance, block, chunk).  Cost of an instance's block:
@@ -1767,10 +1765,44 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
         return bcost[(size_t)x] / pl->K[(size_t)x] > bcost[(size_t)y] / pl->K[(size_t)y];
     });
+    // kernels: in single precision (even ring) every level p whose table shape
+    // is compiled in gets that shape's kernel, the other levels the generic
+    // one; the items grouped by kernel, each group in cost order
+    std::vector<int> kshape(shapes.size(), -1);
+    if (prec == SU_FP32 && ring == RING_EVEN && o.kernel != 1)
+        for (size_t k = 0; k < shapes.size(); ++k) kshape[k] = fixed_shape_index(shapes[k].ncol, shapes[k].len);
+    std::map<int, int> src_of;          // compiled shape -> its index in shapes
+    for (size_t k = 0; k < shapes.size(); ++k)
+        if (kshape[k] >= 0) src_of[kshape[k]] = (int)k;
+    std::vector<int> keys;              // group order: the generic kernel (-1) first, then by shape
+    for (int64_t i : order) {
+        const int key = kshape[(size_t)hin[(size_t)i].shape];
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    std::sort(keys.begin(), keys.end());
     std::vector<int2> items;
     items.reserve((size_t)n_items);
-    for (int64_t i : order)
-        for (int u = 0; u < pl->NB[(size_t)i] * pl->K[(size_t)i]; ++u) items.push_back(make_int2((int)i, u));
+    pl->groups.clear();
+    for (int key : keys) {
+        su_batch_plan::Group g{};
+        g.fixed = key;
+        g.src = key >= 0 ? src_of[key] : 0;
+        g.item0 = (int64_t)items.size();
+        for (int64_t i : order) {
+            if (kshape[(size_t)hin[(size_t)i].shape] != key) continue;
+            for (int u = 0; u < pl->NB[(size_t)i] * pl->K[(size_t)i]; ++u) items.push_back(make_int2((int)i, u));
+        }
+        g.n = (int)((int64_t)items.size() - g.item0);
+        // queue heads: group 0 at scratch int 0, the flags at int 1, group k >= 1 at int k + 1
+        g.counter = pl->groups.empty() ? 0 : (int)pl->groups.size() + 1;
+        BatchParams Bg = B;
+        Bg.fixed_shape = g.fixed;
+        Bg.fixed_src = g.src;
+        const int occ = batch_occupancy(Bg, prec, pl->smem);
+        if (occ < 1) return fail(SU_ECUDA, "batched kernel cannot be resident");
+        g.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * occ, std::max(g.n, 1)));
+        pl->groups.push_back(g);
+    }
 
     const size_t rs = prec == SU_FP32 ? sizeof(float) : sizeof(double);
     std::vector<unsigned char> blob(std::max<size_t>(tabd.size(), 1) * rs, 0);
@@ -1796,7 +1828,7 @@ static int batch_create(int model, const double *params, int n_params, int p, co
     B.shapes = static_cast<const BatchShape *>(pl->d_shapes);
     B.items = static_cast<const int2 *>(pl->d_items);
     B.n_items = (int)items.size();
-    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(slots, std::max(B.n_items, 1)));
+    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>(work_slots, std::max(B.n_items, 1)));
     pl->tuple_bytes = std::max<int64_t>(n_tup, 1) * 4 * (int64_t)sizeof(double);
     pl->scratch_bytes = 256;
     *out = pl.release();
@@ -1837,7 +1869,9 @@ int su_batch_plan_shape(const su_batch_plan *pl, int64_t i, int *seg_log2, int *
 
 int su_batch_plan_kernel(const su_batch_plan *pl, int *fixed_shape) {
     if (!pl || !fixed_shape) return fail(SU_EINVAL, "plan or output missing");
-    *fixed_shape = pl->B.fixed_shape;
+    bool any_fixed = false;
+    for (const auto &g : pl->groups) any_fixed = any_fixed || g.fixed >= 0;
+    *fixed_shape = pl->groups.size() == 1 ? pl->groups[0].fixed : (any_fixed ? -2 : -1);
     return SU_OK;
 }
 
@@ -1852,10 +1886,10 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
     B.tuples = static_cast<double *>(d_tuples);
     B.counter = static_cast<int *>(d_scratch);
     B.base.flags = static_cast<int *>(d_scratch) + 1;
-    const void *fn = su::batch_fn(B, pl->opt.precision);
-    void *args[] = {&B};
     const int64_t stop = g_fault_queue.exchange(0);
-    if (stop > 0) {   // fault injection: the queue ends after `stop` items
+    if (stop > 0) {   // fault injection: the queue (all items, generic kernel) ends after `stop` items
+        const void *fn = su::batch_fn(B, pl->opt.precision);
+        void *args[] = {&B};
         B.n_items = (int)std::min<int64_t>(B.n_items, stop);
         CU(cudaMemsetAsync(d_tuples, 0, (size_t)pl->tuple_bytes, st), "clear tuples");
         CU(cudaMemsetAsync(d_scratch, 0, 8, st), "clear queue");
@@ -1863,24 +1897,36 @@ int su_batch_plan_execute(su_batch_plan *pl, void *d_tuples, void *d_scratch, vo
         if (launches) *launches = 1;
         return SU_OK;
     }
-    cudaKernelNodeParams kp{};
-    kp.func = const_cast<void *>(fn);
-    kp.gridDim = dim3(pl->grid);
-    kp.blockDim = dim3(su::kThreads);
-    kp.sharedMemBytes = (unsigned)pl->smem;
-    kp.kernelParams = args;
     if (!pl->exec) {
-        // one graph per plan: clear the queue head and the flags, then the persistent kernel
+        // one graph per plan: clear the queue heads and the flags, then one
+        // persistent kernel per group (independent: disjoint items, heads and
+        // tuples)
         CU(cudaGraphCreate(&pl->graph, 0), "graph create");
         cudaMemsetParams mp{};
         mp.dst = d_scratch;
         mp.value = 0;
         mp.elementSize = 4;
-        mp.width = 2;
+        mp.width = pl->groups.size() + 1;
         mp.height = 1;
         cudaGraphNode_t mnode;
         CU(cudaGraphAddMemsetNode(&mnode, pl->graph, nullptr, 0, &mp), "graph memset node");
-        CU(cudaGraphAddKernelNode(&pl->knode, pl->graph, &mnode, 1, &kp), "graph kernel node");
+        for (const auto &g : pl->groups) {
+            su::BatchParams Bg = B;
+            Bg.items = B.items + g.item0;
+            Bg.n_items = g.n;
+            Bg.counter = static_cast<int *>(d_scratch) + g.counter;
+            Bg.fixed_shape = g.fixed;
+            Bg.fixed_src = g.src;
+            void *args[] = {&Bg};
+            cudaKernelNodeParams kp{};
+            kp.func = const_cast<void *>(su::batch_fn(Bg, pl->opt.precision));
+            kp.gridDim = dim3(g.grid);
+            kp.blockDim = dim3(su::kThreads);
+            kp.sharedMemBytes = (unsigned)pl->smem;
+            kp.kernelParams = args;   // copied into the node
+            cudaGraphNode_t knode;
+            CU(cudaGraphAddKernelNode(&knode, pl->graph, &mnode, 1, &kp), "graph kernel node");
+        }
         CU(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiate");
         pl->g_tuples = d_tuples;
         pl->g_scratch = d_scratch;

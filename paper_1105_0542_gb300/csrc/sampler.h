@@ -112,7 +112,8 @@ struct BatchParams {
     int64_t tab_max;          // largest L * M: table elements staged per item
     double *tuples;           // per instance from its tup offset
     int *counter;             // work-queue head, zeroed before every launch
-    int fixed_shape;          // >= 0: every instance has this compiled table shape (fixed_shapes.h)
+    int fixed_shape;          // >= 0: every item's instance has this compiled table shape (fixed_shapes.h)
+    int fixed_src;            // ... which is shapes[fixed_src]
 };
 
 // dynamic shared memory the sampler needs

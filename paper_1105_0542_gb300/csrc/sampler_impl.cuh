@@ -1196,9 +1196,9 @@ struct BatchView {
     int len[SU_MAX_P];
 };
 
-// KS >= 0: every instance has table shape KS of fixed_shapes.h (single
-// precision, even ring); items with 2^kMaxFine-slice segments run the path
-// code with that shape compiled in.
+// KS >= 0: every item's instance has table shape KS of fixed_shapes.h
+// (single precision, even ring; shapes[B.fixed_src]); items with
+// 2^kMaxFine-slice segments run the path code with that shape compiled in.
 template <typename R, int RING, int KS = -1>
 __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch_kernel(const __grid_constant__ BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1243,7 +1243,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
     FixedView<(KS >= 0 ? KS : 0)> fv;
     if constexpr (KS >= 0) {
         static_assert(sizeof(R) == 4 && RING == RING_EVEN, "compiled shapes: single precision, even ring");
-        for (int j = 0; j < fixed_ncol(KS); ++j) fv.len[j] = B.shapes[0].len[j];
+        for (int j = 0; j < fixed_ncol(KS); ++j) fv.len[j] = B.shapes[B.fixed_src].len[j];
         fv.alpha = P.alpha;
         fv.lwf = 0;
         fv.hcoef = 0;

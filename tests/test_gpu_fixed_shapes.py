@@ -97,7 +97,25 @@ def test_batched_kernel_with_the_shape_compiled_in_gives_the_generic_bits():
             assert g[key] == r[key] or (np.isnan(g[key]) and np.isnan(r[key])), key
 
 
-def test_batched_kernel_with_several_levels_p_stays_generic():
-    inst = [{"a": 0.0, "b": 1.0, "T": 1.0, "s": 6, "p": p} for p in (4, 10)]
-    k, _ = _batch(inst, 10, "auto")
-    assert k == -1
+def test_batched_levels_p_each_with_their_compiled_shape_give_the_generic_bits():
+    # levels 4 and 10 (two compiled-shape kernels) and 21 (beyond the compiled
+    # shapes: the generic kernel) in one plan
+    inst = [{"a": -0.5 + 0.1 * i, "b": 0.8 - 0.05 * i, "T": (0.5, 1.0)[i % 2], "s": 3 + i % 6, "p": (4, 10, 21)[i % 3],
+             "hierarchy": i % 2} for i in range(18)]
+    k_auto, got = _batch(inst, 10, "auto")
+    k_gen, ref = _batch(inst, 10, "generic")
+    assert k_auto == -2 and k_gen == -1
+    flat = lambda res: [lev for x in res for lev in (x if isinstance(x, list) else [x])]  # noqa: E731
+    got, ref = flat(got), flat(ref)
+    assert len(got) == len(ref)
+    for g, r in zip(got, ref):
+        for key in ("amp", "log_amp", "err", "err_naive", "ess", "n"):
+            assert g[key] == r[key] or (np.isnan(g[key]) and np.isnan(r[key])), key
+
+
+def test_batched_levels_without_a_compiled_shape_stay_generic():
+    pl = su.BatchPlan("poly", [0.2, -0.5, 0.3, 0.25, 0.1], 5, [(0.0, 0.5, 1.0, 6), (0.1, -0.2, 0.5, 4)], 1000, 3,
+                      precision="fp32")
+    assert pl.su_batch_plan_kernel() == -1
+    one = su.BatchPlan("aho", [1.0, 1.0], 7, [(0.0, 0.5, 1.0, 6)], 1000, 3, precision="fp32")
+    assert one.su_batch_plan_kernel() == su.su_fixed_shape("aho", [1.0, 1.0], 7)
