@@ -200,7 +200,7 @@ size_t batch_smem_bytes(const BatchParams &B, int precision) {
     off = (off + 15) & ~(size_t)15;
     off += (2 * sizeof(double) + rs) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
-    if (precision == SU_FP32) off += sizeof(float4) * (size_t)staged_quads(kMaxFine) * kThreads;
+    if (precision == SU_FP32) off += sizeof(float4) * (size_t)staged_quads(kMaxFine, true) * kThreads;
     if (precision == SU_FP64) off += sizeof(bm::Tables);
     return off;
 }

@@ -662,13 +662,18 @@ struct PathCfg {
 // and Box-Muller code in the segment loop instead of one per quad, which keeps
 // that loop inside the instruction cache.
 
-// quads staged per thread for 2^F-slice segments
-__host__ __device__ constexpr int staged_quads(int F) { return F >= 3 ? (1 << (F - 2)) - 1 : 0; }
+// quads staged per thread for 2^F-slice segments: levels 3..F, or 4..F where
+// level 3's one quad stays in registers (Z3REG: the batched kernel, for which
+// the 2 KB per CTA decide its residency; in the sampler the registers are
+// the tighter budget)
+__host__ __device__ constexpr int staged_quads(int F, bool z3reg = false) {
+    return z3reg ? (F >= 4 ? (1 << (F - 2)) - 2 : 0) : (F >= 3 ? (1 << (F - 2)) - 1 : 0);
+}
 
 // This thread's shared-memory columns (stride kThreads): qc holds the C+1
 // segment endpoints, zz the per-level sums of z^2 (width-factor weight only).
 // Writes the log-weight of sampled level d (level n = S - d) to wout[d * wstride].
-template <typename R, int RING, int F, bool WF, typename TT, typename SP>
+template <typename R, int RING, int F, bool WF, bool Z3REG = false, typename TT, typename SP>
 __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
                                             const TT *__restrict__ tab, R *__restrict__ qc,
                                             double *__restrict__ zz, const Stream<R> &st,
@@ -733,23 +738,27 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
         if constexpr (sizeof(R) == 4) {
             // ---- single precision: the segment as pairs Pq[m] = (q_m, q_{m+H})
             constexpr int H = NF / 2;
+            float4 z3 = make_float4(0.f, 0.f, 0.f, 0.f);
             if constexpr (F >= 3) {
-                // stage the normals of levels 3..F (level l: quads from
+                // the normals of levels 3..F (level l: quads from
                 // (2^(n-1) + c 2^(l-1)) / 4 on, normal il at slot il & 3 of quad
                 // il / 4) in the order the paired bisection takes them: pair il
-                // of level l is (z_il, z_{il + 2^(l-2)}), float4 slot
-                // 2^(l-3) - 1 + il / 2 holds pairs il (even) and il + 1
+                // of level l is (z_il, z_{il + 2^(l-2)}); level 3's quad in
+                // registers, levels 4..F staged, float4 slot 2^(l-3) - 2 + il / 2
+                // holding pairs il (even) and il + 1 (2^(l-3) - 1 + il / 2 with
+                // level 3 staged too)
                 {   // level 3: one quad, pairs (z0, z2), (z1, z3)
                     const int n = S - F + 3;
                     float za[4];
                     st.quad(((1u << (n - 1)) + ((uint32_t)c << 2)) >> 2, za);
-                    st.zq[0] = make_float4(za[0], za[2], za[1], za[3]);
+                    z3 = make_float4(za[0], za[2], za[1], za[3]);
+                    if constexpr (!Z3REG) st.zq[0] = z3;
                 }
 #pragma unroll 1
                 for (int l = 4; l <= F; ++l) {   // levels 4..F: quad k pairs with quad k + 2^(l-4)
                     const int n = S - F + l;
                     const uint32_t q0 = ((1u << (n - 1)) + ((uint32_t)c << (l - 1))) >> 2;
-                    const int hq = 1 << (l - 4), base = (1 << (l - 3)) - 1;
+                    const int hq = 1 << (l - 4), base = (1 << (l - 3)) - (Z3REG ? 2 : 1);
 #pragma unroll 1
                     for (int k = 0; k < hq; ++k) {
                         float za[4], zb[4];
@@ -800,7 +809,10 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
                             zp = (c & 1) ? make_float2(Q2[2], Q2[3]) : make_float2(Q2[0], Q2[1]);
                         }
                     } else {
-                        if ((il & 1) == 0) v4 = st.zq[((1 << (l - 3)) - 1 + (il >> 1)) * kThreads];
+                        if (Z3REG && l == 3)
+                            v4 = z3;
+                        else if ((il & 1) == 0)
+                            v4 = st.zq[((1 << (l - 3)) - (Z3REG ? 2 : 1) + (il >> 1)) * kThreads];
                         zp = (il & 1) ? make_float2(v4.z, v4.w) : make_float2(v4.x, v4.y);
                     }
                     if constexpr (WF) {
@@ -902,16 +914,16 @@ __device__ __forceinline__ void sample_path(const SP &P, const PathCfg<R> &pc,
 // The width-factor weight is a template switch: as a run-time test inside
 // the midpoint loop the compiler predicates it, and its double conversions
 // and multiply-add then occupy the FP64 pipe on every midpoint.
-template <typename R, int RING, bool WF, typename TT, typename SP>
+template <typename R, int RING, bool WF, bool Z3REG = false, typename TT, typename SP>
 __device__ __forceinline__ void sample_path_f(int F, const SP &P, const PathCfg<R> &pc,
                                               const TT *tab, R *qc, double *zz, const Stream<R> &st,
                                               R *wout, int wstride, float *qout) {
     switch (F) {
-        case 1: sample_path<R, RING, 1, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 2: sample_path<R, RING, 2, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 3: sample_path<R, RING, 3, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        case 4: sample_path<R, RING, 4, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
-        default: sample_path<R, RING, 5, WF>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 1: sample_path<R, RING, 1, WF, Z3REG>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 2: sample_path<R, RING, 2, WF, Z3REG>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 3: sample_path<R, RING, 3, WF, Z3REG>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        case 4: sample_path<R, RING, 4, WF, Z3REG>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
+        default: sample_path<R, RING, 5, WF, Z3REG>(P, pc, tab, qc, zz, st, wout, wstride, qout); break;
     }
 }
 
@@ -926,11 +938,12 @@ __device__ __forceinline__ void sample_path_any(int F, const SP &P, const PathCf
 }
 
 // batched kernel: no width factor; the per-item view of the instance's
-// table shape (BatchView, in shared memory) in place of SamplerParams
+// table shape (BatchView, in shared memory) in place of SamplerParams; level
+// 3's normals in registers
 template <typename R, int RING, typename TT, typename SP>
 __device__ __forceinline__ void sample_path_plain(int F, const SP &P, const PathCfg<R> &pc, const TT *tab, R *qc,
                                                   const Stream<R> &st, R *wout) {
-    sample_path_f<R, RING, false>(F, P, pc, tab, qc, nullptr, st, wout, 1, nullptr);
+    sample_path_f<R, RING, false, true>(F, P, pc, tab, qc, nullptr, st, wout, 1, nullptr);
 }
 
 // -------------------------------------------------------- warp helpers
@@ -976,16 +989,22 @@ struct Lse {
     __device__ __forceinline__ void push(R w) { lse_push(m, s, q, w); }
 };
 
-// merge b into a (same convention), in double
-__device__ __forceinline__ void lse_merge(double &ma, double &sa, double &qa, double mb, double sb, double qb) {
+// merge tuple b into tuple a (same convention) with the scale factor
+// e^(m_a - m_b) in the kernel's precision (lse_exp): the sums stay in
+// double; in single precision the
+// factor carries float rounding like every per-sample term already does,
+// and the batched kernel's CTA merges (a 32-lane butterfly per level and
+// work item) stay off the FP64 pipe
+template <typename R>
+__device__ __forceinline__ void lse_merge_r(double &ma, double &sa, double &qa, double mb, double sb, double qb) {
     if (!(mb > -INFINITY)) return;
     if (mb > ma) {
-        const double f = exp(ma - mb);
+        const double f = lse_exp((R)(ma - mb));   // 0 for ma = -inf
         sa = fma(sa, f, sb);
         qa = fma(qa, f * f, qb);
         ma = mb;
     } else {
-        const double f = exp(mb - ma);
+        const double f = lse_exp((R)(mb - ma));
         sa = fma(sb, f, sa);
         qa = fma(qb, f * f, qa);
     }
@@ -1169,7 +1188,7 @@ __global__ void __launch_bounds__(kThreads, MinCtas<R, RING, KS>::value) sampler
 // level n = 1..s_i from the same paths.
 // Shared memory: BatchView | tables[L_max * M_max] (R) | sigma[S_max+1] (R) |
 //                qc[(C_max+1)][kThreads] (R) | level states m (R), s, q
-//                (double) [L_max-1][kThreads] | staged quads[2^(kMaxFine-2) - 1]
+//                (double) [L_max-1][kThreads] | staged quads[2^(kMaxFine-2) - 2]
 //                [kThreads] (float4, single path) | Box-Muller node tables (double path)
 // CTAs per SM for the register budget: the generic float form runs the
 // amplitude matrix 2 % faster at 5 (96 registers) than at 4; with a table
@@ -1230,7 +1249,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
     off += sizeof(R) * (size_t)(B.L_max - 1) * kThreads;
     off = (off + 15) & ~(size_t)15;
     float4 *zq = reinterpret_cast<float4 *>(smem_raw + off) + tid;           // single path only
-    off += sizeof(R) == 4 ? sizeof(float4) * (size_t)staged_quads(kMaxFine) * kThreads : 0;
+    off += sizeof(R) == 4 ? sizeof(float4) * (size_t)staged_quads(kMaxFine, true) * kThreads : 0;
     bm::Tables *bm_smem = reinterpret_cast<bm::Tables *>(smem_raw + off);
     if constexpr (sizeof(R) == 8) bm::tables_init(bm_smem, tid, kThreads);
 
@@ -1309,7 +1328,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
             R w[SU_MAX_S];
             if constexpr (KS >= 0) {
                 if (in.F == kMaxFine)
-                    sample_path<R, RING, kMaxFine, false>(fv, pc, tab, qc, nullptr, st, w, 1, nullptr);
+                    sample_path<R, RING, kMaxFine, false, true>(fv, pc, tab, qc, nullptr, st, w, 1, nullptr);
                 else
                     sample_path_plain<R, RING>(in.F, *view, pc, tab, qc, st, w);
             } else {
@@ -1342,7 +1361,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
                 const double mb = __shfl_xor_sync(0xffffffffu, m, o);
                 const double sb = __shfl_xor_sync(0xffffffffu, s, o);
                 const double qb = __shfl_xor_sync(0xffffffffu, q, o);
-                lse_merge(m, s, q, mb, sb, qb);
+                lse_merge_r<R>(m, s, q, mb, sb, qb);
             }
             if (lane == 0) {
                 s_red[warp][d][0] = m;
@@ -1355,7 +1374,7 @@ __global__ void __launch_bounds__(kThreads, BatchCtas<R, RING, KS>::value) batch
             const int d = tid;
             double M0 = s_red[0][d][0], S0 = s_red[0][d][1], Q0 = s_red[0][d][2];
             for (int w2 = 1; w2 < kThreads / 32; ++w2)
-                lse_merge(M0, S0, Q0, s_red[w2][d][0], s_red[w2][d][1], s_red[w2][d][2]);
+                lse_merge_r<R>(M0, S0, Q0, s_red[w2][d][0], s_red[w2][d][1], s_red[w2][d][2]);
             double *o = B.tuples + 4 * (in.tup + (int64_t)it.y * L + d);
             o[0] = M0;
             o[1] = S0;
